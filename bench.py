@@ -1,0 +1,326 @@
+"""Benchmark of batched R-MATEX on one GB300 (or N replicas under torchrun).
+
+Workload: the two-layer 300x300 RC mesh (180,000 nodes, vias every 4th node,
+400 pads), 2,000 triangular-pulse loads in 64 bump groups, 10 ns simulated,
+output every 10 ps (1,001 output times), gamma = 1e-11 s, m <= 20, tol 1e-7.
+One step = one complete batched R-MATEX transient of that grid (every group,
+every segment, every output), inputs resident on the device.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead
+(rank 0 only), on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("node-steps/sec (nodes × output steps × groups) FP64, batched vs one-group "
+          "launches; SpTRSV HBM GB/s")
+UNIT = "node-steps/s"
+WORKLOAD = "rmatex_mesh2x300x300_180k_nodes_2000src_64groups_10ns_10ps"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm, src = 6800.0, "fallback"
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        hbm, src = float(d["hbm_gbs"]), "measured"
+    except Exception:
+        pass
+    # FP64 peak from the unit counts and clocks: 152 SMs x 2070 MHz x 2 FP64 FMA
+    # per SM per clock (= 4 flop), i.e. the 1.25 TFLOP/s FP64 rate of GB300.
+    fp64 = 152 * 2070e6 * 4 / 1e12
+    return hbm, src, fp64
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thr = threading.Thread(target=self._read, daemon=True)
+            self.thr.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def cpu_oracle_sample(n_groups_sample: int) -> dict:
+    """The oracle as it stands on the first groups of the workload (single
+    thread: BLAS pinned to one thread by the parent's environment)."""
+    import gridgen
+    from oracle import rmatex_ref as R
+    p = gridgen.config1()
+    fac = R.factorize(p)
+    t0 = time.perf_counter()
+    R.rmatex(p, fac=fac, groups=list(range(n_groups_sample)), nodes=None)
+    dt = time.perf_counter() - t0
+    units = p.n * (p.n_out - 1) * n_groups_sample
+    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_groups_sample} of 64 groups of the same grid, all 180,000 nodes, "
+                      f"1,000 output steps; factorisation excluded; {dt:.1f} s"}
+
+
+def run_cpu_sample(n_groups_sample: int) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-oracle-sample",
+                          str(n_groups_sample)], env=env, stdout=subprocess.PIPE, text=True,
+                         check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reference_arm(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    env_threads = 1
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import gridgen
+    from oracle import rmatex_ref as R
+    p = gridgen.config1()
+    fac = R.factorize(p)
+    times = []
+    for i in range(args.warmup + args.steps):
+        g = i % p.n_groups
+        t0 = time.perf_counter()
+        R.rmatex(p, fac=fac, groups=[g])
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    step_s = sum(times) / len(times)
+    value = p.n * (p.n_out - 1) * 1 / step_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "working set > L2"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": env_threads, "kind": "oracle",
+                             "sample": "each step: one of the 64 groups of the same grid through "
+                                       "the FP64 oracle (SuperLU, MGS, scipy expm), all nodes "
+                                       "and outputs; factorisation excluded"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-oracle-sample", type=int, default=0)
+    ap.add_argument("--cpu-groups", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serial", action="store_true")
+    args = ap.parse_args()
+    if args.cpu_oracle_sample:
+        print(json.dumps(cpu_oracle_sample(args.cpu_oracle_sample)))
+        return 0
+    if args.impl == "reference":
+        return reference_arm(args)
+    args.warmup = max(args.warmup, 3)
+
+    import numpy as np
+    import torch
+
+    import gridgen
+    from paper_1511_04519_gb300 import build as B
+    B.build()
+    from paper_1511_04519_gb300 import matex as M
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    # replicas: every rank simulates its own independently seeded grid
+    p = gridgen.config1(seed=gridgen.SEED_BASE + 1 + 1000 * rank)
+    stream = torch.cuda.current_stream()
+    sim = M.Sim(p, stream=stream)
+    setup = sim.setup_stats()
+    out = torch.empty((sim.n_times, sim.n_rows), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        sim.run(out)
+    torch.cuda.synchronize()
+    hbm_peak, hbm_src, fp64_peak = _peaks()
+
+    clk = ClockSampler(local)
+    clk.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sim.run(out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    clocks = clk.stop()
+    launches_per_step = sim.stats.kernel_launches
+    stats = sim.stats.as_dict()
+    if pg is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    units = p.n * (p.n_out - 1) * p.n_groups
+    value = world * units / (ms / 1e3)
+
+    # profiled steps (CUDA events around every kernel class on the run's stream)
+    sim.profile(on=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sim.run(out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_prof = ev0.elapsed_time(ev1) / args.steps
+    prof = sim.profile(on=False)
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    per_launch_ms = d["ms"] / max(1, d["units"])
+    ridge = fp64_peak * 1e12 / (hbm_peak * 1e9)
+    intensity = d["flops"] / d["bytes"] if d["bytes"] else float("inf")
+    if intensity > ridge:
+        roof = {"bound": "alu", "achieved": d["flops"] / (d["ms"] / 1e3) / 1e12, "peak": fp64_peak,
+                "unit": "TFLOP/s"}
+        roof["peak_source"] = "FP64 from unit counts and clocks (152 SM x 2070 MHz x 4 flop/clk)"
+    else:
+        roof = {"bound": "hbm", "achieved": d["bytes"] / (d["ms"] / 1e3) / 1e9, "peak": hbm_peak,
+                "unit": "GB/s", "peak_source": f"{hbm_src} copy bandwidth"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = dom
+    roof["per_launch_ms"] = per_launch_ms
+    s = prof["solve"]
+    sptrsv = {"achieved_gbs": s["bytes"] / (s["ms"] / 1e3) / 1e9 if s["ms"] else None,
+              "achieved_tflops": s["flops"] / (s["ms"] / 1e3) / 1e12 if s["ms"] else None,
+              "frac_hbm": (s["bytes"] / (s["ms"] / 1e3) / 1e9) / hbm_peak if s["ms"] else None,
+              "frac_fp64": (s["flops"] / (s["ms"] / 1e3) / 1e12) / fp64_peak if s["ms"] else None}
+
+    # one group at a time: the same kernels, one column per launch
+    serial = None
+    if not args.no_serial:
+        sim.one_group_at_a_time(True)
+        sim.run(out)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        sim.run(out)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_serial = ev0.elapsed_time(ev1)
+        sim.one_group_at_a_time(False)
+        serial = {"value": units / (ms_serial / 1e3), "ms_per_step": ms_serial,
+                  "batched_speedup": ms_serial / ms}
+
+    # end to end through the host-buffer C-ABI call: pinned H2D of the source
+    # currents, the run, and the D2H of every node voltage at every output time
+    pin_v = torch.from_numpy(np.asarray(p.pwl_v, np.float64)).pin_memory().numpy()
+    pin_out = torch.empty((sim.n_times, sim.n_rows), dtype=torch.float64).pin_memory().numpy()
+    sim.run_host(pin_v, pin_out)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.run_host(pin_v, pin_out)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if pg is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(pin_v.nbytes),
+           "d2h_bytes_per_step": int(pin_out.nbytes), "ms_per_step": e2e_s * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = run_cpu_sample(args.cpu_groups)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes": p.n, "groups": p.n_groups,
+                       "output_steps": p.n_out - 1, "sources": p.n_src,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "working set (factors, bases, 1.44 GB of outputs) > 129 MB L2"},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "roofline": roof, "sptrsv": sptrsv, "one_group_at_a_time": serial,
+            "cpu_baseline": cpu, "profile_ms_per_step": ms_prof,
+            "profile": {k: {kk: v[kk] / args.steps for kk in ("ms", "launches", "flops", "bytes")}
+                        for k, v in prof.items()},
+            "run_stats": {k: stats[k] for k in ("n_segments", "krylov_segments", "sum_m", "max_m",
+                                                 "nonconv", "sweeps_M", "sweeps_G", "solve_columns",
+                                                 "rounds")},
+            "setup_ms": {"order": setup["setup_order_ms"], "factor": setup["setup_factor_ms"],
+                         "upload": setup["setup_upload_ms"], "nnz_L": setup["nnz_L"],
+                         "supernodes": setup["n_supernodes"], "levels": setup["n_levels"]},
+        }
+        print(json.dumps(line))
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

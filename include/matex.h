@@ -1,0 +1,232 @@
+/*
+ * matex.h — C ABI of the GB300 batched R-MATEX integrator.
+ *
+ * The library integrates the RC power-grid ODE of Eq. 1,
+ *     C x'(t) = -G x(t) + B u(t),     C = diag(c),  G symmetric positive definite,
+ * with piecewise-linear current loads u(t), by the rational (shift-and-invert)
+ * Krylov matrix-exponential method R-MATEX (Sec. 3.3.2, Alg. 1 with
+ * X1 = C + gamma G, X2 = C; Eq. 9 for H_m; the empirical residual of
+ * Sec. 3.3.3).  The loads are split into "bump" groups (Sec. 3.1); each group
+ * is simulated on its own local transition spots (Alg. 2) and the group
+ * responses are summed by superposition.  Every group is one column of a
+ * batched launch on one GPU.
+ *
+ * Conventions for every call:
+ *   - All floating point is IEEE FP64 (double).  Indices are int32 unless
+ *     noted; CSR row pointers are int64.
+ *   - "host" pointers are read during the call only and copied; the caller
+ *     keeps ownership.  "device" pointers are CUDA global-memory pointers on
+ *     the device that was current at matex_setup; the caller owns them.
+ *   - Work is issued on the CUDA stream given to matex_setup (NULL = legacy
+ *     default stream).  Calls that return results synchronise that stream
+ *     before returning.
+ *   - No call throws or aborts.  Each returns a matex_status; on failure
+ *     matex_last_error() describes it.  A failed call leaves the context
+ *     usable unless the status is MATEX_ERR_CUDA (a sticky device error).
+ *   - One context must not be used from two host threads at once.
+ *
+ * Node order: every node-indexed array in this interface uses the caller's
+ * (original) numbering.  The library reorders internally.
+ */
+#ifndef MATEX_H_
+#define MATEX_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct matex_ctx matex_ctx;
+
+typedef enum matex_status {
+  MATEX_OK = 0,
+  MATEX_ERR_ARG = 1,      /* invalid argument (sizes, indices, NULL, non-increasing PWL times) */
+  MATEX_ERR_NOT_SPD = 2,  /* G or C + gamma G has a non-positive pivot */
+  MATEX_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+  MATEX_ERR_TIMEOUT = 4,  /* a bounded device wait gave up */
+  MATEX_ERR_NOCONV = 5,   /* strict mode: some segment reached m_max without meeting tol
+                             (results are still written) */
+  MATEX_ERR_OOM = 6,      /* device or host allocation failed */
+  MATEX_ERR_STATE = 7     /* call not valid in the context's current state */
+} matex_status;
+
+/* Options of matex_setup.  Start from matex_default_opts(). */
+typedef struct matex_opts {
+  int32_t col_block;       /* column block of the triangular solves: 0 = tuned per tree level,
+                              else 1, 2, 4 or 8 for every level */
+  int32_t group_select;    /* -1: all groups; g >= 0: simulate only group g */
+  int32_t include_dc;      /* 1: add the pads' constant DC state x_dc = G^{-1} dc_inject */
+  int32_t n_rows;          /* 0: output every node; else the number of rows in `rows` */
+  const int32_t* rows;     /* host, n_rows original node indices to output (copied) */
+  const int32_t* replay_m; /* host or NULL: Krylov dimension to use per (group, segment),
+                              groups in order, segments in time order (copied); NULL = adaptive */
+  int64_t n_replay;        /* number of entries in replay_m (must equal the segment total) */
+  int32_t max_width;       /* cap on supernode width (0 = 128) */
+  int32_t strict;          /* 1: return MATEX_ERR_NOCONV when m_max is reached unconverged */
+} matex_opts;
+
+/* Counters and timings of the last matex_run (or of setup for the setup_* fields). */
+typedef struct matex_stats {
+  double setup_order_ms;   /* nested-dissection ordering + symbolic analysis (host) */
+  double setup_factor_ms;  /* numeric L D L^T of C + gamma G and of G (host) */
+  double setup_upload_ms;  /* host -> device upload of factors and tables */
+  double run_ms;           /* wall time of the last matex_run (host clock, synchronised) */
+  int64_t nnz_L;           /* strictly lower nonzeros of one factor */
+  int32_t n_supernodes;
+  int32_t n_levels;        /* depth of the supernodal elimination tree */
+  int32_t n_segments;      /* total (group, segment) pairs */
+  int32_t krylov_segments; /* segments that built a basis (non-quiescent) */
+  int32_t sum_m;           /* sum of Krylov dimensions over segments */
+  int32_t max_m;
+  int32_t nonconv;         /* segments that stopped at m_max above tol */
+  int32_t breakdowns;      /* segments that ended in a happy breakdown */
+  int32_t sweeps_M;        /* batched solves with C + gamma G */
+  int32_t sweeps_G;        /* batched solves with G */
+  int64_t solve_columns;   /* right-hand sides solved, over all sweeps */
+  int32_t kernel_launches; /* kernels launched by the last matex_run */
+  int32_t rounds;          /* segment rounds (max segments over the selected groups) */
+} matex_stats;
+
+void matex_default_opts(matex_opts* opts);
+
+/*
+ * Build a context: check the inputs, order and factor C + gamma G and G once
+ * (the serial part of Alg. 2), build each group's local transition spots
+ * (Sec. 3.1: the breakpoints of its sources inside (0, T) plus 0 and T),
+ * assign every output time t_o = o*dt_out (o = 0..N, N = round(t_end/dt_out),
+ * simulation end T = N*dt_out) to the segment (l_j, l_{j+1}] containing it,
+ * and upload everything to the current device.
+ *
+ *   n                 number of nodes (> 0)
+ *   c                 host[n], node capacitances (F), all > 0
+ *   g_rowptr, g_col,  host CSR of G (both triangles, symmetric, SPD), int64 row
+ *   g_val             pointers [n+1], int32 columns, values in S
+ *   dc_inject         host[n] or NULL, constant injected currents (A), e.g. pads'
+ *                     Norton currents Vdd/R_pad; forms x_dc = G^{-1} dc_inject
+ *   n_src, src_node   host[n_src], node of each piecewise-linear source (>= 0)
+ *   pwl_off           host[n_src+1], offsets into pwl_t / pwl_v (>= 1 point each)
+ *   pwl_t, pwl_v      host, breakpoint times (s, strictly increasing per source)
+ *                     and injected currents (A; loads are negative).  Before the
+ *                     first and after the last breakpoint the value is held.
+ *   src_group         host[n_src], group of each source in [0, n_groups)
+ *   gamma             shift of the rational Krylov space, (C + gamma G)^{-1} C (s)
+ *   tol               residual tolerance of Sec. 3.3.3 (V, absolute)
+ *   m_max             largest Krylov dimension, 1..20
+ *   t_end, dt_out     simulated time span and output spacing (s)
+ *   opts              NULL for defaults
+ *   stream            cudaStream_t, or NULL
+ * On success *out receives a context to be released with matex_destroy.
+ */
+matex_status matex_setup(matex_ctx** out, int64_t n, const double* c, const int64_t* g_rowptr,
+                         const int32_t* g_col, const double* g_val, const double* dc_inject,
+                         int32_t n_src, const int32_t* src_node, const int32_t* pwl_off,
+                         const double* pwl_t, const double* pwl_v, const int32_t* src_group,
+                         int32_t n_groups, double gamma, double tol, int32_t m_max, double t_end,
+                         double dt_out, const matex_opts* opts, void* stream);
+
+/*
+ * Run the batched R-MATEX transient (Alg. 2 per group, Alg. 1 per segment,
+ * superposition over groups) and write the node voltages:
+ *   x_out  device, [N+1][n_rows] row-major (n_rows = n when no row list was
+ *          given): x_out[o*n_rows + r] = x(t_o) at the r-th output node.
+ *   stats  host or NULL.
+ * Synchronises the stream.  Returns MATEX_ERR_NOCONV only in strict mode.
+ */
+matex_status matex_run(matex_ctx* ctx, double* x_out, matex_stats* stats);
+
+/*
+ * End-to-end variant with host buffers: copies the source currents pwl_v
+ * (host, same layout and length as at setup, or NULL to keep the current
+ * ones) to the device, runs, and copies the result to x_out_host (host,
+ * [N+1][n_rows]).  Page-locked host memory makes the copies asynchronous.
+ */
+matex_status matex_run_host(matex_ctx* ctx, const double* pwl_v_host, double* x_out_host,
+                            matex_stats* stats);
+
+/*
+ * Scheduling mode of later runs: 0 (default) runs every group as a column of
+ * one batched sweep per segment round; 1 runs the same kernels one group at a
+ * time (one column per launch, groups in order), the unbatched comparison.
+ * Both give the same result up to rounding.
+ */
+matex_status matex_set_batching(matex_ctx* ctx, int32_t one_group_at_a_time);
+
+/* Replace the source currents (host, layout of pwl_v at setup). */
+matex_status matex_set_sources(matex_ctx* ctx, const double* pwl_v_host);
+
+/*
+ * Solve with one of the two factors for ncols right-hand sides:
+ *   which = 0: x = (C + gamma G)^{-1} b      which = 1: x = G^{-1} b
+ *   b, x   device, [ncols][n] (each column a contiguous n-vector, original order);
+ *          may alias.
+ */
+matex_status matex_solve(matex_ctx* ctx, int32_t which, int32_t ncols, const double* b, double* x);
+
+/*
+ * Batched small dense exponentials as used for e^{h H_m} (Eq. 9):
+ *   A      device, [batch][m][m] row-major;  h device [batch];  E device [batch][m][m]
+ *   E[b] = expm(h[b] * A[b]),  1 <= m <= 20.
+ */
+matex_status matex_expm(matex_ctx* ctx, int32_t batch, int32_t m, const double* A, const double* h,
+                        double* E);
+
+/* Krylov dimension used per (group, segment) by the last run, in the replay_m
+ * layout; *count receives the total (write at most cap entries to m_host). */
+matex_status matex_get_m(matex_ctx* ctx, int32_t* m_host, int64_t cap, int64_t* count);
+
+/* Sizes: N+1 output times, rows per output, total segments. */
+matex_status matex_get_sizes(matex_ctx* ctx, int32_t* n_times, int32_t* n_rows, int64_t* n_segments);
+
+/*
+ * Per-kernel-class profile of the runs made while profiling is on.  Each
+ * timed unit is bracketed by CUDA events on the context's stream:
+ *   class 0 triangular-solve sweeps (all tree levels of one batched solve)
+ *   class 1 node-major <-> vector-major moves around the solves
+ *   class 2 Gram-Schmidt (dot products, reductions, updates, normalisation)
+ *   class 3 small dense work (start norms, residual tests, e^{hH} coefficients)
+ *   class 4 recombination + superposition of the group responses
+ *   class 5 segment inputs, state hand-off, output permutation and the rest
+ * For each class: ms[c] total event time, units[c] timed units, launches[c]
+ * kernels, flops[c] and bytes[c] the algorithmic FP64 flops and DRAM bytes
+ * of the work done (the minimum the method needs; see the kernels' comments).
+ */
+#define MATEX_PROF_CLASSES 6
+typedef struct matex_profile {
+  double ms[MATEX_PROF_CLASSES];
+  int64_t units[MATEX_PROF_CLASSES];
+  int64_t launches[MATEX_PROF_CLASSES];
+  double flops[MATEX_PROF_CLASSES];
+  double bytes[MATEX_PROF_CLASSES];
+} matex_profile;
+
+/* on = 1 starts (and zeroes) profiling, on = 0 stops it. */
+matex_status matex_set_profiling(matex_ctx* ctx, int32_t on);
+matex_status matex_get_profile(matex_ctx* ctx, matex_profile* out);
+
+/* Setup statistics (ordering, factor sizes, timings). */
+matex_status matex_get_setup_stats(matex_ctx* ctx, matex_stats* stats);
+
+/*
+ * Host-only check of the setup path, no GPU needed: nested-dissection
+ * ordering, supernodal symbolic analysis and L D L^T of diag(dshift) + alpha A
+ * (A host CSR as for G; dshift host[n] or NULL), then a CPU forward/backward
+ * substitution with exactly the factor panels the GPU kernels read, for
+ * ncols right-hand sides b (host [ncols][n], original order) into x (host,
+ * same layout).  info (host, may be NULL) receives
+ * {nnz_L, n_supernodes, n_levels, max_width_seen}.
+ */
+matex_status matex_host_factor_solve(int64_t n, const int64_t* rowptr, const int32_t* col,
+                                     const double* val, const double* dshift, double alpha,
+                                     int32_t max_width, int32_t ncols, const double* b, double* x,
+                                     int64_t* info);
+
+const char* matex_last_error(const matex_ctx* ctx);
+const char* matex_status_string(matex_status s);
+void matex_destroy(matex_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MATEX_H_ */

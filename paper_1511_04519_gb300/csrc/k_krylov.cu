@@ -1,0 +1,581 @@
+// Krylov-side kernels of batched R-MATEX: segment inputs (Eq. 5/6), the start
+// vector v = x(t) + F, Gram-Schmidt (two classical passes; Alg. 1 writes
+// modified Gram-Schmidt, which CGS2 matches to rounding), the rational
+// Hessenberg map H_m = (I - Htilde_m^{-1})/gamma (Eq. 9), the residual test of
+// Sec. 3.3.3 and the coefficient vectors ||v|| e^{h H_m} e_1 at the output
+// times of a segment (Alg. 2, "snapshots" reuse the basis).
+#include "kernels.h"
+
+namespace matex {
+
+namespace {
+
+__device__ __forceinline__ double pwl_eval(const double* t, const double* v, int np, double x) {
+  if (x <= t[0]) return v[0];
+  if (x >= t[np - 1]) return v[np - 1];
+  int j = 0;
+  while (j + 1 < np && t[j + 1] <= x) ++j;
+  const double slope = (v[j + 1] - v[j]) / (t[j + 1] - t[j]);
+  return slope * (x - t[j]) + v[j];
+}
+
+__global__ void input_rhs_kernel(double* __restrict__ Y, int ldy, int K, RoundCols rc,
+                                 SourceTable src) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= 2 * K) return;
+  const bool slope = slot >= K;
+  const int q = slope ? slot - K : slot;
+  const int g = rc.group[q];
+  const double l0 = rc.l0[q], L = rc.len[q], l1 = l0 + L;
+  for (int p = src.grp_ptr[g]; p < src.grp_ptr[g + 1]; ++p) {
+    const int s = src.grp_src[p];
+    const int o = src.pwl_off[s], np = src.pwl_off[s + 1] - o;
+    const double u0 = pwl_eval(src.pwl_t + o, src.pwl_v + o, np, l0);
+    double val = u0;
+    if (slope) val = (pwl_eval(src.pwl_t + o, src.pwl_v + o, np, l1) - u0) / L;
+    Y[(int64_t)src.node[s] * ldy + slot] += val;
+  }
+}
+
+__global__ void initial_rhs_kernel(double* __restrict__ Y, int ldy, int K, SourceTable src,
+                                   const int32_t* __restrict__ groups) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= K) return;
+  const int g = groups[q];
+  for (int p = src.grp_ptr[g]; p < src.grp_ptr[g + 1]; ++p) {
+    const int s = src.grp_src[p];
+    const int o = src.pwl_off[s], np = src.pwl_off[s + 1] - o;
+    Y[(int64_t)src.node[s] * ldy + q] += pwl_eval(src.pwl_t + o, src.pwl_v + o, np, 0.0);
+  }
+}
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  return s;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+krylov_start_kernel(double* __restrict__ Vb, int64_t vstride, const double* __restrict__ X,
+                    const double* __restrict__ Z, const double* __restrict__ W, int64_t gstride,
+                    const int32_t* __restrict__ groups, int64_t n, double* __restrict__ partials,
+                    int nchunks) {
+  __shared__ double red[32];
+  const int q = blockIdx.y;
+  const int64_t g = groups[q];
+  const int64_t b = (int64_t)blockIdx.x * kChunk;
+  const int64_t e = min(n, b + kChunk);
+  double acc = 0.0;
+  for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+    const double v = X[g * gstride + i] + (W[g * gstride + i] - Z[g * gstride + i]);
+    Vb[g * vstride + i] = v;
+    acc = fma(v, v, acc);
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[(int64_t)q * nchunks + blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+basis_dots_kernel(const double* __restrict__ Vb, int64_t vstride, const int32_t* __restrict__ groups,
+                  const int32_t* __restrict__ iter, int first, int nb, int wslot, int64_t n,
+                  double* __restrict__ partials, int nchunks) {
+  __shared__ double red[32];
+  const int q = iter[blockIdx.y];
+  const int64_t g = groups[q];
+  const double* __restrict__ base = Vb + g * vstride;
+  const double* __restrict__ w = base + (int64_t)wslot * n;
+  const int64_t b = (int64_t)blockIdx.x * kChunk;
+  const int64_t e = min(n, b + kChunk);
+  double acc[kMaxB];
+#pragma unroll
+  for (int i = 0; i < kMaxB; ++i) acc[i] = 0.0;
+  for (int64_t x = b + threadIdx.x; x < e; x += blockDim.x) {
+    const double wx = w[x];
+#pragma unroll
+    for (int i = 0; i < kMaxB; ++i)
+      if (i < nb) acc[i] = fma(base[(int64_t)(first + i) * n + x], wx, acc[i]);
+  }
+  for (int i = 0; i < nb; ++i) {
+    const double s = block_sum(acc[i], red);
+    if (threadIdx.x == 0) partials[((int64_t)q * kMaxB + i) * nchunks + blockIdx.x] = s;
+  }
+}
+
+__global__ void basis_update_kernel(double* __restrict__ Vb, int64_t vstride,
+                                    const int32_t* __restrict__ groups,
+                                    const int32_t* __restrict__ iter, int nb, int wslot,
+                                    const double* __restrict__ h, int64_t n) {
+  const int q = iter[blockIdx.y];
+  const int64_t g = groups[q];
+  double* __restrict__ base = Vb + g * vstride;
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n) return;
+  double acc = base[(int64_t)wslot * n + x];
+  for (int i = 0; i < nb; ++i) acc = fma(-h[q * kMaxB + i], base[(int64_t)i * n + x], acc);
+  base[(int64_t)wslot * n + x] = acc;
+}
+
+__global__ void basis_scale_kernel(double* __restrict__ Vb, int64_t vstride,
+                                   const int32_t* __restrict__ groups,
+                                   const int32_t* __restrict__ iter, int wslot,
+                                   const double* __restrict__ scale, int64_t n) {
+  const int q = iter[blockIdx.y];
+  const int64_t g = groups[q];
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n) return;
+  Vb[g * vstride + (int64_t)wslot * n + x] *= scale[q];
+}
+
+__global__ void start_finish_kernel(const double* __restrict__ partials, int nchunks, int K,
+                                    SmallState ss, const int32_t* __restrict__ groups,
+                                    int32_t* iter_out, int32_t* iter_grp, int32_t* iter_count) {
+  // one thread per column, then a serial compaction by thread 0 (K <= a few hundred)
+  const int q = threadIdx.x;
+  for (int c = q; c < K; c += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < nchunks; ++k) s += partials[(int64_t)c * nchunks + k];
+    const double beta = sqrt(s);
+    ss.beta[c] = beta;
+    ss.m[c] = 0;
+    for (int i = 0; i < kMaxB * kMaxM; ++i) ss.Ht[(int64_t)c * kMaxB * kMaxM + i] = 0.0;
+    if (beta <= 1e-300) {
+      ss.status[c] = 4;
+      ss.scale[c] = 0.0;
+    } else {
+      ss.status[c] = 0;
+      ss.scale[c] = 1.0 / beta;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int cnt = 0;
+    for (int c = 0; c < K; ++c)
+      if (ss.status[c] == 0) {
+        iter_grp[cnt] = groups[c];
+        iter_out[cnt++] = c;
+      }
+    *iter_count = cnt;
+  }
+}
+
+__global__ void reduce_dots_kernel(const double* __restrict__ partials, int nchunks, int nb,
+                                   const int32_t* __restrict__ iter, SmallState ss, int j,
+                                   int mode) {
+  const int q = iter[blockIdx.x];
+  const int i = threadIdx.x;
+  if (i >= nb) return;
+  double s = 0.0;
+  for (int k = 0; k < nchunks; ++k) s += partials[((int64_t)q * kMaxB + i) * nchunks + k];
+  double* Ht = ss.Ht + (int64_t)q * kMaxB * kMaxM;
+  if (mode == 2) {
+    const double nrm = sqrt(s);
+    Ht[(j + 1) * kMaxM + j] = nrm;
+    ss.scale[q] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  } else {
+    ss.hbuf[q * kMaxB + i] = s;
+    Ht[i * kMaxM + j] += s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Small dense linear algebra on m x m matrices in shared memory (ld = kMaxM),
+// executed by all threads of one CTA.
+// ---------------------------------------------------------------------------
+
+constexpr int kSmallThreads = 128;
+constexpr int kLd = kMaxM;
+constexpr int kMat = kMaxM * kMaxM;
+// theta_13 of Higham (2005), "The scaling and squaring method for the matrix
+// exponential revisited", Table 2.3: the largest 1-norm for which the [13/13]
+// Pade approximant reaches double-precision backward accuracy.
+constexpr double kTheta13 = 5.371920351148152;
+
+__device__ void mat_mul(const double* A, const double* B, double* C, int m) {
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e - i * m;
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) s = fma(A[i * kLd + k], B[k * kLd + j], s);
+    C[i * kLd + j] = s;
+  }
+  __syncthreads();
+}
+
+// Solve Q X = P in place (X overwrites P), Gaussian elimination with partial
+// pivoting; Q is destroyed.
+__device__ void lu_solve(double* Q, double* P, int m, int* piv_sh) {
+  for (int k = 0; k < m; ++k) {
+    if (threadIdx.x == 0) {
+      int p = k;
+      double best = fabs(Q[k * kLd + k]);
+      for (int i = k + 1; i < m; ++i) {
+        const double a = fabs(Q[i * kLd + k]);
+        if (a > best) { best = a; p = i; }
+      }
+      *piv_sh = p;
+    }
+    __syncthreads();
+    const int p = *piv_sh;
+    if (p != k) {
+      for (int c = threadIdx.x; c < m; c += blockDim.x) {
+        double t = Q[k * kLd + c]; Q[k * kLd + c] = Q[p * kLd + c]; Q[p * kLd + c] = t;
+        t = P[k * kLd + c]; P[k * kLd + c] = P[p * kLd + c]; P[p * kLd + c] = t;
+      }
+    }
+    __syncthreads();
+    const double inv = 1.0 / Q[k * kLd + k];
+    const int rows = m - k - 1;
+    for (int e = threadIdx.x; e < rows * (2 * m - k); e += blockDim.x) {
+      const int i = k + 1 + e / (2 * m - k);
+      const int c = e % (2 * m - k);
+      const double f = Q[i * kLd + k] * inv;
+      if (c < m - k) {
+        const int cc = k + c;
+        if (cc > k) Q[i * kLd + cc] = fma(-f, Q[k * kLd + cc], Q[i * kLd + cc]);
+      } else {
+        const int cc = c - (m - k);
+        P[i * kLd + cc] = fma(-f, P[k * kLd + cc], P[i * kLd + cc]);
+      }
+    }
+    __syncthreads();
+    for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) Q[i * kLd + k] = Q[i * kLd + k] * inv;
+    __syncthreads();
+  }
+  // back substitution, one thread per right-hand-side column
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    for (int k = m - 1; k >= 0; --k) {
+      double s = P[k * kLd + c];
+      for (int i = k + 1; i < m; ++i) s = fma(-Q[k * kLd + i], P[i * kLd + c], s);
+      P[k * kLd + c] = s / Q[k * kLd + k];
+    }
+  }
+  __syncthreads();
+}
+
+struct ExpmWork {
+  double A[kMat], A2[kMat], A4[kMat], A6[kMat], U[kMat], V[kMat], T[kMat];
+  double b[14];
+  double red[kSmallThreads];
+  int piv;
+  int s;
+};
+
+// E = expm(h * M) by scaling and squaring with the [13/13] Pade approximant
+// (Higham 2005).  M and E may not alias work arrays; E may alias M.
+__device__ void expm_dev(const double* M, double h, double* E, int m, ExpmWork& w) {
+  if (threadIdx.x == 0) {
+    // Pade coefficients b_k = (26-k)! 13! / (26! k! (13-k)!), scaled to b_0 = 1
+    w.b[0] = 1.0;
+    for (int k = 0; k < 13; ++k) w.b[k + 1] = w.b[k] * (double)(13 - k) / ((double)(26 - k) * (k + 1));
+  }
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e - i * m;
+    w.A[i * kLd + j] = h * M[i * kLd + j];
+  }
+  __syncthreads();
+  // 1-norm
+  double cs = 0.0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double t = 0.0;
+    for (int i = 0; i < m; ++i) t += fabs(w.A[i * kLd + j]);
+    cs = fmax(cs, t);
+  }
+  w.red[threadIdx.x] = cs;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double nrm = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) nrm = fmax(nrm, w.red[i]);
+    int s = 0;
+    if (nrm > kTheta13) s = (int)ceil(log2(nrm / kTheta13));
+    w.s = s > 0 ? s : 0;
+  }
+  __syncthreads();
+  const double sc = ldexp(1.0, -w.s);
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e - i * m;
+    w.A[i * kLd + j] *= sc;
+  }
+  __syncthreads();
+  mat_mul(w.A, w.A, w.A2, m);
+  mat_mul(w.A2, w.A2, w.A4, m);
+  mat_mul(w.A4, w.A2, w.A6, m);
+  const double* b = w.b;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e - i * m, x = i * kLd + j;
+    w.U[x] = b[13] * w.A6[x] + b[11] * w.A4[x] + b[9] * w.A2[x];
+    w.V[x] = b[12] * w.A6[x] + b[10] * w.A4[x] + b[8] * w.A2[x];
+  }
+  __syncthreads();
+  mat_mul(w.A6, w.U, w.T, m);  // T = A6 * (b13 A6 + b11 A4 + b9 A2)
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e - i * m, x = i * kLd + j;
+    w.T[x] += b[7] * w.A6[x] + b[5] * w.A4[x] + b[3] * w.A2[x] + (i == j ? b[1] : 0.0);
+  }
+  __syncthreads();
+  mat_mul(w.A, w.T, w.U, m);  // U = A * (...)
+  mat_mul(w.A6, w.V, w.T, m);  // T = A6 * (b12 A6 + b10 A4 + b8 A2)
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e - i * m, x = i * kLd + j;
+    const double vv = w.T[x] + b[6] * w.A6[x] + b[4] * w.A4[x] + b[2] * w.A2[x] + (i == j ? b[0] : 0.0);
+    w.V[x] = vv - w.U[x];  // Q = V - U
+    w.T[x] = vv + w.U[x];  // P = V + U
+  }
+  __syncthreads();
+  lu_solve(w.V, w.T, m, &w.piv);  // T = Q^{-1} P
+  double* cur = w.T;
+  double* nxt = w.A2;
+  for (int k = 0; k < w.s; ++k) {
+    mat_mul(cur, cur, nxt, m);
+    double* t = cur; cur = nxt; nxt = t;
+  }
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e - i * m;
+    E[i * kLd + j] = cur[i * kLd + j];
+  }
+  __syncthreads();
+}
+
+// H = (I - Ht_m^{-1}) / gamma  (Eq. 9); Ht is the column's (kMaxB x kMaxM) array.
+__device__ void rational_H(const double* Ht, int m, double gamma, double* H, ExpmWork& w) {
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e - i * m;
+    w.V[i * kLd + j] = Ht[i * kMaxM + j];
+    w.T[i * kLd + j] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  lu_solve(w.V, w.T, m, &w.piv);  // T = Ht_m^{-1}
+  const double ig = 1.0 / gamma;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e - i * m;
+    H[i * kLd + j] = ((i == j ? 1.0 : 0.0) - w.T[i * kLd + j]) * ig;
+  }
+  __syncthreads();
+}
+
+struct SmallShared {
+  ExpmWork w;
+  double H[kMat];
+  double E[kMat];
+  double y[kMaxM], y2[kMaxM];
+  int flag;
+};
+
+__global__ void __launch_bounds__(kSmallThreads)
+residual_kernel(SmallState ss, RoundCols rc, const int32_t* __restrict__ iter, int j, double gamma,
+                double tol, int m_max, const int32_t* __restrict__ replay) {
+  extern __shared__ double smem_raw[];
+  SmallShared& sh = *reinterpret_cast<SmallShared*>(smem_raw);
+  const int q = iter[blockIdx.x];
+  const int m = j + 1;
+  const double* Ht = ss.Ht + (int64_t)q * kMaxB * kMaxM;
+  const double hnext = Ht[m * kMaxM + (m - 1)];
+  if (threadIdx.x == 0) {
+    ss.m[q] = m;
+    int st = 0;
+    if (hnext <= 1e-13 * Ht[0]) st = 2;  // happy breakdown
+    else if (replay) st = (replay[rc.segid[q]] <= m) ? 1 : 0;
+    sh.flag = st;
+  }
+  __syncthreads();
+  if (sh.flag != 0 || replay) {
+    if (threadIdx.x == 0) {
+      int st = sh.flag;
+      if (st == 0 && m >= m_max) st = 3;
+      ss.status[q] = st;
+    }
+    return;
+  }
+  rational_H(Ht, m, gamma, sh.H, sh.w);
+  const double L = rc.len[q];
+  const double hc = fmin(rc.hfirst[q], L);
+  double rmax = 0.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    expm_dev(sh.H, pass == 0 ? hc : L, sh.E, m, sh.w);
+    // r = ||v|| |htilde_{m+1,m} e_m^T e^{hH} e_1|
+    rmax = fmax(rmax, ss.beta[q] * fabs(hnext) * fabs(sh.E[(m - 1) * kLd + 0]));
+  }
+  if (threadIdx.x == 0) {
+    int st = 0;
+    if (rmax < tol) st = 1;
+    else if (m >= m_max) st = 3;
+    ss.status[q] = st;
+  }
+}
+
+__global__ void compact_kernel(SmallState ss, const int32_t* __restrict__ groups,
+                               const int32_t* __restrict__ iter_in, int K_in,
+                               int32_t* __restrict__ iter_out, int32_t* __restrict__ iter_grp,
+                               int32_t* __restrict__ count) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int c = 0;
+  for (int p = 0; p < K_in; ++p) {
+    const int q = iter_in[p];
+    if (ss.status[q] == 0) {
+      iter_grp[c] = groups[q];
+      iter_out[c++] = q;
+    }
+  }
+  *count = c;
+}
+
+__global__ void record_kernel(SmallState ss, RoundCols rc, int K, int32_t* m_rec, int32_t* st_rec) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= K) return;
+  m_rec[rc.segid[q]] = ss.m[q];
+  st_rec[rc.segid[q]] = ss.status[q];
+}
+
+__global__ void __launch_bounds__(kSmallThreads)
+coef_kernel(SmallState ss, RoundCols rc, double gamma, double dt_out, double* __restrict__ coef,
+            int ldo, double* __restrict__ yend) {
+  extern __shared__ double smem_raw[];
+  SmallShared& sh = *reinterpret_cast<SmallShared*>(smem_raw);
+  const int q = blockIdx.x;
+  const int m = ss.m[q];
+  if (m <= 0) return;
+  const double* Ht = ss.Ht + (int64_t)q * kMaxB * kMaxM;
+  const double beta = ss.beta[q];
+  rational_H(Ht, m, gamma, sh.H, sh.w);
+  // segment end
+  expm_dev(sh.H, rc.len[q], sh.E, m, sh.w);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) yend[(int64_t)q * kMaxM + i] = beta * sh.E[i * kLd];
+  const int no = rc.nout[q];
+  if (no <= 0) return;
+  __syncthreads();
+  // first output, then the propagator e^{dt H} for the equally spaced rest
+  expm_dev(sh.H, rc.hfirst[q], sh.E, m, sh.w);
+  double* cq = coef + (int64_t)q * ldo * kMaxM;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    sh.y[i] = beta * sh.E[i * kLd];
+    cq[i] = sh.y[i];
+  }
+  __syncthreads();
+  if (no == 1) return;
+  expm_dev(sh.H, dt_out, sh.E, m, sh.w);
+  for (int o = 1; o < no; ++o) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s = fma(sh.E[i * kLd + k], sh.y[k], s);
+      sh.y2[i] = s;
+      cq[(int64_t)o * kMaxM + i] = s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) sh.y[i] = sh.y2[i];
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kSmallThreads)
+expm_batch_kernel(int m, const double* __restrict__ A, const double* __restrict__ h,
+                  double* __restrict__ E) {
+  extern __shared__ double smem_raw[];
+  SmallShared& sh = *reinterpret_cast<SmallShared*>(smem_raw);
+  const int b = blockIdx.x;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e - i * m;
+    sh.H[i * kLd + j] = A[(int64_t)b * m * m + e];
+  }
+  __syncthreads();
+  expm_dev(sh.H, h[b], sh.E, m, sh.w);
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e - i * m;
+    E[(int64_t)b * m * m + e] = sh.E[i * kLd + j];
+  }
+}
+
+}  // namespace
+
+void build_input_rhs(double* Y, int ldy, int K, const RoundCols& rc, const SourceTable& src,
+                     int64_t n, cudaStream_t st) {
+  cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)n * ldy, st);
+  const int slots = 2 * K;
+  input_rhs_kernel<<<(slots + 127) / 128, 128, 0, st>>>(Y, ldy, K, rc, src);
+}
+
+void build_initial_rhs(double* Y, int ldy, int K, const SourceTable& src, const int32_t* groups,
+                       int64_t n, cudaStream_t st) {
+  cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)n * ldy, st);
+  initial_rhs_kernel<<<(K + 127) / 128, 128, 0, st>>>(Y, ldy, K, src, groups);
+}
+
+void krylov_start(double* Vbase, int64_t vstride, const double* X, const double* Z, const double* W,
+                  int64_t gstride, const int32_t* groups, int K, int64_t n, double* partials,
+                  int nchunks, cudaStream_t st) {
+  dim3 grid((unsigned)nchunks, (unsigned)K);
+  krylov_start_kernel<<<grid, kRedThreads, 0, st>>>(Vbase, vstride, X, Z, W, gstride, groups, n,
+                                                    partials, nchunks);
+}
+
+void basis_dots(const double* Vbase, int64_t vstride, const int32_t* groups, const int32_t* iter,
+                int K, int first, int nb, int wslot, int64_t n, double* partials, int nchunks,
+                cudaStream_t st) {
+  dim3 grid((unsigned)nchunks, (unsigned)K);
+  basis_dots_kernel<<<grid, kRedThreads, 0, st>>>(Vbase, vstride, groups, iter, first, nb, wslot,
+                                                  n, partials, nchunks);
+}
+
+void basis_update(double* Vbase, int64_t vstride, const int32_t* groups, const int32_t* iter, int K,
+                  int nb, int wslot, const double* h, int64_t n, cudaStream_t st) {
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)K);
+  basis_update_kernel<<<grid, 256, 0, st>>>(Vbase, vstride, groups, iter, nb, wslot, h, n);
+}
+
+void basis_scale(double* Vbase, int64_t vstride, const int32_t* groups, const int32_t* iter, int K,
+                 int wslot, const double* scale, int64_t n, cudaStream_t st) {
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)K);
+  basis_scale_kernel<<<grid, 256, 0, st>>>(Vbase, vstride, groups, iter, wslot, scale, n);
+}
+
+void start_finish(const double* partials, int nchunks, int K, SmallState ss, const int32_t* groups,
+                  int32_t* iter_out, int32_t* iter_grp, int32_t* iter_count, cudaStream_t st) {
+  start_finish_kernel<<<1, 256, 0, st>>>(partials, nchunks, K, ss, groups, iter_out, iter_grp,
+                                         iter_count);
+}
+
+void reduce_dots(const double* partials, int nchunks, int K, int nb, const int32_t* iter,
+                 SmallState ss, int j, int mode, cudaStream_t st) {
+  reduce_dots_kernel<<<K, 32, 0, st>>>(partials, nchunks, nb, iter, ss, j, mode);
+}
+
+void residual_check(SmallState ss, const RoundCols& rc, int K, int j, double gamma, double tol,
+                    int m_max, const int32_t* replay, const int32_t* iter_in, int32_t* iter_out,
+                    int32_t* iter_grp, int32_t* iter_count, cudaStream_t st) {
+  const size_t smem = sizeof(SmallShared);
+  residual_kernel<<<K, kSmallThreads, smem, st>>>(ss, rc, iter_in, j, gamma, tol, m_max, replay);
+  compact_kernel<<<1, 32, 0, st>>>(ss, rc.group, iter_in, K, iter_out, iter_grp, iter_count);
+}
+
+void record_segments(const SmallState& ss, const RoundCols& rc, int K, int32_t* m_rec,
+                     int32_t* st_rec, cudaStream_t st) {
+  if (K <= 0) return;
+  record_kernel<<<(K + 127) / 128, 128, 0, st>>>(ss, rc, K, m_rec, st_rec);
+}
+
+void output_coefficients(SmallState ss, const RoundCols& rc, int K, double gamma, double dt_out,
+                         double* coef, int ldo, double* yend, cudaStream_t st) {
+  const size_t smem = sizeof(SmallShared);
+  coef_kernel<<<K, kSmallThreads, smem, st>>>(ss, rc, gamma, dt_out, coef, ldo, yend);
+}
+
+void expm_batch(int batch, int m, const double* A, const double* h, double* E, cudaStream_t st) {
+  const size_t smem = sizeof(SmallShared);
+  expm_batch_kernel<<<batch, kSmallThreads, smem, st>>>(m, A, h, E);
+}
+
+size_t small_shared_bytes() { return sizeof(SmallShared); }
+
+void set_small_smem_limits() {
+  const int bytes = (int)sizeof(SmallShared);
+  cudaFuncSetAttribute(residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(coef_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(expm_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+}  // namespace matex

@@ -1,0 +1,147 @@
+// Launch wrappers of the R-MATEX CUDA kernels (internal to the library).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace matex {
+
+constexpr int kMaxM = 20;      // largest Krylov dimension
+constexpr int kMaxB = kMaxM + 1;
+
+// Device view of one factor (unit-lower L, D^{-1}) on the shared structure.
+struct DevFactor {
+  const int32_t* sup_first;
+  const int64_t* sup_rowptr;
+  const int32_t* sup_rows;
+  const int64_t* diag_off;
+  const int64_t* offd_off;
+  const double* dinv;
+  const double* diag_cm;
+  const double* diag_rm;
+  const double* offd_cm;
+  const double* offd_rm;
+};
+
+// One tree level of the supernodal solve: the supernodes of the level and
+// the column block used for them.
+struct LevelPlan {
+  const int32_t* sups;   // device, supernode ids of this level
+  int32_t count;
+  int32_t max_w;         // widest supernode in the level
+  int32_t kb;            // column block: 1, 2, 4 or 8
+};
+
+// Y is node-major [n][ldy] (ldy >= ncols, multiple of 8); solves in place.
+// Returns the number of kernels launched.
+int solve_inplace(const DevFactor& F, const LevelPlan* levels, int nlev, double* Y, int ldy,
+                  int ncols, cudaStream_t st);
+
+// Y[i][q] = (scale ? scale[i] : 1) * src[cols[q]*stride + rowmap[i]]
+// (cols == null: q; rowmap == null: i)
+void gather_cols(double* Y, int ldy, int ncols, const double* src, int64_t stride,
+                 const int32_t* cols, const double* scale, const int32_t* rowmap, int64_t n,
+                 cudaStream_t st);
+// dst[cols[q]*stride + rowmap[i]] = Y[i][q]
+void scatter_cols(const double* Y, int ldy, int ncols, double* dst, int64_t stride,
+                  const int32_t* cols, const int32_t* rowmap, int64_t n, cudaStream_t st);
+
+// Per-column metadata of one segment round (device arrays, length K).
+struct RoundCols {
+  const int32_t* group;    // group of the column
+  const int32_t* seg;      // segment index inside the group
+  const double* l0;        // segment start
+  const double* len;       // segment length L
+  const double* hfirst;    // offset of the first output in the segment (L if none)
+  const int32_t* obeg;     // first output index in the segment
+  const int32_t* nout;     // outputs in the segment
+  const int64_t* segid;    // global (group, segment) index
+};
+
+struct SourceTable {
+  const int32_t* grp_ptr;  // [n_groups+1] into grp_src
+  const int32_t* grp_src;  // sources grouped by group
+  const int32_t* node;     // permuted node of each source
+  const int32_t* pwl_off;
+  const double* pwl_t;
+  const double* pwl_v;
+};
+
+// Y[:, 2q] = B_k u_k(l0), Y[:, 2q+1] = B_k (u_k(l0+L) - u_k(l0)) / L  (Y zeroed here)
+void build_input_rhs(double* Y, int ldy, int K, const RoundCols& rc, const SourceTable& src,
+                     int64_t n, cudaStream_t st);
+// Y[:, q] = B_k u_k(t) for t = 0 per group (initial states)
+void build_initial_rhs(double* Y, int ldy, int K, const SourceTable& src, const int32_t* groups,
+                       int64_t n, cudaStream_t st);
+
+// Krylov start: v = x - z + w written to V_k[0]; partial sums of |v|^2
+void krylov_start(double* Vbase, int64_t vstride, const double* X, const double* Z,
+                  const double* W, int64_t gstride, const int32_t* groups, int K, int64_t n,
+                  double* partials, int nchunks, cudaStream_t st);
+
+// Partial dot products of basis slot wslot (w) with slots first..first+nb-1
+// for each iterating column; partials laid out [K][kMaxB][nchunks].
+void basis_dots(const double* Vbase, int64_t vstride, const int32_t* groups, const int32_t* iter,
+                int K, int first, int nb, int wslot, int64_t n, double* partials, int nchunks,
+                cudaStream_t st);
+// w -= sum_i h[q][i] v_i  (h from coef, [K][kMaxB])
+void basis_update(double* Vbase, int64_t vstride, const int32_t* groups, const int32_t* iter,
+                  int K, int nb, int wslot, const double* h, int64_t n, cudaStream_t st);
+// V[wslot] *= scale[q]
+void basis_scale(double* Vbase, int64_t vstride, const int32_t* groups, const int32_t* iter,
+                 int K, int wslot, const double* scale, int64_t n, cudaStream_t st);
+
+constexpr int kChunk = 4096;  // nodes per reduction chunk
+
+// Small dense per-column work (one CTA per column).
+struct SmallState {
+  double* Ht;        // [ncol][kMaxB][kMaxM] rational Hessenberg (row-major)
+  double* beta;      // [ncol]
+  int32_t* m;        // [ncol] current / final Krylov dimension (0 = quiescent)
+  int32_t* status;   // [ncol] 0 iterating, 1 converged, 2 breakdown, 3 m_max, 4 quiescent
+  double* hbuf;      // [ncol][kMaxB] Gram-Schmidt coefficients of the current pass
+  double* scale;     // [ncol] 1/norm for normalisation
+};
+
+// finish the start vector: beta = sqrt(sum partials), scale = 1/beta, status;
+// writes the list of non-quiescent columns and its count
+void start_finish(const double* partials, int nchunks, int K, SmallState ss, const int32_t* groups,
+                  int32_t* iter_out, int32_t* iter_grp, int32_t* iter_count, cudaStream_t st);
+// reduce dot partials into hbuf (and accumulate into Ht column j when acc != 0)
+void reduce_dots(const double* partials, int nchunks, int K, int nb, const int32_t* iter,
+                 SmallState ss, int j, int mode, cudaStream_t st);
+// residual test after step j (m = j+1): decides status per column; writes
+// the compacted list of still-iterating columns and its count
+void residual_check(SmallState ss, const RoundCols& rc, int K, int j, double gamma, double tol,
+                    int m_max, const int32_t* replay, const int32_t* iter_in, int32_t* iter_out,
+                    int32_t* iter_grp, int32_t* iter_count, cudaStream_t st);
+// record m and status of the round's columns at their global segment ids
+void record_segments(const SmallState& ss, const RoundCols& rc, int K, int32_t* m_rec,
+                     int32_t* st_rec, cudaStream_t st);
+// coefficient vectors beta e^{h H} e_1 for every output of the segment and
+// for the segment end; coef [K][ldo][kMaxM], yend [K][kMaxM]
+void output_coefficients(SmallState ss, const RoundCols& rc, int K, double gamma, double dt_out,
+                         double* coef, int ldo, double* yend, cudaStream_t st);
+size_t small_shared_bytes();
+void set_small_smem_limits();
+// batched expm for the public test entry point
+void expm_batch(int batch, int m, const double* A, const double* h, double* E, cudaStream_t st);
+
+// Recombination + superposition: Xp[o][i] += sum over columns whose segment
+// holds o of (V y_o + z + h z' - w)   (h = t_o - l0)
+void recombine(double* Xp, int64_t n, int n_times, const double* Vbase, int64_t vstride,
+               const double* Z, const double* Zp, const double* W, int64_t gstride,
+               const RoundCols& rc, const int32_t* mcol, const double* coef, int ldo, int K,
+               int obeg_min, int oend_max, double dt_out, cudaStream_t st);
+// next state x_k = V y_end + z + L z' - w
+void next_state(double* X, const double* Vbase, int64_t vstride, const double* Z, const double* Zp,
+                const double* W, int64_t gstride, const RoundCols& rc, const int32_t* mcol,
+                const double* yend, int K, int64_t n, cudaStream_t st);
+// Xp[o][i] = base[i] for all o
+void fill_rows(double* Xp, const double* base, int64_t n, int n_times, cudaStream_t st);
+// Xp[0][i] += sum_q Y[i][q]
+void add_row_sum(double* Xp, const double* Y, int ldy, int K, int64_t n, cudaStream_t st);
+// out[o][r] = Xp[o][map[r]]
+void permute_out(double* out, const double* Xp, const int32_t* map, int64_t nrows, int64_t n,
+                 int n_times, cudaStream_t st);
+
+}  // namespace matex

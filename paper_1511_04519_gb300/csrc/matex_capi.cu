@@ -1,0 +1,987 @@
+// C ABI of the batched R-MATEX library: setup (ordering, factorisation,
+// schedules, upload) and the run loop that drives the CUDA kernels.
+//
+// Run structure (Alg. 2 for every group at once, one group per column):
+//   round r = segment r of every group that has one.  Per round:
+//     inputs   z = G^{-1} B u(l), z' = G^{-1} B s, w = G^{-1} C z'   (Eq. 5/6)
+//     start    v = x + F = x - z + w, beta = ||v||                   (Alg. 1)
+//     Arnoldi  w = (C + gamma G)^{-1} C v_j, two Gram-Schmidt passes, residual
+//              test of Sec. 3.3.3 per column; converged columns retire
+//     outputs  y(t_o) = beta e^{(t_o - l) H_m} e_1,  X[o] += V y + z + h z' - w
+//     hand-off x(l_{j+1}) for the next round.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/matex.h"
+#include "internal.h"
+#include "kernels.h"
+
+using namespace matex;
+
+namespace {
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct Round {
+  int32_t begin;  // first column record
+  int32_t K;      // columns
+  int32_t obeg_min, oend_max;
+};
+
+}  // namespace
+
+struct matex_ctx {
+  std::string err;
+  cudaStream_t st = nullptr;
+  int device = 0;
+  // problem
+  int64_t n = 0;
+  int32_t n_src = 0, n_groups = 0, m_max = 0, n_times = 0;
+  double gamma = 0, tol = 0, dt_out = 0, T = 0;
+  matex_opts opts{};
+  std::vector<int32_t> rows;      // output rows (original numbering); empty = all
+  std::vector<int32_t> replay;    // per segment, empty = adaptive
+  std::vector<int32_t> sel_groups;
+  int64_t n_segments = 0;
+  int32_t nrows_out = 0;
+  std::vector<double> pwl_v_host_shape;  // length of pwl_v
+  // structure
+  Symbolic S;
+  std::vector<LevelPlan> levels;
+  std::vector<Round> rounds;          // batched: segment r of every group per round
+  std::vector<Round> serial_rounds;   // one group at a time: one column per round
+  bool serial = false;
+  std::vector<int32_t> serial_cover;
+  matex_stats setup_stats{};
+  matex_stats last{};
+  // device memory
+  std::vector<void*> allocs;
+  DevFactor fM{}, fG{};
+  SourceTable src{};
+  double* c_perm = nullptr;
+  double* dc_perm = nullptr;
+  int32_t* perm = nullptr;      // new -> old
+  int32_t* out_map = nullptr;   // output row r -> new index
+  int32_t* sel_groups_d = nullptr;
+  double* pwl_v_d = nullptr;
+  // round tables
+  int32_t *rc_group = nullptr, *rc_seg = nullptr, *rc_obeg = nullptr, *rc_nout = nullptr;
+  double *rc_l0 = nullptr, *rc_len = nullptr, *rc_hfirst = nullptr;
+  int64_t* rc_segid = nullptr;
+  int32_t* replay_d = nullptr;
+  // work buffers
+  int ldy = 8;
+  int Kmax = 1;
+  int nchunks = 1;
+  double* Y = nullptr;
+  double* Vb = nullptr;     // [n_groups][kMaxB][n]
+  double *Zb = nullptr, *Zpb = nullptr, *Wb = nullptr, *Xb = nullptr;  // [n_groups][n]
+  double* Xp = nullptr;     // [n_times][n]
+  double* xdc = nullptr;    // [n]
+  double* partials = nullptr;
+  SmallState ss{};
+  int32_t *iterA = nullptr, *iterB = nullptr, *iter_grp = nullptr, *d_count = nullptr;
+  int32_t* h_count = nullptr;  // pinned
+  double* coef = nullptr;
+  double* yend = nullptr;
+  int32_t *m_rec = nullptr, *st_rec = nullptr;
+  double* out_buf = nullptr;   // device output for matex_run_host
+  // host copies of the round tables (profiling arithmetic)
+  std::vector<int32_t> h_nout_all;
+  std::vector<int64_t> h_segid_all;
+  std::vector<int32_t> round_cover;  // outputs covered per round
+  int64_t offd_rows = 0;              // sum over supernodes of off-diagonal rows
+  // profiling
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct Pending { int cls, e0; int64_t launches; double flops, bytes; int round; };
+  std::vector<Pending> pend;
+  matex_profile prof{};
+
+  ~matex_ctx() {
+    for (void* p : allocs) cudaFree(p);
+    if (h_count) cudaFreeHost(h_count);
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  }
+
+  template <typename T>
+  bool alloc(T*& p, size_t count) {
+    void* q = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    allocs.push_back(q);
+    p = static_cast<T*>(q);
+    return true;
+  }
+  template <typename T>
+  bool upload(T*& p, const T* h, size_t count) {
+    if (!alloc(p, count)) return false;
+    if (count && cudaMemcpy(p, h, count * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+      return false;
+    return true;
+  }
+};
+
+namespace {
+
+matex_status fail(matex_ctx* c, matex_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+matex_status cuda_check(matex_ctx* c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return fail(c, MATEX_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return MATEX_OK;
+}
+
+thread_local std::string g_setup_err;
+
+int roundup8(int x) { return (x + 7) & ~7; }
+
+// Local transition spots of one group: its sources' breakpoints inside (0, T)
+// plus 0 and T, sorted and unique (Sec. 3.1).
+std::vector<double> group_lts(const std::vector<int32_t>& srcs, const int32_t* pwl_off,
+                              const double* pwl_t, double T) {
+  std::vector<double> pts = {0.0, T};
+  for (int32_t s : srcs)
+    for (int32_t p = pwl_off[s]; p < pwl_off[s + 1]; ++p)
+      if (pwl_t[p] > 0.0 && pwl_t[p] < T) pts.push_back(pwl_t[p]);
+  std::sort(pts.begin(), pts.end());
+  pts.erase(std::unique(pts.begin(), pts.end()), pts.end());
+  return pts;
+}
+
+void plan_levels(matex_ctx* c, const int32_t* level_sups_d) {
+  const Symbolic& S = c->S;
+  const int nlev = (int)S.level_ptr.size() - 1;
+  c->levels.resize(nlev);
+  for (int l = 0; l < nlev; ++l) {
+    LevelPlan& L = c->levels[l];
+    L.sups = level_sups_d + S.level_ptr[l];
+    L.count = S.level_ptr[l + 1] - S.level_ptr[l];
+    int mw = 1;
+    for (int k = S.level_ptr[l]; k < S.level_ptr[l + 1]; ++k) {
+      int s = S.level_sups[k];
+      mw = std::max(mw, S.sup_first[s + 1] - S.sup_first[s]);
+    }
+    L.max_w = mw;
+    int kb = c->opts.col_block;
+    if (kb <= 0) {
+      // enough (supernode, column block) tasks to fill the GPU, else narrower blocks
+      kb = L.count >= 256 ? 8 : L.count >= 64 ? 4 : L.count >= 16 ? 2 : 1;
+    }
+    L.kb = kb;
+  }
+}
+
+int solve_cols(matex_ctx* c, const DevFactor& F, int ncols) {
+  return solve_inplace(F, c->levels.data(), (int)c->levels.size(), c->Y, c->ldy, ncols, c->st);
+}
+
+RoundCols round_cols(matex_ctx* c, const Round& r) {
+  RoundCols rc;
+  rc.group = c->rc_group + r.begin;
+  rc.seg = c->rc_seg + r.begin;
+  rc.l0 = c->rc_l0 + r.begin;
+  rc.len = c->rc_len + r.begin;
+  rc.hfirst = c->rc_hfirst + r.begin;
+  rc.obeg = c->rc_obeg + r.begin;
+  rc.nout = c->rc_nout + r.begin;
+  rc.segid = c->rc_segid + r.begin;
+  return rc;
+}
+
+matex_status read_count(matex_ctx* c, int* out) {
+  cudaMemcpyAsync(c->h_count, c->d_count, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "sync");
+  *out = *c->h_count;
+  return MATEX_OK;
+}
+
+// ---- profiling: CUDA events around timed units, summed after the run -------
+int prof_begin(matex_ctx* c) {
+  if (!c->prof_on) return -1;
+  while (c->ev_pool.size() < c->ev_used + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    c->ev_pool.push_back(e);
+  }
+  const int idx = (int)c->ev_used;
+  c->ev_used += 2;
+  cudaEventRecord(c->ev_pool[idx], c->st);
+  return idx;
+}
+
+void prof_end(matex_ctx* c, int e0, int cls, int64_t launches, double flops, double bytes,
+              int round = -1) {
+  if (e0 < 0) return;
+  cudaEventRecord(c->ev_pool[e0 + 1], c->st);
+  c->pend.push_back({cls, e0, launches, flops, bytes, round});
+}
+
+// after the stream is synchronised: fold the pending units into the profile
+void prof_collect(matex_ctx* c, const std::vector<int32_t>& m_seg) {
+  for (const auto& p : c->pend) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev_pool[p.e0], c->ev_pool[p.e0 + 1]);
+    c->prof.ms[p.cls] += ms;
+    c->prof.units[p.cls] += 1;
+    c->prof.launches[p.cls] += p.launches;
+    double fl = p.flops, by = p.bytes;
+    if (p.round >= 0) {
+      // recombination: per (node, output, group) m FMAs + the -P term and the sum
+      const Round& r = c->serial ? c->serial_rounds[p.round] : c->rounds[p.round];
+      const int cover = c->serial ? c->serial_cover[p.round] : c->round_cover[p.round];
+      double f = 0.0, vb = 0.0;
+      for (int q = 0; q < r.K; ++q) {
+        const int64_t sid = c->h_segid_all[r.begin + q];
+        const int mq = m_seg[sid];
+        f += (double)c->h_nout_all[r.begin + q] * (2.0 * mq + 4.0);
+        if (c->h_nout_all[r.begin + q] > 0) vb += mq + 3.0;
+      }
+      fl = f * (double)c->n;
+      by = 8.0 * (double)c->n * (vb + 2.0 * cover);
+    }
+    c->prof.flops[p.cls] += fl;
+    c->prof.bytes[p.cls] += by;
+  }
+  c->pend.clear();
+  c->ev_used = 0;
+}
+
+double solve_flops(const matex_ctx* c, int K) {
+  return (4.0 * (double)c->S.nnz_L + (double)c->n) * K;
+}
+double solve_bytes(const matex_ctx* c, int K) {
+  return 16.0 * (double)c->S.nnz_L + 8.0 * c->n + 8.0 * (double)c->offd_rows +
+         32.0 * (double)c->n * K;
+}
+
+enum { P_SOLVE = 0, P_MOVE = 1, P_GS = 2, P_SMALL = 3, P_RECOMB = 4, P_OTHER = 5 };
+
+matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
+  const double t0 = now_ms();
+  cudaStream_t st = c->st;
+  const int64_t n = c->n;
+  const double nd = (double)n;
+  const int64_t vstride = (int64_t)kMaxB * n;
+  int launches = 0, sweepsM = 0, sweepsG = 0;
+  int64_t solve_cols_total = 0;
+  int e;
+  auto solve = [&](const DevFactor& F, int K) {
+    e = prof_begin(c);
+    const int l = solve_cols(c, F, K);
+    prof_end(c, e, P_SOLVE, l, solve_flops(c, K), solve_bytes(c, K));
+    launches += l;
+    solve_cols_total += K;
+  };
+  auto moved = [&](int e0, int nl, int K, bool scaled) {
+    prof_end(c, e0, P_MOVE, nl, scaled ? nd * K : 0.0, 16.0 * nd * K * nl);
+    launches += nl;
+  };
+  // constant part: x_dc = G^{-1} dc_inject
+  if (c->opts.include_dc && c->dc_perm) {
+    e = prof_begin(c);
+    gather_cols(c->Y, c->ldy, 1, c->dc_perm, 0, nullptr, nullptr, nullptr, n, st);
+    moved(e, 1, 1, false);
+    solve(c->fG, 1);
+    sweepsG++;
+    e = prof_begin(c);
+    scatter_cols(c->Y, c->ldy, 1, c->xdc, 0, nullptr, nullptr, n, st);
+    moved(e, 1, 1, false);
+    e = prof_begin(c);
+    fill_rows(c->Xp, c->xdc, n, c->n_times, st);
+    prof_end(c, e, P_OTHER, 1, 0.0, 8.0 * nd * (c->n_times + 1));
+    launches++;
+  } else {
+    e = prof_begin(c);
+    fill_rows(c->Xp, nullptr, n, c->n_times, st);
+    prof_end(c, e, P_OTHER, 1, 0.0, 8.0 * nd * c->n_times);
+    launches++;
+  }
+  // each group's own DC state at t = 0 (Local_Initial_Solution)
+  const int ng = (int)c->sel_groups.size();
+  for (int g0 = 0; g0 < ng; g0 += c->ldy) {
+    const int K = std::min(c->ldy, ng - g0);
+    e = prof_begin(c);
+    build_initial_rhs(c->Y, c->ldy, K, c->src, c->sel_groups_d + g0, n, st);
+    prof_end(c, e, P_OTHER, 2, 0.0, 8.0 * nd * c->ldy);
+    launches += 2;
+    solve(c->fG, K);
+    sweepsG++;
+    e = prof_begin(c);
+    scatter_cols(c->Y, c->ldy, K, c->Xb, n, c->sel_groups_d + g0, nullptr, n, st);
+    moved(e, 1, K, false);
+    e = prof_begin(c);
+    add_row_sum(c->Xp, c->Y, c->ldy, K, n, st);
+    prof_end(c, e, P_OTHER, 1, nd * K, 8.0 * nd * (K + 2));
+    launches++;
+  }
+  matex_status s = cuda_check(c, "initial states");
+  if (s != MATEX_OK) return s;
+  const std::vector<Round>& rounds = c->serial ? c->serial_rounds : c->rounds;
+  for (size_t ri = 0; ri < rounds.size(); ++ri) {
+    const Round& r = rounds[ri];
+    const int K = r.K;
+    RoundCols rc = round_cols(c, r);
+    // z and z' (two columns per group), then w = G^{-1} C z'   (Eq. 5/6)
+    e = prof_begin(c);
+    build_input_rhs(c->Y, c->ldy, K, rc, c->src, n, st);
+    prof_end(c, e, P_OTHER, 2, 0.0, 8.0 * nd * c->ldy);
+    launches += 2;
+    solve(c->fG, 2 * K);
+    e = prof_begin(c);
+    scatter_cols(c->Y, c->ldy, K, c->Zb, n, rc.group, nullptr, n, st);
+    scatter_cols(c->Y + K, c->ldy, K, c->Zpb, n, rc.group, nullptr, n, st);
+    gather_cols(c->Y, c->ldy, K, c->Zpb, n, rc.group, c->c_perm, nullptr, n, st);
+    moved(e, 3, K, true);
+    solve(c->fG, K);
+    e = prof_begin(c);
+    scatter_cols(c->Y, c->ldy, K, c->Wb, n, rc.group, nullptr, n, st);
+    moved(e, 1, K, false);
+    sweepsG += 2;
+    // start vector v = x + F, beta = ||v||
+    e = prof_begin(c);
+    krylov_start(c->Vb, vstride, c->Xb, c->Zb, c->Wb, n, rc.group, K, n, c->partials, c->nchunks, st);
+    prof_end(c, e, P_OTHER, 1, 4.0 * nd * K, 32.0 * nd * K);
+    e = prof_begin(c);
+    start_finish(c->partials, c->nchunks, K, c->ss, rc.group, c->iterA, c->iter_grp, c->d_count, st);
+    prof_end(c, e, P_SMALL, 1, 0.0, 0.0);
+    launches += 2;
+    int kit = 0;
+    if ((s = read_count(c, &kit)) != MATEX_OK) return s;
+    int32_t* iter = c->iterA;
+    int32_t* iter_next = c->iterB;
+    if (kit > 0) {
+      e = prof_begin(c);
+      basis_scale(c->Vb, vstride, rc.group, iter, kit, 0, c->ss.scale, n, st);
+      prof_end(c, e, P_GS, 1, nd * kit, 16.0 * nd * kit);
+      launches++;
+    }
+    for (int j = 0; j < c->m_max && kit > 0; ++j) {
+      // w = (C + gamma G)^{-1} C v_j   (Alg. 1 with X1 = C + gamma G, X2 = C)
+      e = prof_begin(c);
+      gather_cols(c->Y, c->ldy, kit, c->Vb + (int64_t)j * n, vstride, c->iter_grp, c->c_perm,
+                  nullptr, n, st);
+      moved(e, 1, kit, true);
+      solve(c->fM, kit);
+      e = prof_begin(c);
+      scatter_cols(c->Y, c->ldy, kit, c->Vb + (int64_t)(j + 1) * n, vstride, c->iter_grp, nullptr,
+                   n, st);
+      moved(e, 1, kit, false);
+      sweepsM++;
+      // two classical Gram-Schmidt passes, then the norm and the normalisation
+      e = prof_begin(c);
+      for (int pass = 0; pass < 2; ++pass) {
+        basis_dots(c->Vb, vstride, rc.group, iter, kit, 0, j + 1, j + 1, n, c->partials,
+                   c->nchunks, st);
+        reduce_dots(c->partials, c->nchunks, kit, j + 1, iter, c->ss, j, pass, st);
+        basis_update(c->Vb, vstride, rc.group, iter, kit, j + 1, j + 1, c->ss.hbuf, n, st);
+      }
+      basis_dots(c->Vb, vstride, rc.group, iter, kit, j + 1, 1, j + 1, n, c->partials, c->nchunks,
+                 st);
+      reduce_dots(c->partials, c->nchunks, kit, 1, iter, c->ss, j, 2, st);
+      basis_scale(c->Vb, vstride, rc.group, iter, kit, j + 1, c->ss.scale, n, st);
+      prof_end(c, e, P_GS, 9, (8.0 * j + 11.0) * nd * kit, (4.0 * j + 13.0) * 8.0 * nd * kit);
+      e = prof_begin(c);
+      residual_check(c->ss, rc, kit, j, c->gamma, c->tol, c->m_max, c->replay_d, iter, iter_next,
+                     c->iter_grp, c->d_count, st);
+      prof_end(c, e, P_SMALL, 2, 0.0, 0.0);
+      launches += 11;
+      if ((s = read_count(c, &kit)) != MATEX_OK) return s;
+      std::swap(iter, iter_next);
+    }
+    e = prof_begin(c);
+    output_coefficients(c->ss, rc, K, c->gamma, c->dt_out, c->coef, c->n_times, c->yend, st);
+    prof_end(c, e, P_SMALL, 1, 0.0, 0.0);
+    e = prof_begin(c);
+    recombine(c->Xp, n, c->n_times, c->Vb, vstride, c->Zb, c->Zpb, c->Wb, n, rc, c->ss.m, c->coef,
+              c->n_times, K, r.obeg_min, r.oend_max, c->dt_out, st);
+    prof_end(c, e, P_RECOMB, 1, 0.0, 0.0, (int)ri);
+    e = prof_begin(c);
+    next_state(c->Xb, c->Vb, vstride, c->Zb, c->Zpb, c->Wb, n, rc, c->ss.m, c->yend, K, n, st);
+    record_segments(c->ss, rc, K, c->m_rec, c->st_rec, st);
+    prof_end(c, e, P_OTHER, 2, 0.0, 0.0);
+    launches += 4;
+    if ((s = cuda_check(c, "round")) != MATEX_OK) return s;
+  }
+  e = prof_begin(c);
+  permute_out(x_out, c->Xp, c->out_map, c->nrows_out, n, c->n_times, st);
+  prof_end(c, e, P_OTHER, 1, 0.0, 16.0 * (double)c->nrows_out * c->n_times);
+  launches++;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(c, "run sync");
+  if ((s = cuda_check(c, "run")) != MATEX_OK) return s;
+  // statistics from the per-segment records
+  std::vector<int32_t> m(c->n_segments), stt(c->n_segments);
+  if (c->n_segments) {
+    cudaMemcpy(m.data(), c->m_rec, sizeof(int32_t) * c->n_segments, cudaMemcpyDeviceToHost);
+    cudaMemcpy(stt.data(), c->st_rec, sizeof(int32_t) * c->n_segments, cudaMemcpyDeviceToHost);
+  }
+  matex_stats& o = c->last;
+  o = c->setup_stats;
+  o.run_ms = now_ms() - t0;
+  o.n_segments = (int32_t)c->n_segments;
+  o.krylov_segments = o.sum_m = o.max_m = o.nonconv = o.breakdowns = 0;
+  for (int64_t i = 0; i < c->n_segments; ++i) {
+    if (m[i] > 0) o.krylov_segments++;
+    o.sum_m += m[i];
+    o.max_m = std::max(o.max_m, m[i]);
+    if (stt[i] == 3) o.nonconv++;
+    if (stt[i] == 2) o.breakdowns++;
+  }
+  o.sweeps_M = sweepsM;
+  o.sweeps_G = sweepsG;
+  o.solve_columns = solve_cols_total;
+  o.kernel_launches = launches;
+  o.rounds = (int32_t)rounds.size();
+  prof_collect(c, m);
+  if (stats) *stats = o;
+  if (c->opts.strict && o.nonconv > 0)
+    return fail(c, MATEX_ERR_NOCONV, "some segments reached m_max above tol");
+  return MATEX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void matex_default_opts(matex_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->col_block = 0;
+  o->group_select = -1;
+  o->include_dc = 1;
+  o->max_width = 128;
+}
+
+const char* matex_status_string(matex_status s) {
+  switch (s) {
+    case MATEX_OK: return "ok";
+    case MATEX_ERR_ARG: return "invalid argument";
+    case MATEX_ERR_NOT_SPD: return "matrix not symmetric positive definite";
+    case MATEX_ERR_CUDA: return "CUDA error";
+    case MATEX_ERR_TIMEOUT: return "device wait timed out";
+    case MATEX_ERR_NOCONV: return "Krylov iteration did not converge";
+    case MATEX_ERR_OOM: return "out of memory";
+    case MATEX_ERR_STATE: return "invalid state";
+  }
+  return "unknown status";
+}
+
+const char* matex_last_error(const matex_ctx* c) {
+  return c ? c->err.c_str() : g_setup_err.c_str();
+}
+
+void matex_destroy(matex_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  delete c;
+}
+
+matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const int64_t* g_rowptr,
+                         const int32_t* g_col, const double* g_val, const double* dc_inject,
+                         int32_t n_src, const int32_t* src_node, const int32_t* pwl_off,
+                         const double* pwl_t, const double* pwl_v, const int32_t* src_group,
+                         int32_t n_groups, double gamma, double tol, int32_t m_max, double t_end,
+                         double dt_out, const matex_opts* opts, void* stream) {
+  g_setup_err.clear();
+  auto bad = [&](const std::string& m) {
+    g_setup_err = m;
+    return MATEX_ERR_ARG;
+  };
+  if (!out) return bad("out is NULL");
+  *out = nullptr;
+  if (n <= 0 || n > (int64_t)INT32_MAX) return bad("n out of range");
+  if (!cap || !g_rowptr || !g_col || !g_val) return bad("C or G pointer is NULL");
+  if (n_src < 0 || n_groups < 0) return bad("negative source or group count");
+  if (n_src > 0 && (!src_node || !pwl_off || !pwl_t || !pwl_v || !src_group))
+    return bad("source arrays are NULL");
+  if (!(gamma > 0) || !(tol > 0) || m_max < 1 || m_max > kMaxM || !(t_end > 0) || !(dt_out > 0))
+    return bad("gamma/tol/m_max/t_end/dt_out out of range");
+  for (int64_t i = 0; i < n; ++i)
+    if (!(cap[i] > 0) || !std::isfinite(cap[i])) return bad("capacitance must be positive");
+  if (g_rowptr[0] != 0) return bad("G row pointer must start at 0");
+  for (int64_t i = 0; i < n; ++i) {
+    if (g_rowptr[i + 1] < g_rowptr[i]) return bad("G row pointers decrease");
+    bool diag = false;
+    for (int64_t p = g_rowptr[i]; p < g_rowptr[i + 1]; ++p) {
+      if (g_col[p] < 0 || g_col[p] >= n) return bad("G column index out of range");
+      if (!std::isfinite(g_val[p])) return bad("G has a non-finite value");
+      if (p > g_rowptr[i] && g_col[p] <= g_col[p - 1]) return bad("G columns must be sorted and unique");
+      if (g_col[p] == i) diag = true;
+    }
+    if (!diag) return bad("G row without a diagonal entry");
+  }
+  // symmetry
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = g_rowptr[i]; p < g_rowptr[i + 1]; ++p) {
+      const int32_t j = g_col[p];
+      const int32_t* b = g_col + g_rowptr[j];
+      const int32_t* e = g_col + g_rowptr[j + 1];
+      const int32_t* f = std::lower_bound(b, e, (int32_t)i);
+      if (f == e || *f != i || g_val[g_rowptr[j] + (f - b)] != g_val[p]) return bad("G is not symmetric");
+    }
+  for (int32_t s = 0; s < n_src; ++s) {
+    if (src_node[s] < 0 || src_node[s] >= n) return bad("source node out of range");
+    if (src_group[s] < 0 || src_group[s] >= n_groups) return bad("source group out of range");
+    if (pwl_off[s + 1] <= pwl_off[s]) return bad("source without breakpoints");
+    for (int32_t p = pwl_off[s]; p < pwl_off[s + 1]; ++p) {
+      if (!std::isfinite(pwl_t[p]) || !std::isfinite(pwl_v[p])) return bad("non-finite PWL data");
+      if (p > pwl_off[s] && !(pwl_t[p] > pwl_t[p - 1])) return bad("PWL times must increase");
+    }
+  }
+  if (pwl_off && pwl_off[0] != 0) return bad("pwl_off must start at 0");
+  matex_opts o;
+  matex_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.max_width <= 0) o.max_width = 128;
+  if (o.col_block != 0 && o.col_block != 1 && o.col_block != 2 && o.col_block != 4 && o.col_block != 8)
+    return bad("col_block must be 0, 1, 2, 4 or 8");
+  if (o.group_select >= n_groups) return bad("group_select out of range");
+  if (o.n_rows < 0 || (o.n_rows > 0 && !o.rows)) return bad("row list missing");
+  for (int32_t r = 0; r < o.n_rows; ++r)
+    if (o.rows[r] < 0 || o.rows[r] >= n) return bad("output row out of range");
+
+  matex_ctx* c = new (std::nothrow) matex_ctx();
+  if (!c) return MATEX_ERR_OOM;
+  c->opts = o;
+  c->st = static_cast<cudaStream_t>(stream);
+  cudaGetDevice(&c->device);
+  c->n = n;
+  c->n_src = n_src;
+  c->n_groups = n_groups;
+  c->gamma = gamma;
+  c->tol = tol;
+  c->m_max = m_max;
+  c->dt_out = dt_out;
+  const int N = (int)std::llround(t_end / dt_out);
+  if (N < 1) { delete c; return bad("t_end / dt_out must be >= 1"); }
+  c->n_times = N + 1;
+  c->T = (double)N * dt_out;
+  if (o.n_rows > 0) c->rows.assign(o.rows, o.rows + o.n_rows);
+  c->nrows_out = o.n_rows > 0 ? o.n_rows : (int32_t)n;
+  c->opts.rows = nullptr;
+  c->opts.replay_m = nullptr;
+
+  // ---- ordering, symbolic, numeric ------------------------------------
+  double t = now_ms();
+  CsrSym A{n, g_rowptr, g_col, g_val};
+  std::vector<int32_t> nd;
+  std::string e = nested_dissection(A, nd);
+  if (e.empty()) e = symbolic_analysis(A, nd, o.max_width, c->S);
+  if (!e.empty()) { c->err = e; g_setup_err = e; delete c; return MATEX_ERR_ARG; }
+  c->setup_stats.setup_order_ms = now_ms() - t;
+  t = now_ms();
+  Numeric NM, NG;
+  e = numeric_ldlt(A, cap, gamma, c->S, NM);
+  if (e.empty()) e = numeric_ldlt(A, nullptr, 1.0, c->S, NG);
+  if (!e.empty()) { g_setup_err = e; delete c; return MATEX_ERR_NOT_SPD; }
+  c->setup_stats.setup_factor_ms = now_ms() - t;
+  c->setup_stats.nnz_L = c->S.nnz_L;
+  c->setup_stats.n_supernodes = c->S.nsup;
+  c->setup_stats.n_levels = (int32_t)c->S.level_ptr.size() - 1;
+
+  // ---- groups, segments, rounds ------------------------------------------
+  for (int32_t g = 0; g < n_groups; ++g)
+    if (o.group_select < 0 || o.group_select == g) c->sel_groups.push_back(g);
+  std::vector<std::vector<int32_t>> gsrc(n_groups);
+  for (int32_t s = 0; s < n_src; ++s) gsrc[src_group[s]].push_back(s);
+  struct Seg { int32_t g, j, obeg, nout; double l0, len, hfirst; int64_t id; };
+  std::vector<std::vector<Seg>> per_group;
+  int64_t segid = 0;
+  size_t max_segs = 0;
+  for (int32_t g : c->sel_groups) {
+    std::vector<double> lts = group_lts(gsrc[g], pwl_off, pwl_t, c->T);
+    std::vector<Seg> segs;
+    for (size_t j = 0; j + 1 < lts.size(); ++j) {
+      Seg sg;
+      sg.g = g;
+      sg.j = (int32_t)j;
+      sg.l0 = lts[j];
+      sg.len = lts[j + 1] - lts[j];
+      // outputs with l_j < t_o <= l_{j+1}
+      int ob = -1, cnt = 0;
+      int o0 = std::max(0, (int)std::floor(lts[j] / dt_out) - 1);
+      for (int oo = o0; oo < c->n_times; ++oo) {
+        const double to = (double)oo * dt_out;
+        if (to > lts[j + 1]) break;
+        if (to > lts[j]) {
+          if (ob < 0) ob = oo;
+          cnt++;
+        }
+      }
+      sg.obeg = ob < 0 ? 0 : ob;
+      sg.nout = cnt;
+      sg.hfirst = cnt > 0 ? (double)sg.obeg * dt_out - lts[j] : sg.len;
+      sg.id = segid++;
+      segs.push_back(sg);
+    }
+    max_segs = std::max(max_segs, segs.size());
+    per_group.push_back(std::move(segs));
+  }
+  c->n_segments = segid;
+  std::vector<int32_t> h_group, h_seg, h_obeg, h_nout;
+  std::vector<double> h_l0, h_len, h_hfirst;
+  std::vector<int64_t> h_segid;
+  int Kmax = 1;
+  for (size_t r = 0; r < max_segs; ++r) {
+    Round rd;
+    rd.begin = (int32_t)h_group.size();
+    rd.obeg_min = c->n_times;
+    rd.oend_max = 0;
+    for (auto& segs : per_group) {
+      if (r >= segs.size()) continue;
+      const Seg& sg = segs[r];
+      h_group.push_back(sg.g);
+      h_seg.push_back(sg.j);
+      h_obeg.push_back(sg.obeg);
+      h_nout.push_back(sg.nout);
+      h_l0.push_back(sg.l0);
+      h_len.push_back(sg.len);
+      h_hfirst.push_back(sg.hfirst);
+      h_segid.push_back(sg.id);
+      if (sg.nout > 0) {
+        rd.obeg_min = std::min(rd.obeg_min, sg.obeg);
+        rd.oend_max = std::max(rd.oend_max, sg.obeg + sg.nout);
+      }
+    }
+    rd.K = (int32_t)h_group.size() - rd.begin;
+    Kmax = std::max(Kmax, rd.K);
+    c->rounds.push_back(rd);
+  }
+  c->Kmax = Kmax;
+  c->h_nout_all = h_nout;
+  c->h_segid_all = h_segid;
+  for (const Round& rd : c->rounds) {
+    std::vector<char> cov(c->n_times, 0);
+    int cnt = 0;
+    for (int q = 0; q < rd.K; ++q)
+      for (int o = h_obeg[rd.begin + q]; o < h_obeg[rd.begin + q] + h_nout[rd.begin + q]; ++o)
+        if (!cov[o]) { cov[o] = 1; cnt++; }
+    c->round_cover.push_back(cnt);
+  }
+  c->offd_rows = c->S.sup_rowptr[c->S.nsup] - c->S.n;
+  // the same column records, one group at a time in time order
+  {
+    std::vector<std::vector<int32_t>> by_group(n_groups);
+    for (const Round& rd : c->rounds)
+      for (int q = 0; q < rd.K; ++q) by_group[h_group[rd.begin + q]].push_back(rd.begin + q);
+    for (int32_t g = 0; g < n_groups; ++g)
+      for (int32_t rec : by_group[g]) {
+        Round one;
+        one.begin = rec;
+        one.K = 1;
+        one.obeg_min = h_nout[rec] > 0 ? h_obeg[rec] : c->n_times;
+        one.oend_max = h_nout[rec] > 0 ? h_obeg[rec] + h_nout[rec] : 0;
+        c->serial_rounds.push_back(one);
+        c->serial_cover.push_back(h_nout[rec]);
+      }
+  }
+  if (opts && opts->replay_m) {
+    if (opts->n_replay != c->n_segments) {
+      g_setup_err = "replay_m length differs from the number of segments";
+      delete c;
+      return MATEX_ERR_ARG;
+    }
+    c->replay.assign(opts->replay_m, opts->replay_m + opts->n_replay);
+  }
+
+  // ---- upload --------------------------------------------------------------
+  t = now_ms();
+  bool ok = true;
+  const Symbolic& S = c->S;
+  int32_t *sup_first, *sup_rows, *level_sups;
+  int64_t *sup_rowptr, *diag_off, *offd_off;
+  ok = ok && c->upload(sup_first, S.sup_first.data(), S.sup_first.size());
+  ok = ok && c->upload(sup_rowptr, S.sup_rowptr.data(), S.sup_rowptr.size());
+  ok = ok && c->upload(sup_rows, S.sup_rows.data(), S.sup_rows.size());
+  ok = ok && c->upload(diag_off, S.diag_off.data(), S.diag_off.size());
+  ok = ok && c->upload(offd_off, S.offd_off.data(), S.offd_off.size());
+  ok = ok && c->upload(level_sups, S.level_sups.data(), S.level_sups.size());
+  auto up_factor = [&](const Numeric& Nm, DevFactor& F) {
+    double *dinv, *dcm, *drm, *ocm, *orm;
+    bool k = c->upload(dinv, Nm.dinv.data(), Nm.dinv.size()) &&
+             c->upload(dcm, Nm.diag_cm.data(), Nm.diag_cm.size()) &&
+             c->upload(drm, Nm.diag_rm.data(), Nm.diag_rm.size()) &&
+             c->upload(ocm, Nm.offd_cm.data(), Nm.offd_cm.size()) &&
+             c->upload(orm, Nm.offd_rm.data(), Nm.offd_rm.size());
+    F = DevFactor{sup_first, sup_rowptr, sup_rows, diag_off, offd_off, dinv, dcm, drm, ocm, orm};
+    return k;
+  };
+  ok = ok && up_factor(NM, c->fM) && up_factor(NG, c->fG);
+  {
+    std::vector<double> cp(n), dp(n, 0.0);
+    for (int64_t k = 0; k < n; ++k) {
+      cp[k] = cap[S.perm[k]];
+      if (dc_inject) dp[k] = dc_inject[S.perm[k]];
+    }
+    ok = ok && c->upload(c->c_perm, cp.data(), n);
+    if (dc_inject) ok = ok && c->upload(c->dc_perm, dp.data(), n);
+    ok = ok && c->upload(c->perm, S.perm.data(), n);
+    std::vector<int32_t> omap(c->nrows_out);
+    for (int32_t r = 0; r < c->nrows_out; ++r)
+      omap[r] = c->rows.empty() ? S.iperm[r] : S.iperm[c->rows[r]];
+    ok = ok && c->upload(c->out_map, omap.data(), omap.size());
+  }
+  {
+    std::vector<int32_t> gptr(n_groups + 1, 0), gs;
+    for (int32_t g = 0; g < n_groups; ++g) {
+      gptr[g + 1] = gptr[g] + (int32_t)gsrc[g].size();
+      gs.insert(gs.end(), gsrc[g].begin(), gsrc[g].end());
+    }
+    std::vector<int32_t> node(n_src);
+    for (int32_t s = 0; s < n_src; ++s) node[s] = S.iperm[src_node[s]];
+    const size_t npwl = n_src ? (size_t)pwl_off[n_src] : 0;
+    int32_t *gp, *gsd, *nd_d, *po;
+    double* pt;
+    ok = ok && c->upload(gp, gptr.data(), gptr.size()) && c->upload(gsd, gs.data(), gs.size()) &&
+         c->upload(nd_d, node.data(), node.size());
+    std::vector<int32_t> poff(pwl_off ? pwl_off : nullptr, pwl_off ? pwl_off + n_src + 1 : nullptr);
+    if (poff.empty()) poff.push_back(0);
+    ok = ok && c->upload(po, poff.data(), poff.size()) && c->upload(pt, pwl_t, npwl) &&
+         c->upload(c->pwl_v_d, pwl_v, npwl);
+    c->pwl_v_host_shape.resize(npwl);
+    c->src = SourceTable{gp, gsd, nd_d, po, pt, c->pwl_v_d};
+  }
+  ok = ok && c->upload(c->sel_groups_d, c->sel_groups.data(), c->sel_groups.size());
+  ok = ok && c->upload(c->rc_group, h_group.data(), h_group.size()) &&
+       c->upload(c->rc_seg, h_seg.data(), h_seg.size()) &&
+       c->upload(c->rc_obeg, h_obeg.data(), h_obeg.size()) &&
+       c->upload(c->rc_nout, h_nout.data(), h_nout.size()) &&
+       c->upload(c->rc_l0, h_l0.data(), h_l0.size()) &&
+       c->upload(c->rc_len, h_len.data(), h_len.size()) &&
+       c->upload(c->rc_hfirst, h_hfirst.data(), h_hfirst.size()) &&
+       c->upload(c->rc_segid, h_segid.data(), h_segid.size());
+  if (!c->replay.empty()) ok = ok && c->upload(c->replay_d, c->replay.data(), c->replay.size());
+  plan_levels(c, level_sups);
+  // work buffers
+  c->ldy = roundup8(std::max({2 * Kmax, 8, std::min<int>(n_groups, 256)}));
+  c->nchunks = (int)((n + kChunk - 1) / kChunk);
+  const size_t G = (size_t)std::max(n_groups, 1);
+  ok = ok && c->alloc(c->Y, (size_t)n * c->ldy) && c->alloc(c->Vb, G * kMaxB * n) &&
+       c->alloc(c->Zb, G * n) && c->alloc(c->Zpb, G * n) && c->alloc(c->Wb, G * n) &&
+       c->alloc(c->Xb, G * n) && c->alloc(c->Xp, (size_t)c->n_times * n) && c->alloc(c->xdc, n) &&
+       c->alloc(c->partials, (size_t)Kmax * kMaxB * c->nchunks) &&
+       c->alloc(c->ss.Ht, (size_t)Kmax * kMaxB * kMaxM) && c->alloc(c->ss.beta, Kmax) &&
+       c->alloc(c->ss.m, Kmax) && c->alloc(c->ss.status, Kmax) &&
+       c->alloc(c->ss.hbuf, (size_t)Kmax * kMaxB) && c->alloc(c->ss.scale, Kmax) &&
+       c->alloc(c->iterA, Kmax) && c->alloc(c->iterB, Kmax) && c->alloc(c->iter_grp, Kmax) &&
+       c->alloc(c->d_count, 1) && c->alloc(c->coef, (size_t)Kmax * c->n_times * kMaxM) &&
+       c->alloc(c->yend, (size_t)Kmax * kMaxM) && c->alloc(c->m_rec, std::max<int64_t>(1, c->n_segments)) &&
+       c->alloc(c->st_rec, std::max<int64_t>(1, c->n_segments));
+  if (ok && cudaMallocHost(&c->h_count, sizeof(int32_t)) != cudaSuccess) ok = false;
+  if (!ok) {
+    cudaGetLastError();
+    g_setup_err = "device allocation or upload failed";
+    delete c;
+    return MATEX_ERR_OOM;
+  }
+  set_small_smem_limits();
+  cudaMemset(c->Vb, 0, sizeof(double) * G * kMaxB * n);
+  cudaMemset(c->Xb, 0, sizeof(double) * G * n);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    g_setup_err = std::string("setup: ") + cudaGetErrorString(cudaGetLastError());
+    delete c;
+    return MATEX_ERR_CUDA;
+  }
+  c->setup_stats.setup_upload_ms = now_ms() - t;
+  *out = c;
+  return MATEX_OK;
+}
+
+matex_status matex_run(matex_ctx* c, double* x_out, matex_stats* stats) {
+  if (!c) return MATEX_ERR_ARG;
+  if (!x_out) return fail(c, MATEX_ERR_ARG, "x_out is NULL");
+  return run_device(c, x_out, stats);
+}
+
+matex_status matex_set_sources(matex_ctx* c, const double* pwl_v_host) {
+  if (!c) return MATEX_ERR_ARG;
+  if (!pwl_v_host) return fail(c, MATEX_ERR_ARG, "pwl_v is NULL");
+  for (size_t i = 0; i < c->pwl_v_host_shape.size(); ++i)
+    if (!std::isfinite(pwl_v_host[i])) return fail(c, MATEX_ERR_ARG, "non-finite PWL value");
+  cudaMemcpyAsync(c->pwl_v_d, pwl_v_host, sizeof(double) * c->pwl_v_host_shape.size(),
+                  cudaMemcpyHostToDevice, c->st);
+  return cuda_check(c, "set_sources");
+}
+
+matex_status matex_run_host(matex_ctx* c, const double* pwl_v_host, double* x_out_host,
+                            matex_stats* stats) {
+  if (!c) return MATEX_ERR_ARG;
+  if (!x_out_host) return fail(c, MATEX_ERR_ARG, "x_out_host is NULL");
+  const size_t bytes = sizeof(double) * (size_t)c->n_times * c->nrows_out;
+  if (!c->out_buf && !c->alloc(c->out_buf, (size_t)c->n_times * c->nrows_out))
+    return fail(c, MATEX_ERR_OOM, "output buffer");
+  if (pwl_v_host) {
+    cudaMemcpyAsync(c->pwl_v_d, pwl_v_host, sizeof(double) * c->pwl_v_host_shape.size(),
+                    cudaMemcpyHostToDevice, c->st);
+  }
+  matex_status s = run_device(c, c->out_buf, stats);
+  if (s != MATEX_OK && s != MATEX_ERR_NOCONV) return s;
+  if (cudaMemcpyAsync(x_out_host, c->out_buf, bytes, cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+      cudaStreamSynchronize(c->st) != cudaSuccess)
+    return cuda_check(c, "run_host copy");
+  return s;
+}
+
+matex_status matex_solve(matex_ctx* c, int32_t which, int32_t ncols, const double* b, double* x) {
+  if (!c) return MATEX_ERR_ARG;
+  if ((which != 0 && which != 1) || ncols < 0 || (ncols > 0 && (!b || !x)))
+    return fail(c, MATEX_ERR_ARG, "bad solve arguments");
+  const DevFactor& F = which == 0 ? c->fM : c->fG;
+  const int64_t n = c->n;
+  for (int32_t q0 = 0; q0 < ncols; q0 += c->ldy) {
+    const int K = std::min<int>(c->ldy, ncols - q0);
+    gather_cols(c->Y, c->ldy, K, b + (int64_t)q0 * n, n, nullptr, nullptr, c->perm, n, c->st);
+    solve_cols(c, F, K);
+    scatter_cols(c->Y, c->ldy, K, x + (int64_t)q0 * n, n, nullptr, c->perm, n, c->st);
+  }
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "solve sync");
+  return cuda_check(c, "solve");
+}
+
+matex_status matex_expm(matex_ctx* c, int32_t batch, int32_t m, const double* A, const double* h,
+                        double* E) {
+  if (!c) return MATEX_ERR_ARG;
+  if (batch < 0 || m < 1 || m > kMaxM || (batch > 0 && (!A || !h || !E)))
+    return fail(c, MATEX_ERR_ARG, "bad expm arguments");
+  if (batch == 0) return MATEX_OK;
+  expm_batch(batch, m, A, h, E, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "expm sync");
+  return cuda_check(c, "expm");
+}
+
+matex_status matex_get_m(matex_ctx* c, int32_t* m_host, int64_t cap, int64_t* count) {
+  if (!c) return MATEX_ERR_ARG;
+  if (count) *count = c->n_segments;
+  if (m_host && cap > 0 && c->n_segments > 0) {
+    const int64_t k = std::min(cap, c->n_segments);
+    if (cudaMemcpy(m_host, c->m_rec, sizeof(int32_t) * k, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return cuda_check(c, "get_m");
+  }
+  return MATEX_OK;
+}
+
+matex_status matex_get_sizes(matex_ctx* c, int32_t* n_times, int32_t* n_rows, int64_t* n_segments) {
+  if (!c) return MATEX_ERR_ARG;
+  if (n_times) *n_times = c->n_times;
+  if (n_rows) *n_rows = c->nrows_out;
+  if (n_segments) *n_segments = c->n_segments;
+  return MATEX_OK;
+}
+
+matex_status matex_set_batching(matex_ctx* c, int32_t one_group_at_a_time) {
+  if (!c) return MATEX_ERR_ARG;
+  c->serial = one_group_at_a_time != 0;
+  return MATEX_OK;
+}
+
+matex_status matex_set_profiling(matex_ctx* c, int32_t on) {
+  if (!c) return MATEX_ERR_ARG;
+  c->prof_on = on != 0;
+  if (c->prof_on) {
+    std::memset(&c->prof, 0, sizeof(c->prof));
+    c->pend.clear();
+    c->ev_used = 0;
+  }
+  return MATEX_OK;
+}
+
+matex_status matex_get_profile(matex_ctx* c, matex_profile* out) {
+  if (!c || !out) return MATEX_ERR_ARG;
+  *out = c->prof;
+  return MATEX_OK;
+}
+
+matex_status matex_get_setup_stats(matex_ctx* c, matex_stats* stats) {
+  if (!c) return MATEX_ERR_ARG;
+  if (stats) *stats = c->setup_stats;
+  return MATEX_OK;
+}
+
+}  // extern "C"
+
+extern "C" matex_status matex_host_factor_solve(int64_t n, const int64_t* rowptr, const int32_t* col,
+                                                const double* val, const double* dshift,
+                                                double alpha, int32_t max_width, int32_t ncols,
+                                                const double* b, double* x, int64_t* info) {
+  g_setup_err.clear();
+  if (n <= 0 || !rowptr || !col || !val || ncols < 0 || (ncols > 0 && (!b || !x))) {
+    g_setup_err = "bad arguments";
+    return MATEX_ERR_ARG;
+  }
+  CsrSym A{n, rowptr, col, val};
+  std::vector<int32_t> nd;
+  Symbolic S;
+  std::string e = nested_dissection(A, nd);
+  if (e.empty()) e = symbolic_analysis(A, nd, max_width > 0 ? max_width : 128, S);
+  if (!e.empty()) { g_setup_err = e; return MATEX_ERR_ARG; }
+  Numeric F;
+  e = numeric_ldlt(A, dshift, alpha, S, F);
+  if (!e.empty()) { g_setup_err = e; return MATEX_ERR_NOT_SPD; }
+  int64_t maxw = 0;
+  for (int32_t s = 0; s < S.nsup; ++s) maxw = std::max<int64_t>(maxw, S.sup_first[s + 1] - S.sup_first[s]);
+  if (info) {
+    info[0] = S.nnz_L;
+    info[1] = S.nsup;
+    info[2] = (int64_t)S.level_ptr.size() - 1;
+    info[3] = maxw;
+  }
+  std::vector<double> y(n);
+  for (int32_t q = 0; q < ncols; ++q) {
+    for (int64_t k = 0; k < n; ++k) y[k] = b[(int64_t)q * n + S.perm[k]];
+    // forward, supernodes in level order (as the GPU launches them)
+    for (size_t li = 0; li < S.level_sups.size(); ++li) {
+      const int32_t s = S.level_sups[li];
+      const int32_t f = S.sup_first[s], w = S.sup_first[s + 1] - f;
+      const int64_t rp = S.sup_rowptr[s];
+      const int32_t r = (int32_t)(S.sup_rowptr[s + 1] - rp) - w;
+      const double* Lc = &F.diag_cm[S.diag_off[s]];
+      for (int32_t j = 0; j < w; ++j)
+        for (int32_t i = j + 1; i < w; ++i) y[f + i] -= Lc[i + j * w] * y[f + j];
+      const double* Oc = &F.offd_cm[S.offd_off[s]];
+      for (int32_t i = 0; i < r; ++i) {
+        double acc = 0.0;
+        for (int32_t j = 0; j < w; ++j) acc += Oc[i + (int64_t)j * r] * y[f + j];
+        y[S.sup_rows[rp + w + i]] -= acc;
+      }
+    }
+    for (size_t li = S.level_sups.size(); li-- > 0;) {
+      const int32_t s = S.level_sups[li];
+      const int32_t f = S.sup_first[s], w = S.sup_first[s + 1] - f;
+      const int64_t rp = S.sup_rowptr[s];
+      const int32_t r = (int32_t)(S.sup_rowptr[s + 1] - rp) - w;
+      const double* Or = &F.offd_rm[S.offd_off[s]];
+      std::vector<double> sb(w);
+      for (int32_t j = 0; j < w; ++j) {
+        double acc = y[f + j] * F.dinv[f + j];
+        for (int32_t i = 0; i < r; ++i) acc -= Or[(int64_t)i * w + j] * y[S.sup_rows[rp + w + i]];
+        sb[j] = acc;
+      }
+      const double* Lr = &F.diag_rm[S.diag_off[s]];
+      for (int32_t j = w - 1; j > 0; --j)
+        for (int32_t i = 0; i < j; ++i) sb[i] -= Lr[j * w + i] * sb[j];
+      for (int32_t j = 0; j < w; ++j) y[f + j] = sb[j];
+    }
+    for (int64_t k = 0; k < n; ++k) x[(int64_t)q * n + S.perm[k]] = y[k];
+  }
+  return MATEX_OK;
+}

@@ -1,0 +1,338 @@
+"""Thin ctypes binding of the C ABI in ``include/matex.h``.
+
+Argument marshalling only: every step of the integrator runs in the CUDA
+library.  Device buffers and the stream come from PyTorch.  Importing this
+module loads ``_lib/libmatex.so`` and raises if it is missing; there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmatex.so")
+
+MATEX_OK = 0
+MATEX_ERR_NOCONV = 5
+STATUS = {0: "MATEX_OK", 1: "MATEX_ERR_ARG", 2: "MATEX_ERR_NOT_SPD", 3: "MATEX_ERR_CUDA",
+          4: "MATEX_ERR_TIMEOUT", 5: "MATEX_ERR_NOCONV", 6: "MATEX_ERR_OOM", 7: "MATEX_ERR_STATE"}
+
+
+class MatexError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MatexOpts(C.Structure):
+    _fields_ = [("col_block", C.c_int32), ("group_select", C.c_int32), ("include_dc", C.c_int32),
+                ("n_rows", C.c_int32), ("rows", C.POINTER(C.c_int32)),
+                ("replay_m", C.POINTER(C.c_int32)), ("n_replay", C.c_int64),
+                ("max_width", C.c_int32), ("strict", C.c_int32)]
+
+
+class MatexStats(C.Structure):
+    _fields_ = [("setup_order_ms", C.c_double), ("setup_factor_ms", C.c_double),
+                ("setup_upload_ms", C.c_double), ("run_ms", C.c_double), ("nnz_L", C.c_int64),
+                ("n_supernodes", C.c_int32), ("n_levels", C.c_int32), ("n_segments", C.c_int32),
+                ("krylov_segments", C.c_int32), ("sum_m", C.c_int32), ("max_m", C.c_int32),
+                ("nonconv", C.c_int32), ("breakdowns", C.c_int32), ("sweeps_M", C.c_int32),
+                ("sweeps_G", C.c_int32), ("solve_columns", C.c_int64),
+                ("kernel_launches", C.c_int32), ("rounds", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class MatexProfile(C.Structure):
+    _fields_ = [("ms", C.c_double * 6), ("units", C.c_int64 * 6), ("launches", C.c_int64 * 6),
+                ("flops", C.c_double * 6), ("bytes", C.c_double * 6)]
+
+    CLASSES = ["solve", "move", "gram_schmidt", "small_dense", "recombine", "other"]
+
+    def as_dict(self):
+        return {name: dict(ms=self.ms[i], units=self.units[i], launches=self.launches[i],
+                           flops=self.flops[i], bytes=self.bytes[i])
+                for i, name in enumerate(self.CLASSES)}
+
+
+EXPORTS = ["matex_default_opts", "matex_setup", "matex_run", "matex_run_host", "matex_set_sources",
+           "matex_solve", "matex_expm", "matex_get_m", "matex_get_sizes", "matex_get_setup_stats",
+           "matex_last_error", "matex_status_string", "matex_destroy", "matex_set_profiling",
+           "matex_get_profile", "matex_host_factor_solve", "matex_set_batching"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libmatex.so is not built ({LIB_PATH}); run "
+                          "paper_1511_04519_gb300.build.build() first")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    i32p, i64p, dp = C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_double)
+    lib.matex_default_opts.argtypes = [C.POINTER(MatexOpts)]
+    lib.matex_default_opts.restype = None
+    lib.matex_setup.argtypes = [C.POINTER(P), C.c_int64, dp, i64p, i32p, dp, dp, C.c_int32, i32p,
+                                i32p, dp, dp, i32p, C.c_int32, C.c_double, C.c_double, C.c_int32,
+                                C.c_double, C.c_double, C.POINTER(MatexOpts), P]
+    lib.matex_setup.restype = C.c_int
+    lib.matex_run.argtypes = [P, P, C.POINTER(MatexStats)]
+    lib.matex_run.restype = C.c_int
+    lib.matex_run_host.argtypes = [P, dp, dp, C.POINTER(MatexStats)]
+    lib.matex_run_host.restype = C.c_int
+    lib.matex_set_sources.argtypes = [P, dp]
+    lib.matex_set_sources.restype = C.c_int
+    lib.matex_solve.argtypes = [P, C.c_int32, C.c_int32, P, P]
+    lib.matex_solve.restype = C.c_int
+    lib.matex_expm.argtypes = [P, C.c_int32, C.c_int32, P, P, P]
+    lib.matex_expm.restype = C.c_int
+    lib.matex_get_m.argtypes = [P, i32p, C.c_int64, i64p]
+    lib.matex_get_m.restype = C.c_int
+    lib.matex_get_sizes.argtypes = [P, i32p, i32p, i64p]
+    lib.matex_get_sizes.restype = C.c_int
+    lib.matex_get_setup_stats.argtypes = [P, C.POINTER(MatexStats)]
+    lib.matex_get_setup_stats.restype = C.c_int
+    lib.matex_last_error.argtypes = [P]
+    lib.matex_last_error.restype = C.c_char_p
+    lib.matex_status_string.argtypes = [C.c_int]
+    lib.matex_status_string.restype = C.c_char_p
+    lib.matex_set_batching.argtypes = [P, C.c_int32]
+    lib.matex_set_batching.restype = C.c_int
+    lib.matex_set_profiling.argtypes = [P, C.c_int32]
+    lib.matex_set_profiling.restype = C.c_int
+    lib.matex_get_profile.argtypes = [P, C.POINTER(MatexProfile)]
+    lib.matex_get_profile.restype = C.c_int
+    lib.matex_destroy.argtypes = [P]
+    lib.matex_destroy.restype = None
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype)) if a is not None else None
+
+
+def _check(ctx, status, allow=(MATEX_OK,)):
+    if status not in allow:
+        msg = _lib.matex_last_error(ctx)
+        raise MatexError(status, msg.decode() if msg else "")
+    return status
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def matex_default_opts():
+    o = MatexOpts()
+    _lib.matex_default_opts(C.byref(o))
+    return o
+
+
+def matex_setup(n, c, g_rowptr, g_col, g_val, dc_inject, src_node, pwl_off, pwl_t, pwl_v,
+                src_group, n_groups, gamma, tol, m_max, t_end, dt_out, opts=None, stream=None):
+    """matex_setup of the C ABI; arrays are host numpy arrays (copied)."""
+    keep = []
+
+    def arr(x, dt):
+        a = np.ascontiguousarray(np.asarray(x, dtype=dt))
+        keep.append(a)
+        return a
+
+    c_ = arr(c, np.float64)
+    rp = arr(g_rowptr, np.int64)
+    gc = arr(g_col, np.int32)
+    gv = arr(g_val, np.float64)
+    dc = arr(dc_inject, np.float64) if dc_inject is not None else None
+    sn = arr(src_node, np.int32)
+    po = arr(pwl_off, np.int32)
+    pt = arr(pwl_t, np.float64)
+    pv = arr(pwl_v, np.float64)
+    sg = arr(src_group, np.int32)
+    o = opts if opts is not None else matex_default_opts()
+    ctx = C.c_void_p()
+    st = _lib.matex_setup(C.byref(ctx), int(n), _ptr(c_, C.c_double), _ptr(rp, C.c_int64),
+                          _ptr(gc, C.c_int32), _ptr(gv, C.c_double),
+                          _ptr(dc, C.c_double) if dc is not None else None, int(sn.shape[0]),
+                          _ptr(sn, C.c_int32), _ptr(po, C.c_int32), _ptr(pt, C.c_double),
+                          _ptr(pv, C.c_double), _ptr(sg, C.c_int32), int(n_groups), float(gamma),
+                          float(tol), int(m_max), float(t_end), float(dt_out), C.byref(o),
+                          _stream_handle(stream))
+    if st != MATEX_OK:
+        msg = _lib.matex_last_error(None)
+        raise MatexError(st, msg.decode() if msg else "")
+    return ctx
+
+
+def matex_run(ctx, x_out_ptr, strict_ok=True):
+    s = MatexStats()
+    st = _lib.matex_run(ctx, C.c_void_p(x_out_ptr), C.byref(s))
+    _check(ctx, st, allow=(MATEX_OK, MATEX_ERR_NOCONV) if strict_ok else (MATEX_OK,))
+    return s
+
+
+def matex_run_host(ctx, pwl_v_host, x_out_host):
+    s = MatexStats()
+    st = _lib.matex_run_host(ctx, _ptr(pwl_v_host, C.c_double) if pwl_v_host is not None else None,
+                             _ptr(x_out_host, C.c_double), C.byref(s))
+    _check(ctx, st, allow=(MATEX_OK, MATEX_ERR_NOCONV))
+    return s
+
+
+def matex_set_sources(ctx, pwl_v_host):
+    a = np.ascontiguousarray(pwl_v_host, dtype=np.float64)
+    _check(ctx, _lib.matex_set_sources(ctx, _ptr(a, C.c_double)))
+
+
+def matex_solve(ctx, which, ncols, b_ptr, x_ptr):
+    _check(ctx, _lib.matex_solve(ctx, int(which), int(ncols), C.c_void_p(b_ptr), C.c_void_p(x_ptr)))
+
+
+def matex_expm(ctx, batch, m, a_ptr, h_ptr, e_ptr):
+    _check(ctx, _lib.matex_expm(ctx, int(batch), int(m), C.c_void_p(a_ptr), C.c_void_p(h_ptr),
+                                C.c_void_p(e_ptr)))
+
+
+def matex_get_m(ctx):
+    cnt = C.c_int64()
+    _check(ctx, _lib.matex_get_m(ctx, None, 0, C.byref(cnt)))
+    out = np.zeros(max(cnt.value, 1), np.int32)
+    _check(ctx, _lib.matex_get_m(ctx, _ptr(out, C.c_int32), cnt.value, C.byref(cnt)))
+    return out[: cnt.value]
+
+
+def matex_get_sizes(ctx):
+    nt, nr, ns = C.c_int32(), C.c_int32(), C.c_int64()
+    _check(ctx, _lib.matex_get_sizes(ctx, C.byref(nt), C.byref(nr), C.byref(ns)))
+    return nt.value, nr.value, ns.value
+
+
+def matex_get_setup_stats(ctx):
+    s = MatexStats()
+    _check(ctx, _lib.matex_get_setup_stats(ctx, C.byref(s)))
+    return s
+
+
+def matex_set_batching(ctx, one_group_at_a_time):
+    _check(ctx, _lib.matex_set_batching(ctx, int(bool(one_group_at_a_time))))
+
+
+def matex_set_profiling(ctx, on):
+    _check(ctx, _lib.matex_set_profiling(ctx, int(bool(on))))
+
+
+def matex_get_profile(ctx):
+    p = MatexProfile()
+    _check(ctx, _lib.matex_get_profile(ctx, C.byref(p)))
+    return p
+
+
+def matex_destroy(ctx):
+    if ctx:
+        _lib.matex_destroy(ctx)
+
+
+class Sim:
+    """Owner of one context built from a problem-like object (attributes n, c,
+    g_rowptr, g_col, g_val, dc_inject, src_node, pwl_off, pwl_t, pwl_v,
+    src_group, n_groups, gamma, tol, m_max, t_end, dt_out)."""
+
+    def __init__(self, p, col_block=0, group_select=-1, include_dc=True, rows=None,
+                 replay_m=None, max_width=0, strict=False, stream=None, **overrides):
+        o = matex_default_opts()
+        o.col_block = col_block
+        o.group_select = group_select
+        o.include_dc = int(bool(include_dc))
+        if max_width:
+            o.max_width = max_width
+        o.strict = int(bool(strict))
+        self._keep = []
+        if rows is not None:
+            r = np.ascontiguousarray(rows, dtype=np.int32)
+            self._keep.append(r)
+            o.n_rows = int(r.shape[0])
+            o.rows = _ptr(r, C.c_int32)
+        if replay_m is not None:
+            rm = np.ascontiguousarray(replay_m, dtype=np.int32)
+            self._keep.append(rm)
+            o.replay_m = _ptr(rm, C.c_int32)
+            o.n_replay = int(rm.shape[0])
+        g = dict(gamma=p.gamma, tol=p.tol, m_max=p.m_max, t_end=p.t_end, dt_out=p.dt_out)
+        g.update(overrides)
+        self.ctx = matex_setup(p.n, p.c, p.g_rowptr, p.g_col, p.g_val, p.dc_inject, p.src_node,
+                               p.pwl_off, p.pwl_t, p.pwl_v, p.src_group, p.n_groups, g["gamma"],
+                               g["tol"], g["m_max"], g["t_end"], g["dt_out"], opts=o, stream=stream)
+        self.n = int(p.n)
+        self.n_times, self.n_rows, self.n_segments = matex_get_sizes(self.ctx)
+        self.pwl_len = int(np.asarray(p.pwl_v).shape[0])
+
+    def run(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.n_times, self.n_rows), dtype=torch.float64, device="cuda")
+        self.stats = matex_run(self.ctx, out.data_ptr())
+        return out
+
+    def run_host(self, pwl_v=None, out=None):
+        if out is None:
+            out = np.empty((self.n_times, self.n_rows), np.float64)
+        pv = None if pwl_v is None else np.ascontiguousarray(pwl_v, dtype=np.float64)
+        self.stats = matex_run_host(self.ctx, pv, out)
+        return out
+
+    def m_sequence(self):
+        return matex_get_m(self.ctx)
+
+    def solve(self, which, b):
+        import torch
+        b = b.contiguous()
+        x = torch.empty_like(b)
+        ncols = 1 if b.dim() == 1 else b.shape[0]
+        matex_solve(self.ctx, which, ncols, b.data_ptr(), x.data_ptr())
+        torch.cuda.synchronize()
+        return x
+
+    def one_group_at_a_time(self, on=True):
+        matex_set_batching(self.ctx, on)
+
+    def profile(self, on=None):
+        if on is not None:
+            matex_set_profiling(self.ctx, on)
+        return matex_get_profile(self.ctx).as_dict()
+
+    def setup_stats(self):
+        return matex_get_setup_stats(self.ctx).as_dict()
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            matex_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def expm(sim, A, h):
+    """Batched e^{h A} through matex_expm (A: [batch, m, m] cuda float64)."""
+    import torch
+    A = A.contiguous()
+    h = h.contiguous()
+    E = torch.empty_like(A)
+    matex_expm(sim.ctx, A.shape[0], A.shape[1], A.data_ptr(), h.data_ptr(), E.data_ptr())
+    return E
