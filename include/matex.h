@@ -62,7 +62,7 @@ typedef struct matex_opts {
   const int32_t* replay_m; /* host or NULL: Krylov dimension to use per (group, segment),
                               groups in order, segments in time order (copied); NULL = adaptive */
   int64_t n_replay;        /* number of entries in replay_m (must equal the segment total) */
-  int32_t max_width;       /* cap on supernode width (0 = 128) */
+  int32_t max_width;       /* cap on supernode width (0 = 1024) */
   int32_t strict;          /* 1: return MATEX_ERR_NOCONV when m_max is reached unconverged */
 } matex_opts;
 

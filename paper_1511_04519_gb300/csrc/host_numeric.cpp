@@ -13,10 +13,8 @@ std::string numeric_ldlt(const CsrSym& A, const double* dshift, double alpha,
                          const Symbolic& S, Numeric& F) {
   const int64_t n = S.n;
   F.dinv.assign(n, 0.0);
-  F.diag_cm.assign(S.diag_off[S.nsup], 0.0);
-  F.diag_rm.assign(S.diag_off[S.nsup], 0.0);
-  F.offd_cm.assign(S.offd_off[S.nsup], 0.0);
-  F.offd_rm.assign(S.offd_off[S.nsup], 0.0);
+  F.pan_cm.assign(S.pan_off[S.nsup], 0.0);
+  F.pan_rm.assign(S.pan_off[S.nsup], 0.0);
   std::vector<int32_t> pos(n, -1);
   std::vector<std::vector<double>> upd(S.nsup);
   std::vector<std::vector<int32_t>> kids(S.nsup);
@@ -75,22 +73,24 @@ std::string numeric_ldlt(const CsrSym& A, const double* dshift, double alpha,
       for (int64_t k = j + 1; k < nr; ++k) cj[k] = lcol[k];
       F.dinv[f + j] = di;
     }
-    // store the panels (strictly lower diagonal block, off-diagonal block)
-    double* dcm = &F.diag_cm[S.diag_off[s]];
-    double* drm = &F.diag_rm[S.diag_off[s]];
-    double* ocm = &F.offd_cm[S.offd_off[s]];
-    double* orm = &F.offd_rm[S.offd_off[s]];
-    for (int64_t j = 0; j < w; ++j) {
-      const double* cj = &front[j * nr];
-      for (int64_t i = j + 1; i < w; ++i) {
-        dcm[i + j * w] = cj[i];
-        drm[i * w + j] = cj[i];
-      }
-      for (int64_t i = 0; i < r; ++i) {
-        ocm[i + j * r] = cj[w + i];
-        orm[i * w + j] = cj[w + i];
+    // solve panel P = [L_ss^{-1}; L_Rs L_ss^{-1}]: column k of L_ss^{-1} by
+    // forward substitution on e_k, then column k of L_Rs L_ss^{-1}
+    double* pcm = &F.pan_cm[S.pan_off[s]];
+    double* prm = &F.pan_rm[S.pan_off[s]];
+    const int64_t ld = w + r;
+    for (int64_t k = 0; k < w; ++k) {
+      double* x = &pcm[k * ld];  // x[0..w) = L_ss^{-1} e_k, x[w..w+r) = L_Rs x[0..w)
+      x[k] = 1.0;
+      for (int64_t j = k; j < w; ++j) {
+        const double xj = x[j];
+        if (xj == 0.0) continue;
+        const double* cj = &front[j * nr];
+        for (int64_t i = j + 1; i < w; ++i) x[i] -= cj[i] * xj;
+        for (int64_t i = 0; i < r; ++i) x[w + i] += cj[w + i] * xj;
       }
     }
+    for (int64_t k = 0; k < w; ++k)
+      for (int64_t i = 0; i < ld; ++i) prm[i * w + k] = pcm[k * ld + i];
     // Schur complement handed to the parent
     if (r > 0 && S.sup_parent[s] >= 0) {
       std::vector<double>& U = upd[s];

@@ -28,21 +28,22 @@ struct Symbolic {
   std::vector<int64_t> sup_rowptr;  // nsup+1
   std::vector<int32_t> sup_rows;
   std::vector<int32_t> sup_parent;  // -1 for roots
-  std::vector<int64_t> diag_off;    // nsup+1, offsets of w*w diagonal blocks
-  std::vector<int64_t> offd_off;    // nsup+1, offsets of r*w off-diagonal blocks
+  std::vector<int64_t> pan_off;     // nsup+1, offsets of the (w+r) x w solve panels
   std::vector<int32_t> level_ptr;   // levels of the supernodal tree, leaves first
   std::vector<int32_t> level_sups;
   int64_t nnz_L = 0;                // strictly lower nonzeros of L (dense panels)
   double flops_factor = 0.0;
 };
 
-// Unit-lower L and D of M = L D L^T on the symbolic structure.  Each block is
-// stored twice: column-major (used by the forward solve) and row-major (used
-// by the backward solve), so that both read it with unit stride.
+// M = L D L^T on the symbolic structure (L unit lower).  What the solves read
+// per supernode s is the panel P_s = [L_ss^{-1}; L_Rs L_ss^{-1}] ((w+r) x w):
+//   forward   y_s = L_ss^{-1} b_s and b_R -= L_Rs y_s  are  P_s b_s,
+//   backward  x_s = L_ss^{-T} (D_s^{-1} y_s - L_Rs^T x_R)  is  P_s^T [D_s^{-1} y_s; -x_R],
+// so neither direction has a sequential step inside a supernode.  P_s is
+// stored column-major (forward reads) and row-major (backward reads).
 struct Numeric {
   std::vector<double> dinv;         // n, 1/D in new numbering
-  std::vector<double> diag_cm, diag_rm;
-  std::vector<double> offd_cm, offd_rm;
+  std::vector<double> pan_cm, pan_rm;
 };
 
 // Host setup (host_symbolic.cpp / host_numeric.cpp).  Both return an empty

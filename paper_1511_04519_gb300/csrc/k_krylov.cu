@@ -439,6 +439,11 @@ coef_kernel(SmallState ss, RoundCols rc, double gamma, double dt_out, double* __
   SmallShared& sh = *reinterpret_cast<SmallShared*>(smem_raw);
   const int q = blockIdx.x;
   const int m = ss.m[q];
+  const int no = rc.nout[q];
+  double* cq = coef + (int64_t)q * ldo * kCoefLd;
+  // step of the -P term at every output: h = t_o - l_j with t_o = o * dt_out
+  for (int o = threadIdx.x; o < no; o += blockDim.x)
+    cq[(int64_t)o * kCoefLd + kMaxM] = (double)(rc.obeg[q] + o) * dt_out - rc.l0[q];
   if (m <= 0) return;
   const double* Ht = ss.Ht + (int64_t)q * kMaxB * kMaxM;
   const double beta = ss.beta[q];
@@ -446,12 +451,10 @@ coef_kernel(SmallState ss, RoundCols rc, double gamma, double dt_out, double* __
   // segment end
   expm_dev(sh.H, rc.len[q], sh.E, m, sh.w);
   for (int i = threadIdx.x; i < m; i += blockDim.x) yend[(int64_t)q * kMaxM + i] = beta * sh.E[i * kLd];
-  const int no = rc.nout[q];
   if (no <= 0) return;
   __syncthreads();
   // first output, then the propagator e^{dt H} for the equally spaced rest
   expm_dev(sh.H, rc.hfirst[q], sh.E, m, sh.w);
-  double* cq = coef + (int64_t)q * ldo * kMaxM;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     sh.y[i] = beta * sh.E[i * kLd];
     cq[i] = sh.y[i];
@@ -464,7 +467,7 @@ coef_kernel(SmallState ss, RoundCols rc, double gamma, double dt_out, double* __
       double s = 0.0;
       for (int k = 0; k < m; ++k) s = fma(sh.E[i * kLd + k], sh.y[k], s);
       sh.y2[i] = s;
-      cq[(int64_t)o * kMaxM + i] = s;
+      cq[(int64_t)o * kCoefLd + i] = s;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < m; i += blockDim.x) sh.y[i] = sh.y2[i];

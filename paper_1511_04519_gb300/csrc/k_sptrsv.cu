@@ -3,13 +3,18 @@
 // w = U \ (L \ (X2 v_j)); here X1 = C + gamma G or G, both SPD, so U = D L^T).
 //
 // Layout: the right-hand sides live node-major in Y[n][ldy] (permuted node
-// order), so the K columns of one row are contiguous.  A task is one
-// (supernode, column block) pair; one launch covers one level of the
-// supernodal elimination tree.
-//   forward : y_s = L_ss^{-1} b_s  (unit lower, dense, in shared memory);
-//             b_R -= L_Rs y_s pushed to the ancestors' rows with FP64 atomics.
-//   backward: x_s = L_ss^{-T} (D_s^{-1} y_s - L_Rs^T x_R), pulling the final
-//             x_R of the ancestors (already solved one level up).
+// order), so the K columns of one row are contiguous.  The forward result y
+// goes to a second buffer Y2 of the same shape, because the tasks of one
+// supernode read b_s while their siblings write y_s; the backward reads y_s
+// from Y2 and writes x into Y.  Each supernode s
+// carries the panel P_s = [L_ss^{-1}; L_Rs L_ss^{-1}] built at setup, which
+// turns both substitutions inside a supernode into dense products:
+//   forward : [y_s; u_R] = P_s b_s, then b_R -= u_R (FP64 atomics into the
+//             ancestors' rows, which a later level reads);
+//   backward: x_s = P_s^T [D_s^{-1} y_s; -x_R], pulling the ancestors' final
+//             x_R (solved one level up).
+// One launch covers one level of the supernodal elimination tree; a task is
+// (supernode, 32 panel rows or columns) x (column block of KB right-hand sides).
 #include "kernels.h"
 
 namespace matex {
@@ -18,106 +23,110 @@ namespace {
 
 constexpr int kSolveThreads = 128;
 
+// S threads share one dot product when a task has fewer outputs than threads.
+template <int KB>
+struct SolveShape {
+  static constexpr int S = (kRowBlock * KB >= kSolveThreads) ? 1 : kSolveThreads / (kRowBlock * KB);
+};
+
 template <int KB>
 __global__ void __launch_bounds__(kSolveThreads)
-fwd_level_kernel(DevFactor F, const int32_t* __restrict__ sups, int ncb, double* __restrict__ Y,
-                 int ldy) {
-  extern __shared__ double sb[];  // [w][KB]
-  const int t = blockIdx.x;
-  const int s = sups[t / ncb];
-  const int c0 = (t % ncb) * KB;
+fwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* __restrict__ Y,
+                 double* __restrict__ Y2, int ldy) {
+  extern __shared__ double sb[];  // b_s as [w][KB]
+  constexpr int S = SolveShape<KB>::S;
+  const int2 tk = tasks[blockIdx.x / ncb];
+  const int c0 = (blockIdx.x % ncb) * KB;
+  const int s = tk.x, i0 = tk.y;
   const int f = F.sup_first[s];
   const int w = F.sup_first[s + 1] - f;
   const int64_t rp = F.sup_rowptr[s];
-  const int r = (int)(F.sup_rowptr[s + 1] - rp) - w;
+  const int ld = (int)(F.sup_rowptr[s + 1] - rp);  // w + r
   for (int e = threadIdx.x; e < w * KB; e += blockDim.x) {
-    const int i = e / KB, q = e - i * KB;
-    sb[e] = Y[(int64_t)(f + i) * ldy + c0 + q];
+    const int j = e / KB, q = e - j * KB;
+    sb[e] = Y[(int64_t)(f + j) * ldy + c0 + q];
   }
   __syncthreads();
-  const double* __restrict__ Lc = F.diag_cm + F.diag_off[s];
-  for (int j = 0; j < w - 1; ++j) {
-    const int cnt = (w - 1 - j) * KB;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const int ii = e / KB, q = e - ii * KB;
-      const int i = j + 1 + ii;
-      sb[i * KB + q] -= Lc[i + j * w] * sb[j * KB + q];
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < w * KB; e += blockDim.x) {
-    const int i = e / KB, q = e - i * KB;
-    Y[(int64_t)(f + i) * ldy + c0 + q] = sb[e];
-  }
-  if (r == 0) return;
-  const double* __restrict__ Oc = F.offd_cm + F.offd_off[s];
-  const int32_t* __restrict__ rows = F.sup_rows + rp + w;
-  for (int e = threadIdx.x; e < r * KB; e += blockDim.x) {
-    const int q = e / r, i = e - q * r;
+  const double* __restrict__ P = F.pan_cm + F.pan_off[s];
+  const int32_t* __restrict__ rows = F.sup_rows + rp;
+  const int sub = threadIdx.x % S;
+  for (int o = threadIdx.x / S; o < kRowBlock * KB; o += kSolveThreads / S) {
+    const int i = i0 + (o % kRowBlock), q = o / kRowBlock;
     double acc = 0.0;
-    for (int j = 0; j < w; ++j) acc = fma(Oc[i + (int64_t)j * r], sb[j * KB + q], acc);
-    atomicAdd(&Y[(int64_t)rows[i] * ldy + c0 + q], -acc);
+    if (i < ld)
+      for (int j = sub; j < w; j += S) acc = fma(P[(int64_t)j * ld + i], sb[j * KB + q], acc);
+    if (S > 1) {
+#pragma unroll
+      for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, S);
+    }
+    if (sub == 0 && i < ld) {
+      if (i < w)
+        Y2[(int64_t)(f + i) * ldy + c0 + q] = acc;
+      else
+        atomicAdd(&Y[(int64_t)rows[i] * ldy + c0 + q], -acc);
+    }
   }
 }
 
 template <int KB>
 __global__ void __launch_bounds__(kSolveThreads)
-bwd_level_kernel(DevFactor F, const int32_t* __restrict__ sups, int ncb, double* __restrict__ Y,
-                 int ldy) {
-  extern __shared__ double sb[];  // [w][KB]
-  const int t = blockIdx.x;
-  const int s = sups[t / ncb];
-  const int c0 = (t % ncb) * KB;
+bwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* __restrict__ Y,
+                 const double* __restrict__ Y2, int ldy) {
+  extern __shared__ double ub[];  // [D_s^{-1} y_s; -x_R] as [w+r][KB]
+  constexpr int S = SolveShape<KB>::S;
+  const int2 tk = tasks[blockIdx.x / ncb];
+  const int c0 = (blockIdx.x % ncb) * KB;
+  const int s = tk.x, j0 = tk.y;
   const int f = F.sup_first[s];
   const int w = F.sup_first[s + 1] - f;
   const int64_t rp = F.sup_rowptr[s];
-  const int r = (int)(F.sup_rowptr[s + 1] - rp) - w;
-  const double* __restrict__ Or = F.offd_rm + F.offd_off[s];
-  const int32_t* __restrict__ rows = F.sup_rows + rp + w;
-  for (int e = threadIdx.x; e < w * KB; e += blockDim.x) {
-    const int q = e / w, j = e - q * w;
-    double acc = Y[(int64_t)(f + j) * ldy + c0 + q] * F.dinv[f + j];
-    for (int i = 0; i < r; ++i)
-      acc = fma(-Or[(int64_t)i * w + j], Y[(int64_t)rows[i] * ldy + c0 + q], acc);
-    sb[j * KB + q] = acc;
+  const int ld = (int)(F.sup_rowptr[s + 1] - rp);
+  const int32_t* __restrict__ rows = F.sup_rows + rp;
+  for (int e = threadIdx.x; e < ld * KB; e += blockDim.x) {
+    const int i = e / KB, q = e - i * KB;
+    ub[e] = i < w ? Y2[(int64_t)(f + i) * ldy + c0 + q] * F.dinv[f + i]
+                  : -Y[(int64_t)rows[i] * ldy + c0 + q];
   }
   __syncthreads();
-  const double* __restrict__ Lr = F.diag_rm + F.diag_off[s];
-  for (int j = w - 1; j > 0; --j) {
-    const int cnt = j * KB;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const int i = e / KB, q = e - i * KB;
-      sb[i * KB + q] -= Lr[j * w + i] * sb[j * KB + q];
+  const double* __restrict__ P = F.pan_rm + F.pan_off[s];
+  const int sub = threadIdx.x % S;
+  for (int o = threadIdx.x / S; o < kRowBlock * KB; o += kSolveThreads / S) {
+    const int j = j0 + (o % kRowBlock), q = o / kRowBlock;
+    double acc = 0.0;
+    if (j < w)
+      for (int i = sub; i < ld; i += S) acc = fma(P[(int64_t)i * w + j], ub[i * KB + q], acc);
+    if (S > 1) {
+#pragma unroll
+      for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, S);
     }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < w * KB; e += blockDim.x) {
-    const int i = e / KB, q = e - i * KB;
-    Y[(int64_t)(f + i) * ldy + c0 + q] = sb[e];
+    if (sub == 0 && j < w) Y[(int64_t)(f + j) * ldy + c0 + q] = acc;
   }
 }
 
 template <int KB>
-void launch_level(bool fwd, const DevFactor& F, const LevelPlan& L, double* Y, int ldy, int ncols,
-                  cudaStream_t st) {
+void launch_level(bool fwd, const DevFactor& F, const LevelPlan& L, double* Y, double* Y2, int ldy,
+                  int ncols, cudaStream_t st) {
   const int ncb = (ncols + KB - 1) / KB;
-  const size_t smem = (size_t)L.max_w * KB * sizeof(double);
-  dim3 grid((unsigned)(L.count * ncb));
-  if (fwd)
-    fwd_level_kernel<KB><<<grid, kSolveThreads, smem, st>>>(F, L.sups, ncb, Y, ldy);
-  else
-    bwd_level_kernel<KB><<<grid, kSolveThreads, smem, st>>>(F, L.sups, ncb, Y, ldy);
+  if (fwd) {
+    const size_t smem = (size_t)L.max_w * KB * sizeof(double);
+    fwd_level_kernel<KB><<<(unsigned)(L.nf * ncb), kSolveThreads, smem, st>>>(F, L.ftasks, ncb, Y, Y2,
+                                                                             ldy);
+  } else {
+    const size_t smem = (size_t)L.max_wr * KB * sizeof(double);
+    bwd_level_kernel<KB><<<(unsigned)(L.nb * ncb), kSolveThreads, smem, st>>>(F, L.btasks, ncb, Y, Y2,
+                                                                             ldy);
+  }
 }
 
-void run_level(bool fwd, const DevFactor& F, const LevelPlan& L, double* Y, int ldy, int ncols,
-               cudaStream_t st) {
+void run_level(bool fwd, const DevFactor& F, const LevelPlan& L, double* Y, double* Y2, int ldy,
+               int ncols, cudaStream_t st) {
   int kb = L.kb;
   while (kb > 1 && kb / 2 >= ncols) kb /= 2;
   switch (kb) {
-    case 1: launch_level<1>(fwd, F, L, Y, ldy, ncols, st); break;
-    case 2: launch_level<2>(fwd, F, L, Y, ldy, ncols, st); break;
-    case 4: launch_level<4>(fwd, F, L, Y, ldy, ncols, st); break;
-    default: launch_level<8>(fwd, F, L, Y, ldy, ncols, st); break;
+    case 1: launch_level<1>(fwd, F, L, Y, Y2, ldy, ncols, st); break;
+    case 2: launch_level<2>(fwd, F, L, Y, Y2, ldy, ncols, st); break;
+    case 4: launch_level<4>(fwd, F, L, Y, Y2, ldy, ncols, st); break;
+    default: launch_level<8>(fwd, F, L, Y, Y2, ldy, ncols, st); break;
   }
 }
 
@@ -174,11 +183,22 @@ __global__ void scatter_cols_kernel(const double* __restrict__ Y, int ldy, int n
 
 }  // namespace
 
-int solve_inplace(const DevFactor& F, const LevelPlan* levels, int nlev, double* Y, int ldy,
-                  int ncols, cudaStream_t st) {
+void set_solve_smem_limit(int bytes) {
+  cudaFuncSetAttribute(fwd_level_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(fwd_level_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(fwd_level_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(fwd_level_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(bwd_level_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(bwd_level_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(bwd_level_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(bwd_level_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+int solve_inplace(const DevFactor& F, const LevelPlan* levels, int nlev, double* Y, double* Y2,
+                  int ldy, int ncols, cudaStream_t st) {
   if (ncols <= 0) return 0;
-  for (int l = 0; l < nlev; ++l) run_level(true, F, levels[l], Y, ldy, ncols, st);
-  for (int l = nlev - 1; l >= 0; --l) run_level(false, F, levels[l], Y, ldy, ncols, st);
+  for (int l = 0; l < nlev; ++l) run_level(true, F, levels[l], Y, Y2, ldy, ncols, st);
+  for (int l = nlev - 1; l >= 0; --l) run_level(false, F, levels[l], Y, Y2, ldy, ncols, st);
   return 2 * nlev;
 }
 

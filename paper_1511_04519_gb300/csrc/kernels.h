@@ -7,34 +7,42 @@ namespace matex {
 
 constexpr int kMaxM = 20;      // largest Krylov dimension
 constexpr int kMaxB = kMaxM + 1;
+// coefficient row per (column, output): y_0..y_{m-1} in slots 0..m-1 and the
+// step h = t_o - l_j of the -P term in slot kMaxM
+constexpr int kCoefLd = kMaxM + 1;
 
-// Device view of one factor (unit-lower L, D^{-1}) on the shared structure.
+// Device view of one factor on the shared structure: D^{-1} and the solve
+// panels P_s = [L_ss^{-1}; L_Rs L_ss^{-1}] ((w+r) x w), column- and row-major.
 struct DevFactor {
   const int32_t* sup_first;
   const int64_t* sup_rowptr;
   const int32_t* sup_rows;
-  const int64_t* diag_off;
-  const int64_t* offd_off;
+  const int64_t* pan_off;
   const double* dinv;
-  const double* diag_cm;
-  const double* diag_rm;
-  const double* offd_cm;
-  const double* offd_rm;
+  const double* pan_cm;
+  const double* pan_rm;
 };
 
-// One tree level of the supernodal solve: the supernodes of the level and
-// the column block used for them.
+constexpr int kRowBlock = 32;  // panel rows (forward) / columns (backward) per task
+
+// One tree level of the supernodal solve.  A task is (supernode, block of 32
+// panel rows) in the forward direction and (supernode, block of 32 panel
+// columns) in the backward one; each task runs once per column block.
 struct LevelPlan {
-  const int32_t* sups;   // device, supernode ids of this level
-  int32_t count;
+  const int2* ftasks;    // device, {supernode, first panel row}
+  const int2* btasks;    // device, {supernode, first panel column}
+  int32_t nf, nb;
   int32_t max_w;         // widest supernode in the level
+  int32_t max_wr;        // largest w + r in the level
   int32_t kb;            // column block: 1, 2, 4 or 8
 };
+void set_solve_smem_limit(int bytes);
 
-// Y is node-major [n][ldy] (ldy >= ncols, multiple of 8); solves in place.
+// Y is node-major [n][ldy] (ldy >= ncols, multiple of 8); solves in place,
+// using Y2 (same shape) for the intermediate forward result.
 // Returns the number of kernels launched.
-int solve_inplace(const DevFactor& F, const LevelPlan* levels, int nlev, double* Y, int ldy,
-                  int ncols, cudaStream_t st);
+int solve_inplace(const DevFactor& F, const LevelPlan* levels, int nlev, double* Y, double* Y2,
+                  int ldy, int ncols, cudaStream_t st);
 
 // Y[i][q] = (scale ? scale[i] : 1) * src[cols[q]*stride + rowmap[i]]
 // (cols == null: q; rowmap == null: i)
@@ -118,7 +126,7 @@ void residual_check(SmallState ss, const RoundCols& rc, int K, int j, double gam
 void record_segments(const SmallState& ss, const RoundCols& rc, int K, int32_t* m_rec,
                      int32_t* st_rec, cudaStream_t st);
 // coefficient vectors beta e^{h H} e_1 for every output of the segment and
-// for the segment end; coef [K][ldo][kMaxM], yend [K][kMaxM]
+// for the segment end; coef [K][ldo][kCoefLd] (slot kMaxM holds h), yend [K][kMaxM]
 void output_coefficients(SmallState ss, const RoundCols& rc, int K, double gamma, double dt_out,
                          double* coef, int ldo, double* yend, cudaStream_t st);
 size_t small_shared_bytes();

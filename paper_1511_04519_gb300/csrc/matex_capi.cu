@@ -86,6 +86,7 @@ struct matex_ctx {
   int Kmax = 1;
   int nchunks = 1;
   double* Y = nullptr;
+  double* Y2 = nullptr;     // forward-solve intermediate, same shape as Y
   double* Vb = nullptr;     // [n_groups][kMaxB][n]
   double *Zb = nullptr, *Zpb = nullptr, *Wb = nullptr, *Xb = nullptr;  // [n_groups][n]
   double* Xp = nullptr;     // [n_times][n]
@@ -169,31 +170,61 @@ std::vector<double> group_lts(const std::vector<int32_t>& srcs, const int32_t* p
   return pts;
 }
 
-void plan_levels(matex_ctx* c, const int32_t* level_sups_d) {
+// Per tree level: forward tasks (supernode, 32 panel rows), backward tasks
+// (supernode, 32 panel columns) and the column block.  Returns false on an
+// allocation failure.
+constexpr int kSolveSmemCap = 160 * 1024;
+
+bool plan_levels(matex_ctx* c) {
   const Symbolic& S = c->S;
   const int nlev = (int)S.level_ptr.size() - 1;
   c->levels.resize(nlev);
+  std::vector<int2> ft, bt;
+  std::vector<size_t> fofs(nlev + 1), bofs(nlev + 1);
+  int smem_need = 0;
   for (int l = 0; l < nlev; ++l) {
     LevelPlan& L = c->levels[l];
-    L.sups = level_sups_d + S.level_ptr[l];
-    L.count = S.level_ptr[l + 1] - S.level_ptr[l];
-    int mw = 1;
+    fofs[l] = ft.size();
+    bofs[l] = bt.size();
+    int mw = 1, mwr = 1;
     for (int k = S.level_ptr[l]; k < S.level_ptr[l + 1]; ++k) {
-      int s = S.level_sups[k];
-      mw = std::max(mw, S.sup_first[s + 1] - S.sup_first[s]);
+      const int s = S.level_sups[k];
+      const int w = S.sup_first[s + 1] - S.sup_first[s];
+      const int wr = (int)(S.sup_rowptr[s + 1] - S.sup_rowptr[s]);
+      mw = std::max(mw, w);
+      mwr = std::max(mwr, wr);
+      for (int i0 = 0; i0 < wr; i0 += kRowBlock) ft.push_back(make_int2(s, i0));
+      for (int j0 = 0; j0 < w; j0 += kRowBlock) bt.push_back(make_int2(s, j0));
     }
+    L.nf = (int32_t)(ft.size() - fofs[l]);
+    L.nb = (int32_t)(bt.size() - bofs[l]);
     L.max_w = mw;
+    L.max_wr = mwr;
     int kb = c->opts.col_block;
     if (kb <= 0) {
-      // enough (supernode, column block) tasks to fill the GPU, else narrower blocks
-      kb = L.count >= 256 ? 8 : L.count >= 64 ? 4 : L.count >= 16 ? 2 : 1;
+      // enough (task, column block) pairs to fill 152 SMs, else narrower blocks
+      const int tasks = std::min(L.nf, L.nb * 4);
+      kb = tasks >= 1024 ? 8 : tasks >= 256 ? 4 : tasks >= 64 ? 2 : 1;
     }
+    while (kb > 1 && (size_t)mwr * kb * sizeof(double) > (size_t)kSolveSmemCap) kb /= 2;
     L.kb = kb;
+    smem_need = std::max(smem_need, (int)(mwr * kb * sizeof(double)));
   }
+  fofs[nlev] = ft.size();
+  bofs[nlev] = bt.size();
+  int2 *fd, *bd;
+  if (!c->upload(fd, ft.data(), ft.size()) || !c->upload(bd, bt.data(), bt.size())) return false;
+  for (int l = 0; l < nlev; ++l) {
+    c->levels[l].ftasks = fd + fofs[l];
+    c->levels[l].btasks = bd + bofs[l];
+  }
+  set_solve_smem_limit(std::max(smem_need, 48 * 1024));
+  return true;
 }
 
 int solve_cols(matex_ctx* c, const DevFactor& F, int ncols) {
-  return solve_inplace(F, c->levels.data(), (int)c->levels.size(), c->Y, c->ldy, ncols, c->st);
+  return solve_inplace(F, c->levels.data(), (int)c->levels.size(), c->Y, c->Y2, c->ldy, ncols,
+                       c->st);
 }
 
 RoundCols round_cols(matex_ctx* c, const Round& r) {
@@ -267,11 +298,15 @@ void prof_collect(matex_ctx* c, const std::vector<int32_t>& m_seg) {
   c->ev_used = 0;
 }
 
+// Algorithmic work of one batched solve pair with K right-hand sides: a
+// multiply-add per stored panel entry and column in each direction, the
+// D^{-1} scaling; bytes: each panel read once per direction, D^{-1}, the row
+// lists, and the right-hand sides read and written once per direction.
 double solve_flops(const matex_ctx* c, int K) {
-  return (4.0 * (double)c->S.nnz_L + (double)c->n) * K;
+  return (4.0 * (double)c->S.pan_off[c->S.nsup] + (double)c->n) * K;
 }
 double solve_bytes(const matex_ctx* c, int K) {
-  return 16.0 * (double)c->S.nnz_L + 8.0 * c->n + 8.0 * (double)c->offd_rows +
+  return 16.0 * (double)c->S.pan_off[c->S.nsup] + 8.0 * c->n + 8.0 * (double)c->S.sup_rowptr[c->S.nsup] +
          32.0 * (double)c->n * K;
 }
 
@@ -469,7 +504,7 @@ void matex_default_opts(matex_opts* o) {
   o->col_block = 0;
   o->group_select = -1;
   o->include_dc = 1;
-  o->max_width = 128;
+  o->max_width = 1024;
 }
 
 const char* matex_status_string(matex_status s) {
@@ -552,7 +587,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   matex_opts o;
   matex_default_opts(&o);
   if (opts) o = *opts;
-  if (o.max_width <= 0) o.max_width = 128;
+  if (o.max_width <= 0) o.max_width = 1024;
   if (o.col_block != 0 && o.col_block != 1 && o.col_block != 2 && o.col_block != 4 && o.col_block != 8)
     return bad("col_block must be 0, 1, 2, 4 or 8");
   if (o.group_select >= n_groups) return bad("group_select out of range");
@@ -708,22 +743,18 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   t = now_ms();
   bool ok = true;
   const Symbolic& S = c->S;
-  int32_t *sup_first, *sup_rows, *level_sups;
-  int64_t *sup_rowptr, *diag_off, *offd_off;
+  int32_t *sup_first, *sup_rows;
+  int64_t *sup_rowptr, *pan_off;
   ok = ok && c->upload(sup_first, S.sup_first.data(), S.sup_first.size());
   ok = ok && c->upload(sup_rowptr, S.sup_rowptr.data(), S.sup_rowptr.size());
   ok = ok && c->upload(sup_rows, S.sup_rows.data(), S.sup_rows.size());
-  ok = ok && c->upload(diag_off, S.diag_off.data(), S.diag_off.size());
-  ok = ok && c->upload(offd_off, S.offd_off.data(), S.offd_off.size());
-  ok = ok && c->upload(level_sups, S.level_sups.data(), S.level_sups.size());
+  ok = ok && c->upload(pan_off, S.pan_off.data(), S.pan_off.size());
   auto up_factor = [&](const Numeric& Nm, DevFactor& F) {
-    double *dinv, *dcm, *drm, *ocm, *orm;
+    double *dinv, *pcm, *prm;
     bool k = c->upload(dinv, Nm.dinv.data(), Nm.dinv.size()) &&
-             c->upload(dcm, Nm.diag_cm.data(), Nm.diag_cm.size()) &&
-             c->upload(drm, Nm.diag_rm.data(), Nm.diag_rm.size()) &&
-             c->upload(ocm, Nm.offd_cm.data(), Nm.offd_cm.size()) &&
-             c->upload(orm, Nm.offd_rm.data(), Nm.offd_rm.size());
-    F = DevFactor{sup_first, sup_rowptr, sup_rows, diag_off, offd_off, dinv, dcm, drm, ocm, orm};
+             c->upload(pcm, Nm.pan_cm.data(), Nm.pan_cm.size()) &&
+             c->upload(prm, Nm.pan_rm.data(), Nm.pan_rm.size());
+    F = DevFactor{sup_first, sup_rowptr, sup_rows, pan_off, dinv, pcm, prm};
     return k;
   };
   ok = ok && up_factor(NM, c->fM) && up_factor(NG, c->fG);
@@ -771,12 +802,12 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
        c->upload(c->rc_hfirst, h_hfirst.data(), h_hfirst.size()) &&
        c->upload(c->rc_segid, h_segid.data(), h_segid.size());
   if (!c->replay.empty()) ok = ok && c->upload(c->replay_d, c->replay.data(), c->replay.size());
-  plan_levels(c, level_sups);
+  ok = ok && plan_levels(c);
   // work buffers
   c->ldy = roundup8(std::max({2 * Kmax, 8, std::min<int>(n_groups, 256)}));
   c->nchunks = (int)((n + kChunk - 1) / kChunk);
   const size_t G = (size_t)std::max(n_groups, 1);
-  ok = ok && c->alloc(c->Y, (size_t)n * c->ldy) && c->alloc(c->Vb, G * kMaxB * n) &&
+  ok = ok && c->alloc(c->Y, (size_t)n * c->ldy) && c->alloc(c->Y2, (size_t)n * c->ldy) && c->alloc(c->Vb, G * kMaxB * n) &&
        c->alloc(c->Zb, G * n) && c->alloc(c->Zpb, G * n) && c->alloc(c->Wb, G * n) &&
        c->alloc(c->Xb, G * n) && c->alloc(c->Xp, (size_t)c->n_times * n) && c->alloc(c->xdc, n) &&
        c->alloc(c->partials, (size_t)Kmax * kMaxB * c->nchunks) &&
@@ -784,7 +815,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
        c->alloc(c->ss.m, Kmax) && c->alloc(c->ss.status, Kmax) &&
        c->alloc(c->ss.hbuf, (size_t)Kmax * kMaxB) && c->alloc(c->ss.scale, Kmax) &&
        c->alloc(c->iterA, Kmax) && c->alloc(c->iterB, Kmax) && c->alloc(c->iter_grp, Kmax) &&
-       c->alloc(c->d_count, 1) && c->alloc(c->coef, (size_t)Kmax * c->n_times * kMaxM) &&
+       c->alloc(c->d_count, 1) && c->alloc(c->coef, (size_t)Kmax * c->n_times * kCoefLd) &&
        c->alloc(c->yend, (size_t)Kmax * kMaxM) && c->alloc(c->m_rec, std::max<int64_t>(1, c->n_segments)) &&
        c->alloc(c->st_rec, std::max<int64_t>(1, c->n_segments));
   if (ok && cudaMallocHost(&c->h_count, sizeof(int32_t)) != cudaSuccess) ok = false;
@@ -945,41 +976,39 @@ extern "C" matex_status matex_host_factor_solve(int64_t n, const int64_t* rowptr
     info[2] = (int64_t)S.level_ptr.size() - 1;
     info[3] = maxw;
   }
-  std::vector<double> y(n);
+  std::vector<double> y(n), tmp;
   for (int32_t q = 0; q < ncols; ++q) {
     for (int64_t k = 0; k < n; ++k) y[k] = b[(int64_t)q * n + S.perm[k]];
-    // forward, supernodes in level order (as the GPU launches them)
+    // forward, supernodes in level order (as the GPU launches them): P_s b_s
     for (size_t li = 0; li < S.level_sups.size(); ++li) {
       const int32_t s = S.level_sups[li];
       const int32_t f = S.sup_first[s], w = S.sup_first[s + 1] - f;
       const int64_t rp = S.sup_rowptr[s];
-      const int32_t r = (int32_t)(S.sup_rowptr[s + 1] - rp) - w;
-      const double* Lc = &F.diag_cm[S.diag_off[s]];
+      const int32_t ld = (int32_t)(S.sup_rowptr[s + 1] - rp);
+      const double* P = &F.pan_cm[S.pan_off[s]];
+      tmp.assign(ld, 0.0);
       for (int32_t j = 0; j < w; ++j)
-        for (int32_t i = j + 1; i < w; ++i) y[f + i] -= Lc[i + j * w] * y[f + j];
-      const double* Oc = &F.offd_cm[S.offd_off[s]];
-      for (int32_t i = 0; i < r; ++i) {
-        double acc = 0.0;
-        for (int32_t j = 0; j < w; ++j) acc += Oc[i + (int64_t)j * r] * y[f + j];
-        y[S.sup_rows[rp + w + i]] -= acc;
-      }
+        for (int32_t i = 0; i < ld; ++i) tmp[i] += P[(int64_t)j * ld + i] * y[f + j];
+      for (int32_t i = 0; i < w; ++i) y[f + i] = tmp[i];
+      for (int32_t i = w; i < ld; ++i) y[S.sup_rows[rp + i]] -= tmp[i];
     }
+    // backward, reverse level order: P_s^T [D^{-1} y_s; -x_R]
     for (size_t li = S.level_sups.size(); li-- > 0;) {
       const int32_t s = S.level_sups[li];
       const int32_t f = S.sup_first[s], w = S.sup_first[s + 1] - f;
       const int64_t rp = S.sup_rowptr[s];
-      const int32_t r = (int32_t)(S.sup_rowptr[s + 1] - rp) - w;
-      const double* Or = &F.offd_rm[S.offd_off[s]];
-      std::vector<double> sb(w);
-      for (int32_t j = 0; j < w; ++j) {
-        double acc = y[f + j] * F.dinv[f + j];
-        for (int32_t i = 0; i < r; ++i) acc -= Or[(int64_t)i * w + j] * y[S.sup_rows[rp + w + i]];
-        sb[j] = acc;
+      const int32_t ld = (int32_t)(S.sup_rowptr[s + 1] - rp);
+      const double* P = &F.pan_rm[S.pan_off[s]];
+      tmp.assign(ld, 0.0);
+      for (int32_t i = 0; i < ld; ++i) {
+        const double v = y[S.sup_rows[rp + i]];
+        tmp[i] = i < w ? v * F.dinv[f + i] : -v;
       }
-      const double* Lr = &F.diag_rm[S.diag_off[s]];
-      for (int32_t j = w - 1; j > 0; --j)
-        for (int32_t i = 0; i < j; ++i) sb[i] -= Lr[j * w + i] * sb[j];
-      for (int32_t j = 0; j < w; ++j) y[f + j] = sb[j];
+      for (int32_t j = 0; j < w; ++j) {
+        double acc = 0.0;
+        for (int32_t i = 0; i < ld; ++i) acc += P[(int64_t)i * w + j] * tmp[i];
+        y[f + j] = acc;
+      }
     }
     for (int64_t k = 0; k < n; ++k) x[(int64_t)q * n + S.perm[k]] = y[k];
   }

@@ -49,9 +49,10 @@ def compare_run(M, p, ref=None, fac=None, **kw):
     return err, X, ref, m_gpu, m_ref, sim.stats
 
 
+@pytest.mark.parametrize("width", [0, 16])
 @pytest.mark.parametrize("which", [0, 1])
 @pytest.mark.parametrize("case", ["small", "config0", "ragged3layer"])
-def test_solve_matches_sparse_direct(M, which, case):
+def test_solve_matches_sparse_direct(M, which, case, width):
     import torch
     import scipy.sparse as sp
     if case == "small":
@@ -60,7 +61,7 @@ def test_solve_matches_sparse_direct(M, which, case):
         p = gridgen.config0()
     else:
         p = gridgen.small_mesh(2, nx=37, ny=23, layers=3, n_src=3)
-    sim = M.Sim(p)
+    sim = M.Sim(p, max_width=width)
     rng = np.random.default_rng(3)
     for ncols in (1, 3, 8, 13):
         b = rng.standard_normal((ncols, p.n))
@@ -149,6 +150,18 @@ def test_column_blocks_agree(M, col_block):
     base = M.Sim(p, col_block=1).run().cpu().numpy()
     X = M.Sim(p, col_block=col_block).run().cpu().numpy()
     assert np.abs(X - base).max() <= 1e-13
+
+
+def test_one_group_at_a_time_matches_batched(M):
+    p = gridgen.small_mesh(12, nx=25, ny=20, layers=2, n_src=30, group_templates=[3, 1, 4, 1, 5, 6],
+                           t_end=0.4e-9)
+    sim = M.Sim(p)
+    Xb = sim.run().cpu().numpy()
+    mb = sim.m_sequence()
+    sim.one_group_at_a_time(True)
+    Xs = sim.run().cpu().numpy()
+    assert np.array_equal(sim.m_sequence(), mb)
+    assert np.abs(Xs - Xb).max() <= 1e-13
 
 
 def test_m_max_one_and_replay(M):
