@@ -16,28 +16,43 @@ constexpr int kOT = 16;  // output times per thread
 
 // One group's contribution to a thread's node over the tile's output times.
 // M is the group's Krylov dimension, so every FP64 instruction issued is
-// useful work: per (node, output) one FMA for h z' + acc, one add of (z - w),
-// and M FMAs for V y.  `full` (warp-uniform) skips the range tests when the
-// group's segment covers the whole tile.
+// useful work.  When the group's segment covers the whole tile (`full`,
+// warp-uniform), its -P term z + (t_o - l_j) z' - w = (z - w - l_j z') + t_o z'
+// is folded into two per-tile sums (a, zsum) applied once per output after all
+// groups, leaving M FMAs per (node, output, group); a partially covering
+// group adds its -P term per output.
 template <int M>
-__device__ __forceinline__ void group_tile(double (&acc)[kOT], const double* __restrict__ vcol,
-                                           int64_t n, double z, double zp, double w,
+__device__ __forceinline__ void group_tile(double (&acc)[kOT], double& asum, double& zsum,
+                                           const double* __restrict__ vcol, int64_t n, double z,
+                                           double zp, double w, double l0,
                                            const double* __restrict__ cq, int o0, int ob, int lo,
                                            int hi) {
   double v[M > 0 ? M : 1];
 #pragma unroll
   for (int j = 0; j < M; ++j) v[j] = vcol[(int64_t)j * n];
   const double zmw = z - w;
-  const bool full = lo == o0 && hi == o0 + kOT;
+  if (lo == o0 && hi == o0 + kOT) {
+    asum += fma(-l0, zp, zmw);
+    zsum += zp;
 #pragma unroll
-  for (int t = 0; t < kOT; ++t) {
-    const int o = o0 + t;
-    if (!full && (o < lo || o >= hi)) continue;
-    const double* __restrict__ y = cq + (int64_t)(o - ob) * kCoefLd;
-    double a = fma(y[kMaxM], zp, acc[t]) + zmw;
+    for (int t = 0; t < kOT; ++t) {
+      const double* __restrict__ y = cq + (int64_t)(o0 + t - ob) * kCoefLd;
+      double a = acc[t];
 #pragma unroll
-    for (int j = 0; j < M; ++j) a = fma(v[j], y[j], a);
-    acc[t] = a;
+      for (int j = 0; j < M; ++j) a = fma(v[j], y[j], a);
+      acc[t] = a;
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < kOT; ++t) {
+      const int o = o0 + t;
+      if (o < lo || o >= hi) continue;
+      const double* __restrict__ y = cq + (int64_t)(o - ob) * kCoefLd;
+      double a = fma(y[kMaxM], zp, acc[t]) + zmw;
+#pragma unroll
+      for (int j = 0; j < M; ++j) a = fma(v[j], y[j], a);
+      acc[t] = a;
+    }
   }
 }
 
@@ -46,26 +61,28 @@ recombine_kernel(double* __restrict__ Xp, int64_t n, const double* __restrict__ 
                  const double* __restrict__ Z, const double* __restrict__ Zp,
                  const double* __restrict__ W, int64_t gstride, RoundCols rc,
                  const int32_t* __restrict__ mcol, const double* __restrict__ coef, int ldo, int K,
-                 int obeg_min) {
+                 int obeg_min, double dt_out) {
   const int64_t i = (int64_t)blockIdx.x * kRecThreads + threadIdx.x;
   const int o0 = obeg_min + blockIdx.y * kOT;
   if (i >= n) return;
   double acc[kOT];
 #pragma unroll
   for (int t = 0; t < kOT; ++t) acc[t] = 0.0;
+  double asum = 0.0, zsum = 0.0;
   unsigned covered = 0;
   for (int q = 0; q < K; ++q) {
     const int ob = rc.obeg[q], no = rc.nout[q];
     const int lo = max(ob, o0), hi = min(ob + no, o0 + kOT);
     if (lo >= hi) continue;
-    covered |= ((hi - lo) == 32 ? 0xffffffffu : ((1u << (hi - lo)) - 1u)) << (lo - o0);
+    covered |= ((1u << (hi - lo)) - 1u) << (lo - o0);
     const int64_t g = rc.group[q];
     const double* __restrict__ vcol = Vb + g * vstride + i;
     const double z = Z[g * gstride + i], zp = Zp[g * gstride + i], w = W[g * gstride + i];
+    const double l0 = rc.l0[q];
     const double* __restrict__ cq = coef + (int64_t)q * ldo * kCoefLd;
     switch (mcol[q]) {
 #define MATEX_GT(MM) \
-  case MM: group_tile<MM>(acc, vcol, n, z, zp, w, cq, o0, ob, lo, hi); break;
+  case MM: group_tile<MM>(acc, asum, zsum, vcol, n, z, zp, w, l0, cq, o0, ob, lo, hi); break;
       MATEX_GT(0) MATEX_GT(1) MATEX_GT(2) MATEX_GT(3) MATEX_GT(4) MATEX_GT(5) MATEX_GT(6)
       MATEX_GT(7) MATEX_GT(8) MATEX_GT(9) MATEX_GT(10) MATEX_GT(11) MATEX_GT(12) MATEX_GT(13)
       MATEX_GT(14) MATEX_GT(15) MATEX_GT(16) MATEX_GT(17) MATEX_GT(18) MATEX_GT(19) MATEX_GT(20)
@@ -75,7 +92,10 @@ recombine_kernel(double* __restrict__ Xp, int64_t n, const double* __restrict__ 
   }
 #pragma unroll
   for (int t = 0; t < kOT; ++t)
-    if (covered & (1u << t)) Xp[(int64_t)(o0 + t) * n + i] += acc[t];
+    if (covered & (1u << t)) {
+      const double to = (double)(o0 + t) * dt_out;
+      Xp[(int64_t)(o0 + t) * n + i] += acc[t] + fma(to, zsum, asum);
+    }
 }
 
 __global__ void next_state_kernel(double* __restrict__ X, const double* __restrict__ Vb,
@@ -127,12 +147,11 @@ void recombine(double* Xp, int64_t n, int n_times, const double* Vbase, int64_t 
                const RoundCols& rc, const int32_t* mcol, const double* coef, int ldo, int K,
                int obeg_min, int oend_max, double dt_out, cudaStream_t st) {
   (void)n_times;
-  (void)dt_out;
   if (K <= 0 || oend_max <= obeg_min) return;
   dim3 grid((unsigned)((n + kRecThreads - 1) / kRecThreads),
             (unsigned)((oend_max - obeg_min + kOT - 1) / kOT));
   recombine_kernel<<<grid, kRecThreads, 0, st>>>(Xp, n, Vbase, vstride, Z, Zp, W, gstride, rc, mcol,
-                                                  coef, ldo, K, obeg_min);
+                                                  coef, ldo, K, obeg_min, dt_out);
 }
 
 void next_state(double* X, const double* Vbase, int64_t vstride, const double* Z, const double* Zp,

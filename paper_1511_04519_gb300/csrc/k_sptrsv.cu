@@ -14,7 +14,8 @@
 //   backward: x_s = P_s^T [D_s^{-1} y_s; -x_R], pulling the ancestors' final
 //             x_R (solved one level up).
 // One launch covers one level of the supernodal elimination tree; a task is
-// (supernode, 32 panel rows or columns) x (column block of KB right-hand sides).
+// (supernode, 32 panel rows or columns) x (column block of KB right-hand sides),
+// four threads per panel row/column, each thread holding all KB columns.
 #include "kernels.h"
 
 namespace matex {
@@ -22,19 +23,16 @@ namespace matex {
 namespace {
 
 constexpr int kSolveThreads = 128;
+constexpr int kSplit = kSolveThreads / kRowBlock;  // threads sharing one dot product
 
-// S threads share one dot product when a task has fewer outputs than threads.
-template <int KB>
-struct SolveShape {
-  static constexpr int S = (kRowBlock * KB >= kSolveThreads) ? 1 : kSolveThreads / (kRowBlock * KB);
-};
-
+// Forward task: rows [i0, i0+32) of P_s b_s for KB right-hand sides.  Thread
+// (row, sub) accumulates all KB columns of its row over panel columns
+// j = sub, sub+4, ..., so each panel entry is loaded once per task.
 template <int KB>
 __global__ void __launch_bounds__(kSolveThreads)
 fwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* __restrict__ Y,
                  double* __restrict__ Y2, int ldy) {
   extern __shared__ double sb[];  // b_s as [w][KB]
-  constexpr int S = SolveShape<KB>::S;
   const int2 tk = tasks[blockIdx.x / ncb];
   const int c0 = (blockIdx.x % ncb) * KB;
   const int s = tk.x, i0 = tk.y;
@@ -48,32 +46,42 @@ fwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* _
   }
   __syncthreads();
   const double* __restrict__ P = F.pan_cm + F.pan_off[s];
-  const int32_t* __restrict__ rows = F.sup_rows + rp;
-  const int sub = threadIdx.x % S;
-  for (int o = threadIdx.x / S; o < kRowBlock * KB; o += kSolveThreads / S) {
-    const int i = i0 + (o % kRowBlock), q = o / kRowBlock;
-    double acc = 0.0;
-    if (i < ld)
-      for (int j = sub; j < w; j += S) acc = fma(P[(int64_t)j * ld + i], sb[j * KB + q], acc);
-    if (S > 1) {
+  const int sub = threadIdx.x % kSplit;
+  const int i = i0 + threadIdx.x / kSplit;
+  double acc[KB];
 #pragma unroll
-      for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, S);
+  for (int q = 0; q < KB; ++q) acc[q] = 0.0;
+  if (i < ld) {
+    for (int j = sub; j < w; j += kSplit) {
+      const double p = P[(int64_t)j * ld + i];
+#pragma unroll
+      for (int q = 0; q < KB; ++q) acc[q] = fma(p, sb[j * KB + q], acc[q]);
     }
-    if (sub == 0 && i < ld) {
-      if (i < w)
-        Y2[(int64_t)(f + i) * ldy + c0 + q] = acc;
-      else
-        atomicAdd(&Y[(int64_t)rows[i] * ldy + c0 + q], -acc);
+  }
+#pragma unroll
+  for (int q = 0; q < KB; ++q)
+#pragma unroll
+    for (int off = kSplit / 2; off > 0; off >>= 1)
+      acc[q] += __shfl_down_sync(0xffffffffu, acc[q], off, kSplit);
+  if (sub == 0 && i < ld) {
+    if (i < w) {
+      double* __restrict__ dst = Y2 + (int64_t)(f + i) * ldy + c0;
+#pragma unroll
+      for (int q = 0; q < KB; ++q) dst[q] = acc[q];
+    } else {
+      double* __restrict__ dst = Y + (int64_t)F.sup_rows[rp + i] * ldy + c0;
+#pragma unroll
+      for (int q = 0; q < KB; ++q) atomicAdd(dst + q, -acc[q]);
     }
   }
 }
 
+// Backward task: panel columns [j0, j0+32) of P_s^T [D_s^{-1} y_s; -x_R].
 template <int KB>
 __global__ void __launch_bounds__(kSolveThreads)
 bwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* __restrict__ Y,
                  const double* __restrict__ Y2, int ldy) {
   extern __shared__ double ub[];  // [D_s^{-1} y_s; -x_R] as [w+r][KB]
-  constexpr int S = SolveShape<KB>::S;
   const int2 tk = tasks[blockIdx.x / ncb];
   const int c0 = (blockIdx.x % ncb) * KB;
   const int s = tk.x, j0 = tk.y;
@@ -89,17 +97,27 @@ bwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* _
   }
   __syncthreads();
   const double* __restrict__ P = F.pan_rm + F.pan_off[s];
-  const int sub = threadIdx.x % S;
-  for (int o = threadIdx.x / S; o < kRowBlock * KB; o += kSolveThreads / S) {
-    const int j = j0 + (o % kRowBlock), q = o / kRowBlock;
-    double acc = 0.0;
-    if (j < w)
-      for (int i = sub; i < ld; i += S) acc = fma(P[(int64_t)i * w + j], ub[i * KB + q], acc);
-    if (S > 1) {
+  const int sub = threadIdx.x % kSplit;
+  const int j = j0 + threadIdx.x / kSplit;
+  double acc[KB];
 #pragma unroll
-      for (int off = S / 2; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, S);
+  for (int q = 0; q < KB; ++q) acc[q] = 0.0;
+  if (j < w) {
+    for (int i = sub; i < ld; i += kSplit) {
+      const double p = P[(int64_t)i * w + j];
+#pragma unroll
+      for (int q = 0; q < KB; ++q) acc[q] = fma(p, ub[i * KB + q], acc[q]);
     }
-    if (sub == 0 && j < w) Y[(int64_t)(f + j) * ldy + c0 + q] = acc;
+  }
+#pragma unroll
+  for (int q = 0; q < KB; ++q)
+#pragma unroll
+    for (int off = kSplit / 2; off > 0; off >>= 1)
+      acc[q] += __shfl_down_sync(0xffffffffu, acc[q], off, kSplit);
+  if (sub == 0 && j < w) {
+    double* __restrict__ dst = Y + (int64_t)(f + j) * ldy + c0;
+#pragma unroll
+    for (int q = 0; q < KB; ++q) dst[q] = acc[q];
   }
 }
 
