@@ -167,6 +167,8 @@ def main():
     ap.add_argument("--cpu-groups", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serial", action="store_true")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="warm up, run one step inside cudaProfilerStart/Stop, print its stats")
     args = ap.parse_args()
     if args.cpu_oracle_sample:
         print(json.dumps(cpu_oracle_sample(args.cpu_oracle_sample)))
@@ -204,6 +206,13 @@ def main():
     for _ in range(args.warmup):
         sim.run(out)
     torch.cuda.synchronize()
+    if args.profile_step:
+        torch.cuda.profiler.start()
+        sim.run(out)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile_step": sim.stats.as_dict()}))
+        return 0
     hbm_peak, hbm_src, fp64_peak = _peaks()
 
     clk = ClockSampler(local)

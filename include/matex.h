@@ -64,6 +64,8 @@ typedef struct matex_opts {
   int64_t n_replay;        /* number of entries in replay_m (must equal the segment total) */
   int32_t max_width;       /* cap on supernode width (0 = 1024) */
   int32_t strict;          /* 1: return MATEX_ERR_NOCONV when m_max is reached unconverged */
+  int32_t solve_mode;      /* 0: one persistent launch per triangular-solve pair, tasks ordered
+                              by dependency counters (default); 1: one launch per tree level */
 } matex_opts;
 
 /* Counters and timings of the last matex_run (or of setup for the setup_* fields). */
@@ -199,6 +201,15 @@ typedef struct matex_profile {
   double flops[MATEX_PROF_CLASSES];
   double bytes[MATEX_PROF_CLASSES];
 } matex_profile;
+
+/*
+ * Failure-injection hook for tests of the bounded waits: while on, every
+ * persistent solve gets one dependency that never completes (the last root
+ * supernode waits for a child that does not exist).  Its wait gives up after
+ * about one second, the kernel returns, and the call reports
+ * MATEX_ERR_TIMEOUT; the context stays usable once the hook is off.
+ */
+matex_status matex_debug_inject_wait(matex_ctx* ctx, int32_t on);
 
 /* on = 1 starts (and zeroes) profiling, on = 0 stops it. */
 matex_status matex_set_profiling(matex_ctx* ctx, int32_t on);

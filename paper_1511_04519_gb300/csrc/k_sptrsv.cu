@@ -27,22 +27,19 @@ constexpr int kSplit = kSolveThreads / kRowBlock;  // threads sharing one dot pr
 
 // Forward task: rows [i0, i0+32) of P_s b_s for KB right-hand sides.  Thread
 // (row, sub) accumulates all KB columns of its row over panel columns
-// j = sub, sub+4, ..., so each panel entry is loaded once per task.
+// j = sub, sub+4, ..., so each panel entry is loaded once per task.  Loads of
+// Y go through L2 only (__ldcg): other CTAs of a persistent launch write them.
 template <int KB>
-__global__ void __launch_bounds__(kSolveThreads)
-fwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* __restrict__ Y,
-                 double* __restrict__ Y2, int ldy) {
-  extern __shared__ double sb[];  // b_s as [w][KB]
-  const int2 tk = tasks[blockIdx.x / ncb];
-  const int c0 = (blockIdx.x % ncb) * KB;
-  const int s = tk.x, i0 = tk.y;
+__device__ __forceinline__ void fwd_task(const DevFactor& F, int s, int i0, int c0,
+                                         double* __restrict__ Y, double* __restrict__ Y2, int ldy,
+                                         double* sb) {
   const int f = F.sup_first[s];
   const int w = F.sup_first[s + 1] - f;
   const int64_t rp = F.sup_rowptr[s];
   const int ld = (int)(F.sup_rowptr[s + 1] - rp);  // w + r
   for (int e = threadIdx.x; e < w * KB; e += blockDim.x) {
     const int j = e / KB, q = e - j * KB;
-    sb[e] = Y[(int64_t)(f + j) * ldy + c0 + q];
+    sb[e] = __ldcg(Y + (int64_t)(f + j) * ldy + c0 + q);
   }
   __syncthreads();
   const double* __restrict__ P = F.pan_cm + F.pan_off[s];
@@ -78,13 +75,9 @@ fwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* _
 
 // Backward task: panel columns [j0, j0+32) of P_s^T [D_s^{-1} y_s; -x_R].
 template <int KB>
-__global__ void __launch_bounds__(kSolveThreads)
-bwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* __restrict__ Y,
-                 const double* __restrict__ Y2, int ldy) {
-  extern __shared__ double ub[];  // [D_s^{-1} y_s; -x_R] as [w+r][KB]
-  const int2 tk = tasks[blockIdx.x / ncb];
-  const int c0 = (blockIdx.x % ncb) * KB;
-  const int s = tk.x, j0 = tk.y;
+__device__ __forceinline__ void bwd_task(const DevFactor& F, int s, int j0, int c0,
+                                         double* __restrict__ Y, const double* __restrict__ Y2,
+                                         int ldy, double* ub) {
   const int f = F.sup_first[s];
   const int w = F.sup_first[s + 1] - f;
   const int64_t rp = F.sup_rowptr[s];
@@ -92,8 +85,8 @@ bwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* _
   const int32_t* __restrict__ rows = F.sup_rows + rp;
   for (int e = threadIdx.x; e < ld * KB; e += blockDim.x) {
     const int i = e / KB, q = e - i * KB;
-    ub[e] = i < w ? Y2[(int64_t)(f + i) * ldy + c0 + q] * F.dinv[f + i]
-                  : -Y[(int64_t)rows[i] * ldy + c0 + q];
+    ub[e] = i < w ? __ldcg(Y2 + (int64_t)(f + i) * ldy + c0 + q) * F.dinv[f + i]
+                  : -__ldcg(Y + (int64_t)rows[i] * ldy + c0 + q);
   }
   __syncthreads();
   const double* __restrict__ P = F.pan_rm + F.pan_off[s];
@@ -118,6 +111,147 @@ bwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* _
     double* __restrict__ dst = Y + (int64_t)(f + j) * ldy + c0;
 #pragma unroll
     for (int q = 0; q < KB; ++q) dst[q] = acc[q];
+  }
+}
+
+template <int KB>
+__global__ void __launch_bounds__(kSolveThreads)
+fwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* __restrict__ Y,
+                 double* __restrict__ Y2, int ldy) {
+  extern __shared__ double sb[];
+  const int2 tk = tasks[blockIdx.x / ncb];
+  fwd_task<KB>(F, tk.x, tk.y, (blockIdx.x % ncb) * KB, Y, Y2, ldy, sb);
+}
+
+template <int KB>
+__global__ void __launch_bounds__(kSolveThreads)
+bwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* __restrict__ Y,
+                 const double* __restrict__ Y2, int ldy) {
+  extern __shared__ double ub[];
+  const int2 tk = tasks[blockIdx.x / ncb];
+  bwd_task<KB>(F, tk.x, tk.y, (blockIdx.x % ncb) * KB, Y, Y2, ldy, ub);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent solve: one launch runs every forward task (levels bottom-up) and
+// then every backward task (top-down).  CTAs take tickets in that order; a
+// task starts when its dependencies are met:
+//   forward (s, .)  : every forward task of every child of s is done
+//                     (fpend[s] counts children not yet complete);
+//   backward (s, .) : every backward task of parent(s) is done, or for a root
+//                     every forward task of s.
+// Tickets go out in dependency order and a CTA only waits on tasks holding
+// earlier tickets (already running), so the waits end; each wait is still
+// bounded, and on expiry the kernel raises the error flag and stops.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s per wait
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *((const volatile int*)p); }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Spin (thread 0 only) until *p >= target (or *p <= 0 when zero); gives up
+// after kWaitLimitNs or when another CTA has raised the error flag.
+__device__ bool wait_until(const int* p, int target, bool zero, int* err) {
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    const int v = ld_volatile(p);
+    if (zero ? v <= 0 : v >= target) break;
+    if (ld_volatile(err) || global_ns() - t0 > kWaitLimitNs) {
+      atomicExch(err, 1);
+      return false;
+    }
+    __nanosleep(64);
+  }
+  __threadfence();
+  return true;
+}
+
+__global__ void bump_kernel(int* p) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *p += 1;
+}
+
+__global__ void __launch_bounds__(kSolveThreads)
+persistent_solve_kernel(DevFactor F, PersistSched ps, double* __restrict__ Y,
+                        double* __restrict__ Y2, int ldy) {
+  extern __shared__ double sm[];
+  __shared__ long long sh_t;
+  __shared__ int sh_ok;
+  const long long total = ps.nf_total + ps.nb_total;
+  for (;;) {
+    if (threadIdx.x == 0) sh_t = atomicAdd(ps.ticket, 1ull);
+    __syncthreads();
+    const long long t = sh_t;
+    if (t >= total) break;
+    const bool fwd = t < ps.nf_total;
+    // locate the level of this ticket
+    int l;
+    long long local;
+    if (fwd) {
+      l = 0;
+      while (l + 1 < ps.nlev && ps.lev[l + 1].fbase <= t) ++l;
+      local = t - ps.lev[l].fbase;
+    } else {
+      const long long tb = t - ps.nf_total;
+      l = ps.nlev - 1;
+      while (l > 0 && ps.lev[l - 1].bbase <= tb) --l;
+      local = tb - ps.lev[l].bbase;
+    }
+    const PersistLevel& L = ps.lev[l];
+    const int task = (int)(local / L.ncb);
+    const int c0 = (int)(local % L.ncb) * L.kb;
+    const int2 tk = fwd ? L.ftasks[task] : L.btasks[task];
+    const int s = tk.x;
+    if (threadIdx.x == 0) {
+      bool ok;
+      if (fwd) {
+        ok = wait_until(ps.fpend + s, 0, true, ps.err);
+      } else {
+        const int p = F.sup_parent[s];
+        if (p >= 0) {
+          const PersistLevel& Lp = ps.lev[ps.sup_level[p]];
+          ok = wait_until(ps.bdone + p, ps.nbt[p] * Lp.ncb, false, ps.err);
+        } else {
+          ok = wait_until(ps.fdone + s, ps.nft[s] * L.ncb, false, ps.err);
+        }
+      }
+      sh_ok = ok;
+    }
+    __syncthreads();
+    if (!sh_ok) break;
+    if (fwd) {
+      switch (L.kb) {
+        case 1: fwd_task<1>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
+        case 2: fwd_task<2>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
+        case 4: fwd_task<4>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
+        default: fwd_task<8>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
+      }
+    } else {
+      switch (L.kb) {
+        case 1: bwd_task<1>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
+        case 2: bwd_task<2>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
+        case 4: bwd_task<4>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
+        default: bwd_task<8>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (fwd) {
+        const int old = atomicAdd(ps.fdone + s, 1);
+        const int p = F.sup_parent[s];
+        if (old == ps.nft[s] * L.ncb - 1 && p >= 0) {
+          __threadfence();
+          atomicSub(ps.fpend + p, 1);
+        }
+      } else {
+        atomicAdd(ps.bdone + s, 1);
+      }
+    }
   }
 }
 
@@ -200,6 +334,21 @@ __global__ void scatter_cols_kernel(const double* __restrict__ Y, int ldy, int n
 }
 
 }  // namespace
+
+void persistent_solve(const DevFactor& F, const PersistSched& ps, int grid, size_t smem,
+                      double* Y, double* Y2, int ldy, cudaStream_t st) {
+  persistent_solve_kernel<<<grid, kSolveThreads, smem, st>>>(F, ps, Y, Y2, ldy);
+}
+
+void bump_counter(int* p, cudaStream_t st) { bump_kernel<<<1, 32, 0, st>>>(p); }
+
+int persistent_blocks_per_sm(size_t smem) {
+  int nb = 0;
+  cudaFuncSetAttribute(persistent_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_solve_kernel, kSolveThreads, smem);
+  return nb;
+}
 
 void set_solve_smem_limit(int bytes) {
   cudaFuncSetAttribute(fwd_level_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);

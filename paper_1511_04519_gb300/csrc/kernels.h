@@ -15,6 +15,7 @@ constexpr int kCoefLd = kMaxM + 1;
 // panels P_s = [L_ss^{-1}; L_Rs L_ss^{-1}] ((w+r) x w), column- and row-major.
 struct DevFactor {
   const int32_t* sup_first;
+  const int32_t* sup_parent;
   const int64_t* sup_rowptr;
   const int32_t* sup_rows;
   const int64_t* pan_off;
@@ -37,6 +38,34 @@ struct LevelPlan {
   int32_t kb;            // column block: 1, 2, 4 or 8
 };
 void set_solve_smem_limit(int bytes);
+
+// Persistent (one launch per solve) schedule for a given column count.
+struct PersistLevel {
+  const int2* ftasks;
+  const int2* btasks;
+  int32_t nf, nb;       // tasks of the level in each direction
+  int32_t kb, ncb;      // column block and number of column blocks
+  long long fbase;      // first forward ticket of the level
+  long long bbase;      // first backward ticket of the level (backward counts top-down)
+};
+struct PersistSched {
+  const PersistLevel* lev;
+  int nlev;
+  long long nf_total, nb_total;
+  unsigned long long* ticket;
+  int* fdone;            // [nsup] completed forward tasks
+  int* bdone;            // [nsup] completed backward tasks
+  int* fpend;            // [nsup] children whose forward tasks are not all done
+  int* err;              // set on a wait timeout
+  const int32_t* sup_level;
+  const int32_t* nft;    // [nsup] forward row blocks per supernode
+  const int32_t* nbt;    // [nsup] backward column blocks per supernode
+};
+void persistent_solve(const DevFactor& F, const PersistSched& ps, int grid, size_t smem,
+                      double* Y, double* Y2, int ldy, cudaStream_t st);
+int persistent_blocks_per_sm(size_t smem);
+// adds one to *p on the stream (failure-injection hook of the tests)
+void bump_counter(int* p, cudaStream_t st);
 
 // Y is node-major [n][ldy] (ldy >= ncols, multiple of 8); solves in place,
 // using Y2 (same shape) for the intermediate forward result.

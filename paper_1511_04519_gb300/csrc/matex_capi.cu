@@ -60,6 +60,16 @@ struct matex_ctx {
   // structure
   Symbolic S;
   std::vector<LevelPlan> levels;
+  // persistent solve: per column count (1..ldy) one PersistLevel row per level
+  PersistLevel* plev_d = nullptr;
+  std::vector<long long> pf_total, pb_total;   // per column count
+  unsigned long long* pcounters = nullptr;     // ticket, then fdone[nsup], bdone[nsup]
+  int* fpend = nullptr;
+  int* fpend_init = nullptr;
+  int32_t *sup_level_d = nullptr, *nft_d = nullptr, *nbt_d = nullptr;
+  size_t psmem = 0;
+  int pgrid = 0;
+  bool inject_wait = false;  // test hook: a dependency that never completes
   std::vector<Round> rounds;          // batched: segment r of every group per round
   std::vector<Round> serial_rounds;   // one group at a time: one column per round
   bool serial = false;
@@ -173,7 +183,7 @@ std::vector<double> group_lts(const std::vector<int32_t>& srcs, const int32_t* p
 // Per tree level: forward tasks (supernode, 32 panel rows), backward tasks
 // (supernode, 32 panel columns) and the column block.  Returns false on an
 // allocation failure.
-constexpr int kSolveSmemCap = 160 * 1024;
+constexpr int kSolveSmemCap = 24 * 1024;  // keeps ~8 solve CTAs resident per SM
 
 bool plan_levels(matex_ctx* c) {
   const Symbolic& S = c->S;
@@ -204,7 +214,7 @@ bool plan_levels(matex_ctx* c) {
     if (kb <= 0) {
       // enough (task, column block) pairs to fill 152 SMs, else narrower blocks
       const int tasks = std::min(L.nf, L.nb * 4);
-      kb = tasks >= 1024 ? 8 : tasks >= 256 ? 4 : tasks >= 64 ? 2 : 1;
+      kb = tasks >= 512 ? 8 : tasks >= 128 ? 4 : tasks >= 32 ? 2 : 1;
     }
     while (kb > 1 && (size_t)mwr * kb * sizeof(double) > (size_t)kSolveSmemCap) kb /= 2;
     L.kb = kb;
@@ -219,12 +229,85 @@ bool plan_levels(matex_ctx* c) {
     c->levels[l].btasks = bd + bofs[l];
   }
   set_solve_smem_limit(std::max(smem_need, 48 * 1024));
+  // persistent schedules for every column count 1..ldy
+  std::vector<PersistLevel> pl((size_t)c->ldy * nlev);
+  c->pf_total.assign(c->ldy + 1, 0);
+  c->pb_total.assign(c->ldy + 1, 0);
+  for (int nc = 1; nc <= c->ldy; ++nc) {
+    long long fb = 0;
+    for (int l = 0; l < nlev; ++l) {
+      PersistLevel& P = pl[(size_t)(nc - 1) * nlev + l];
+      int kb = c->levels[l].kb;
+      while (kb > 1 && kb / 2 >= nc) kb /= 2;
+      P.ftasks = fd + fofs[l];
+      P.btasks = bd + bofs[l];
+      P.nf = c->levels[l].nf;
+      P.nb = c->levels[l].nb;
+      P.kb = kb;
+      P.ncb = (nc + kb - 1) / kb;
+      P.fbase = fb;
+      fb += (long long)P.nf * P.ncb;
+    }
+    long long bb = 0;
+    for (int l = nlev - 1; l >= 0; --l) {
+      PersistLevel& P = pl[(size_t)(nc - 1) * nlev + l];
+      P.bbase = bb;
+      bb += (long long)P.nb * P.ncb;
+    }
+    c->pf_total[nc] = fb;
+    c->pb_total[nc] = bb;
+  }
+  if (!c->upload(c->plev_d, pl.data(), pl.size())) return false;
+  std::vector<int32_t> lev(S.nsup), nft(S.nsup), nbt(S.nsup), kids(S.nsup, 0);
+  for (int l = 0; l < nlev; ++l)
+    for (int k = S.level_ptr[l]; k < S.level_ptr[l + 1]; ++k) lev[S.level_sups[k]] = l;
+  for (int32_t s = 0; s < S.nsup; ++s) {
+    const int w = S.sup_first[s + 1] - S.sup_first[s];
+    const int wr = (int)(S.sup_rowptr[s + 1] - S.sup_rowptr[s]);
+    nft[s] = (wr + kRowBlock - 1) / kRowBlock;
+    nbt[s] = (w + kRowBlock - 1) / kRowBlock;
+    if (S.sup_parent[s] >= 0) kids[S.sup_parent[s]]++;
+  }
+  if (!c->upload(c->sup_level_d, lev.data(), lev.size()) || !c->upload(c->nft_d, nft.data(), nft.size()) ||
+      !c->upload(c->nbt_d, nbt.data(), nbt.size()) ||
+      !c->upload(c->fpend_init, kids.data(), kids.size()) || !c->alloc(c->fpend, S.nsup) ||
+      !c->alloc(c->pcounters, 1 + (size_t)S.nsup))
+    return false;
+  c->psmem = std::max<size_t>(smem_need, sizeof(double) * 8);
+  int bps = persistent_blocks_per_sm(c->psmem);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  c->pgrid = std::max(1, bps) * std::max(1, sms);
   return true;
 }
 
 int solve_cols(matex_ctx* c, const DevFactor& F, int ncols) {
-  return solve_inplace(F, c->levels.data(), (int)c->levels.size(), c->Y, c->Y2, c->ldy, ncols,
-                       c->st);
+  if (ncols <= 0) return 0;
+  if (c->opts.solve_mode == 1)
+    return solve_inplace(F, c->levels.data(), (int)c->levels.size(), c->Y, c->Y2, c->ldy, ncols,
+                         c->st);
+  const int nlev = (int)c->levels.size();
+  const int32_t nsup = c->S.nsup;
+  PersistSched ps;
+  ps.lev = c->plev_d + (size_t)(ncols - 1) * nlev;
+  ps.nlev = nlev;
+  ps.nf_total = c->pf_total[ncols];
+  ps.nb_total = c->pb_total[ncols];
+  ps.ticket = c->pcounters;
+  int* cnt = reinterpret_cast<int*>(c->pcounters + 1);
+  ps.fdone = cnt;
+  ps.bdone = cnt + nsup;
+  ps.fpend = c->fpend;
+  ps.err = c->d_count + 1;
+  ps.sup_level = c->sup_level_d;
+  ps.nft = c->nft_d;
+  ps.nbt = c->nbt_d;
+  cudaMemsetAsync(c->pcounters, 0, sizeof(unsigned long long) * (1 + (size_t)nsup), c->st);
+  cudaMemcpyAsync(c->fpend, c->fpend_init, sizeof(int) * nsup, cudaMemcpyDeviceToDevice, c->st);
+  if (c->inject_wait) bump_counter(c->fpend + (nsup - 1), c->st);
+  persistent_solve(F, ps, c->pgrid, c->psmem, c->Y, c->Y2, c->ldy, c->st);
+  return 1;
 }
 
 RoundCols round_cols(matex_ctx* c, const Round& r) {
@@ -241,9 +324,11 @@ RoundCols round_cols(matex_ctx* c, const Round& r) {
 }
 
 matex_status read_count(matex_ctx* c, int* out) {
-  cudaMemcpyAsync(c->h_count, c->d_count, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(c->h_count, c->d_count, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "sync");
-  *out = *c->h_count;
+  *out = c->h_count[0];
+  if (c->h_count[1] != 0)
+    return fail(c, MATEX_ERR_TIMEOUT, "a bounded wait of the persistent solve expired");
   return MATEX_OK;
 }
 
@@ -321,6 +406,7 @@ matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
   int launches = 0, sweepsM = 0, sweepsG = 0;
   int64_t solve_cols_total = 0;
   int e;
+  cudaMemsetAsync(c->d_count, 0, 2 * sizeof(int32_t), st);
   auto solve = [&](const DevFactor& F, int K) {
     e = prof_begin(c);
     const int l = solve_cols(c, F, K);
@@ -464,6 +550,10 @@ matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
   launches++;
   if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(c, "run sync");
   if ((s = cuda_check(c, "run")) != MATEX_OK) return s;
+  {
+    int tmp = 0;
+    if ((s = read_count(c, &tmp)) != MATEX_OK) return s;
+  }
   // statistics from the per-segment records
   std::vector<int32_t> m(c->n_segments), stt(c->n_segments);
   if (c->n_segments) {
@@ -743,9 +833,10 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   t = now_ms();
   bool ok = true;
   const Symbolic& S = c->S;
-  int32_t *sup_first, *sup_rows;
+  int32_t *sup_first, *sup_rows, *sup_parent;
   int64_t *sup_rowptr, *pan_off;
   ok = ok && c->upload(sup_first, S.sup_first.data(), S.sup_first.size());
+  ok = ok && c->upload(sup_parent, S.sup_parent.data(), S.sup_parent.size());
   ok = ok && c->upload(sup_rowptr, S.sup_rowptr.data(), S.sup_rowptr.size());
   ok = ok && c->upload(sup_rows, S.sup_rows.data(), S.sup_rows.size());
   ok = ok && c->upload(pan_off, S.pan_off.data(), S.pan_off.size());
@@ -754,7 +845,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     bool k = c->upload(dinv, Nm.dinv.data(), Nm.dinv.size()) &&
              c->upload(pcm, Nm.pan_cm.data(), Nm.pan_cm.size()) &&
              c->upload(prm, Nm.pan_rm.data(), Nm.pan_rm.size());
-    F = DevFactor{sup_first, sup_rowptr, sup_rows, pan_off, dinv, pcm, prm};
+    F = DevFactor{sup_first, sup_parent, sup_rowptr, sup_rows, pan_off, dinv, pcm, prm};
     return k;
   };
   ok = ok && up_factor(NM, c->fM) && up_factor(NG, c->fG);
@@ -802,9 +893,9 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
        c->upload(c->rc_hfirst, h_hfirst.data(), h_hfirst.size()) &&
        c->upload(c->rc_segid, h_segid.data(), h_segid.size());
   if (!c->replay.empty()) ok = ok && c->upload(c->replay_d, c->replay.data(), c->replay.size());
-  ok = ok && plan_levels(c);
   // work buffers
   c->ldy = roundup8(std::max({2 * Kmax, 8, std::min<int>(n_groups, 256)}));
+  ok = ok && plan_levels(c);
   c->nchunks = (int)((n + kChunk - 1) / kChunk);
   const size_t G = (size_t)std::max(n_groups, 1);
   ok = ok && c->alloc(c->Y, (size_t)n * c->ldy) && c->alloc(c->Y2, (size_t)n * c->ldy) && c->alloc(c->Vb, G * kMaxB * n) &&
@@ -815,10 +906,10 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
        c->alloc(c->ss.m, Kmax) && c->alloc(c->ss.status, Kmax) &&
        c->alloc(c->ss.hbuf, (size_t)Kmax * kMaxB) && c->alloc(c->ss.scale, Kmax) &&
        c->alloc(c->iterA, Kmax) && c->alloc(c->iterB, Kmax) && c->alloc(c->iter_grp, Kmax) &&
-       c->alloc(c->d_count, 1) && c->alloc(c->coef, (size_t)Kmax * c->n_times * kCoefLd) &&
+       c->alloc(c->d_count, 2) && c->alloc(c->coef, (size_t)Kmax * c->n_times * kCoefLd) &&
        c->alloc(c->yend, (size_t)Kmax * kMaxM) && c->alloc(c->m_rec, std::max<int64_t>(1, c->n_segments)) &&
        c->alloc(c->st_rec, std::max<int64_t>(1, c->n_segments));
-  if (ok && cudaMallocHost(&c->h_count, sizeof(int32_t)) != cudaSuccess) ok = false;
+  if (ok && cudaMallocHost(&c->h_count, 2 * sizeof(int32_t)) != cudaSuccess) ok = false;
   if (!ok) {
     cudaGetLastError();
     g_setup_err = "device allocation or upload failed";
@@ -879,6 +970,7 @@ matex_status matex_solve(matex_ctx* c, int32_t which, int32_t ncols, const doubl
     return fail(c, MATEX_ERR_ARG, "bad solve arguments");
   const DevFactor& F = which == 0 ? c->fM : c->fG;
   const int64_t n = c->n;
+  cudaMemsetAsync(c->d_count, 0, 2 * sizeof(int32_t), c->st);
   for (int32_t q0 = 0; q0 < ncols; q0 += c->ldy) {
     const int K = std::min<int>(c->ldy, ncols - q0);
     gather_cols(c->Y, c->ldy, K, b + (int64_t)q0 * n, n, nullptr, nullptr, c->perm, n, c->st);
@@ -886,7 +978,10 @@ matex_status matex_solve(matex_ctx* c, int32_t which, int32_t ncols, const doubl
     scatter_cols(c->Y, c->ldy, K, x + (int64_t)q0 * n, n, nullptr, c->perm, n, c->st);
   }
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "solve sync");
-  return cuda_check(c, "solve");
+  matex_status s = cuda_check(c, "solve");
+  if (s != MATEX_OK) return s;
+  int tmp = 0;
+  return read_count(c, &tmp);
 }
 
 matex_status matex_expm(matex_ctx* c, int32_t batch, int32_t m, const double* A, const double* h,
@@ -922,6 +1017,12 @@ matex_status matex_get_sizes(matex_ctx* c, int32_t* n_times, int32_t* n_rows, in
 matex_status matex_set_batching(matex_ctx* c, int32_t one_group_at_a_time) {
   if (!c) return MATEX_ERR_ARG;
   c->serial = one_group_at_a_time != 0;
+  return MATEX_OK;
+}
+
+matex_status matex_debug_inject_wait(matex_ctx* c, int32_t on) {
+  if (!c) return MATEX_ERR_ARG;
+  c->inject_wait = on != 0;
   return MATEX_OK;
 }
 

@@ -31,7 +31,7 @@ class MatexOpts(C.Structure):
     _fields_ = [("col_block", C.c_int32), ("group_select", C.c_int32), ("include_dc", C.c_int32),
                 ("n_rows", C.c_int32), ("rows", C.POINTER(C.c_int32)),
                 ("replay_m", C.POINTER(C.c_int32)), ("n_replay", C.c_int64),
-                ("max_width", C.c_int32), ("strict", C.c_int32)]
+                ("max_width", C.c_int32), ("strict", C.c_int32), ("solve_mode", C.c_int32)]
 
 
 class MatexStats(C.Structure):
@@ -62,7 +62,8 @@ class MatexProfile(C.Structure):
 EXPORTS = ["matex_default_opts", "matex_setup", "matex_run", "matex_run_host", "matex_set_sources",
            "matex_solve", "matex_expm", "matex_get_m", "matex_get_sizes", "matex_get_setup_stats",
            "matex_last_error", "matex_status_string", "matex_destroy", "matex_set_profiling",
-           "matex_get_profile", "matex_host_factor_solve", "matex_set_batching"]
+           "matex_get_profile", "matex_host_factor_solve", "matex_set_batching",
+           "matex_debug_inject_wait"]
 
 
 def _load():
@@ -98,6 +99,8 @@ def _load():
     lib.matex_last_error.restype = C.c_char_p
     lib.matex_status_string.argtypes = [C.c_int]
     lib.matex_status_string.restype = C.c_char_p
+    lib.matex_debug_inject_wait.argtypes = [P, C.c_int32]
+    lib.matex_debug_inject_wait.restype = C.c_int
     lib.matex_set_batching.argtypes = [P, C.c_int32]
     lib.matex_set_batching.restype = C.c_int
     lib.matex_set_profiling.argtypes = [P, C.c_int32]
@@ -226,6 +229,10 @@ def matex_get_setup_stats(ctx):
     return s
 
 
+def matex_debug_inject_wait(ctx, on):
+    _check(ctx, _lib.matex_debug_inject_wait(ctx, int(bool(on))))
+
+
 def matex_set_batching(ctx, one_group_at_a_time):
     _check(ctx, _lib.matex_set_batching(ctx, int(bool(one_group_at_a_time))))
 
@@ -251,7 +258,8 @@ class Sim:
     src_group, n_groups, gamma, tol, m_max, t_end, dt_out)."""
 
     def __init__(self, p, col_block=0, group_select=-1, include_dc=True, rows=None,
-                 replay_m=None, max_width=0, strict=False, stream=None, **overrides):
+                 replay_m=None, max_width=0, strict=False, stream=None, solve_mode=0,
+                 **overrides):
         o = matex_default_opts()
         o.col_block = col_block
         o.group_select = group_select
@@ -259,6 +267,7 @@ class Sim:
         if max_width:
             o.max_width = max_width
         o.strict = int(bool(strict))
+        o.solve_mode = int(solve_mode)
         self._keep = []
         if rows is not None:
             r = np.ascontiguousarray(rows, dtype=np.int32)

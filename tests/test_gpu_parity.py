@@ -164,6 +164,31 @@ def test_one_group_at_a_time_matches_batched(M):
     assert np.abs(Xs - Xb).max() <= 1e-13
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_persistent_and_level_solves_agree(M, mode):
+    p = gridgen.small_mesh(13, nx=30, ny=30, layers=2, n_src=20, group_templates=[5] * 4, t_end=0.3e-9)
+    ref = R.rmatex(p)
+    sim = M.Sim(p, solve_mode=mode, replay_m=oracle_m(ref))
+    X = sim.run().cpu().numpy()
+    assert np.abs(X - ref.X).max() <= TOL_V * p.vdd
+
+
+def test_bounded_wait_reports_timeout_and_context_recovers(M):
+    import time
+    p = gridgen.small_mesh(14, nx=12, ny=12, n_src=4)
+    sim = M.Sim(p)
+    good = sim.run().cpu().numpy()
+    M.matex_debug_inject_wait(sim.ctx, True)
+    t0 = time.time()
+    with pytest.raises(M.MatexError) as ei:
+        sim.run()
+    assert ei.value.status == 4  # MATEX_ERR_TIMEOUT
+    assert time.time() - t0 < 30
+    M.matex_debug_inject_wait(sim.ctx, False)
+    again = sim.run().cpu().numpy()
+    assert np.array_equal(again, good)
+
+
 def test_m_max_one_and_replay(M):
     p = gridgen.small_mesh(9, nx=7, ny=7, n_src=4)
     p.m_max = 1
