@@ -83,6 +83,28 @@ krylov_start_kernel(double* __restrict__ Vb, int64_t vstride, const double* __re
   if (threadIdx.x == 0) partials[(int64_t)q * nchunks + blockIdx.x] = s;
 }
 
+// Dot products of w (slot wslot) with NB basis slots first..first+NB-1 over one
+// chunk of nodes; NB is a template parameter so no predicated FP64 work is
+// issued for slots that do not exist (the FP64 pipe counts those too).
+template <int NB>
+__device__ __forceinline__ void dots_chunk(const double* __restrict__ base, const double* __restrict__ w,
+                                           int first, int64_t n, int64_t b, int64_t e,
+                                           double* __restrict__ out, int nchunks, double* red) {
+  double acc[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) acc[i] = 0.0;
+  for (int64_t x = b + threadIdx.x; x < e; x += blockDim.x) {
+    const double wx = w[x];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) acc[i] = fma(base[(int64_t)(first + i) * n + x], wx, acc[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const double s = block_sum(acc[i], red);
+    if (threadIdx.x == 0) out[(int64_t)i * nchunks] = s;
+  }
+}
+
 __global__ void __launch_bounds__(kRedThreads)
 basis_dots_kernel(const double* __restrict__ Vb, int64_t vstride, const int32_t* __restrict__ groups,
                   const int32_t* __restrict__ iter, int first, int nb, int wslot, int64_t n,
@@ -94,18 +116,15 @@ basis_dots_kernel(const double* __restrict__ Vb, int64_t vstride, const int32_t*
   const double* __restrict__ w = base + (int64_t)wslot * n;
   const int64_t b = (int64_t)blockIdx.x * kChunk;
   const int64_t e = min(n, b + kChunk);
-  double acc[kMaxB];
-#pragma unroll
-  for (int i = 0; i < kMaxB; ++i) acc[i] = 0.0;
-  for (int64_t x = b + threadIdx.x; x < e; x += blockDim.x) {
-    const double wx = w[x];
-#pragma unroll
-    for (int i = 0; i < kMaxB; ++i)
-      if (i < nb) acc[i] = fma(base[(int64_t)(first + i) * n + x], wx, acc[i]);
-  }
-  for (int i = 0; i < nb; ++i) {
-    const double s = block_sum(acc[i], red);
-    if (threadIdx.x == 0) partials[((int64_t)q * kMaxB + i) * nchunks + blockIdx.x] = s;
+  double* out = partials + ((int64_t)q * kMaxB) * nchunks + blockIdx.x;
+  switch (nb) {
+#define MATEX_DC(NB) \
+  case NB: dots_chunk<NB>(base, w, first, n, b, e, out, nchunks, red); break;
+    MATEX_DC(1) MATEX_DC(2) MATEX_DC(3) MATEX_DC(4) MATEX_DC(5) MATEX_DC(6) MATEX_DC(7)
+    MATEX_DC(8) MATEX_DC(9) MATEX_DC(10) MATEX_DC(11) MATEX_DC(12) MATEX_DC(13) MATEX_DC(14)
+    MATEX_DC(15) MATEX_DC(16) MATEX_DC(17) MATEX_DC(18) MATEX_DC(19) MATEX_DC(20) MATEX_DC(21)
+#undef MATEX_DC
+    default: break;
   }
 }
 

@@ -49,7 +49,22 @@ __device__ __forceinline__ void fwd_task(const DevFactor& F, int s, int i0, int 
 #pragma unroll
   for (int q = 0; q < KB; ++q) acc[q] = 0.0;
   if (i < ld) {
-    for (int j = sub; j < w; j += kSplit) {
+    int j = sub;
+    // four panel loads in flight per thread, then their FMAs
+    for (; j + 3 * kSplit < w; j += 4 * kSplit) {
+      const double p0 = P[(int64_t)j * ld + i];
+      const double p1 = P[(int64_t)(j + kSplit) * ld + i];
+      const double p2 = P[(int64_t)(j + 2 * kSplit) * ld + i];
+      const double p3 = P[(int64_t)(j + 3 * kSplit) * ld + i];
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        double a = fma(p0, sb[j * KB + q], acc[q]);
+        a = fma(p1, sb[(j + kSplit) * KB + q], a);
+        a = fma(p2, sb[(j + 2 * kSplit) * KB + q], a);
+        acc[q] = fma(p3, sb[(j + 3 * kSplit) * KB + q], a);
+      }
+    }
+    for (; j < w; j += kSplit) {
       const double p = P[(int64_t)j * ld + i];
 #pragma unroll
       for (int q = 0; q < KB; ++q) acc[q] = fma(p, sb[j * KB + q], acc[q]);
@@ -96,7 +111,21 @@ __device__ __forceinline__ void bwd_task(const DevFactor& F, int s, int j0, int 
 #pragma unroll
   for (int q = 0; q < KB; ++q) acc[q] = 0.0;
   if (j < w) {
-    for (int i = sub; i < ld; i += kSplit) {
+    int i = sub;
+    for (; i + 3 * kSplit < ld; i += 4 * kSplit) {
+      const double p0 = P[(int64_t)i * w + j];
+      const double p1 = P[(int64_t)(i + kSplit) * w + j];
+      const double p2 = P[(int64_t)(i + 2 * kSplit) * w + j];
+      const double p3 = P[(int64_t)(i + 3 * kSplit) * w + j];
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        double a = fma(p0, ub[i * KB + q], acc[q]);
+        a = fma(p1, ub[(i + kSplit) * KB + q], a);
+        a = fma(p2, ub[(i + 2 * kSplit) * KB + q], a);
+        acc[q] = fma(p3, ub[(i + 3 * kSplit) * KB + q], a);
+      }
+    }
+    for (; i < ld; i += kSplit) {
       const double p = P[(int64_t)i * w + j];
 #pragma unroll
       for (int q = 0; q < KB; ++q) acc[q] = fma(p, ub[i * KB + q], acc[q]);
@@ -145,6 +174,7 @@ bwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* _
 // bounded, and on expiry the kernel raises the error flag and stops.
 // ---------------------------------------------------------------------------
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s per wait
+constexpr int kTicketBatch = 4;
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *((const volatile int*)p); }
 
@@ -175,17 +205,24 @@ __global__ void bump_kernel(int* p) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *p += 1;
 }
 
-__global__ void __launch_bounds__(kSolveThreads)
+__global__ void __launch_bounds__(kSolveThreads, 6)
 persistent_solve_kernel(DevFactor F, PersistSched ps, double* __restrict__ Y,
                         double* __restrict__ Y2, int ldy) {
   extern __shared__ double sm[];
   __shared__ long long sh_t;
   __shared__ int sh_ok;
   const long long total = ps.nf_total + ps.nb_total;
+  long long t = 0, t_end = 0;
   for (;;) {
-    if (threadIdx.x == 0) sh_t = atomicAdd(ps.ticket, 1ull);
-    __syncthreads();
-    const long long t = sh_t;
+    if (t >= t_end) {
+      // a batch of consecutive tickets: tasks inside it run in ticket order,
+      // which respects every dependency among them
+      if (threadIdx.x == 0) sh_t = (long long)atomicAdd(ps.ticket, (unsigned long long)kTicketBatch);
+      __syncthreads();
+      t = sh_t;
+      t_end = t + kTicketBatch;
+      __syncthreads();
+    }
     if (t >= total) break;
     const bool fwd = t < ps.nf_total;
     // locate the level of this ticket
@@ -252,6 +289,7 @@ persistent_solve_kernel(DevFactor F, PersistSched ps, double* __restrict__ Y,
         atomicAdd(ps.bdone + s, 1);
       }
     }
+    ++t;
   }
 }
 
