@@ -174,7 +174,6 @@ bwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* _
 // bounded, and on expiry the kernel raises the error flag and stops.
 // ---------------------------------------------------------------------------
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s per wait
-constexpr int kTicketBatch = 4;
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *((const volatile int*)p); }
 
@@ -212,84 +211,83 @@ persistent_solve_kernel(DevFactor F, PersistSched ps, double* __restrict__ Y,
   __shared__ long long sh_t;
   __shared__ int sh_ok;
   const long long total = ps.nf_total + ps.nb_total;
-  long long t = 0, t_end = 0;
   for (;;) {
-    if (t >= t_end) {
-      // a batch of consecutive tickets: tasks inside it run in ticket order,
-      // which respects every dependency among them
-      if (threadIdx.x == 0) sh_t = (long long)atomicAdd(ps.ticket, (unsigned long long)kTicketBatch);
-      __syncthreads();
-      t = sh_t;
-      t_end = t + kTicketBatch;
-      __syncthreads();
-    }
+    if (threadIdx.x == 0) sh_t = (long long)atomicAdd(ps.ticket, 1ull);
+    __syncthreads();
+    const long long t = sh_t;
     if (t >= total) break;
     const bool fwd = t < ps.nf_total;
-    // locate the level of this ticket
+    // locate the level of this ticket and its first task
     int l;
-    long long local;
+    long long unit;
     if (fwd) {
       l = 0;
       while (l + 1 < ps.nlev && ps.lev[l + 1].fbase <= t) ++l;
-      local = t - ps.lev[l].fbase;
+      unit = t - ps.lev[l].fbase;
     } else {
       const long long tb = t - ps.nf_total;
       l = ps.nlev - 1;
       while (l > 0 && ps.lev[l - 1].bbase <= tb) --l;
-      local = tb - ps.lev[l].bbase;
+      unit = tb - ps.lev[l].bbase;
     }
     const PersistLevel& L = ps.lev[l];
-    const int task = (int)(local / L.ncb);
-    const int c0 = (int)(local % L.ncb) * L.kb;
-    const int2 tk = fwd ? L.ftasks[task] : L.btasks[task];
-    const int s = tk.x;
-    if (threadIdx.x == 0) {
-      bool ok;
-      if (fwd) {
-        ok = wait_until(ps.fpend + s, 0, true, ps.err);
-      } else {
-        const int p = F.sup_parent[s];
-        if (p >= 0) {
-          const PersistLevel& Lp = ps.lev[ps.sup_level[p]];
-          ok = wait_until(ps.bdone + p, ps.nbt[p] * Lp.ncb, false, ps.err);
+    const int batch = fwd ? L.fbatch : L.bbatch;
+    const long long ntask = (long long)(fwd ? L.nf : L.nb) * L.ncb;
+    const long long lo = unit * batch, hi = min(ntask, lo + batch);
+    bool failed = false;
+    for (long long local = lo; local < hi; ++local) {
+      const int task = (int)(local / L.ncb);
+      const int c0 = (int)(local % L.ncb) * L.kb;
+      const int2 tk = fwd ? L.ftasks[task] : L.btasks[task];
+      const int s = tk.x;
+      if (threadIdx.x == 0) {
+        bool ok;
+        if (fwd) {
+          ok = wait_until(ps.fpend + s, 0, true, ps.err);
         } else {
-          ok = wait_until(ps.fdone + s, ps.nft[s] * L.ncb, false, ps.err);
+          const int p = F.sup_parent[s];
+          if (p >= 0) {
+            const PersistLevel& Lp = ps.lev[ps.sup_level[p]];
+            ok = wait_until(ps.bdone + p, ps.nbt[p] * Lp.ncb, false, ps.err);
+          } else {
+            ok = wait_until(ps.fdone + s, ps.nft[s] * L.ncb, false, ps.err);
+          }
         }
+        sh_ok = ok;
       }
-      sh_ok = ok;
-    }
-    __syncthreads();
-    if (!sh_ok) break;
-    if (fwd) {
-      switch (L.kb) {
-        case 1: fwd_task<1>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
-        case 2: fwd_task<2>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
-        case 4: fwd_task<4>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
-        default: fwd_task<8>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
-      }
-    } else {
-      switch (L.kb) {
-        case 1: bwd_task<1>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
-        case 2: bwd_task<2>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
-        case 4: bwd_task<4>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
-        default: bwd_task<8>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
+      __syncthreads();
+      if (!sh_ok) { failed = true; break; }
       if (fwd) {
-        const int old = atomicAdd(ps.fdone + s, 1);
-        const int p = F.sup_parent[s];
-        if (old == ps.nft[s] * L.ncb - 1 && p >= 0) {
-          __threadfence();
-          atomicSub(ps.fpend + p, 1);
+        switch (L.kb) {
+          case 1: fwd_task<1>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
+          case 2: fwd_task<2>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
+          case 4: fwd_task<4>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
+          default: fwd_task<8>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
         }
       } else {
-        atomicAdd(ps.bdone + s, 1);
+        switch (L.kb) {
+          case 1: bwd_task<1>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
+          case 2: bwd_task<2>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
+          case 4: bwd_task<4>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
+          default: bwd_task<8>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        if (fwd) {
+          const int old = atomicAdd(ps.fdone + s, 1);
+          const int p = F.sup_parent[s];
+          if (old == ps.nft[s] * L.ncb - 1 && p >= 0) {
+            __threadfence();
+            atomicSub(ps.fpend + p, 1);
+          }
+        } else {
+          atomicAdd(ps.bdone + s, 1);
+        }
       }
     }
-    ++t;
+    if (failed) break;
   }
 }
 

@@ -40,11 +40,15 @@ struct LevelPlan {
 void set_solve_smem_limit(int bytes);
 
 // Persistent (one launch per solve) schedule for a given column count.
+// A ticket covers `fbatch` (forward) or `bbatch` (backward) consecutive tasks
+// of one level, run in order by the CTA that draws it: large levels of small
+// tasks draw fewer tickets, small levels keep one task per ticket.
 struct PersistLevel {
   const int2* ftasks;
   const int2* btasks;
-  int32_t nf, nb;       // tasks of the level in each direction
+  int32_t nf, nb;       // tasks of the level in each direction (before column blocks)
   int32_t kb, ncb;      // column block and number of column blocks
+  int32_t fbatch, bbatch;
   long long fbase;      // first forward ticket of the level
   long long bbase;      // first backward ticket of the level (backward counts top-down)
 };

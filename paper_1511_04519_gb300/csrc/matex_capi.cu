@@ -245,14 +245,19 @@ bool plan_levels(matex_ctx* c) {
       P.nb = c->levels[l].nb;
       P.kb = kb;
       P.ncb = (nc + kb - 1) / kb;
+      auto batch_for = [](long long tasks) {
+        return tasks >= 8192 ? 8 : tasks >= 2048 ? 4 : tasks >= 512 ? 2 : 1;
+      };
+      P.fbatch = batch_for((long long)P.nf * P.ncb);
+      P.bbatch = batch_for((long long)P.nb * P.ncb);
       P.fbase = fb;
-      fb += (long long)P.nf * P.ncb;
+      fb += ((long long)P.nf * P.ncb + P.fbatch - 1) / P.fbatch;
     }
     long long bb = 0;
     for (int l = nlev - 1; l >= 0; --l) {
       PersistLevel& P = pl[(size_t)(nc - 1) * nlev + l];
       P.bbase = bb;
-      bb += (long long)P.nb * P.ncb;
+      bb += ((long long)P.nb * P.ncb + P.bbatch - 1) / P.bbatch;
     }
     c->pf_total[nc] = fb;
     c->pb_total[nc] = bb;
