@@ -143,13 +143,122 @@ __device__ __forceinline__ void bwd_task(const DevFactor& F, int s, int j0, int 
   }
 }
 
+// Packed forward task: up to 128 panel rows of several small supernodes of
+// one level, one thread per row (no split: their panels are narrow).
+template <int KB>
+__device__ __forceinline__ void fwd_small(const DevFactor& F, const int32_t* __restrict__ ents,
+                                          int ne, int c0, double* __restrict__ Y,
+                                          double* __restrict__ Y2, int ldy, double* sb) {
+  int boff = 0;
+  for (int k = 0; k < ne; ++k) {
+    const int s = ents[k];
+    const int f = F.sup_first[s];
+    const int w = F.sup_first[s + 1] - f;
+    for (int e = threadIdx.x; e < w * KB; e += blockDim.x) {
+      const int j = e / KB, q = e - j * KB;
+      sb[boff + e] = __ldcg(Y + (int64_t)(f + j) * ldy + c0 + q);
+    }
+    boff += w * KB;
+  }
+  __syncthreads();
+  // this thread's supernode and row
+  int k = 0, r = threadIdx.x, bo = 0, s = -1, w = 0, ld = 0;
+  for (; k < ne; ++k) {
+    s = ents[k];
+    w = F.sup_first[s + 1] - F.sup_first[s];
+    ld = (int)(F.sup_rowptr[s + 1] - F.sup_rowptr[s]);
+    if (r < ld) break;
+    r -= ld;
+    bo += w * KB;
+  }
+  if (k >= ne) return;
+  const int f = F.sup_first[s];
+  const double* __restrict__ P = F.pan_cm + F.pan_off[s];
+  double acc[KB];
+#pragma unroll
+  for (int q = 0; q < KB; ++q) acc[q] = 0.0;
+  for (int j = 0; j < w; ++j) {
+    const double p = P[(int64_t)j * ld + r];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) acc[q] = fma(p, sb[bo + j * KB + q], acc[q]);
+  }
+  if (r < w) {
+    double* __restrict__ dst = Y2 + (int64_t)(f + r) * ldy + c0;
+#pragma unroll
+    for (int q = 0; q < KB; ++q) dst[q] = acc[q];
+  } else {
+    double* __restrict__ dst = Y + (int64_t)F.sup_rows[F.sup_rowptr[s] + r] * ldy + c0;
+#pragma unroll
+    for (int q = 0; q < KB; ++q) atomicAdd(dst + q, -acc[q]);
+  }
+}
+
+// Packed backward task: up to 128 panel columns of several small supernodes.
+template <int KB>
+__device__ __forceinline__ void bwd_small(const DevFactor& F, const int32_t* __restrict__ ents,
+                                          int ne, int c0, double* __restrict__ Y,
+                                          const double* __restrict__ Y2, int ldy, double* ub) {
+  int uoff = 0;
+  for (int k = 0; k < ne; ++k) {
+    const int s = ents[k];
+    const int f = F.sup_first[s];
+    const int w = F.sup_first[s + 1] - f;
+    const int64_t rp = F.sup_rowptr[s];
+    const int ld = (int)(F.sup_rowptr[s + 1] - rp);
+    for (int e = threadIdx.x; e < ld * KB; e += blockDim.x) {
+      const int i = e / KB, q = e - i * KB;
+      ub[uoff + e] = i < w ? __ldcg(Y2 + (int64_t)(f + i) * ldy + c0 + q) * F.dinv[f + i]
+                           : -__ldcg(Y + (int64_t)F.sup_rows[rp + i] * ldy + c0 + q);
+    }
+    uoff += ld * KB;
+  }
+  __syncthreads();
+  int k = 0, c = threadIdx.x, uo = 0, s = -1, w = 0, ld = 0;
+  for (; k < ne; ++k) {
+    s = ents[k];
+    w = F.sup_first[s + 1] - F.sup_first[s];
+    ld = (int)(F.sup_rowptr[s + 1] - F.sup_rowptr[s]);
+    if (c < w) break;
+    c -= w;
+    uo += ld * KB;
+  }
+  if (k >= ne) return;
+  const int f = F.sup_first[s];
+  const double* __restrict__ P = F.pan_rm + F.pan_off[s];
+  double acc[KB];
+#pragma unroll
+  for (int q = 0; q < KB; ++q) acc[q] = 0.0;
+  for (int i = 0; i < ld; ++i) {
+    const double p = P[(int64_t)i * w + c];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) acc[q] = fma(p, ub[uo + i * KB + q], acc[q]);
+  }
+  double* __restrict__ dst = Y + (int64_t)(f + c) * ldy + c0;
+#pragma unroll
+  for (int q = 0; q < KB; ++q) dst[q] = acc[q];
+}
+
+template <int KB>
+__device__ __forceinline__ void run_fwd(const DevFactor& F, int2 tk, int c0, double* Y, double* Y2,
+                                        int ldy, double* sm) {
+  if (tk.x >= 0) fwd_task<KB>(F, tk.x, tk.y, c0, Y, Y2, ldy, sm);
+  else fwd_small<KB>(F, F.pack + (-1 - tk.x), tk.y, c0, Y, Y2, ldy, sm);
+}
+
+template <int KB>
+__device__ __forceinline__ void run_bwd(const DevFactor& F, int2 tk, int c0, double* Y,
+                                        const double* Y2, int ldy, double* sm) {
+  if (tk.x >= 0) bwd_task<KB>(F, tk.x, tk.y, c0, Y, Y2, ldy, sm);
+  else bwd_small<KB>(F, F.pack + (-1 - tk.x), tk.y, c0, Y, Y2, ldy, sm);
+}
+
 template <int KB>
 __global__ void __launch_bounds__(kSolveThreads)
 fwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* __restrict__ Y,
                  double* __restrict__ Y2, int ldy) {
   extern __shared__ double sb[];
   const int2 tk = tasks[blockIdx.x / ncb];
-  fwd_task<KB>(F, tk.x, tk.y, (blockIdx.x % ncb) * KB, Y, Y2, ldy, sb);
+  run_fwd<KB>(F, tk, (blockIdx.x % ncb) * KB, Y, Y2, ldy, sb);
 }
 
 template <int KB>
@@ -158,7 +267,7 @@ bwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* _
                  const double* __restrict__ Y2, int ldy) {
   extern __shared__ double ub[];
   const int2 tk = tasks[blockIdx.x / ncb];
-  bwd_task<KB>(F, tk.x, tk.y, (blockIdx.x % ncb) * KB, Y, Y2, ldy, ub);
+  run_bwd<KB>(F, tk, (blockIdx.x % ncb) * KB, Y, Y2, ldy, ub);
 }
 
 // ---------------------------------------------------------------------------
@@ -239,18 +348,23 @@ persistent_solve_kernel(DevFactor F, PersistSched ps, double* __restrict__ Y,
       const int task = (int)(local / L.ncb);
       const int c0 = (int)(local % L.ncb) * L.kb;
       const int2 tk = fwd ? L.ftasks[task] : L.btasks[task];
-      const int s = tk.x;
+      // supernodes of this task: one, or a packed list
+      const int32_t* ents = tk.x >= 0 ? nullptr : F.pack + (-1 - tk.x);
+      const int ne = tk.x >= 0 ? 1 : tk.y;
       if (threadIdx.x == 0) {
-        bool ok;
-        if (fwd) {
-          ok = wait_until(ps.fpend + s, 0, true, ps.err);
-        } else {
-          const int p = F.sup_parent[s];
-          if (p >= 0) {
-            const PersistLevel& Lp = ps.lev[ps.sup_level[p]];
-            ok = wait_until(ps.bdone + p, ps.nbt[p] * Lp.ncb, false, ps.err);
+        bool ok = true;
+        for (int k = 0; k < ne && ok; ++k) {
+          const int s = ents ? ents[k] : tk.x;
+          if (fwd) {
+            ok = wait_until(ps.fpend + s, 0, true, ps.err);
           } else {
-            ok = wait_until(ps.fdone + s, ps.nft[s] * L.ncb, false, ps.err);
+            const int p = F.sup_parent[s];
+            if (p >= 0) {
+              const PersistLevel& Lp = ps.lev[ps.sup_level[p]];
+              ok = wait_until(ps.bdone + p, ps.nbt[p] * Lp.ncb, false, ps.err);
+            } else {
+              ok = wait_until(ps.fdone + s, ps.nft[s] * L.ncb, false, ps.err);
+            }
           }
         }
         sh_ok = ok;
@@ -259,31 +373,34 @@ persistent_solve_kernel(DevFactor F, PersistSched ps, double* __restrict__ Y,
       if (!sh_ok) { failed = true; break; }
       if (fwd) {
         switch (L.kb) {
-          case 1: fwd_task<1>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
-          case 2: fwd_task<2>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
-          case 4: fwd_task<4>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
-          default: fwd_task<8>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
+          case 1: run_fwd<1>(F, tk, c0, Y, Y2, ldy, sm); break;
+          case 2: run_fwd<2>(F, tk, c0, Y, Y2, ldy, sm); break;
+          case 4: run_fwd<4>(F, tk, c0, Y, Y2, ldy, sm); break;
+          default: run_fwd<8>(F, tk, c0, Y, Y2, ldy, sm); break;
         }
       } else {
         switch (L.kb) {
-          case 1: bwd_task<1>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
-          case 2: bwd_task<2>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
-          case 4: bwd_task<4>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
-          default: bwd_task<8>(F, s, tk.y, c0, Y, Y2, ldy, sm); break;
+          case 1: run_bwd<1>(F, tk, c0, Y, Y2, ldy, sm); break;
+          case 2: run_bwd<2>(F, tk, c0, Y, Y2, ldy, sm); break;
+          case 4: run_bwd<4>(F, tk, c0, Y, Y2, ldy, sm); break;
+          default: run_bwd<8>(F, tk, c0, Y, Y2, ldy, sm); break;
         }
       }
       __syncthreads();
       if (threadIdx.x == 0) {
         __threadfence();
-        if (fwd) {
-          const int old = atomicAdd(ps.fdone + s, 1);
-          const int p = F.sup_parent[s];
-          if (old == ps.nft[s] * L.ncb - 1 && p >= 0) {
-            __threadfence();
-            atomicSub(ps.fpend + p, 1);
+        for (int k = 0; k < ne; ++k) {
+          const int s = ents ? ents[k] : tk.x;
+          if (fwd) {
+            const int old = atomicAdd(ps.fdone + s, 1);
+            const int p = F.sup_parent[s];
+            if (old == ps.nft[s] * L.ncb - 1 && p >= 0) {
+              __threadfence();
+              atomicSub(ps.fpend + p, 1);
+            }
+          } else {
+            atomicAdd(ps.bdone + s, 1);
           }
-        } else {
-          atomicAdd(ps.bdone + s, 1);
         }
       }
     }

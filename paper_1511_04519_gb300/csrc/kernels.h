@@ -22,9 +22,15 @@ struct DevFactor {
   const double* dinv;
   const double* pan_cm;
   const double* pan_rm;
+  const int32_t* pack;   // supernode lists of packed tasks
 };
 
 constexpr int kRowBlock = 32;  // panel rows (forward) / columns (backward) per task
+constexpr int kPackRows = 128; // rows (forward) / columns (backward) of a packed task
+constexpr int kPackMax = 64;   // supernodes per packed task
+// A task is int2 {s, first row/column} for one supernode, or, for many small
+// supernodes of one level, int2 {-1 - e, count}: pack[e .. e+count) lists them
+// and the task runs one thread per panel row (forward) / column (backward).
 
 // One tree level of the supernodal solve.  A task is (supernode, block of 32
 // panel rows) in the forward direction and (supernode, block of 32 panel

@@ -183,47 +183,96 @@ std::vector<double> group_lts(const std::vector<int32_t>& srcs, const int32_t* p
 // Per tree level: forward tasks (supernode, 32 panel rows), backward tasks
 // (supernode, 32 panel columns) and the column block.  Returns false on an
 // allocation failure.
-constexpr int kSolveSmemCap = 24 * 1024;  // keeps ~8 solve CTAs resident per SM
+constexpr int kSolveSmemCap = 24 * 1024 + 512;  // keeps ~8 solve CTAs resident per SM
 
 bool plan_levels(matex_ctx* c) {
   const Symbolic& S = c->S;
   const int nlev = (int)S.level_ptr.size() - 1;
   c->levels.resize(nlev);
   std::vector<int2> ft, bt;
+  std::vector<int32_t> pack;
+  std::vector<char> fpacked(S.nsup, 0), bpacked(S.nsup, 0);
   std::vector<size_t> fofs(nlev + 1), bofs(nlev + 1);
   int smem_need = 0;
+  // small supernodes of a level share one task: forward packs rows of panels
+  // at most 16 wide, backward packs columns of panels at most 384 rows long
+  constexpr int kPackLd = 384;
+  auto flush = [&](std::vector<int32_t>& cur, std::vector<int2>& out) {
+    if (cur.empty()) return;
+    out.push_back(make_int2(-1 - (int)pack.size(), (int)cur.size()));
+    pack.insert(pack.end(), cur.begin(), cur.end());
+    cur.clear();
+  };
   for (int l = 0; l < nlev; ++l) {
     LevelPlan& L = c->levels[l];
     fofs[l] = ft.size();
     bofs[l] = bt.size();
     int mw = 1, mwr = 1;
+    bool any_bpack = false;
+    std::vector<int32_t> cur;
+    int rows = 0;
     for (int k = S.level_ptr[l]; k < S.level_ptr[l + 1]; ++k) {
       const int s = S.level_sups[k];
       const int w = S.sup_first[s + 1] - S.sup_first[s];
       const int wr = (int)(S.sup_rowptr[s + 1] - S.sup_rowptr[s]);
       mw = std::max(mw, w);
-      mwr = std::max(mwr, wr);
-      for (int i0 = 0; i0 < wr; i0 += kRowBlock) ft.push_back(make_int2(s, i0));
-      for (int j0 = 0; j0 < w; j0 += kRowBlock) bt.push_back(make_int2(s, j0));
+      if (wr <= kPackRows && w <= 16) {
+        if (rows + wr > kPackRows || (int)cur.size() == kPackMax) { flush(cur, ft); rows = 0; }
+        cur.push_back(s);
+        rows += wr;
+        fpacked[s] = 1;
+      } else {
+        mwr = std::max(mwr, wr);
+        for (int i0 = 0; i0 < wr; i0 += kRowBlock) ft.push_back(make_int2(s, i0));
+      }
     }
+    flush(cur, ft);
+    int cols = 0, ldsum = 0;
+    for (int k = S.level_ptr[l]; k < S.level_ptr[l + 1]; ++k) {
+      const int s = S.level_sups[k];
+      const int w = S.sup_first[s + 1] - S.sup_first[s];
+      const int wr = (int)(S.sup_rowptr[s + 1] - S.sup_rowptr[s]);
+      if (w <= kRowBlock && wr <= kPackLd) {
+        if (cols + w > kPackRows || ldsum + wr > kPackLd || (int)cur.size() == kPackMax) {
+          flush(cur, bt);
+          cols = ldsum = 0;
+        }
+        cur.push_back(s);
+        cols += w;
+        ldsum += wr;
+        bpacked[s] = 1;
+        any_bpack = true;
+      } else {
+        mwr = std::max(mwr, wr);
+        for (int j0 = 0; j0 < w; j0 += kRowBlock) bt.push_back(make_int2(s, j0));
+      }
+    }
+    flush(cur, bt);
     L.nf = (int32_t)(ft.size() - fofs[l]);
     L.nb = (int32_t)(bt.size() - bofs[l]);
-    L.max_w = mw;
-    L.max_wr = mwr;
+    L.max_w = std::max(mw, kPackRows);
+    const int ld_need = std::max(mwr, any_bpack ? kPackLd : 1);
+    L.max_wr = ld_need;
     int kb = c->opts.col_block;
     if (kb <= 0) {
       // enough (task, column block) pairs to fill 152 SMs, else narrower blocks
       const int tasks = std::min(L.nf, L.nb * 4);
       kb = tasks >= 512 ? 8 : tasks >= 128 ? 4 : tasks >= 32 ? 2 : 1;
     }
-    while (kb > 1 && (size_t)mwr * kb * sizeof(double) > (size_t)kSolveSmemCap) kb /= 2;
+    while (kb > 1 && (size_t)ld_need * kb * sizeof(double) > (size_t)kSolveSmemCap) kb /= 2;
     L.kb = kb;
-    smem_need = std::max(smem_need, (int)(mwr * kb * sizeof(double)));
+    smem_need = std::max(smem_need, (int)(std::max(ld_need, L.max_w) * kb * sizeof(double)));
   }
   fofs[nlev] = ft.size();
   bofs[nlev] = bt.size();
   int2 *fd, *bd;
-  if (!c->upload(fd, ft.data(), ft.size()) || !c->upload(bd, bt.data(), bt.size())) return false;
+  int32_t* pk;
+  if (pack.empty()) pack.push_back(0);
+  if (!c->upload(fd, ft.data(), ft.size()) || !c->upload(bd, bt.data(), bt.size()) ||
+      !c->upload(pk, pack.data(), pack.size()))
+    return false;
+  c->fM.pack = pk;
+  c->fG.pack = pk;
   for (int l = 0; l < nlev; ++l) {
     c->levels[l].ftasks = fd + fofs[l];
     c->levels[l].btasks = bd + bofs[l];
@@ -269,8 +318,8 @@ bool plan_levels(matex_ctx* c) {
   for (int32_t s = 0; s < S.nsup; ++s) {
     const int w = S.sup_first[s + 1] - S.sup_first[s];
     const int wr = (int)(S.sup_rowptr[s + 1] - S.sup_rowptr[s]);
-    nft[s] = (wr + kRowBlock - 1) / kRowBlock;
-    nbt[s] = (w + kRowBlock - 1) / kRowBlock;
+    nft[s] = fpacked[s] ? 1 : (wr + kRowBlock - 1) / kRowBlock;
+    nbt[s] = bpacked[s] ? 1 : (w + kRowBlock - 1) / kRowBlock;
     if (S.sup_parent[s] >= 0) kids[S.sup_parent[s]]++;
   }
   if (!c->upload(c->sup_level_d, lev.data(), lev.size()) || !c->upload(c->nft_d, nft.data(), nft.size()) ||
@@ -850,7 +899,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     bool k = c->upload(dinv, Nm.dinv.data(), Nm.dinv.size()) &&
              c->upload(pcm, Nm.pan_cm.data(), Nm.pan_cm.size()) &&
              c->upload(prm, Nm.pan_rm.data(), Nm.pan_rm.size());
-    F = DevFactor{sup_first, sup_parent, sup_rowptr, sup_rows, pan_off, dinv, pcm, prm};
+    F = DevFactor{sup_first, sup_parent, sup_rowptr, sup_rows, pan_off, dinv, pcm, prm, nullptr};
     return k;
   };
   ok = ok && up_factor(NM, c->fM) && up_factor(NG, c->fG);
