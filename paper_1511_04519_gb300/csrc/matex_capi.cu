@@ -195,7 +195,8 @@ bool plan_levels(matex_ctx* c) {
   std::vector<size_t> fofs(nlev + 1), bofs(nlev + 1);
   int smem_need = 0;
   // small supernodes of a level share one task: forward packs rows of panels
-  // at most 16 wide, backward packs columns of panels at most 384 rows long
+  // at most 16 wide, backward packs columns of panels at most 16 wide and 64
+  // rows long (a longer panel keeps the 4-thread split dot of its own task)
   constexpr int kPackLd = 384;
   auto flush = [&](std::vector<int32_t>& cur, std::vector<int2>& out) {
     if (cur.empty()) return;
@@ -232,7 +233,7 @@ bool plan_levels(matex_ctx* c) {
       const int s = S.level_sups[k];
       const int w = S.sup_first[s + 1] - S.sup_first[s];
       const int wr = (int)(S.sup_rowptr[s + 1] - S.sup_rowptr[s]);
-      if (w <= kRowBlock && wr <= kPackLd) {
+      if (w <= 16 && wr <= 64) {
         if (cols + w > kPackRows || ldsum + wr > kPackLd || (int)cur.size() == kPackMax) {
           flush(cur, bt);
           cols = ldsum = 0;
