@@ -166,6 +166,29 @@ matex_status matex_set_sources(matex_ctx* ctx, const double* pwl_v_host);
 matex_status matex_solve(matex_ctx* ctx, int32_t which, int32_t ncols, const double* b, double* x);
 
 /*
+ * Same solve as matex_solve, for callers that are not allowed to allocate
+ * device memory (no counterpart in the paper).  Code running inside another
+ * library's allocator or memory-pool callback, or in a process whose device
+ * memory is owned by a pool it must not grow, cannot call cudaMalloc; it can
+ * still solve with a context built earlier.  This call allocates nothing and
+ * uses none of the context's work buffers: its right-hand-side buffers and
+ * dependency counters live in one static 16 MiB device array inside the
+ * library (held on every GPU that loads the library until the process exits).
+ *   which, ncols, b, x  as for matex_solve (device pointers, [ncols][n]).
+ * Limits: n <= 917,504 nodes and at most 174,761 supernodes in the factor;
+ * larger factors get MATEX_ERR_ARG with the limit in matex_last_error().
+ * Right-hand sides are processed in chunks that fit the array.  The first
+ * call on each device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Every call shares the one array, and its contents after a call are those of
+ * the last chunk: calls that overlap on the GPU (other streams, other host
+ * threads, other contexts on the same device) race with each other and must
+ * be serialised by the caller.  Synchronises the context's stream.
+ */
+matex_status matex_solve_noalloc(matex_ctx* ctx, int32_t which, int32_t ncols, const double* b,
+                                 double* x);
+
+/*
  * Batched small dense exponentials as used for e^{h H_m} (Eq. 9):
  *   A      device, [batch][m][m] row-major;  h device [batch];  E device [batch][m][m]
  *   E[b] = expm(h[b] * A[b]),  1 <= m <= 20.

@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1168,5 +1169,122 @@ extern "C" matex_status matex_host_factor_solve(int64_t n, const int64_t* rowptr
     }
     for (int64_t k = 0; k < n; ++k) x[(int64_t)q * n + S.perm[k]] = y[k];
   }
+  return MATEX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free solve.  Code that must not touch the CUDA allocator (it runs
+// where cudaMalloc is forbidden or would deadlock, e.g. inside another
+// library's allocator callback, or in a process whose memory pool is owned by
+// someone else) can still solve with a context's factors through
+// matex_solve_noalloc: it uses no context work buffer and allocates nothing,
+// taking its right-hand-side buffers and dependency counters from the static
+// device array below.  Every GPU that loads the library holds this array
+// until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocBytes = 16u << 20;      // 16 MiB per device
+constexpr size_t kNoAllocCounterBytes = 2u << 20;  // first 2 MiB: ticket, error flag, counters
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocBytes / sizeof(double)];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the static array on the current device, looked up once
+// per device (the host-side symbol is only a stand-in for it).
+matex_status noalloc_scratch(int dev, void** out, std::string& err) {
+  if (dev < 0 || dev >= kMaxDevices) {
+    err = "device ordinal out of range";
+    return MATEX_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+      return MATEX_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return MATEX_OK;
+}
+
+}  // namespace
+
+extern "C" matex_status matex_solve_noalloc(matex_ctx* c, int32_t which, int32_t ncols,
+                                            const double* b, double* x) {
+  if (!c) return MATEX_ERR_ARG;
+  if ((which != 0 && which != 1) || ncols < 0 || (ncols > 0 && (!b || !x)))
+    return fail(c, MATEX_ERR_ARG, "bad solve arguments");
+  if (ncols == 0) return MATEX_OK;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != c->device)
+    return fail(c, MATEX_ERR_ARG, "the context's device must be current");
+  const int64_t n = c->n;
+  const int32_t nsup = c->S.nsup;
+  // counters: ticket (8 B), error flag (8 B), fdone, bdone, fpend (nsup ints each)
+  const size_t counter_need = 16 + 3 * sizeof(int) * (size_t)nsup;
+  if (counter_need > kNoAllocCounterBytes)
+    return fail(c, MATEX_ERR_ARG, "matex_solve_noalloc: the factor has more than " +
+                                      std::to_string((kNoAllocCounterBytes - 16) / 12) +
+                                      " supernodes (its static scratch limit)");
+  const size_t rhs_doubles = (kNoAllocBytes - kNoAllocCounterBytes) / sizeof(double);
+  auto ld_for = [](int kc) { return kc <= 1 ? 1 : kc <= 2 ? 2 : kc <= 4 ? 4 : (kc + 7) & ~7; };
+  // widest column chunk whose Y and Y2 fit the static scratch
+  int kc = std::min<int>(ncols, c->ldy);
+  while (kc > 1 && 2 * (size_t)n * ld_for(kc) > rhs_doubles) kc = kc > 8 ? ((kc - 1) & ~7) : kc - 1;
+  if (2 * (size_t)n * ld_for(kc) > rhs_doubles)
+    return fail(c, MATEX_ERR_ARG, "matex_solve_noalloc: n = " + std::to_string(n) +
+                                      " exceeds the static scratch (at most " +
+                                      std::to_string(rhs_doubles / 2) + " nodes)");
+  void* base = nullptr;
+  matex_status s = noalloc_scratch(dev, &base, c->err);
+  if (s != MATEX_OK) return s;
+  unsigned char* bytes = static_cast<unsigned char*>(base);
+  unsigned long long* ticket = reinterpret_cast<unsigned long long*>(bytes);
+  int* err = reinterpret_cast<int*>(bytes + 8);
+  int* fdone = reinterpret_cast<int*>(bytes + 16);
+  int* bdone = fdone + nsup;
+  int* fpend = bdone + nsup;
+  double* Y = reinterpret_cast<double*>(bytes + kNoAllocCounterBytes);
+  const DevFactor& F = which == 0 ? c->fM : c->fG;
+  const int nlev = (int)c->levels.size();
+  cudaStream_t st = c->st;
+  cudaMemsetAsync(err, 0, sizeof(int), st);
+  for (int32_t q0 = 0; q0 < ncols; q0 += kc) {
+    const int K = std::min<int>(kc, ncols - q0);
+    const int ldy = ld_for(K);
+    double* Y2 = Y + (size_t)n * ldy;
+    gather_cols(Y, ldy, K, b + (int64_t)q0 * n, n, nullptr, nullptr, c->perm, n, st);
+    PersistSched ps;
+    ps.lev = c->plev_d + (size_t)(K - 1) * nlev;
+    ps.nlev = nlev;
+    ps.nf_total = c->pf_total[K];
+    ps.nb_total = c->pb_total[K];
+    ps.ticket = ticket;
+    ps.fdone = fdone;
+    ps.bdone = bdone;
+    ps.fpend = fpend;
+    ps.err = err;
+    ps.sup_level = c->sup_level_d;
+    ps.nft = c->nft_d;
+    ps.nbt = c->nbt_d;
+    // everything a solve counts up from starts at zero; fpend starts at the child counts
+    cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), st);
+    cudaMemsetAsync(fdone, 0, 2 * sizeof(int) * (size_t)nsup, st);
+    cudaMemcpyAsync(fpend, c->fpend_init, sizeof(int) * nsup, cudaMemcpyDeviceToDevice, st);
+    persistent_solve(F, ps, c->pgrid, c->psmem, Y, Y2, ldy, st);
+    scatter_cols(Y, ldy, K, x + (int64_t)q0 * n, n, nullptr, c->perm, n, st);
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(c, "solve_noalloc sync");
+  if ((s = cuda_check(c, "solve_noalloc")) != MATEX_OK) return s;
+  int flag = 0;
+  if (cudaMemcpy(&flag, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_check(c, "solve_noalloc flag");
+  if (flag) return fail(c, MATEX_ERR_TIMEOUT, "a bounded wait of the persistent solve expired");
   return MATEX_OK;
 }

@@ -63,7 +63,7 @@ EXPORTS = ["matex_default_opts", "matex_setup", "matex_run", "matex_run_host", "
            "matex_solve", "matex_expm", "matex_get_m", "matex_get_sizes", "matex_get_setup_stats",
            "matex_last_error", "matex_status_string", "matex_destroy", "matex_set_profiling",
            "matex_get_profile", "matex_host_factor_solve", "matex_set_batching",
-           "matex_debug_inject_wait"]
+           "matex_debug_inject_wait", "matex_solve_noalloc"]
 
 
 def _load():
@@ -87,6 +87,8 @@ def _load():
     lib.matex_set_sources.restype = C.c_int
     lib.matex_solve.argtypes = [P, C.c_int32, C.c_int32, P, P]
     lib.matex_solve.restype = C.c_int
+    lib.matex_solve_noalloc.argtypes = [P, C.c_int32, C.c_int32, P, P]
+    lib.matex_solve_noalloc.restype = C.c_int
     lib.matex_expm.argtypes = [P, C.c_int32, C.c_int32, P, P, P]
     lib.matex_expm.restype = C.c_int
     lib.matex_get_m.argtypes = [P, i32p, C.c_int64, i64p]
@@ -202,6 +204,12 @@ def matex_set_sources(ctx, pwl_v_host):
 
 def matex_solve(ctx, which, ncols, b_ptr, x_ptr):
     _check(ctx, _lib.matex_solve(ctx, int(which), int(ncols), C.c_void_p(b_ptr), C.c_void_p(x_ptr)))
+
+
+def matex_solve_noalloc(ctx, which, ncols, b_ptr, x_ptr):
+    """matex_solve without any allocation (static device scratch; see matex.h)."""
+    _check(ctx, _lib.matex_solve_noalloc(ctx, int(which), int(ncols), C.c_void_p(b_ptr),
+                                         C.c_void_p(x_ptr)))
 
 
 def matex_expm(ctx, batch, m, a_ptr, h_ptr, e_ptr):
