@@ -157,6 +157,42 @@ def reference_arm(args):
     return 0
 
 
+def ncu_case(what: str) -> int:
+    """The bench grid restricted to groups 0-7 (about 2.5 GB on the device, solve
+    panels still larger than L2): one warm call, then the profiled call."""
+    import numpy as np
+    import torch
+
+    import gridgen
+    from paper_1511_04519_gb300 import build as B
+    B.build()
+    from paper_1511_04519_gb300 import matex as M
+    p = gridgen.config1()
+    groups = 8
+    sel = p.src_group < groups
+    off = np.concatenate([[0], np.cumsum(np.diff(p.pwl_off)[sel])]).astype(np.int32)
+    q = gridgen.with_sources(p, p.src_node[sel], off, p.pwl_t.reshape(-1, 3)[sel].ravel(),
+                             p.pwl_v.reshape(-1, 3)[sel].ravel(), p.src_group[sel], groups)
+    sim = M.Sim(q)
+    if what == "solve":
+        k = 16
+        b = torch.randn(k, p.n, dtype=torch.float64, device="cuda")
+        x = torch.empty_like(b)
+        M.matex_solve(sim.ctx, 0, k, b.data_ptr(), x.data_ptr())
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        M.matex_solve(sim.ctx, 0, k, b.data_ptr(), x.data_ptr())
+    else:
+        out = sim.run()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        sim.run(out)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"ncu_case": what, "max_memory_gb": torch.cuda.max_memory_allocated() / 1e9}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -169,12 +205,17 @@ def main():
     ap.add_argument("--no-serial", action="store_true")
     ap.add_argument("--profile-step", action="store_true",
                     help="warm up, run one step inside cudaProfilerStart/Stop, print its stats")
+    ap.add_argument("--ncu-case", choices=["solve", "run"], default=None,
+                    help="reduced case for full ncu captures: the same grid with 8 groups; "
+                         "one warm call, then one call inside cudaProfilerStart/Stop")
     args = ap.parse_args()
     if args.cpu_oracle_sample:
         print(json.dumps(cpu_oracle_sample(args.cpu_oracle_sample)))
         return 0
     if args.impl == "reference":
         return reference_arm(args)
+    if args.ncu_case:
+        return ncu_case(args.ncu_case)
     args.warmup = max(args.warmup, 3)
 
     import numpy as np
