@@ -21,20 +21,29 @@ __device__ __forceinline__ double pwl_eval(const double* t, const double* v, int
 
 __global__ void input_rhs_kernel(double* __restrict__ Y, int ldy, int K, RoundCols rc,
                                  SourceTable src) {
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= 2 * K) return;
-  const bool slope = slot >= K;
-  const int q = slope ? slot - K : slot;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= K) return;
   const int g = rc.group[q];
   const double l0 = rc.l0[q], L = rc.len[q], l1 = l0 + L;
   for (int p = src.grp_ptr[g]; p < src.grp_ptr[g + 1]; ++p) {
     const int s = src.grp_src[p];
     const int o = src.pwl_off[s], np = src.pwl_off[s + 1] - o;
     const double u0 = pwl_eval(src.pwl_t + o, src.pwl_v + o, np, l0);
-    double val = u0;
-    if (slope) val = (pwl_eval(src.pwl_t + o, src.pwl_v + o, np, l1) - u0) / L;
-    Y[(int64_t)src.node[s] * ldy + slot] += val;
+    const double val = (pwl_eval(src.pwl_t + o, src.pwl_v + o, np, l1) - u0) / L;
+    Y[(int64_t)src.node[s] * ldy + q] += val;
   }
+}
+
+__global__ void advance_z_kernel(double* __restrict__ Z, const double* __restrict__ Zp,
+                                 const double* __restrict__ X, int64_t gstride, RoundCols rc,
+                                 int64_t n) {
+  const int q = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t g = rc.group[q];
+  const int64_t k = g * gstride + i;
+  if (rc.seg[q] == 0) Z[k] = X[k];
+  else Z[k] = fma(rc.lprev[q], Zp[k], Z[k]);
 }
 
 __global__ void initial_rhs_kernel(double* __restrict__ Y, int ldy, int K, SourceTable src,
@@ -517,8 +526,14 @@ expm_batch_kernel(int m, const double* __restrict__ A, const double* __restrict_
 void build_input_rhs(double* Y, int ldy, int K, const RoundCols& rc, const SourceTable& src,
                      int64_t n, cudaStream_t st) {
   cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)n * ldy, st);
-  const int slots = 2 * K;
-  input_rhs_kernel<<<(slots + 127) / 128, 128, 0, st>>>(Y, ldy, K, rc, src);
+  input_rhs_kernel<<<(K + 127) / 128, 128, 0, st>>>(Y, ldy, K, rc, src);
+}
+
+void advance_z(double* Z, const double* Zp, const double* X, int64_t gstride, const RoundCols& rc,
+               int K, int64_t n, cudaStream_t st) {
+  if (K <= 0) return;
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)K);
+  advance_z_kernel<<<grid, 256, 0, st>>>(Z, Zp, X, gstride, rc, n);
 }
 
 void build_initial_rhs(double* Y, int ldy, int K, const SourceTable& src, const int32_t* groups,

@@ -99,6 +99,7 @@ struct RoundCols {
   const double* l0;        // segment start
   const double* len;       // segment length L
   const double* hfirst;    // offset of the first output in the segment (L if none)
+  const double* lprev;     // length of the group's previous segment (0 for the first)
   const int32_t* obeg;     // first output index in the segment
   const int32_t* nout;     // outputs in the segment
   const int64_t* segid;    // global (group, segment) index
@@ -113,9 +114,12 @@ struct SourceTable {
   const double* pwl_v;
 };
 
-// Y[:, 2q] = B_k u_k(l0), Y[:, 2q+1] = B_k (u_k(l0+L) - u_k(l0)) / L  (Y zeroed here)
+// Y[:, q] = B_k (u_k(l0+L) - u_k(l0)) / L, the input slope on the segment (Y zeroed here)
 void build_input_rhs(double* Y, int ldy, int K, const RoundCols& rc, const SourceTable& src,
                      int64_t n, cudaStream_t st);
+// z_k = x_k for a group's first segment, else z_k += lprev * z'_k
+void advance_z(double* Z, const double* Zp, const double* X, int64_t gstride, const RoundCols& rc,
+               int K, int64_t n, cudaStream_t st);
 // Y[:, q] = B_k u_k(t) for t = 0 per group (initial states)
 void build_initial_rhs(double* Y, int ldy, int K, const SourceTable& src, const int32_t* groups,
                        int64_t n, cudaStream_t st);

@@ -89,7 +89,9 @@ struct matex_ctx {
   double* pwl_v_d = nullptr;
   // round tables
   int32_t *rc_group = nullptr, *rc_seg = nullptr, *rc_obeg = nullptr, *rc_nout = nullptr;
-  double *rc_l0 = nullptr, *rc_len = nullptr, *rc_hfirst = nullptr;
+  double *rc_l0 = nullptr, *rc_len = nullptr, *rc_hfirst = nullptr, *rc_lprev = nullptr;
+  std::vector<int32_t> init_groups;   // groups whose input is non-zero at t = 0
+  int32_t* init_groups_d = nullptr;
   int64_t* rc_segid = nullptr;
   int32_t* replay_d = nullptr;
   // work buffers
@@ -167,6 +169,26 @@ matex_status cuda_check(matex_ctx* c, const char* where) {
 thread_local std::string g_setup_err;
 
 int roundup8(int x) { return (x + 7) & ~7; }
+
+// Value of one PWL source at time x: held before the first and after the last
+// breakpoint, linear in between (the same rule as the device evaluation).
+double pwl_value(const double* t, const double* v, int np, double x) {
+  if (x <= t[0]) return v[0];
+  if (x >= t[np - 1]) return v[np - 1];
+  int j = 0;
+  while (j + 1 < np && t[j + 1] <= x) ++j;
+  return (v[j + 1] - v[j]) / (t[j + 1] - t[j]) * (x - t[j]) + v[j];
+}
+
+// True when every source of the group injects exactly zero at time x.
+bool group_input_zero(const std::vector<int32_t>& srcs, const int32_t* pwl_off, const double* pwl_t,
+                      const double* pwl_v, double x) {
+  for (int32_t s : srcs) {
+    const int o = pwl_off[s], np = pwl_off[s + 1] - o;
+    if (pwl_value(pwl_t + o, pwl_v + o, np, x) != 0.0) return false;
+  }
+  return true;
+}
 
 // Local transition spots of one group: its sources' breakpoints inside (0, T)
 // plus 0 and T, sorted and unique (Sec. 3.1).
@@ -373,6 +395,7 @@ RoundCols round_cols(matex_ctx* c, const Round& r) {
   rc.l0 = c->rc_l0 + r.begin;
   rc.len = c->rc_len + r.begin;
   rc.hfirst = c->rc_hfirst + r.begin;
+  rc.lprev = c->rc_lprev + r.begin;
   rc.obeg = c->rc_obeg + r.begin;
   rc.nout = c->rc_nout + r.begin;
   rc.segid = c->rc_segid + r.begin;
@@ -494,18 +517,28 @@ matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
     prof_end(c, e, P_OTHER, 1, 0.0, 8.0 * nd * c->n_times);
     launches++;
   }
-  // each group's own DC state at t = 0 (Local_Initial_Solution)
-  const int ng = (int)c->sel_groups.size();
+  // per-run state starts at zero: x, z, z' of every group, the segment records
+  {
+    const size_t gb = sizeof(double) * (size_t)std::max(c->n_groups, 1) * (size_t)n;
+    cudaMemsetAsync(c->Xb, 0, gb, st);
+    cudaMemsetAsync(c->Zb, 0, gb, st);
+    cudaMemsetAsync(c->Zpb, 0, gb, st);
+    cudaMemsetAsync(c->m_rec, 0, sizeof(int32_t) * std::max<int64_t>(1, c->n_segments), st);
+    cudaMemsetAsync(c->st_rec, 0, sizeof(int32_t) * std::max<int64_t>(1, c->n_segments), st);
+  }
+  // each group's own DC state at t = 0 (Local_Initial_Solution); groups with
+  // zero input at t = 0 start from x = 0
+  const int ng = (int)c->init_groups.size();
   for (int g0 = 0; g0 < ng; g0 += c->ldy) {
     const int K = std::min(c->ldy, ng - g0);
     e = prof_begin(c);
-    build_initial_rhs(c->Y, c->ldy, K, c->src, c->sel_groups_d + g0, n, st);
+    build_initial_rhs(c->Y, c->ldy, K, c->src, c->init_groups_d + g0, n, st);
     prof_end(c, e, P_OTHER, 2, 0.0, 8.0 * nd * c->ldy);
     launches += 2;
     solve(c->fG, K);
     sweepsG++;
     e = prof_begin(c);
-    scatter_cols(c->Y, c->ldy, K, c->Xb, n, c->sel_groups_d + g0, nullptr, n, st);
+    scatter_cols(c->Y, c->ldy, K, c->Xb, n, c->init_groups_d + g0, nullptr, n, st);
     moved(e, 1, K, false);
     e = prof_begin(c);
     add_row_sum(c->Xp, c->Y, c->ldy, K, n, st);
@@ -519,17 +552,19 @@ matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
     const Round& r = rounds[ri];
     const int K = r.K;
     RoundCols rc = round_cols(c, r);
-    // z and z' (two columns per group), then w = G^{-1} C z'   (Eq. 5/6)
+    // z = G^{-1} B u(l_j) carried forward (u is continuous and linear on every
+    // segment: z_j = z_{j-1} + L_{j-1} z'_{j-1}, z_0 = x(0)); then
+    // z' = G^{-1} B s_j and w = G^{-1} C z'   (Eq. 5/6)
     e = prof_begin(c);
+    advance_z(c->Zb, c->Zpb, c->Xb, n, rc, K, n, st);
     build_input_rhs(c->Y, c->ldy, K, rc, c->src, n, st);
-    prof_end(c, e, P_OTHER, 2, 0.0, 8.0 * nd * c->ldy);
-    launches += 2;
-    solve(c->fG, 2 * K);
+    prof_end(c, e, P_OTHER, 3, 2.0 * nd * K, 24.0 * nd * K + 8.0 * nd * c->ldy);
+    launches += 3;
+    solve(c->fG, K);
     e = prof_begin(c);
-    scatter_cols(c->Y, c->ldy, K, c->Zb, n, rc.group, nullptr, n, st);
-    scatter_cols(c->Y + K, c->ldy, K, c->Zpb, n, rc.group, nullptr, n, st);
+    scatter_cols(c->Y, c->ldy, K, c->Zpb, n, rc.group, nullptr, n, st);
     gather_cols(c->Y, c->ldy, K, c->Zpb, n, rc.group, c->c_perm, nullptr, n, st);
-    moved(e, 3, K, true);
+    moved(e, 2, K, true);
     solve(c->fG, K);
     e = prof_begin(c);
     scatter_cols(c->Y, c->ldy, K, c->Wb, n, rc.group, nullptr, n, st);
@@ -785,19 +820,30 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     if (o.group_select < 0 || o.group_select == g) c->sel_groups.push_back(g);
   std::vector<std::vector<int32_t>> gsrc(n_groups);
   for (int32_t s = 0; s < n_src; ++s) gsrc[src_group[s]].push_back(s);
-  struct Seg { int32_t g, j, obeg, nout; double l0, len, hfirst; int64_t id; };
+  // A segment whose group has injected nothing since t = 0 and injects nothing
+  // on it has x = z = z' = w = 0 and contributes exactly zero: it is recorded
+  // (m = 0) but never solved.  A group whose input is zero at t = 0 starts
+  // from x = 0 without a solve.
+  struct Seg { int32_t g, j, obeg, nout; double l0, len, hfirst, lprev; int64_t id; bool zero; };
   std::vector<std::vector<Seg>> per_group;
   int64_t segid = 0;
   size_t max_segs = 0;
+  std::vector<int32_t> init_groups;
   for (int32_t g : c->sel_groups) {
     std::vector<double> lts = group_lts(gsrc[g], pwl_off, pwl_t, c->T);
     std::vector<Seg> segs;
+    bool quiet = group_input_zero(gsrc[g], pwl_off, pwl_t, pwl_v, 0.0);
+    if (!quiet) init_groups.push_back(g);
     for (size_t j = 0; j + 1 < lts.size(); ++j) {
       Seg sg;
       sg.g = g;
       sg.j = (int32_t)j;
       sg.l0 = lts[j];
       sg.len = lts[j + 1] - lts[j];
+      sg.lprev = j > 0 ? lts[j] - lts[j - 1] : 0.0;
+      quiet = quiet && group_input_zero(gsrc[g], pwl_off, pwl_t, pwl_v, lts[j]) &&
+              group_input_zero(gsrc[g], pwl_off, pwl_t, pwl_v, lts[j + 1]);
+      sg.zero = quiet;
       // outputs with l_j < t_o <= l_{j+1}
       int ob = -1, cnt = 0;
       int o0 = std::max(0, (int)std::floor(lts[j] / dt_out) - 1);
@@ -820,7 +866,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   }
   c->n_segments = segid;
   std::vector<int32_t> h_group, h_seg, h_obeg, h_nout;
-  std::vector<double> h_l0, h_len, h_hfirst;
+  std::vector<double> h_l0, h_len, h_hfirst, h_lprev;
   std::vector<int64_t> h_segid;
   int Kmax = 1;
   for (size_t r = 0; r < max_segs; ++r) {
@@ -829,7 +875,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     rd.obeg_min = c->n_times;
     rd.oend_max = 0;
     for (auto& segs : per_group) {
-      if (r >= segs.size()) continue;
+      if (r >= segs.size() || segs[r].zero) continue;
       const Seg& sg = segs[r];
       h_group.push_back(sg.g);
       h_seg.push_back(sg.j);
@@ -838,6 +884,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
       h_l0.push_back(sg.l0);
       h_len.push_back(sg.len);
       h_hfirst.push_back(sg.hfirst);
+      h_lprev.push_back(sg.lprev);
       h_segid.push_back(sg.id);
       if (sg.nout > 0) {
         rd.obeg_min = std::min(rd.obeg_min, sg.obeg);
@@ -846,8 +893,9 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     }
     rd.K = (int32_t)h_group.size() - rd.begin;
     Kmax = std::max(Kmax, rd.K);
-    c->rounds.push_back(rd);
+    if (rd.K > 0) c->rounds.push_back(rd);
   }
+  c->init_groups = init_groups;
   c->Kmax = Kmax;
   c->h_nout_all = h_nout;
   c->h_segid_all = h_segid;
@@ -940,6 +988,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     c->src = SourceTable{gp, gsd, nd_d, po, pt, c->pwl_v_d};
   }
   ok = ok && c->upload(c->sel_groups_d, c->sel_groups.data(), c->sel_groups.size());
+  ok = ok && c->upload(c->init_groups_d, c->init_groups.data(), c->init_groups.size());
   ok = ok && c->upload(c->rc_group, h_group.data(), h_group.size()) &&
        c->upload(c->rc_seg, h_seg.data(), h_seg.size()) &&
        c->upload(c->rc_obeg, h_obeg.data(), h_obeg.size()) &&
@@ -947,10 +996,11 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
        c->upload(c->rc_l0, h_l0.data(), h_l0.size()) &&
        c->upload(c->rc_len, h_len.data(), h_len.size()) &&
        c->upload(c->rc_hfirst, h_hfirst.data(), h_hfirst.size()) &&
+       c->upload(c->rc_lprev, h_lprev.data(), h_lprev.size()) &&
        c->upload(c->rc_segid, h_segid.data(), h_segid.size());
   if (!c->replay.empty()) ok = ok && c->upload(c->replay_d, c->replay.data(), c->replay.size());
   // work buffers
-  c->ldy = roundup8(std::max({2 * Kmax, 8, std::min<int>(n_groups, 256)}));
+  c->ldy = roundup8(std::max({Kmax, 8, std::min<int>(n_groups, 256)}));
   ok = ok && plan_levels(c);
   c->nchunks = (int)((n + kChunk - 1) / kChunk);
   const size_t G = (size_t)std::max(n_groups, 1);
