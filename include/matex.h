@@ -66,6 +66,8 @@ typedef struct matex_opts {
   int32_t strict;          /* 1: return MATEX_ERR_NOCONV when m_max is reached unconverged */
   int32_t solve_mode;      /* 0: one persistent launch per triangular-solve pair, tasks ordered
                               by dependency counters (default); 1: one launch per tree level */
+  int32_t tape;            /* 1: every run keeps each segment's Krylov basis, solve outputs and
+                              Hessenberg on the device so that matex_grad can follow it */
 } matex_opts;
 
 /* Counters and timings of the last matex_run (or of setup for the setup_* fields). */
@@ -153,6 +155,27 @@ matex_status matex_run_host(matex_ctx* ctx, const double* pwl_v_host, double* x_
  * Both give the same result up to rounding.
  */
 matex_status matex_set_batching(matex_ctx* ctx, int32_t one_group_at_a_time);
+
+/*
+ * Vector-Jacobian product of the last run's outputs (no counterpart in the
+ * paper; the discrete adjoint of Alg. 2 / Alg. 1 as run): given
+ *   xbar   device, [N+1][n_rows], dL/dx_out for the run's output rows,
+ * writes
+ *   dc     device [n], dL/dc_i (original node order), and
+ *   damp   device [n_src], dL/da_s for a scale a_s multiplying source s's currents
+ *          (evaluated at a_s = 1, i.e. d/da of the current pwl_v).
+ * The Krylov dimensions are those of the last run (as if replayed).  Requires
+ * a context set up with opts.tape = 1 and a preceding matex_run.  Reuses the
+ * forward's factors (both matrices are symmetric).  Synchronises the stream.
+ */
+matex_status matex_grad(matex_ctx* ctx, const double* xbar, double* dc, double* damp);
+
+/*
+ * Replace the node capacitances (host [n], original order, all > 0): C + gamma G
+ * is refactorised on the host with the existing symbolic structure and its
+ * panels re-uploaded (G is unchanged).
+ */
+matex_status matex_set_caps(matex_ctx* ctx, const double* c);
 
 /* Replace the source currents (host, layout of pwl_v at setup). */
 matex_status matex_set_sources(matex_ctx* ctx, const double* pwl_v_host);

@@ -79,33 +79,41 @@ def _with_c(p, c):
     return q
 
 
-def loss_and_grad(p, obs, theta, c=None, amp_scale=None, replay_m=None):
-    """Returns (L, dL/dc [n], dL/damp_scale [n_src], m sequence per group)."""
+def forward_tape(p, obs, c=None, amp_scale=None, replay_m=None, groups=None):
+    """Oracle forward (all nodes per group) keeping each segment's data; returns
+    (X at the observed rows, tapes, m per group, factors, x_dc)."""
     c = p.c if c is None else np.asarray(c, dtype=np.float64)
     amp = np.ones(p.n_src) if amp_scale is None else np.asarray(amp_scale, dtype=np.float64)
     pc = _with_c(p, c)
     fac = R.factorize(pc, c)
     t_out = R.output_times(p)
     obs = np.asarray(obs)
-    # ---- forward with a tape, all nodes ----------------------------------------
     x_dc = fac.solve_G(p.dc_inject)
     X = np.zeros((t_out.shape[0], obs.shape[0]))
     X += x_dc[obs][None, :]
-    tapes, ms = [], []
-    for k in range(p.n_groups):
+    tapes, ms = {}, {}
+    for k in (range(p.n_groups) if groups is None else groups):
         keep = []
         rm = None if replay_m is None else replay_m[k]
         Xg = np.zeros((t_out.shape[0], p.n))
         log = R.run_group(pc, fac, k, Xg, t_out, replay_m=rm, amp_scale=amp, keep=keep)
         X += Xg[:, obs]
-        tapes.append((log.lts, keep))
-        ms.append(list(log.m))
-    L, Gobs = hinge_loss(X, p.vdd, theta, p.dt_out)
-    # ---- reverse ------------------------------------------------------------------
+        tapes[k] = (log.lts, keep)
+        ms[k] = list(log.m)
+    return X, tapes, ms, fac
+
+
+def reverse(p, obs, fac, c, tapes, Gobs):
+    """Hand-written reverse of the taped groups for output adjoints Gobs
+    ((N+1) x n_obs, dL/dX at the observed rows); returns (cbar, abar) summed
+    over the taped groups."""
+    c = np.asarray(c, dtype=np.float64)
+    t_out = R.output_times(p)
+    obs = np.asarray(obs)
     cbar = np.zeros(p.n)
     abar = np.zeros(p.n_src)
     gam = p.gamma
-    for k, (lts, keep) in enumerate(tapes):
+    for k, (lts, keep) in tapes.items():
         src = R.group_sources(p, k)
         outs = R.segment_outputs(lts, t_out)
         xbar_next = np.zeros(p.n)
@@ -178,4 +186,13 @@ def loss_and_grad(p, obs, theta, c=None, amp_scale=None, replay_m=None):
         v0 = source_values(p, lts[0])
         for s in src:
             abar[s] += v0[s] * u_bar[p.src_node[s]]
-    return L, cbar, abar, ms
+    return cbar, abar
+
+
+def loss_and_grad(p, obs, theta, c=None, amp_scale=None, replay_m=None):
+    """Returns (L, dL/dc [n], dL/damp_scale [n_src], m sequence per group)."""
+    c = p.c if c is None else np.asarray(c, dtype=np.float64)
+    X, tapes, ms, fac = forward_tape(p, obs, c=c, amp_scale=amp_scale, replay_m=replay_m)
+    L, Gobs = hinge_loss(X, p.vdd, theta, p.dt_out)
+    cbar, abar = reverse(p, obs, fac, c, tapes, Gobs)
+    return L, cbar, abar, [ms[k] for k in range(p.n_groups)]

@@ -76,7 +76,7 @@ recombine_kernel(double* __restrict__ Xp, int64_t n, const double* __restrict__ 
     if (lo >= hi) continue;
     covered |= ((1u << (hi - lo)) - 1u) << (lo - o0);
     const int64_t g = rc.group[q];
-    const double* __restrict__ vcol = Vb + g * vstride + i;
+    const double* __restrict__ vcol = Vb + (int64_t)rc.vslot[q] * vstride + i;
     const double z = Z[g * gstride + i], zp = Zp[g * gstride + i], w = W[g * gstride + i];
     const double l0 = rc.l0[q];
     const double* __restrict__ cq = coef + (int64_t)q * ldo * kCoefLd;
@@ -110,7 +110,7 @@ __global__ void next_state_kernel(double* __restrict__ X, const double* __restri
   const int m = mcol[q];
   const double L = rc.len[q];
   double s = Z[g * gstride + i] + L * Zp[g * gstride + i] - W[g * gstride + i];
-  const double* __restrict__ base = Vb + g * vstride + i;
+  const double* __restrict__ base = Vb + (int64_t)rc.vslot[q] * vstride + i;
   for (int j = 0; j < m; ++j) s = fma(base[(int64_t)j * n], yend[q * kMaxM + j], s);
   X[g * gstride + i] = s;
 }

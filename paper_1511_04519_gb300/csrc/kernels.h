@@ -95,6 +95,8 @@ void scatter_cols(const double* Y, int ldy, int ncols, double* dst, int64_t stri
 // Per-column metadata of one segment round (device arrays, length K).
 struct RoundCols {
   const int32_t* group;    // group of the column
+  const int32_t* vslot;    // slot of its Krylov basis: the group, or the segment record
+                           // when every segment keeps its basis (adjoint tape)
   const int32_t* seg;      // segment index inside the group
   const double* l0;        // segment start
   const double* len;       // segment length L
@@ -124,10 +126,10 @@ void advance_z(double* Z, const double* Zp, const double* X, int64_t gstride, co
 void build_initial_rhs(double* Y, int ldy, int K, const SourceTable& src, const int32_t* groups,
                        int64_t n, cudaStream_t st);
 
-// Krylov start: v = x - z + w written to V_k[0]; partial sums of |v|^2
+// Krylov start: v = x - z + w written to V[vslot][0]; partial sums of |v|^2
 void krylov_start(double* Vbase, int64_t vstride, const double* X, const double* Z,
-                  const double* W, int64_t gstride, const int32_t* groups, int K, int64_t n,
-                  double* partials, int nchunks, cudaStream_t st);
+                  const double* W, int64_t gstride, const int32_t* groups, const int32_t* vslots,
+                  int K, int64_t n, double* partials, int nchunks, cudaStream_t st);
 
 // Partial dot products of basis slot wslot (w) with slots first..first+nb-1
 // for each iterating column; partials laid out [K][kMaxB][nchunks].
@@ -194,5 +196,85 @@ void add_row_sum(double* Xp, const double* Y, int ldy, int K, int64_t n, cudaStr
 // out[o][r] = Xp[o][map[r]]
 void permute_out(double* out, const double* Xp, const int32_t* map, int64_t nrows, int64_t n,
                  int n_times, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Adjoint (reverse of the batched forward; see k_adjoint.cu)
+// ---------------------------------------------------------------------------
+// Per-column work slots: qbar_0..qbar_{kMaxB-1}, then zbar, zbar', wbar, rbar, abar.
+constexpr int kWZ = kMaxB, kWZp = kMaxB + 1, kWW = kMaxB + 2, kWR = kMaxB + 3, kWA = kMaxB + 4;
+constexpr int kWSlots = kMaxB + 5;
+
+// One reverse round: the columns of a forward round, with the forward tape.
+struct AdjRound {
+  const int32_t* rec;     // per column: tape record (its basis slot)
+  const int32_t* group;
+  const int32_t* m;       // per column Krylov dimension
+  const int32_t* obeg;
+  const int32_t* nout;
+  const int32_t* seg;
+  const double* l0;
+  const double* len;
+  const double* hfirst;
+  const double* V;        // tape bases [records][kMaxB][n]
+  int64_t vstride;
+  const double* A;        // tape solve outputs a_k [records][kMaxM][n]
+  int64_t astride;
+  const double* Zp;       // tape z' [records][n]
+  const double* Ht;       // tape Hessenbergs [records][kMaxB][kMaxM]
+  const double* beta;     // tape norms [records]
+  int64_t n;
+  double dt;
+};
+struct AdjWork {
+  double* work;           // [K][kWSlots][n]
+  int64_t wstride;
+  double* XB;             // [G][n] xbar flowing into the group's previous segment
+  double* CARRY;          // [G][n] zbar carried to the previous segment (z_{j+1} = z_j + L_j z'_j)
+  double* CB;             // [G][n] capacitance adjoint per group
+};
+// out[q][i] = a_q . b_q[i] for i < nb, a_q = a + a_idx[q]*a_stride + a_slot*n, likewise b
+struct AdjDots {
+  const double* a;
+  int64_t a_stride;
+  const int32_t* a_idx;
+  int a_slot;
+  const double* b;
+  int64_t b_stride;
+  const int32_t* b_idx;
+  int b_slot;
+  const int32_t* cols;    // columns to process (null: 0..K-1)
+};
+
+void tape_small(const SmallState& ss, const RoundCols& rc, int K, double* THt, double* Tbeta,
+                cudaStream_t st);
+size_t adj_small_shared_bytes();
+void adj_set_limits();
+void adj_obs(const AdjRound& ar, int K, const double* xbar, const int32_t* map, int nrows,
+             double* ybo, int ldo, double* S1, double* S2, cudaStream_t st);
+void adj_dots(const AdjDots& d, int K, int nb, int64_t n, double* partials, int nchunks, double* out,
+              cudaStream_t st);
+void adj_small(const AdjRound& ar, int K, double gamma, const double* ybo, int ldo,
+               const double* ybL, double* yout, double* yL, double* Htbar, double* betabar,
+               cudaStream_t st);
+void adj_build(const AdjRound& ar, const AdjWork& aw, int K, const double* yL, const double* xbar,
+               const int32_t* map, int nrows, const double* yout, int ldo, const double* S1,
+               const double* S2, cudaStream_t st);
+void adj_rbar(const AdjRound& ar, const AdjWork& aw, const int32_t* act, int Ka, int k,
+              const double* d1, const double* Htbar, cudaStream_t st);
+void adj_abar(const AdjRound& ar, const AdjWork& aw, const int32_t* act, int Ka, int k,
+              const double* hdot, const double* Htbar, cudaStream_t st);
+void adj_after_m(const AdjRound& ar, const AdjWork& aw, const int32_t* act, int Ka, int k,
+                 const double* Y, int ldy, const double* c, cudaStream_t st);
+void adj_vbar(const AdjRound& ar, const AdjWork& aw, int K, const double* d0, const double* betabar,
+              cudaStream_t st);
+void adj_after_w(const AdjRound& ar, const AdjWork& aw, int K, const double* Y, int ldy,
+                 const double* c, cudaStream_t st);
+void adj_sources(const AdjRound& ar, int K, const SourceTable& src, const double* Y, int ldy,
+                 double* ampbar, cudaStream_t st);
+void adj_init_sources(const int32_t* groups, int K, const SourceTable& src, const double* Y, int ldy,
+                      double* ampbar, cudaStream_t st);
+void adj_x0_obs(const int32_t* groups, int K, double* XB, int64_t n, const double* xbar0,
+                const int32_t* map, int nrows, cudaStream_t st);
+void adj_csum(const double* CB, int G, int64_t n, const int32_t* perm, double* dc, cudaStream_t st);
 
 }  // namespace matex

@@ -71,6 +71,15 @@ struct matex_ctx {
   size_t psmem = 0;
   int pgrid = 0;
   bool inject_wait = false;  // test hook: a dependency that never completes
+  // adjoint tape (opts.tape): per record (non-zero segment) basis slot = record
+  int64_t n_records = 0;
+  bool taped = false;        // a run with the tape has completed
+  double *TA = nullptr, *TZp = nullptr, *THt = nullptr, *Tbeta = nullptr;
+  // adjoint work
+  double *AW = nullptr, *XBg = nullptr, *CARRYg = nullptr, *CBg = nullptr;
+  double *YBO = nullptr, *YOUT = nullptr, *YBL = nullptr, *YL = nullptr, *HTB = nullptr;
+  double *BETAB = nullptr, *D1 = nullptr, *HD = nullptr, *D0 = nullptr, *S1 = nullptr, *S2 = nullptr;
+  int32_t *iota_d = nullptr, *mrec_d = nullptr, *act_d = nullptr;
   std::vector<Round> rounds;          // batched: segment r of every group per round
   std::vector<Round> serial_rounds;   // one group at a time: one column per round
   bool serial = false;
@@ -87,8 +96,14 @@ struct matex_ctx {
   int32_t* out_map = nullptr;   // output row r -> new index
   int32_t* sel_groups_d = nullptr;
   double* pwl_v_d = nullptr;
+  double* pwl_base_d = nullptr;  // the currents given at setup (amplitude scale 1)
+  std::vector<double> c_host;    // capacitances, original order (refactorisation)
+  std::vector<int64_t> g_rowptr_h;
+  std::vector<int32_t> g_col_h;
+  std::vector<double> g_val_h;
   // round tables
   int32_t *rc_group = nullptr, *rc_seg = nullptr, *rc_obeg = nullptr, *rc_nout = nullptr;
+  int32_t* rc_vslot = nullptr;
   double *rc_l0 = nullptr, *rc_len = nullptr, *rc_hfirst = nullptr, *rc_lprev = nullptr;
   std::vector<int32_t> init_groups;   // groups whose input is non-zero at t = 0
   int32_t* init_groups_d = nullptr;
@@ -391,6 +406,7 @@ int solve_cols(matex_ctx* c, const DevFactor& F, int ncols) {
 RoundCols round_cols(matex_ctx* c, const Round& r) {
   RoundCols rc;
   rc.group = c->rc_group + r.begin;
+  rc.vslot = c->rc_vslot + r.begin;
   rc.seg = c->rc_seg + r.begin;
   rc.l0 = c->rc_l0 + r.begin;
   rc.len = c->rc_len + r.begin;
@@ -563,6 +579,7 @@ matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
     solve(c->fG, K);
     e = prof_begin(c);
     scatter_cols(c->Y, c->ldy, K, c->Zpb, n, rc.group, nullptr, n, st);
+    if (c->opts.tape) scatter_cols(c->Y, c->ldy, K, c->TZp, n, rc.vslot, nullptr, n, st);
     gather_cols(c->Y, c->ldy, K, c->Zpb, n, rc.group, c->c_perm, nullptr, n, st);
     moved(e, 2, K, true);
     solve(c->fG, K);
@@ -572,10 +589,11 @@ matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
     sweepsG += 2;
     // start vector v = x + F, beta = ||v||
     e = prof_begin(c);
-    krylov_start(c->Vb, vstride, c->Xb, c->Zb, c->Wb, n, rc.group, K, n, c->partials, c->nchunks, st);
+    krylov_start(c->Vb, vstride, c->Xb, c->Zb, c->Wb, n, rc.group, rc.vslot, K, n, c->partials,
+                 c->nchunks, st);
     prof_end(c, e, P_OTHER, 1, 4.0 * nd * K, 32.0 * nd * K);
     e = prof_begin(c);
-    start_finish(c->partials, c->nchunks, K, c->ss, rc.group, c->iterA, c->iter_grp, c->d_count, st);
+    start_finish(c->partials, c->nchunks, K, c->ss, rc.vslot, c->iterA, c->iter_grp, c->d_count, st);
     prof_end(c, e, P_SMALL, 1, 0.0, 0.0);
     launches += 2;
     int kit = 0;
@@ -584,7 +602,7 @@ matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
     int32_t* iter_next = c->iterB;
     if (kit > 0) {
       e = prof_begin(c);
-      basis_scale(c->Vb, vstride, rc.group, iter, kit, 0, c->ss.scale, n, st);
+      basis_scale(c->Vb, vstride, rc.vslot, iter, kit, 0, c->ss.scale, n, st);
       prof_end(c, e, P_GS, 1, nd * kit, 16.0 * nd * kit);
       launches++;
     }
@@ -598,20 +616,23 @@ matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
       e = prof_begin(c);
       scatter_cols(c->Y, c->ldy, kit, c->Vb + (int64_t)(j + 1) * n, vstride, c->iter_grp, nullptr,
                    n, st);
+      if (c->opts.tape)  // keep a_k = (C + gamma G)^{-1} C q_k for the adjoint
+        scatter_cols(c->Y, c->ldy, kit, c->TA + (int64_t)j * n, (int64_t)kMaxM * n, c->iter_grp,
+                     nullptr, n, st);
       moved(e, 1, kit, false);
       sweepsM++;
       // two classical Gram-Schmidt passes, then the norm and the normalisation
       e = prof_begin(c);
       for (int pass = 0; pass < 2; ++pass) {
-        basis_dots(c->Vb, vstride, rc.group, iter, kit, 0, j + 1, j + 1, n, c->partials,
+        basis_dots(c->Vb, vstride, rc.vslot, iter, kit, 0, j + 1, j + 1, n, c->partials,
                    c->nchunks, st);
         reduce_dots(c->partials, c->nchunks, kit, j + 1, iter, c->ss, j, pass, st);
-        basis_update(c->Vb, vstride, rc.group, iter, kit, j + 1, j + 1, c->ss.hbuf, n, st);
+        basis_update(c->Vb, vstride, rc.vslot, iter, kit, j + 1, j + 1, c->ss.hbuf, n, st);
       }
-      basis_dots(c->Vb, vstride, rc.group, iter, kit, j + 1, 1, j + 1, n, c->partials, c->nchunks,
+      basis_dots(c->Vb, vstride, rc.vslot, iter, kit, j + 1, 1, j + 1, n, c->partials, c->nchunks,
                  st);
       reduce_dots(c->partials, c->nchunks, kit, 1, iter, c->ss, j, 2, st);
-      basis_scale(c->Vb, vstride, rc.group, iter, kit, j + 1, c->ss.scale, n, st);
+      basis_scale(c->Vb, vstride, rc.vslot, iter, kit, j + 1, c->ss.scale, n, st);
       prof_end(c, e, P_GS, 9, (8.0 * j + 11.0) * nd * kit, (4.0 * j + 13.0) * 8.0 * nd * kit);
       e = prof_begin(c);
       residual_check(c->ss, rc, kit, j, c->gamma, c->tol, c->m_max, c->replay_d, iter, iter_next,
@@ -621,6 +642,7 @@ matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
       if ((s = read_count(c, &kit)) != MATEX_OK) return s;
       std::swap(iter, iter_next);
     }
+    if (c->opts.tape) tape_small(c->ss, rc, K, c->THt, c->Tbeta, st);
     e = prof_begin(c);
     output_coefficients(c->ss, rc, K, c->gamma, c->dt_out, c->coef, c->n_times, c->yend, st);
     prof_end(c, e, P_SMALL, 1, 0.0, 0.0);
@@ -668,6 +690,7 @@ matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
   o.solve_columns = solve_cols_total;
   o.kernel_launches = launches;
   o.rounds = (int32_t)rounds.size();
+  c->taped = c->opts.tape && !c->serial;
   prof_collect(c, m);
   if (stats) *stats = o;
   if (c->opts.strict && o.nonconv > 0)
@@ -675,9 +698,134 @@ matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
   return MATEX_OK;
 }
 
+// Reverse sweep over the forward's rounds (latest first); per round the
+// columns (groups) are handled together, like the forward.
+matex_status run_grad(matex_ctx* c, const double* xbar, double* dc, double* damp) {
+  cudaStream_t st = c->st;
+  const int64_t n = c->n;
+  const int G = std::max(c->n_groups, 1);
+  const int nrows = c->nrows_out;
+  const int64_t vstride = (int64_t)kMaxB * n;
+  // Krylov dimension per record, from the forward's per-segment record
+  std::vector<int32_t> mseg(std::max<int64_t>(1, c->n_segments)), mrec(c->n_records);
+  if (cudaMemcpy(mseg.data(), c->m_rec, sizeof(int32_t) * mseg.size(), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return cuda_check(c, "grad m");
+  for (int64_t r = 0; r < c->n_records; ++r) mrec[r] = mseg[c->h_segid_all[r]];
+  if (!mrec.empty())
+    cudaMemcpyAsync(c->mrec_d, mrec.data(), sizeof(int32_t) * mrec.size(), cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(c->XBg, 0, sizeof(double) * G * n, st);
+  cudaMemsetAsync(c->CARRYg, 0, sizeof(double) * G * n, st);
+  cudaMemsetAsync(c->CBg, 0, sizeof(double) * G * n, st);
+  cudaMemsetAsync(damp, 0, sizeof(double) * std::max(c->n_src, 1), st);
+  AdjWork aw{c->AW, (int64_t)kWSlots * n, c->XBg, c->CARRYg, c->CBg};
+  SourceTable base = c->src;  // d(B u)/d a_s uses the currents given at setup
+  base.pwl_v = c->pwl_base_d;
+  std::vector<int32_t> act;
+  for (size_t ri = c->rounds.size(); ri-- > 0;) {
+    const Round& r = c->rounds[ri];
+    const int K = r.K;
+    AdjRound ar;
+    ar.rec = c->rc_vslot + r.begin;
+    ar.group = c->rc_group + r.begin;
+    ar.m = c->mrec_d + r.begin;
+    ar.obeg = c->rc_obeg + r.begin;
+    ar.nout = c->rc_nout + r.begin;
+    ar.seg = c->rc_seg + r.begin;
+    ar.l0 = c->rc_l0 + r.begin;
+    ar.len = c->rc_len + r.begin;
+    ar.hfirst = c->rc_hfirst + r.begin;
+    ar.V = c->Vb;
+    ar.vstride = vstride;
+    ar.A = c->TA;
+    ar.astride = (int64_t)kMaxM * n;
+    ar.Zp = c->TZp;
+    ar.Ht = c->THt;
+    ar.beta = c->Tbeta;
+    ar.n = n;
+    ar.dt = c->dt_out;
+    int mmax = 0;
+    for (int q = 0; q < K; ++q) mmax = std::max(mmax, mrec[r.begin + q]);
+    // active column lists for k = 0..mmax-1, uploaded once
+    act.clear();
+    std::vector<int> aoff(mmax + 1, 0);
+    for (int k = 0; k < mmax; ++k) {
+      aoff[k] = (int)act.size();
+      for (int q = 0; q < K; ++q)
+        if (mrec[r.begin + q] > k) act.push_back(q);
+    }
+    aoff[mmax] = (int)act.size();
+    if (!act.empty())
+      cudaMemcpyAsync(c->act_d, act.data(), sizeof(int32_t) * act.size(), cudaMemcpyHostToDevice, st);
+    // output adjoints and the small dense reverse
+    if (mmax > 0) {
+      AdjDots d{c->XBg, n, ar.group, 0, c->Vb, vstride, ar.rec, 0, nullptr};
+      adj_dots(d, K, mmax, n, c->partials, c->nchunks, c->YBL, st);
+    }
+    adj_obs(ar, K, xbar, c->out_map, nrows, c->YBO, c->n_times, c->S1, c->S2, st);
+    adj_small(ar, K, c->gamma, c->YBO, c->n_times, c->YBL, c->YOUT, c->YL, c->HTB, c->BETAB, st);
+    adj_build(ar, aw, K, c->YL, xbar, c->out_map, nrows, c->YOUT, c->n_times, c->S1, c->S2, st);
+    // reverse Arnoldi steps
+    for (int k = mmax - 1; k >= 0; --k) {
+      const int Ka = aoff[k + 1] - aoff[k];
+      const int32_t* ak = c->act_d + aoff[k];
+      AdjDots d1{c->AW, (int64_t)kWSlots * n, c->iota_d, k + 1, c->Vb, vstride, ar.rec, k + 1, ak};
+      adj_dots(d1, Ka, 1, n, c->partials, c->nchunks, c->D1, st);
+      adj_rbar(ar, aw, ak, Ka, k, c->D1, c->HTB, st);
+      AdjDots dh{c->AW, (int64_t)kWSlots * n, c->iota_d, kWR, c->Vb, vstride, ar.rec, 0, ak};
+      adj_dots(dh, Ka, k + 1, n, c->partials, c->nchunks, c->HD, st);
+      adj_abar(ar, aw, ak, Ka, k, c->HD, c->HTB, st);
+      gather_cols(c->Y, c->ldy, Ka, c->AW + (int64_t)kWA * n, (int64_t)kWSlots * n, ak, nullptr,
+                  nullptr, n, st);
+      solve_cols(c, c->fM, Ka);
+      adj_after_m(ar, aw, ak, Ka, k, c->Y, c->ldy, c->c_perm, st);
+    }
+    {
+      AdjDots d0{c->AW, (int64_t)kWSlots * n, c->iota_d, 0, c->Vb, vstride, ar.rec, 0, nullptr};
+      if (mmax > 0) adj_dots(d0, K, 1, n, c->partials, c->nchunks, c->D0, st);
+    }
+    adj_vbar(ar, aw, K, c->D0, c->BETAB, st);
+    // w = G^{-1}(c z'), then z' = G^{-1} B s
+    gather_cols(c->Y, c->ldy, K, c->AW + (int64_t)kWW * n, (int64_t)kWSlots * n, nullptr, nullptr,
+                nullptr, n, st);
+    solve_cols(c, c->fG, K);
+    adj_after_w(ar, aw, K, c->Y, c->ldy, c->c_perm, st);
+    gather_cols(c->Y, c->ldy, K, c->AW + (int64_t)kWZp * n, (int64_t)kWSlots * n, nullptr, nullptr,
+                nullptr, n, st);
+    solve_cols(c, c->fG, K);
+    adj_sources(ar, K, base, c->Y, c->ldy, damp, st);
+    matex_status s = cuda_check(c, "grad round");
+    if (s != MATEX_OK) return s;
+  }
+  // initial states x(0) = G^{-1} B u(0) of the groups whose input is non-zero at t = 0
+  const int ng = (int)c->init_groups.size();
+  for (int g0 = 0; g0 < ng; g0 += c->ldy) {
+    const int K = std::min(c->ldy, ng - g0);
+    adj_x0_obs(c->init_groups_d + g0, K, c->XBg, n, xbar, c->out_map, nrows, st);
+    gather_cols(c->Y, c->ldy, K, c->XBg, n, c->init_groups_d + g0, nullptr, nullptr, n, st);
+    solve_cols(c, c->fG, K);
+    adj_init_sources(c->init_groups_d + g0, K, base, c->Y, c->ldy, damp, st);
+  }
+  adj_csum(c->CBg, G, n, c->perm, dc, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(c, "grad sync");
+  matex_status s = cuda_check(c, "grad");
+  if (s != MATEX_OK) return s;
+  int tmp = 0;
+  return read_count(c, &tmp);
+}
+
 }  // namespace
 
 extern "C" {
+
+matex_status matex_grad(matex_ctx* c, const double* xbar, double* dc, double* damp) {
+  if (!c) return MATEX_ERR_ARG;
+  if (!xbar || !dc || (c->n_src > 0 && !damp)) return fail(c, MATEX_ERR_ARG, "NULL argument");
+  if (!c->opts.tape) return fail(c, MATEX_ERR_STATE, "matex_grad needs a context set up with tape = 1");
+  if (!c->taped) return fail(c, MATEX_ERR_STATE, "matex_grad needs a preceding batched matex_run");
+  cudaMemsetAsync(c->d_count, 0, 2 * sizeof(int32_t), c->st);
+  return run_grad(c, xbar, dc, damp);
+}
 
 void matex_default_opts(matex_opts* o) {
   if (!o) return;
@@ -769,6 +917,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   matex_default_opts(&o);
   if (opts) o = *opts;
   if (o.max_width <= 0) o.max_width = 1024;
+  if (o.tape && o.group_select >= 0) return bad("tape needs all groups (group_select = -1)");
   if (o.col_block != 0 && o.col_block != 1 && o.col_block != 2 && o.col_block != 4 && o.col_block != 8)
     return bad("col_block must be 0, 1, 2, 4 or 8");
   if (o.group_select >= n_groups) return bad("group_select out of range");
@@ -799,6 +948,10 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
 
   // ---- ordering, symbolic, numeric ------------------------------------
   double t = now_ms();
+  c->c_host.assign(cap, cap + n);
+  c->g_rowptr_h.assign(g_rowptr, g_rowptr + n + 1);
+  c->g_col_h.assign(g_col, g_col + g_rowptr[n]);
+  c->g_val_h.assign(g_val, g_val + g_rowptr[n]);
   CsrSym A{n, g_rowptr, g_col, g_val};
   std::vector<int32_t> nd;
   std::string e = nested_dissection(A, nd);
@@ -983,12 +1136,15 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     std::vector<int32_t> poff(pwl_off ? pwl_off : nullptr, pwl_off ? pwl_off + n_src + 1 : nullptr);
     if (poff.empty()) poff.push_back(0);
     ok = ok && c->upload(po, poff.data(), poff.size()) && c->upload(pt, pwl_t, npwl) &&
-         c->upload(c->pwl_v_d, pwl_v, npwl);
+         c->upload(c->pwl_v_d, pwl_v, npwl) && c->upload(c->pwl_base_d, pwl_v, npwl);
     c->pwl_v_host_shape.resize(npwl);
     c->src = SourceTable{gp, gsd, nd_d, po, pt, c->pwl_v_d};
   }
   ok = ok && c->upload(c->sel_groups_d, c->sel_groups.data(), c->sel_groups.size());
   ok = ok && c->upload(c->init_groups_d, c->init_groups.data(), c->init_groups.size());
+  std::vector<int32_t> h_vslot(h_group.size());
+  for (size_t r = 0; r < h_group.size(); ++r) h_vslot[r] = o.tape ? (int32_t)r : h_group[r];
+  ok = ok && c->upload(c->rc_vslot, h_vslot.data(), h_vslot.size());
   ok = ok && c->upload(c->rc_group, h_group.data(), h_group.size()) &&
        c->upload(c->rc_seg, h_seg.data(), h_seg.size()) &&
        c->upload(c->rc_obeg, h_obeg.data(), h_obeg.size()) &&
@@ -1004,7 +1160,9 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   ok = ok && plan_levels(c);
   c->nchunks = (int)((n + kChunk - 1) / kChunk);
   const size_t G = (size_t)std::max(n_groups, 1);
-  ok = ok && c->alloc(c->Y, (size_t)n * c->ldy) && c->alloc(c->Y2, (size_t)n * c->ldy) && c->alloc(c->Vb, G * kMaxB * n) &&
+  c->n_records = (int64_t)h_group.size();
+  const size_t vslots = o.tape ? (size_t)std::max<int64_t>(1, c->n_records) : G;
+  ok = ok && c->alloc(c->Y, (size_t)n * c->ldy) && c->alloc(c->Y2, (size_t)n * c->ldy) && c->alloc(c->Vb, vslots * kMaxB * n) &&
        c->alloc(c->Zb, G * n) && c->alloc(c->Zpb, G * n) && c->alloc(c->Wb, G * n) &&
        c->alloc(c->Xb, G * n) && c->alloc(c->Xp, (size_t)c->n_times * n) && c->alloc(c->xdc, n) &&
        c->alloc(c->partials, (size_t)Kmax * kMaxB * c->nchunks) &&
@@ -1016,6 +1174,23 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
        c->alloc(c->yend, (size_t)Kmax * kMaxM) && c->alloc(c->m_rec, std::max<int64_t>(1, c->n_segments)) &&
        c->alloc(c->st_rec, std::max<int64_t>(1, c->n_segments));
   if (ok && cudaMallocHost(&c->h_count, 2 * sizeof(int32_t)) != cudaSuccess) ok = false;
+  if (ok && o.tape) {
+    const size_t R = (size_t)std::max<int64_t>(1, c->n_records);
+    const size_t KM = (size_t)Kmax;
+    std::vector<int32_t> iota(std::max(Kmax, 1));
+    for (int q = 0; q < (int)iota.size(); ++q) iota[q] = q;
+    ok = c->alloc(c->TA, R * kMaxM * n) && c->alloc(c->TZp, R * n) &&
+         c->alloc(c->THt, R * kMaxB * kMaxM) && c->alloc(c->Tbeta, R) &&
+         c->alloc(c->AW, KM * kWSlots * n) && c->alloc(c->XBg, G * n) && c->alloc(c->CARRYg, G * n) &&
+         c->alloc(c->CBg, G * n) && c->alloc(c->YBO, KM * c->n_times * kCoefLd) &&
+         c->alloc(c->YOUT, KM * c->n_times * kCoefLd) && c->alloc(c->YBL, KM * kMaxB) &&
+         c->alloc(c->YL, KM * kMaxM) && c->alloc(c->HTB, KM * kMaxB * kMaxM) &&
+         c->alloc(c->BETAB, KM) && c->alloc(c->D1, KM * kMaxB) && c->alloc(c->HD, KM * kMaxB) &&
+         c->alloc(c->D0, KM * kMaxB) && c->alloc(c->S1, KM * c->nrows_out) &&
+         c->alloc(c->S2, KM * c->nrows_out) && c->upload(c->iota_d, iota.data(), iota.size()) &&
+         c->alloc(c->mrec_d, R) && c->alloc(c->act_d, KM * (kMaxM + 1));
+    adj_set_limits();
+  }
   if (!ok) {
     cudaGetLastError();
     g_setup_err = "device allocation or upload failed";
@@ -1023,7 +1198,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     return MATEX_ERR_OOM;
   }
   set_small_smem_limits();
-  cudaMemset(c->Vb, 0, sizeof(double) * G * kMaxB * n);
+  cudaMemset(c->Vb, 0, sizeof(double) * vslots * kMaxB * n);
   cudaMemset(c->Xb, 0, sizeof(double) * G * n);
   if (cudaDeviceSynchronize() != cudaSuccess) {
     g_setup_err = std::string("setup: ") + cudaGetErrorString(cudaGetLastError());
@@ -1041,6 +1216,34 @@ matex_status matex_run(matex_ctx* c, double* x_out, matex_stats* stats) {
   return run_device(c, x_out, stats);
 }
 
+matex_status matex_set_caps(matex_ctx* c, const double* cap) {
+  if (!c) return MATEX_ERR_ARG;
+  if (!cap) return fail(c, MATEX_ERR_ARG, "capacitances are NULL");
+  for (int64_t i = 0; i < c->n; ++i)
+    if (!(cap[i] > 0) || !std::isfinite(cap[i])) return fail(c, MATEX_ERR_ARG, "capacitance must be positive");
+  const double t = now_ms();
+  CsrSym A{c->n, c->g_rowptr_h.data(), c->g_col_h.data(), c->g_val_h.data()};
+  Numeric NM;
+  std::string e = numeric_ldlt(A, cap, c->gamma, c->S, NM);
+  if (!e.empty()) return fail(c, MATEX_ERR_NOT_SPD, e);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "set_caps sync");
+  std::vector<double> cp(c->n);
+  for (int64_t k = 0; k < c->n; ++k) cp[k] = cap[c->S.perm[k]];
+  bool ok = cudaMemcpy(const_cast<double*>(c->fM.dinv), NM.dinv.data(), sizeof(double) * NM.dinv.size(),
+                       cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(const_cast<double*>(c->fM.pan_cm), NM.pan_cm.data(),
+                       sizeof(double) * NM.pan_cm.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(const_cast<double*>(c->fM.pan_rm), NM.pan_rm.data(),
+                       sizeof(double) * NM.pan_rm.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(c->c_perm, cp.data(), sizeof(double) * c->n, cudaMemcpyHostToDevice) ==
+                cudaSuccess;
+  if (!ok) return cuda_check(c, "set_caps upload");
+  c->c_host.assign(cap, cap + c->n);
+  c->taped = false;
+  c->setup_stats.setup_factor_ms = now_ms() - t;
+  return MATEX_OK;
+}
+
 matex_status matex_set_sources(matex_ctx* c, const double* pwl_v_host) {
   if (!c) return MATEX_ERR_ARG;
   if (!pwl_v_host) return fail(c, MATEX_ERR_ARG, "pwl_v is NULL");
@@ -1048,6 +1251,7 @@ matex_status matex_set_sources(matex_ctx* c, const double* pwl_v_host) {
     if (!std::isfinite(pwl_v_host[i])) return fail(c, MATEX_ERR_ARG, "non-finite PWL value");
   cudaMemcpyAsync(c->pwl_v_d, pwl_v_host, sizeof(double) * c->pwl_v_host_shape.size(),
                   cudaMemcpyHostToDevice, c->st);
+  c->taped = false;
   return cuda_check(c, "set_sources");
 }
 

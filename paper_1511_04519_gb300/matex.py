@@ -31,7 +31,8 @@ class MatexOpts(C.Structure):
     _fields_ = [("col_block", C.c_int32), ("group_select", C.c_int32), ("include_dc", C.c_int32),
                 ("n_rows", C.c_int32), ("rows", C.POINTER(C.c_int32)),
                 ("replay_m", C.POINTER(C.c_int32)), ("n_replay", C.c_int64),
-                ("max_width", C.c_int32), ("strict", C.c_int32), ("solve_mode", C.c_int32)]
+                ("max_width", C.c_int32), ("strict", C.c_int32), ("solve_mode", C.c_int32),
+                ("tape", C.c_int32)]
 
 
 class MatexStats(C.Structure):
@@ -63,7 +64,7 @@ EXPORTS = ["matex_default_opts", "matex_setup", "matex_run", "matex_run_host", "
            "matex_solve", "matex_expm", "matex_get_m", "matex_get_sizes", "matex_get_setup_stats",
            "matex_last_error", "matex_status_string", "matex_destroy", "matex_set_profiling",
            "matex_get_profile", "matex_host_factor_solve", "matex_set_batching",
-           "matex_debug_inject_wait", "matex_solve_noalloc"]
+           "matex_debug_inject_wait", "matex_solve_noalloc", "matex_grad", "matex_set_caps"]
 
 
 def _load():
@@ -101,6 +102,10 @@ def _load():
     lib.matex_last_error.restype = C.c_char_p
     lib.matex_status_string.argtypes = [C.c_int]
     lib.matex_status_string.restype = C.c_char_p
+    lib.matex_set_caps.argtypes = [P, dp]
+    lib.matex_set_caps.restype = C.c_int
+    lib.matex_grad.argtypes = [P, P, P, P]
+    lib.matex_grad.restype = C.c_int
     lib.matex_debug_inject_wait.argtypes = [P, C.c_int32]
     lib.matex_debug_inject_wait.restype = C.c_int
     lib.matex_set_batching.argtypes = [P, C.c_int32]
@@ -237,6 +242,15 @@ def matex_get_setup_stats(ctx):
     return s
 
 
+def matex_set_caps(ctx, c_host):
+    a = np.ascontiguousarray(c_host, dtype=np.float64)
+    _check(ctx, _lib.matex_set_caps(ctx, _ptr(a, C.c_double)))
+
+
+def matex_grad(ctx, xbar_ptr, dc_ptr, damp_ptr):
+    _check(ctx, _lib.matex_grad(ctx, C.c_void_p(xbar_ptr), C.c_void_p(dc_ptr), C.c_void_p(damp_ptr)))
+
+
 def matex_debug_inject_wait(ctx, on):
     _check(ctx, _lib.matex_debug_inject_wait(ctx, int(bool(on))))
 
@@ -267,7 +281,7 @@ class Sim:
 
     def __init__(self, p, col_block=0, group_select=-1, include_dc=True, rows=None,
                  replay_m=None, max_width=0, strict=False, stream=None, solve_mode=0,
-                 **overrides):
+                 tape=False, **overrides):
         o = matex_default_opts()
         o.col_block = col_block
         o.group_select = group_select
@@ -276,6 +290,7 @@ class Sim:
             o.max_width = max_width
         o.strict = int(bool(strict))
         o.solve_mode = int(solve_mode)
+        o.tape = int(bool(tape))
         self._keep = []
         if rows is not None:
             r = np.ascontiguousarray(rows, dtype=np.int32)
@@ -295,6 +310,7 @@ class Sim:
         self.n = int(p.n)
         self.n_times, self.n_rows, self.n_segments = matex_get_sizes(self.ctx)
         self.pwl_len = int(np.asarray(p.pwl_v).shape[0])
+        self.n_src = int(np.asarray(p.src_node).shape[0])
 
     def run(self, out=None):
         import torch
@@ -309,6 +325,21 @@ class Sim:
         pv = None if pwl_v is None else np.ascontiguousarray(pwl_v, dtype=np.float64)
         self.stats = matex_run_host(self.ctx, pv, out)
         return out
+
+    def set_caps(self, c):
+        matex_set_caps(self.ctx, c)
+
+    def set_sources(self, pwl_v):
+        matex_set_sources(self.ctx, pwl_v)
+
+    def grad(self, xbar):
+        """(dL/dc, dL/d amp_scale) for dL/dX_out = xbar ([N+1][n_rows] cuda float64)."""
+        import torch
+        xbar = xbar.contiguous()
+        dc = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        da = torch.empty(self.n_src, dtype=torch.float64, device="cuda")
+        matex_grad(self.ctx, xbar.data_ptr(), dc.data_ptr(), da.data_ptr())
+        return dc, da
 
     def m_sequence(self):
         return matex_get_m(self.ctx)

@@ -1,0 +1,179 @@
+"""GPU adjoint (matex_grad, IRDrop autograd) against the FP64 CPU adjoint and
+central differences.
+
+The GPU reverse differentiates the computation the GPU forward performed, with
+its Krylov dimensions; the CPU adjoint is run with the same dimensions
+(replay), so the two must agree to rounding.  Central differences use the same
+replayed dimensions (the map is then smooth): amplitudes h = 1e-6 (relative);
+capacitances Richardson-extrapolated with h = 4e-3 (a 1e-6 step moves the loss
+below the forward's rounding).
+"""
+import numpy as np
+import pytest
+
+import gridgen
+from oracle import adjoint_ref as A
+from oracle import rmatex_ref as R
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1511_04519_gb300 import build
+    build.build()
+    from paper_1511_04519_gb300 import autograd as AG
+    from paper_1511_04519_gb300 import matex as M
+    return torch, M, AG
+
+
+def small_case(seed, layers=1, nx=8, ny=7):
+    p = gridgen.small_mesh(seed, nx=nx, ny=ny, layers=layers, n_src=8, group_templates=[2, 3, 3],
+                           t_end=0.3e-9, dt_out=10e-12, c_range=(1e-14, 1e-12))
+    obs = np.sort(np.random.default_rng(seed).choice(p.n, 9, replace=False)).astype(np.int32)
+    drop = p.vdd - R.rmatex(p, nodes=obs).X
+    theta = float(np.quantile(drop, 0.6))
+    return p, obs, theta
+
+
+def gpu_loss_grad(env, p, obs, theta, sim=None):
+    torch, M, AG = env
+    sim = sim or AG.make_sim(p, obs)
+    c = torch.tensor(p.c, dtype=torch.float64, requires_grad=True)
+    amp = torch.ones(p.n_src, dtype=torch.float64, requires_grad=True)
+    X = AG.IRDrop.apply(c, amp, sim)
+    L = AG.hinge_ir_drop_loss(X, p.vdd, theta, p.dt_out)
+    L.backward()
+    return float(L), c.grad.cpu().numpy(), amp.grad.cpu().numpy(), sim
+
+
+def per_group_m(p, sim):
+    """The GPU's m sequence split per group (replay layout)."""
+    m = sim.m_sequence()
+    out, pos = [], 0
+    for k in range(p.n_groups):
+        nseg = len(R.local_transition_spots(p, k)) - 1
+        out.append(list(m[pos:pos + nseg]))
+        pos += nseg
+    return out
+
+
+@pytest.mark.parametrize("seed,layers", [(3, 1), (4, 2), (5, 1)])
+def test_gpu_adjoint_matches_cpu_adjoint(env, seed, layers):
+    p, obs, theta = small_case(seed, layers=layers)
+    L, dc, da, sim = gpu_loss_grad(env, p, obs, theta)
+    ms = per_group_m(p, sim)
+    Lr, cbar, abar, _ = A.loss_and_grad(p, obs, theta, replay_m=ms)
+    assert L > 0 and abs(L - Lr) <= 1e-9 * Lr
+    assert np.abs(dc - cbar).max() <= 1e-9 * np.abs(cbar).max()
+    assert np.abs(da - abar).max() <= 1e-9 * np.abs(abar).max()
+
+
+def test_gpu_adjoint_matches_central_differences(env):
+    torch, M, AG = env
+    p, obs, theta = small_case(6, layers=2, nx=9, ny=9)
+    L, dc, da, sim = gpu_loss_grad(env, p, obs, theta)
+    ms = np.concatenate(per_group_m(p, sim)).astype(np.int32)
+    fd_sim = M.Sim(p, rows=obs, replay_m=ms)
+    base = np.asarray(p.pwl_v, dtype=np.float64)
+    src_of = np.repeat(np.arange(p.n_src), np.diff(p.pwl_off))
+
+    def loss(c=None, amp=None):
+        fd_sim.set_caps(p.c if c is None else c)
+        fd_sim.set_sources(base * (np.ones(p.n_src) if amp is None else amp)[src_of])
+        return float(AG.hinge_ir_drop_loss(fd_sim.run(), p.vdd, theta, p.dt_out))
+
+    rng = np.random.default_rng(0)
+    for s in range(p.n_src):
+        ap = np.ones(p.n_src); ap[s] += 1e-6
+        am = np.ones(p.n_src); am[s] -= 1e-6
+        fd = (loss(amp=ap) - loss(amp=am)) / 2e-6
+        assert abs(da[s] - fd) <= 1e-6 * abs(fd), (s, da[s], fd)
+    rel = []
+    for i in rng.choice(p.n, 6, replace=False):
+        def D(h):
+            cp = p.c.copy(); cp[i] += h
+            cm = p.c.copy(); cm[i] -= h
+            return (loss(c=cp) - loss(c=cm)) / (2 * h)
+        h = 4e-3 * p.c[i]
+        fd = (4 * D(h / 2) - D(h)) / 3
+        rel.append(abs(dc[i] - fd) / abs(fd))
+    assert np.median(rel) <= 1e-6 and max(rel) <= 5e-6, rel
+
+
+def test_grad_requires_tape_and_a_run(env):
+    torch, M, AG = env
+    p, obs, theta = small_case(7)
+    plain = M.Sim(p, rows=obs)
+    plain.run()
+    with pytest.raises(M.MatexError):
+        plain.grad(torch.zeros((plain.n_times, plain.n_rows), dtype=torch.float64, device="cuda"))
+    taped = AG.make_sim(p, obs)
+    with pytest.raises(M.MatexError):
+        taped.grad(torch.zeros((taped.n_times, taped.n_rows), dtype=torch.float64, device="cuda"))
+
+
+@pytest.fixture(scope="module")
+def cfg3(env):
+    p = gridgen.config3()
+    return p
+
+
+def test_config3_adjoint_against_cpu_adjoint_and_differences(env, cfg3):
+    """The config-1 grid with 256 observed nodes: GPU gradients with respect to
+    all 180k capacitances and 2000 amplitudes; the amplitudes of two groups'
+    sources against the CPU reverse of those groups (driven by the same output
+    adjoint), and central differences on 16 capacitances and 16 amplitudes."""
+    torch, M, AG = env
+    p = cfg3
+    obs = p.observed.astype(np.int32)
+    sim = AG.make_sim(p, obs)
+    X0 = sim.run().cpu().numpy()
+    drop = p.vdd - X0
+    theta = float(np.quantile(drop, 0.9))
+    assert (drop > theta).mean() >= 0.09
+    L, dc, da, sim = gpu_loss_grad(env, p, obs, theta, sim=sim)
+    assert L > 0 and np.isfinite(dc).all() and np.isfinite(da).all()
+    ms = per_group_m(p, sim)
+    # CPU reverse of two groups, output adjoint from the GPU forward's rows
+    Lr, G = A.hinge_loss(X0, p.vdd, theta, p.dt_out)
+    groups = [5, 41]
+    _, tapes, _, fac = A.forward_tape(p, obs, replay_m={k: ms[k] for k in groups}, groups=groups)
+    _, abar = A.reverse(p, obs, fac, p.c, tapes, G)
+    sel = np.isin(p.src_group, groups)
+    assert np.abs(da[sel] - abar[sel]).max() <= 1e-8 * np.abs(abar[sel]).max()
+    # central differences with the GPU's m replayed
+    msr = np.concatenate(ms).astype(np.int32)
+    fd_sim = M.Sim(p, rows=obs, replay_m=msr)
+    base = np.asarray(p.pwl_v, dtype=np.float64)
+    src_of = np.repeat(np.arange(p.n_src), np.diff(p.pwl_off))
+
+    def loss(c=None, amp=None):
+        if c is not None:
+            fd_sim.set_caps(c)
+        fd_sim.set_sources(base * (np.ones(p.n_src) if amp is None else amp)[src_of])
+        return float(AG.hinge_ir_drop_loss(fd_sim.run(), p.vdd, theta, p.dt_out))
+
+    rng = np.random.default_rng(1)
+    active = np.nonzero(np.abs(da) > 1e-3 * np.abs(da).max())[0]
+    rel_a = []
+    for s in rng.choice(active, 16, replace=False):
+        ap = np.ones(p.n_src); ap[s] += 1e-6
+        am = np.ones(p.n_src); am[s] -= 1e-6
+        fd = (loss(amp=ap) - loss(amp=am)) / 2e-6
+        rel_a.append(abs(da[s] - fd) / abs(fd))
+    assert max(rel_a) <= 1e-6, rel_a
+    bigc = np.argsort(-np.abs(dc))[:400]
+    rel_c = []
+    for i in rng.choice(bigc, 16, replace=False):
+        def D(h):
+            cp = p.c.copy(); cp[i] += h
+            cm = p.c.copy(); cm[i] -= h
+            return (loss(c=cp) - loss(c=cm)) / (2 * h)
+        h = 4e-3 * p.c[i]
+        fd = (4 * D(h / 2) - D(h)) / 3
+        rel_c.append(abs(dc[i] - fd) / abs(fd))
+    assert np.median(rel_c) <= 1e-6 and max(rel_c) <= 5e-6, rel_c
