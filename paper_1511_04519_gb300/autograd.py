@@ -30,12 +30,13 @@ class IRDrop(torch.autograd.Function):
         sim.set_sources(sim.base_pwl_v * an[sim.pwl_source])
         X = sim.run()
         ctx.sim = sim
+        ctx.devices = (c.device, amp.device)
         return X
 
     @staticmethod
     def backward(ctx, xbar):
         dc, da = ctx.sim.grad(xbar)
-        return dc, da, None
+        return dc.to(ctx.devices[0]), da.to(ctx.devices[1]), None
 
 
 def hinge_ir_drop_loss(X, vdd, theta, dt):
