@@ -79,7 +79,7 @@ def _with_c(p, c):
     return q
 
 
-def forward_tape(p, obs, c=None, amp_scale=None, replay_m=None, groups=None):
+def forward_tape(p, obs, c=None, amp_scale=None, replay_m=None, groups=None, include_dc=True):
     """Oracle forward (all nodes per group) keeping each segment's data; returns
     (X at the observed rows, tapes, m per group, factors, x_dc)."""
     c = p.c if c is None else np.asarray(c, dtype=np.float64)
@@ -90,7 +90,8 @@ def forward_tape(p, obs, c=None, amp_scale=None, replay_m=None, groups=None):
     obs = np.asarray(obs)
     x_dc = fac.solve_G(p.dc_inject)
     X = np.zeros((t_out.shape[0], obs.shape[0]))
-    X += x_dc[obs][None, :]
+    if include_dc:
+        X += x_dc[obs][None, :]
     tapes, ms = {}, {}
     for k in (range(p.n_groups) if groups is None else groups):
         keep = []

@@ -4,9 +4,12 @@ central differences.
 The GPU reverse differentiates the computation the GPU forward performed, with
 its Krylov dimensions; the CPU adjoint is run with the same dimensions
 (replay), so the two must agree to rounding.  Central differences use the same
-replayed dimensions (the map is then smooth): amplitudes h = 1e-6 (relative);
-capacitances Richardson-extrapolated with h = 4e-3 (a 1e-6 step moves the loss
-below the forward's rounding).
+replayed dimensions (the map is then smooth) and runs without the constant DC
+part (x_dc = Vdd on these grids, and it does not depend on the parameters), so
+that the loss sees the IR drop itself rather than a voltage near 1 V with
+three fewer significant digits: amplitudes h = 1e-6 (relative); capacitances
+Richardson-extrapolated with h = 4e-3 (a 1e-6 step moves the loss by about
+1e-10 of itself, at the forward's rounding).
 """
 import numpy as np
 import pytest
@@ -39,15 +42,17 @@ def small_case(seed, layers=1, nx=8, ny=7):
     return p, obs, theta
 
 
-def gpu_loss_grad(env, p, obs, theta, sim=None):
+def gpu_loss_grad(env, p, obs, theta, sim=None, vdd=None):
+    """Loss max(0, vdd - v - theta)^2 integrated over the rows; vdd = 0 with a
+    Sim built without the DC part (then -v is the IR drop)."""
     torch, M, AG = env
     sim = sim or AG.make_sim(p, obs)
     c = torch.tensor(p.c, dtype=torch.float64, requires_grad=True)
     amp = torch.ones(p.n_src, dtype=torch.float64, requires_grad=True)
     X = AG.IRDrop.apply(c, amp, sim)
-    L = AG.hinge_ir_drop_loss(X, p.vdd, theta, p.dt_out)
+    L = AG.hinge_ir_drop_loss(X, p.vdd if vdd is None else vdd, theta, p.dt_out)
     L.backward()
-    return float(L), c.grad.cpu().numpy(), amp.grad.cpu().numpy(), sim
+    return L.item(), c.grad.cpu().numpy(), amp.grad.cpu().numpy(), sim
 
 
 def per_group_m(p, sim):
@@ -75,16 +80,17 @@ def test_gpu_adjoint_matches_cpu_adjoint(env, seed, layers):
 def test_gpu_adjoint_matches_central_differences(env):
     torch, M, AG = env
     p, obs, theta = small_case(6, layers=2, nx=9, ny=9)
-    L, dc, da, sim = gpu_loss_grad(env, p, obs, theta)
+    sim = AG.make_sim(p, obs, include_dc=False)
+    L, dc, da, sim = gpu_loss_grad(env, p, obs, theta, sim=sim, vdd=0.0)
     ms = np.concatenate(per_group_m(p, sim)).astype(np.int32)
-    fd_sim = M.Sim(p, rows=obs, replay_m=ms)
+    fd_sim = M.Sim(p, rows=obs, replay_m=ms, include_dc=False)
     base = np.asarray(p.pwl_v, dtype=np.float64)
     src_of = np.repeat(np.arange(p.n_src), np.diff(p.pwl_off))
 
     def loss(c=None, amp=None):
         fd_sim.set_caps(p.c if c is None else c)
         fd_sim.set_sources(base * (np.ones(p.n_src) if amp is None else amp)[src_of])
-        return float(AG.hinge_ir_drop_loss(fd_sim.run(), p.vdd, theta, p.dt_out))
+        return float(AG.hinge_ir_drop_loss(fd_sim.run(), 0.0, theta, p.dt_out))
 
     rng = np.random.default_rng(0)
     for s in range(p.n_src):
@@ -130,16 +136,16 @@ def test_config3_adjoint_against_cpu_adjoint_and_differences(env, cfg3):
     torch, M, AG = env
     p = cfg3
     obs = p.observed.astype(np.int32)
-    sim = AG.make_sim(p, obs)
+    sim = AG.make_sim(p, obs, include_dc=False)
     X0 = sim.run().cpu().numpy()
-    drop = p.vdd - X0
+    drop = -X0                      # x_dc = Vdd on this grid: the load response is the drop
     theta = float(np.quantile(drop, 0.9))
     assert (drop > theta).mean() >= 0.09
-    L, dc, da, sim = gpu_loss_grad(env, p, obs, theta, sim=sim)
+    L, dc, da, sim = gpu_loss_grad(env, p, obs, theta, sim=sim, vdd=0.0)
     assert L > 0 and np.isfinite(dc).all() and np.isfinite(da).all()
     ms = per_group_m(p, sim)
     # CPU reverse of two groups, output adjoint from the GPU forward's rows
-    Lr, G = A.hinge_loss(X0, p.vdd, theta, p.dt_out)
+    Lr, G = A.hinge_loss(X0, 0.0, theta, p.dt_out)
     groups = [5, 41]
     _, tapes, _, fac = A.forward_tape(p, obs, replay_m={k: ms[k] for k in groups}, groups=groups)
     _, abar = A.reverse(p, obs, fac, p.c, tapes, G)
@@ -147,7 +153,7 @@ def test_config3_adjoint_against_cpu_adjoint_and_differences(env, cfg3):
     assert np.abs(da[sel] - abar[sel]).max() <= 1e-8 * np.abs(abar[sel]).max()
     # central differences with the GPU's m replayed
     msr = np.concatenate(ms).astype(np.int32)
-    fd_sim = M.Sim(p, rows=obs, replay_m=msr)
+    fd_sim = M.Sim(p, rows=obs, replay_m=msr, include_dc=False)
     base = np.asarray(p.pwl_v, dtype=np.float64)
     src_of = np.repeat(np.arange(p.n_src), np.diff(p.pwl_off))
 
@@ -155,7 +161,7 @@ def test_config3_adjoint_against_cpu_adjoint_and_differences(env, cfg3):
         if c is not None:
             fd_sim.set_caps(c)
         fd_sim.set_sources(base * (np.ones(p.n_src) if amp is None else amp)[src_of])
-        return float(AG.hinge_ir_drop_loss(fd_sim.run(), p.vdd, theta, p.dt_out))
+        return float(AG.hinge_ir_drop_loss(fd_sim.run(), 0.0, theta, p.dt_out))
 
     rng = np.random.default_rng(1)
     active = np.nonzero(np.abs(da) > 1e-3 * np.abs(da).max())[0]
