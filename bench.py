@@ -203,6 +203,7 @@ def main():
     ap.add_argument("--cpu-groups", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serial", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--profile-step", action="store_true",
                     help="warm up, run one step inside cudaProfilerStart/Stop, print its stats")
     ap.add_argument("--ncu-case", choices=["solve", "run"], default=None,
@@ -341,6 +342,39 @@ def main():
     e2e = {"value": world * units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(pin_v.nbytes),
            "d2h_bytes_per_step": int(pin_out.nbytes), "ms_per_step": e2e_s * 1e3}
 
+    # adjoint: the same grid with 256 observed nodes, IR-drop hinge loss; cost
+    # of matex_grad relative to the forward run that taped it
+    adjoint = None
+    if not args.no_adjoint:
+        from paper_1511_04519_gb300 import autograd as AG
+        del sim
+        torch.cuda.empty_cache()
+        p3 = gridgen.config3(seed=gridgen.SEED_BASE + 1 + 1000 * rank)
+        obs = p3.observed.astype(np.int32)
+        sim3 = AG.make_sim(p3, obs, include_dc=False, stream=stream)
+        X3 = sim3.run()
+        theta = float(torch.quantile((-X3).flatten(), 0.9))
+        Xr = X3.detach().clone().requires_grad_(True)
+        AG.hinge_ir_drop_loss(Xr, 0.0, theta, p3.dt_out).backward()
+        xbar = Xr.grad.detach()
+        f_ms, g_ms = [], []
+        for it in range(args.warmup + args.steps):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            sim3.run(X3)
+            e1.record(stream)
+            sim3.grad(xbar)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                f_ms.append(e0.elapsed_time(e1))
+                g_ms.append(e1.elapsed_time(e2))
+        fm, gm = sum(f_ms) / len(f_ms), sum(g_ms) / len(g_ms)
+        adjoint = {"workload": "mesh2x300x300_256_observed_nodes_hinge_loss",
+                   "params": {"caps": p3.n, "amplitudes": p3.n_src},
+                   "forward_taped_ms": fm, "grad_ms": gm, "grad_over_forward": gm / fm}
+        del sim3
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = run_cpu_sample(args.cpu_groups)
@@ -356,7 +390,7 @@ def main():
                        "l2": "working set (factors, bases, 1.44 GB of outputs) > 129 MB L2"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "sptrsv": sptrsv, "one_group_at_a_time": serial,
-            "cpu_baseline": cpu, "profile_ms_per_step": ms_prof,
+            "cpu_baseline": cpu, "adjoint": adjoint, "profile_ms_per_step": ms_prof,
             "profile": {k: {kk: v[kk] / args.steps for kk in ("ms", "launches", "flops", "bytes")}
                         for k, v in prof.items()},
             "run_stats": {k: stats[k] for k in ("n_segments", "krylov_segments", "sum_m", "max_m",
