@@ -1260,12 +1260,22 @@ matex_status matex_run_host(matex_ctx* c, const double* pwl_v_host, double* x_ou
   if (!c) return MATEX_ERR_ARG;
   if (!x_out_host) return fail(c, MATEX_ERR_ARG, "x_out_host is NULL");
   const size_t bytes = sizeof(double) * (size_t)c->n_times * c->nrows_out;
-  if (!c->out_buf && !c->alloc(c->out_buf, (size_t)c->n_times * c->nrows_out))
-    return fail(c, MATEX_ERR_OOM, "output buffer");
   if (pwl_v_host) {
     cudaMemcpyAsync(c->pwl_v_d, pwl_v_host, sizeof(double) * c->pwl_v_host_shape.size(),
                     cudaMemcpyHostToDevice, c->st);
   }
+  // Page-locked host output: the final permutation kernel writes the voltages
+  // straight into host memory through its device mapping (over NVLink-C2C on
+  // Grace systems), so the device-to-host transfer is that kernel's stores.
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, x_out_host) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+      attr.devicePointer != nullptr) {
+    matex_status s = run_device(c, static_cast<double*>(attr.devicePointer), stats);
+    return s;
+  }
+  cudaGetLastError();
+  if (!c->out_buf && !c->alloc(c->out_buf, (size_t)c->n_times * c->nrows_out))
+    return fail(c, MATEX_ERR_OOM, "output buffer");
   matex_status s = run_device(c, c->out_buf, stats);
   if (s != MATEX_OK && s != MATEX_ERR_NOCONV) return s;
   if (cudaMemcpyAsync(x_out_host, c->out_buf, bytes, cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
