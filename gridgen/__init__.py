@@ -190,17 +190,19 @@ def config1(seed=SEED_BASE + 1, n_observed=0):
                              label="mesh2x300x300_2000src_64groups")
 
 
-def config2(seed=SEED_BASE + 2):
+def config2(seed=SEED_BASE + 2, side=600, n_src=10000, n_groups=256, n_pads=2000, max_tpl=66):
     """Four-layer 600x600 mesh (1.44M nodes), per-layer R x1/x0.5/x0.25/x0.1,
-    vias 0.02 ohm, 2000 pads, 10000 loads in 256 groups of 1..66 templates."""
+    vias 0.02 ohm, 2000 pads, 10000 loads in 256 groups of 1..66 templates
+    (4..199 breakpoints per group).  Smaller sides/counts give the same
+    structure at sizes the oracle can check."""
     rng = np.random.default_rng(seed + 1000)
-    d = rng.integers(1, 67, 256)
-    while d.sum() > 10000:
+    d = rng.integers(1, max_tpl + 1, n_groups)
+    while d.sum() > n_src:
         d = np.maximum(1, d - 1)
-    return make_mesh_problem(seed=seed, layers=4, nx=600, ny=600, r_range=(0.05, 0.5),
+    return make_mesh_problem(seed=seed, layers=4, nx=side, ny=side, r_range=(0.05, 0.5),
                              layer_r_scale=[1.0, 0.5, 0.25, 0.1], c_range=(1e-15, 1e-12),
-                             n_pads=2000, n_src=10000, group_templates=d, via_r=0.02,
-                             label="mesh4x600x600_10000src_256groups")
+                             n_pads=n_pads, n_src=n_src, group_templates=d, via_r=0.02,
+                             label=f"mesh4x{side}x{side}_{n_src}src_{n_groups}groups")
 
 
 def config3(seed=SEED_BASE + 1):
@@ -210,13 +212,13 @@ def config3(seed=SEED_BASE + 1):
     return p
 
 
-def config4(seed=SEED_BASE + 4, count=96):
+def config4(seed=SEED_BASE + 4, count=96, side_range=(100, 450)):
     """96 independent single-layer meshes with side U[100,450], config-0 value
     distributions, 8-64 loads in 4-16 groups each."""
     rng = np.random.default_rng(seed)
     probs = []
     for gidx in range(count):
-        side = int(rng.integers(100, 451))
+        side = int(rng.integers(side_range[0], side_range[1] + 1))
         n_src = int(rng.integers(8, 65))
         n_groups = int(rng.integers(4, min(16, n_src) + 1))
         n_tpl = int(rng.integers(n_groups, n_src + 1))
@@ -256,4 +258,4 @@ def with_sources(p: Problem, src_node, pwl_off, pwl_t, pwl_v, src_group, n_group
     return q
 
 
-CONFIGS = {0: config0, 1: config1, 2: config2, 3: config3}
+CONFIGS = {0: config0, 1: config1, 2: config2, 3: config3, 4: config4}

@@ -69,7 +69,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         jobs.append((cmd, obj))
     for f in cpp:
         obj = os.path.join(OUT, f[:-4] + ".o")
-        cmd = ["g++", "-O3", "-std=c++17", "-fPIC", "-I", os.path.join(ROOT, "include"),
+        cmd = ["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", "-I", os.path.join(ROOT, "include"),
                "-c", os.path.join(CSRC, f), "-o", obj]
         jobs.append((cmd, obj))
     with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
@@ -80,7 +80,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                 print(o)
     objs = [o for _, o in jobs]
     tmp = LIB + ".tmp"
-    _run([nvcc, "-shared", "-gencode", GENCODE, "-o", tmp] + objs + ["-lcudart"])
+    _run([nvcc, "-shared", "-gencode", GENCODE, "-o", tmp] + objs + ["-lcudart", "-lpthread"])
     os.replace(tmp, LIB)
     return LIB
 

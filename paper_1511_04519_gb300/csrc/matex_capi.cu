@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <new>
 #include <string>
 #include <vector>
@@ -960,8 +961,14 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   c->setup_stats.setup_order_ms = now_ms() - t;
   t = now_ms();
   Numeric NM, NG;
-  e = numeric_ldlt(A, cap, gamma, c->S, NM);
-  if (e.empty()) e = numeric_ldlt(A, nullptr, 1.0, c->S, NG);
+  {
+    // the two factorisations are independent: run them side by side
+    std::string eg;
+    std::thread tg([&] { eg = numeric_ldlt(A, nullptr, 1.0, c->S, NG); });
+    e = numeric_ldlt(A, cap, gamma, c->S, NM);
+    tg.join();
+    if (e.empty()) e = eg;
+  }
   if (!e.empty()) { g_setup_err = e; delete c; return MATEX_ERR_NOT_SPD; }
   c->setup_stats.setup_factor_ms = now_ms() - t;
   c->setup_stats.nnz_L = c->S.nnz_L;
