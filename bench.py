@@ -244,6 +244,7 @@ def main():
     stream = torch.cuda.current_stream()
     sim = M.Sim(p, stream=stream)
     setup = sim.setup_stats()
+    tuning = sim.autotune()
     out = torch.empty((sim.n_times, sim.n_rows), dtype=torch.float64, device="cuda")
     for _ in range(args.warmup):
         sim.run(out)
@@ -396,6 +397,8 @@ def main():
             "run_stats": {k: stats[k] for k in ("n_segments", "krylov_segments", "sum_m", "max_m",
                                                  "nonconv", "sweeps_M", "sweeps_G", "solve_columns",
                                                  "rounds")},
+            "autotune": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in t.items()}
+                         for t in tuning],
             "setup_ms": {"order": setup["setup_order_ms"], "factor": setup["setup_factor_ms"],
                          "upload": setup["setup_upload_ms"], "nnz_L": setup["nnz_L"],
                          "supernodes": setup["n_supernodes"], "levels": setup["n_levels"]},

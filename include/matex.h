@@ -65,7 +65,8 @@ typedef struct matex_opts {
   int32_t max_width;       /* cap on supernode width (0 = 1024) */
   int32_t strict;          /* 1: return MATEX_ERR_NOCONV when m_max is reached unconverged */
   int32_t solve_mode;      /* 0: one persistent launch per triangular-solve pair, tasks ordered
-                              by dependency counters (default); 1: one launch per tree level */
+                              by dependency counters; 1: one launch per tree level; 2 (default):
+                              chosen per column count by the setup-time autotuner */
   int32_t tape;            /* 1: every run keeps each segment's Krylov basis, solve outputs and
                               Hessenberg on the device so that matex_grad can follow it */
 } matex_opts;
@@ -260,6 +261,16 @@ matex_status matex_debug_inject_wait(matex_ctx* ctx, int32_t on);
 /* on = 1 starts (and zeroes) profiling, on = 0 stops it. */
 matex_status matex_set_profiling(matex_ctx* ctx, int32_t on);
 matex_status matex_get_profile(matex_ctx* ctx, matex_profile* out);
+
+/*
+ * Result of the setup-time autotuner (solve_mode 2): for each measured column
+ * count ncols[i] the launch mode chosen (0 persistent, 1 per level) and the
+ * best times of both (ms[2i], ms[2i+1]; -1 when read from the cache file named
+ * by the environment variable MATEX_AUTOTUNE_CACHE).  Writes at most cap entries;
+ * *count receives the number measured.
+ */
+matex_status matex_get_autotune(matex_ctx* ctx, int32_t* ncols, int32_t* mode, float* ms,
+                               int32_t cap, int32_t* count);
 
 /* Setup statistics (ordering, factor sizes, timings). */
 matex_status matex_get_setup_stats(matex_ctx* ctx, matex_stats* stats);

@@ -15,6 +15,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <thread>
@@ -72,6 +73,10 @@ struct matex_ctx {
   size_t psmem = 0;
   int pgrid = 0;
   bool inject_wait = false;  // test hook: a dependency that never completes
+  // autotuned solve launch mode per column count (0 persistent, 1 per level)
+  std::vector<int8_t> mode_by_ncols;
+  std::vector<int32_t> tune_reps, tune_modes;
+  std::vector<float> tune_ms;
   // adjoint tape (opts.tape): per record (non-zero segment) basis slot = record
   int64_t n_records = 0;
   bool taped = false;        // a run with the tape has completed
@@ -378,7 +383,9 @@ bool plan_levels(matex_ctx* c) {
 
 int solve_cols(matex_ctx* c, const DevFactor& F, int ncols) {
   if (ncols <= 0) return 0;
-  if (c->opts.solve_mode == 1)
+  int mode = c->opts.solve_mode;
+  if (mode == 2) mode = c->mode_by_ncols.empty() ? 0 : c->mode_by_ncols[std::min(ncols, c->ldy)];
+  if (mode == 1)
     return solve_inplace(F, c->levels.data(), (int)c->levels.size(), c->Y, c->Y2, c->ldy, ncols,
                          c->st);
   const int nlev = (int)c->levels.size();
@@ -492,6 +499,98 @@ double solve_bytes(const matex_ctx* c, int K) {
 }
 
 enum { P_SOLVE = 0, P_MOVE = 1, P_GS = 2, P_SMALL = 3, P_RECOMB = 4, P_OTHER = 5 };
+
+// Autotuner: for column counts 1, 2, 4, ..., ldy, time the batched solve with
+// one persistent launch and with one launch per tree level (CUDA events, best
+// of three after a warm-up) and keep the faster one for every column count up
+// to the next measured one.  The choice depends on the factor's tree (how
+// many levels, how much work per level) and on the GPU, so it is measured
+// rather than fixed.  An optional cache file (MATEX_AUTOTUNE_CACHE) keyed by
+// the factor's shape and the device name avoids re-measuring.
+std::string tune_key(matex_ctx* c) {
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, c->device);
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "n=%lld;nsup=%d;pan=%lld;lev=%d;ldy=%d;dev=%s", (long long)c->n,
+                c->S.nsup, (long long)c->S.pan_off[c->S.nsup], (int)c->levels.size(), c->ldy,
+                prop.name);
+  for (char* p = buf; *p; ++p)
+    if (*p == ' ') *p = '_';
+  return buf;
+}
+
+void autotune_solve(matex_ctx* c) {
+  c->mode_by_ncols.assign(c->ldy + 1, 0);
+  c->tune_reps.clear();
+  c->tune_modes.clear();
+  c->tune_ms.clear();
+  for (int r = 1; r <= c->ldy; r *= 2) c->tune_reps.push_back(r);
+  if (c->tune_reps.back() != c->ldy) c->tune_reps.push_back(c->ldy);
+  const char* cache = std::getenv("MATEX_AUTOTUNE_CACHE");
+  const std::string key = tune_key(c);
+  bool found = false;
+  if (cache) {
+    FILE* f = std::fopen(cache, "r");
+    if (f) {
+      char line[1024];
+      while (std::fgets(line, sizeof(line), f)) {
+        std::string l(line);
+        if (l.compare(0, key.size() + 1, key + " ") != 0) continue;
+        std::vector<int32_t> modes;
+        for (size_t i = key.size() + 1; i < l.size(); ++i)
+          if (l[i] == '0' || l[i] == '1') modes.push_back(l[i] - '0');
+        if (modes.size() == c->tune_reps.size()) {
+          c->tune_modes = modes;
+          found = true;
+        }
+      }
+      std::fclose(f);
+    }
+  }
+  if (!found) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaMemsetAsync(c->Y, 0, sizeof(double) * (size_t)c->n * c->ldy, c->st);
+    const int saved = c->opts.solve_mode;
+    for (int r : c->tune_reps) {
+      float best[2] = {1e30f, 1e30f};
+      for (int mode = 0; mode < 2; ++mode) {
+        c->opts.solve_mode = mode;
+        solve_cols(c, c->fM, r);
+        for (int rep = 0; rep < 3; ++rep) {
+          cudaEventRecord(e0, c->st);
+          solve_cols(c, c->fM, r);
+          cudaEventRecord(e1, c->st);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          best[mode] = std::min(best[mode], ms);
+        }
+      }
+      c->tune_modes.push_back(best[1] < best[0] ? 1 : 0);
+      c->tune_ms.push_back(best[0]);
+      c->tune_ms.push_back(best[1]);
+    }
+    c->opts.solve_mode = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cache) {
+      FILE* f = std::fopen(cache, "a");
+      if (f) {
+        std::fprintf(f, "%s ", key.c_str());
+        for (int32_t m : c->tune_modes) std::fprintf(f, "%d", m);
+        std::fprintf(f, "\n");
+        std::fclose(f);
+      }
+    }
+  }
+  for (size_t b = 0; b < c->tune_reps.size(); ++b) {
+    const int lo = c->tune_reps[b];
+    const int hi = b + 1 < c->tune_reps.size() ? c->tune_reps[b + 1] - 1 : c->ldy;
+    for (int nc = lo; nc <= hi; ++nc) c->mode_by_ncols[nc] = (int8_t)c->tune_modes[b];
+  }
+}
 
 matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
   const double t0 = now_ms();
@@ -835,6 +934,7 @@ void matex_default_opts(matex_opts* o) {
   o->group_select = -1;
   o->include_dc = 1;
   o->max_width = 1024;
+  o->solve_mode = 2;
 }
 
 const char* matex_status_string(matex_status s) {
@@ -919,6 +1019,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   if (opts) o = *opts;
   if (o.max_width <= 0) o.max_width = 1024;
   if (o.tape && o.group_select >= 0) return bad("tape needs all groups (group_select = -1)");
+  if (o.solve_mode < 0 || o.solve_mode > 2) return bad("solve_mode must be 0, 1 or 2");
   if (o.col_block != 0 && o.col_block != 1 && o.col_block != 2 && o.col_block != 4 && o.col_block != 8)
     return bad("col_block must be 0, 1, 2, 4 or 8");
   if (o.group_select >= n_groups) return bad("group_select out of range");
@@ -1205,6 +1306,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     return MATEX_ERR_OOM;
   }
   set_small_smem_limits();
+  if (o.solve_mode == 2) autotune_solve(c);
   cudaMemset(c->Vb, 0, sizeof(double) * vslots * kMaxB * n);
   cudaMemset(c->Xb, 0, sizeof(double) * G * n);
   if (cudaDeviceSynchronize() != cudaSuccess) {
@@ -1350,6 +1452,23 @@ matex_status matex_set_batching(matex_ctx* c, int32_t one_group_at_a_time) {
 matex_status matex_debug_inject_wait(matex_ctx* c, int32_t on) {
   if (!c) return MATEX_ERR_ARG;
   c->inject_wait = on != 0;
+  return MATEX_OK;
+}
+
+matex_status matex_get_autotune(matex_ctx* c, int32_t* ncols, int32_t* mode, float* ms,
+                               int32_t cap, int32_t* count) {
+  if (!c) return MATEX_ERR_ARG;
+  const int k = (int)c->tune_reps.size();
+  if (count) *count = k;
+  for (int i = 0; i < std::min(cap, k); ++i) {
+    if (ncols) ncols[i] = c->tune_reps[i];
+    if (mode) mode[i] = c->tune_modes[i];
+    if (ms) {
+      const bool have = 2 * (size_t)i + 1 < c->tune_ms.size();
+      ms[2 * i] = have ? c->tune_ms[2 * i] : -1.f;
+      ms[2 * i + 1] = have ? c->tune_ms[2 * i + 1] : -1.f;
+    }
+  }
   return MATEX_OK;
 }
 

@@ -64,7 +64,8 @@ EXPORTS = ["matex_default_opts", "matex_setup", "matex_run", "matex_run_host", "
            "matex_solve", "matex_expm", "matex_get_m", "matex_get_sizes", "matex_get_setup_stats",
            "matex_last_error", "matex_status_string", "matex_destroy", "matex_set_profiling",
            "matex_get_profile", "matex_host_factor_solve", "matex_set_batching",
-           "matex_debug_inject_wait", "matex_solve_noalloc", "matex_grad", "matex_set_caps"]
+           "matex_debug_inject_wait", "matex_solve_noalloc", "matex_grad", "matex_set_caps",
+           "matex_get_autotune"]
 
 
 def _load():
@@ -102,6 +103,8 @@ def _load():
     lib.matex_last_error.restype = C.c_char_p
     lib.matex_status_string.argtypes = [C.c_int]
     lib.matex_status_string.restype = C.c_char_p
+    lib.matex_get_autotune.argtypes = [P, i32p, i32p, C.POINTER(C.c_float), C.c_int32, i32p]
+    lib.matex_get_autotune.restype = C.c_int
     lib.matex_set_caps.argtypes = [P, dp]
     lib.matex_set_caps.restype = C.c_int
     lib.matex_grad.argtypes = [P, P, P, P]
@@ -242,6 +245,19 @@ def matex_get_setup_stats(ctx):
     return s
 
 
+def matex_get_autotune(ctx):
+    cnt = C.c_int32()
+    _check(ctx, _lib.matex_get_autotune(ctx, None, None, None, 0, C.byref(cnt)))
+    k = cnt.value
+    nc = np.zeros(max(k, 1), np.int32)
+    md = np.zeros(max(k, 1), np.int32)
+    ms = np.zeros(max(2 * k, 2), np.float32)
+    _check(ctx, _lib.matex_get_autotune(ctx, _ptr(nc, C.c_int32), _ptr(md, C.c_int32),
+                                        ms.ctypes.data_as(C.POINTER(C.c_float)), k, C.byref(cnt)))
+    return [dict(ncols=int(nc[i]), mode=int(md[i]), persistent_ms=float(ms[2 * i]),
+                 level_ms=float(ms[2 * i + 1])) for i in range(k)]
+
+
 def matex_set_caps(ctx, c_host):
     a = np.ascontiguousarray(c_host, dtype=np.float64)
     _check(ctx, _lib.matex_set_caps(ctx, _ptr(a, C.c_double)))
@@ -280,7 +296,7 @@ class Sim:
     src_group, n_groups, gamma, tol, m_max, t_end, dt_out)."""
 
     def __init__(self, p, col_block=0, group_select=-1, include_dc=True, rows=None,
-                 replay_m=None, max_width=0, strict=False, stream=None, solve_mode=0,
+                 replay_m=None, max_width=0, strict=False, stream=None, solve_mode=2,
                  tape=False, **overrides):
         o = matex_default_opts()
         o.col_block = col_block
@@ -355,6 +371,9 @@ class Sim:
 
     def one_group_at_a_time(self, on=True):
         matex_set_batching(self.ctx, on)
+
+    def autotune(self):
+        return matex_get_autotune(self.ctx)
 
     def profile(self, on=None):
         if on is not None:

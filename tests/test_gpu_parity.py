@@ -176,7 +176,7 @@ def test_persistent_and_level_solves_agree(M, mode):
 def test_bounded_wait_reports_timeout_and_context_recovers(M):
     import time
     p = gridgen.small_mesh(14, nx=12, ny=12, n_src=4)
-    sim = M.Sim(p)
+    sim = M.Sim(p, solve_mode=0)  # the hook acts on the persistent solve
     good = sim.run().cpu().numpy()
     M.matex_debug_inject_wait(sim.ctx, True)
     t0 = time.time()
@@ -187,6 +187,16 @@ def test_bounded_wait_reports_timeout_and_context_recovers(M):
     M.matex_debug_inject_wait(sim.ctx, False)
     again = sim.run().cpu().numpy()
     assert np.array_equal(again, good)
+
+
+def test_autotuner_measures_both_modes(M):
+    p = gridgen.small_mesh(15, nx=30, ny=30, layers=2, n_src=20, group_templates=[2] * 10)
+    sim = M.Sim(p)
+    tab = sim.autotune()
+    assert [t["ncols"] for t in tab][:4] == [1, 2, 4, 8]
+    for t in tab:
+        assert t["mode"] in (0, 1) and t["persistent_ms"] > 0 and t["level_ms"] > 0
+        assert t["mode"] == (1 if t["level_ms"] < t["persistent_ms"] else 0)
 
 
 def test_m_max_one_and_replay(M):
