@@ -158,8 +158,11 @@ def reference_arm(args):
 
 
 def ncu_case(what: str) -> int:
-    """The bench grid restricted to groups 0-7 (about 2.5 GB on the device, solve
-    panels still larger than L2): one warm call, then the profiled call."""
+    """The bench grid restricted to groups 0-7 (32 for "levels"; a few GB on the
+    device, solve panels still larger than L2): one warm call, then the
+    profiled call.  "solve": matex_solve of 16 columns with the persistent
+    kernel; "levels": 64 columns with one launch per tree level; "run": one
+    full matex_run."""
     import numpy as np
     import torch
 
@@ -168,14 +171,14 @@ def ncu_case(what: str) -> int:
     B.build()
     from paper_1511_04519_gb300 import matex as M
     p = gridgen.config1()
-    groups = 8
+    groups = 32 if what == "levels" else 8
     sel = p.src_group < groups
     off = np.concatenate([[0], np.cumsum(np.diff(p.pwl_off)[sel])]).astype(np.int32)
     q = gridgen.with_sources(p, p.src_node[sel], off, p.pwl_t.reshape(-1, 3)[sel].ravel(),
                              p.pwl_v.reshape(-1, 3)[sel].ravel(), p.src_group[sel], groups)
-    sim = M.Sim(q)
-    if what == "solve":
-        k = 16
+    sim = M.Sim(q, solve_mode={"solve": 0, "levels": 1}.get(what, 2))
+    if what in ("solve", "levels"):
+        k = 16 if what == "solve" else 64
         b = torch.randn(k, p.n, dtype=torch.float64, device="cuda")
         x = torch.empty_like(b)
         M.matex_solve(sim.ctx, 0, k, b.data_ptr(), x.data_ptr())
@@ -206,7 +209,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--profile-step", action="store_true",
                     help="warm up, run one step inside cudaProfilerStart/Stop, print its stats")
-    ap.add_argument("--ncu-case", choices=["solve", "run"], default=None,
+    ap.add_argument("--ncu-case", choices=["solve", "levels", "run"], default=None,
                     help="reduced case for full ncu captures: the same grid with 8 groups; "
                          "one warm call, then one call inside cudaProfilerStart/Stop")
     args = ap.parse_args()
