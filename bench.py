@@ -196,6 +196,61 @@ def ncu_case(what: str) -> int:
     return 0
 
 
+def batch_grids(args, M, stream):
+    """The uneven-grid workload: independent single-layer meshes (side
+    U[100, 450], 4-16 groups each) run as one CUDA graph launch, one branch per
+    grid.  Each grid outputs 64 sampled nodes (its internal output buffer
+    still holds every node)."""
+    import numpy as np
+    import torch
+
+    import gridgen
+    probs = gridgen.config4()[: args.grids]
+    t0 = time.perf_counter()
+    sims = []
+    for p in probs:
+        rows = np.sort(np.random.default_rng(p.n).choice(p.n, 64, replace=False)).astype(np.int32)
+        sims.append(M.Sim(p, rows=rows, stream=stream))
+    setup_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    batch = M.Batch(sims)          # a plain, recorded run of every grid
+    record_s = time.perf_counter() - t0
+    outs = [torch.empty((s.n_times, s.n_rows), dtype=torch.float64, device="cuda") for s in sims]
+    for _ in range(args.warmup):
+        batch.run(outs)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    grid_ms = []
+    for _ in range(args.steps):
+        _, gm = batch.run(outs)
+        grid_ms.append(gm)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    gm = np.mean(np.array(grid_ms), axis=0)
+    replayed = sum(int(s.stats.graph_replay) for s in sims)
+    units = sum(p.n * (p.n_out - 1) * p.n_groups for p in probs)
+    # the same grids one after another (each its own graph replay)
+    ev0.record(stream)
+    for s, o in zip(sims, outs):
+        s.run(o)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = ev0.elapsed_time(ev1)
+    res = {"workload": f"{len(probs)}_single_layer_meshes_side_100_450",
+           "nodes": int(sum(p.n for p in probs)), "groups": int(sum(p.n_groups for p in probs)),
+           "value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+           "grids_replayed": replayed, "sequential_ms": seq_ms,
+           "concurrency_speedup": seq_ms / ms,
+           "grid_ms": {"min": float(gm.min()), "median": float(np.median(gm)), "max": float(gm.max())},
+           "setup_s": setup_s, "record_s": record_s}
+    batch.close()
+    del sims
+    torch.cuda.empty_cache()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,6 +262,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serial", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--grids", type=int, default=0,
+                    help="also run that many of the 96 uneven single-layer grids as one "
+                         "batch graph launch and report their aggregate rate")
     ap.add_argument("--profile-step", action="store_true",
                     help="warm up, run one step inside cudaProfilerStart/Stop, print its stats")
     ap.add_argument("--ncu-case", choices=["solve", "levels", "run"], default=None,
@@ -379,6 +437,8 @@ def main():
                    "forward_taped_ms": fm, "grad_ms": gm, "grad_over_forward": gm / fm}
         del sim3
 
+    grids = batch_grids(args, M, stream) if args.grids else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = run_cpu_sample(args.cpu_groups)
@@ -399,7 +459,9 @@ def main():
                         for k, v in prof.items()},
             "run_stats": {k: stats[k] for k in ("n_segments", "krylov_segments", "sum_m", "max_m",
                                                  "nonconv", "sweeps_M", "sweeps_G", "solve_columns",
-                                                 "rounds")},
+                                                 "rounds", "kernel_launches", "graph_replay",
+                                                 "graph_capture_ms")},
+            "batch_grids": grids,
             "autotune": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in t.items()}
                          for t in tuning],
             "setup_ms": {"order": setup["setup_order_ms"], "factor": setup["setup_factor_ms"],

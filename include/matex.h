@@ -69,6 +69,11 @@ typedef struct matex_opts {
                               chosen per column count by the setup-time autotuner */
   int32_t tape;            /* 1: every run keeps each segment's Krylov basis, solve outputs and
                               Hessenberg on the device so that matex_grad can follow it */
+  int32_t graph;           /* 1 (default): after a plain run, record the run's launches as a
+                              CUDA graph and replay it in later runs while the device's
+                              active-column counts match the recorded ones (checked on the
+                              device; on a mismatch the run is redone plainly and re-recorded);
+                              0: every run is issued launch by launch */
 } matex_opts;
 
 /* Counters and timings of the last matex_run (or of setup for the setup_* fields). */
@@ -91,6 +96,8 @@ typedef struct matex_stats {
   int64_t solve_columns;   /* right-hand sides solved, over all sweeps */
   int32_t kernel_launches; /* kernels launched by the last matex_run */
   int32_t rounds;          /* segment rounds (max segments over the selected groups) */
+  int32_t graph_replay;    /* 1: the last run replayed the captured CUDA graph */
+  double graph_capture_ms; /* host time of the last graph capture + instantiation */
 } matex_stats;
 
 void matex_default_opts(matex_opts* opts);
@@ -150,6 +157,30 @@ matex_status matex_run_host(matex_ctx* ctx, const double* pwl_v_host, double* x_
                             matex_stats* stats);
 
 /*
+ * Several independent contexts (e.g. grids of different sizes, each set up on
+ * its own) run as one CUDA graph launch: each context's recorded run is a
+ * branch of one graph, the branches have no edges between them, so the GPU
+ * runs the grids concurrently.  Built with matex_batch_create (contexts
+ * without a recorded run are run once plainly and recorded; each needs
+ * opts.graph = 1), run with matex_batch_run:
+ *   x_outs     host array [count] of device output pointers, one per context
+ *              (layout as matex_run)
+ *   stats      host [count] or NULL
+ *   grid_ms    host [count] or NULL: per context, the time from the start of
+ *              the batch launch to the end of that context's branch (CUDA
+ *              events inside the graph)
+ * A context whose device counts diverged from its recording is redone plainly,
+ * re-recorded, and the batch graph rebuilt; results are then the plain run's.
+ * The batch does not own the contexts; destroy it before any of them.
+ */
+typedef struct matex_batch matex_batch;
+matex_status matex_batch_create(matex_batch** out, matex_ctx* const* ctxs, int32_t count);
+matex_status matex_batch_run(matex_batch* batch, double* const* x_outs, matex_stats* stats,
+                             float* grid_ms);
+const char* matex_batch_last_error(const matex_batch* batch);
+void matex_batch_destroy(matex_batch* batch);
+
+/*
  * Scheduling mode of later runs: 0 (default) runs every group as a column of
  * one batched sweep per segment round; 1 runs the same kernels one group at a
  * time (one column per launch, groups in order), the unbatched comparison.
@@ -178,7 +209,14 @@ matex_status matex_grad(matex_ctx* ctx, const double* xbar, double* dc, double* 
  */
 matex_status matex_set_caps(matex_ctx* ctx, const double* c);
 
-/* Replace the source currents (host, layout of pwl_v at setup). */
+/*
+ * Replace the source currents (host, layout of pwl_v at setup).  The
+ * breakpoint times stay those of setup.  Setup skips the segments on which a
+ * group has injected nothing since t = 0 (their response is exactly zero);
+ * values that would make such a segment, or a group's current at t = 0,
+ * non-zero return MATEX_ERR_ARG and change nothing (set up a new context).
+ * Scaling the setup currents never does.
+ */
 matex_status matex_set_sources(matex_ctx* ctx, const double* pwl_v_host);
 
 /*

@@ -422,6 +422,26 @@ void reduce_dots(const double* partials, int nchunks, int K, int nb, const int32
   reduce_dots_kernel<<<K, 32, 0, st>>>(partials, nchunks, nb, iter, ss, j, mode);
 }
 
+namespace {
+__global__ void expect_count_kernel(const int32_t* __restrict__ count, int expected,
+                                    int32_t* __restrict__ iter, int32_t* __restrict__ iter_grp,
+                                    const int32_t* __restrict__ vslot, int32_t* __restrict__ flag) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int got = *count;
+  if (got == expected) return;
+  *flag = 1;
+  for (int k = got > 0 ? got : 0; k < expected; ++k) {
+    iter[k] = 0;
+    iter_grp[k] = vslot[0];
+  }
+}
+}  // namespace
+
+void expect_count(const int32_t* count, int expected, int32_t* iter, int32_t* iter_grp,
+                  const int32_t* vslot, int32_t* flag, cudaStream_t st) {
+  expect_count_kernel<<<1, 32, 0, st>>>(count, expected, iter, iter_grp, vslot, flag);
+}
+
 void residual_check(SmallState ss, const RoundCols& rc, int K, int j, double gamma, double tol,
                     int m_max, const int32_t* replay, const int32_t* iter_in, int32_t* iter_out,
                     int32_t* iter_grp, int32_t* iter_count, cudaStream_t st) {

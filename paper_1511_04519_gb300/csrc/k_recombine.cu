@@ -64,7 +64,7 @@ recombine_kernel(double* __restrict__ Xp, int64_t n, const double* __restrict__ 
                  int obeg_min, double dt_out) {
   const int64_t i = (int64_t)blockIdx.x * kRecThreads + threadIdx.x;
   const int o0 = obeg_min + blockIdx.y * kOT;
-  if (i >= n) return;
+  if (i >= n || (rc.abort && *rc.abort)) return;
   double acc[kOT];
 #pragma unroll
   for (int t = 0; t < kOT; ++t) acc[t] = 0.0;

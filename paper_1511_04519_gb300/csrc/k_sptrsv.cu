@@ -18,6 +18,8 @@
 // four threads per panel row/column, each thread holding all KB columns.
 #include "kernels.h"
 
+#include <mutex>
+
 namespace matex {
 
 namespace {
@@ -37,7 +39,10 @@ __device__ __forceinline__ void fwd_task(const DevFactor& F, int s, int i0, int 
   const int w = F.sup_first[s + 1] - f;
   const int64_t rp = F.sup_rowptr[s];
   const int ld = (int)(F.sup_rowptr[s + 1] - rp);  // w + r
-  for (int e = threadIdx.x; e < w * KB; e += blockDim.x) {
+  // L_ss^{-1} is lower triangular: rows below i0 + 32 of the diagonal block
+  // have no entries right of column i0 + 32, so the block stops there
+  const int jend = min(w, i0 + kRowBlock);
+  for (int e = threadIdx.x; e < jend * KB; e += blockDim.x) {
     const int j = e / KB, q = e - j * KB;
     sb[e] = __ldcg(Y + (int64_t)(f + j) * ldy + c0 + q);
   }
@@ -45,13 +50,15 @@ __device__ __forceinline__ void fwd_task(const DevFactor& F, int s, int i0, int 
   const double* __restrict__ P = F.pan_cm + F.pan_off[s];
   const int sub = threadIdx.x % kSplit;
   const int i = i0 + threadIdx.x / kSplit;
+  // the same bound per warp (its 8 rows), uniform across the warp
+  const int jw = min(jend, i0 + (int)(threadIdx.x / 32 + 1) * (32 / kSplit));
   double acc[KB];
 #pragma unroll
   for (int q = 0; q < KB; ++q) acc[q] = 0.0;
   if (i < ld) {
     int j = sub;
     // four panel loads in flight per thread, then their FMAs
-    for (; j + 3 * kSplit < w; j += 4 * kSplit) {
+    for (; j + 3 * kSplit < jw; j += 4 * kSplit) {
       const double p0 = P[(int64_t)j * ld + i];
       const double p1 = P[(int64_t)(j + kSplit) * ld + i];
       const double p2 = P[(int64_t)(j + 2 * kSplit) * ld + i];
@@ -64,7 +71,7 @@ __device__ __forceinline__ void fwd_task(const DevFactor& F, int s, int i0, int 
         acc[q] = fma(p3, sb[(j + 3 * kSplit) * KB + q], a);
       }
     }
-    for (; j < w; j += kSplit) {
+    for (; j < jw; j += kSplit) {
       const double p = P[(int64_t)j * ld + i];
 #pragma unroll
       for (int q = 0; q < KB; ++q) acc[q] = fma(p, sb[j * KB + q], acc[q]);
@@ -98,7 +105,9 @@ __device__ __forceinline__ void bwd_task(const DevFactor& F, int s, int j0, int 
   const int64_t rp = F.sup_rowptr[s];
   const int ld = (int)(F.sup_rowptr[s + 1] - rp);
   const int32_t* __restrict__ rows = F.sup_rows + rp;
-  for (int e = threadIdx.x; e < ld * KB; e += blockDim.x) {
+  // column j of the lower-triangular L_ss^{-1} is zero above row j, so the
+  // panel rows of this block of columns start at j0
+  for (int e = j0 * KB + threadIdx.x; e < ld * KB; e += blockDim.x) {
     const int i = e / KB, q = e - i * KB;
     ub[e] = i < w ? __ldcg(Y2 + (int64_t)(f + i) * ldy + c0 + q) * F.dinv[f + i]
                   : -__ldcg(Y + (int64_t)rows[i] * ldy + c0 + q);
@@ -111,7 +120,8 @@ __device__ __forceinline__ void bwd_task(const DevFactor& F, int s, int j0, int 
 #pragma unroll
   for (int q = 0; q < KB; ++q) acc[q] = 0.0;
   if (j < w) {
-    int i = sub;
+    // the warp's 8 columns start at j0 + 8 * warp: rows above are zero for all of them
+    int i = j0 + (int)(threadIdx.x / 32) * (32 / kSplit) + sub;
     for (; i + 3 * kSplit < ld; i += 4 * kSplit) {
       const double p0 = P[(int64_t)i * w + j];
       const double p1 = P[(int64_t)(i + kSplit) * w + j];
@@ -257,6 +267,7 @@ __global__ void __launch_bounds__(kSolveThreads)
 fwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* __restrict__ Y,
                  double* __restrict__ Y2, int ldy) {
   extern __shared__ double sb[];
+  if (F.abort && *F.abort) return;
   const int2 tk = tasks[blockIdx.x / ncb];
   run_fwd<KB>(F, tk, (blockIdx.x % ncb) * KB, Y, Y2, ldy, sb);
 }
@@ -266,6 +277,7 @@ __global__ void __launch_bounds__(kSolveThreads)
 bwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* __restrict__ Y,
                  const double* __restrict__ Y2, int ldy) {
   extern __shared__ double ub[];
+  if (F.abort && *F.abort) return;
   const int2 tk = tasks[blockIdx.x / ncb];
   run_bwd<KB>(F, tk, (blockIdx.x % ncb) * KB, Y, Y2, ldy, ub);
 }
@@ -319,6 +331,7 @@ persistent_solve_kernel(DevFactor F, PersistSched ps, double* __restrict__ Y,
   extern __shared__ double sm[];
   __shared__ long long sh_t;
   __shared__ int sh_ok;
+  if (F.abort && *F.abort) return;  // set before the launch: every CTA leaves, none waits
   const long long total = ps.nf_total + ps.nb_total;
   for (;;) {
     if (threadIdx.x == 0) sh_t = (long long)atomicAdd(ps.ticket, 1ull);
@@ -495,15 +508,40 @@ void persistent_solve(const DevFactor& F, const PersistSched& ps, int grid, size
 
 void bump_counter(int* p, cudaStream_t st) { bump_kernel<<<1, 32, 0, st>>>(p); }
 
+// The dynamic shared-memory cap of a kernel is a process-wide attribute (per
+// device), while each context needs its own amount: only ever raise it, so a
+// context set up later with smaller panels does not lower it below what an
+// earlier context launches with.
+namespace {
+std::mutex g_smem_mu;
+int g_solve_smem[64] = {0};
+int g_persist_smem[64] = {0};
+int cur_device_slot() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return dev >= 0 && dev < 64 ? dev : 63;
+}
+}  // namespace
+
 int persistent_blocks_per_sm(size_t smem) {
+  {
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    int& cur = g_persist_smem[cur_device_slot()];
+    if ((int)smem > cur) {
+      cudaFuncSetAttribute(persistent_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      cur = (int)smem;
+    }
+  }
   int nb = 0;
-  cudaFuncSetAttribute(persistent_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_solve_kernel, kSolveThreads, smem);
   return nb;
 }
-
 void set_solve_smem_limit(int bytes) {
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  int& cur = g_solve_smem[cur_device_slot()];
+  if (bytes <= cur) return;
+  cur = bytes;
   cudaFuncSetAttribute(fwd_level_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   cudaFuncSetAttribute(fwd_level_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   cudaFuncSetAttribute(fwd_level_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);

@@ -23,6 +23,8 @@ struct DevFactor {
   const double* pan_cm;
   const double* pan_rm;
   const int32_t* pack;   // supernode lists of packed tasks
+  const int32_t* abort = nullptr;  // device flag or null: when set before a launch, its CTAs exit at once
+                         // (a graph replay whose counts diverged; its result is discarded)
 };
 
 constexpr int kRowBlock = 32;  // panel rows (forward) / columns (backward) per task
@@ -105,6 +107,7 @@ struct RoundCols {
   const int32_t* obeg;     // first output index in the segment
   const int32_t* nout;     // outputs in the segment
   const int64_t* segid;    // global (group, segment) index
+  const int32_t* abort = nullptr;  // device flag or null: set, the recombination exits at once
 };
 
 struct SourceTable {
@@ -164,6 +167,12 @@ void reduce_dots(const double* partials, int nchunks, int K, int nb, const int32
                  SmallState ss, int j, int mode, cudaStream_t st);
 // residual test after step j (m = j+1): decides status per column; writes
 // the compacted list of still-iterating columns and its count
+// Guard of a recorded (graph) run: when *count differs from the count the
+// recorded launches were sized for, raise *flag and point the entries
+// [*count, expected) of iter / iter_grp at column 0 of the round, so that the
+// rest of the replay (whose result is then discarded) stays in range.
+void expect_count(const int32_t* count, int expected, int32_t* iter, int32_t* iter_grp,
+                  const int32_t* vslot, int32_t* flag, cudaStream_t st);
 void residual_check(SmallState ss, const RoundCols& rc, int K, int j, double gamma, double tol,
                     int m_max, const int32_t* replay, const int32_t* iter_in, int32_t* iter_out,
                     int32_t* iter_grp, int32_t* iter_count, cudaStream_t st);

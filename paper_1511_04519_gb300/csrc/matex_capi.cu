@@ -43,6 +43,12 @@ struct Round {
   int32_t obeg_min, oend_max;
 };
 
+// Launch and sweep counts of one pass of the run.
+struct PassCounts {
+  int launches = 0, sweepsM = 0, sweepsG = 0;
+  int64_t solve_cols = 0;
+};
+
 }  // namespace
 
 struct matex_ctx {
@@ -113,6 +119,15 @@ struct matex_ctx {
   double *rc_l0 = nullptr, *rc_len = nullptr, *rc_hfirst = nullptr, *rc_lprev = nullptr;
   std::vector<int32_t> init_groups;   // groups whose input is non-zero at t = 0
   int32_t* init_groups_d = nullptr;
+  // zero pattern of the setup currents, per selected group: the local
+  // transition spots, which segments were skipped as identically zero, and
+  // whether the current at t = 0 is non-zero (checked by set_sources)
+  std::vector<int32_t> pwl_off_h;
+  std::vector<double> pwl_t_h;
+  std::vector<std::vector<int32_t>> gsrc_h;
+  std::vector<std::vector<double>> glts_h;
+  std::vector<std::vector<char>> gzero_h;
+  std::vector<char> ginit_h;
   int64_t* rc_segid = nullptr;
   int32_t* replay_d = nullptr;
   // work buffers
@@ -138,6 +153,15 @@ struct matex_ctx {
   std::vector<int64_t> h_segid_all;
   std::vector<int32_t> round_cover;  // outputs covered per round
   int64_t offd_rows = 0;              // sum over supernodes of off-diagonal rows
+  // CUDA graph of one run: recorded after a plain run, replayed while the
+  // device's active-column counts equal the recorded ones
+  std::vector<int32_t> kit_trace;  // counts read by the host in the plain run, in order
+  cudaStream_t gst = nullptr;      // private capture stream
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  PassCounts graph_counts;
+  double graph_ms = 0.0;
+  int64_t graph_gen = 0;           // bumped at every new recording
   // profiling
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -149,6 +173,9 @@ struct matex_ctx {
   ~matex_ctx() {
     for (void* p : allocs) cudaFree(p);
     if (h_count) cudaFreeHost(h_count);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (gst) cudaStreamDestroy(gst);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   }
 
@@ -228,6 +255,7 @@ std::vector<double> group_lts(const std::vector<int32_t>& srcs, const int32_t* p
 // (supernode, 32 panel columns) and the column block.  Returns false on an
 // allocation failure.
 constexpr int kSolveSmemCap = 24 * 1024 + 512;  // keeps ~8 solve CTAs resident per SM
+constexpr int kSplitFor = 4;                    // threads sharing one panel row / column
 
 bool plan_levels(matex_ctx* c) {
   const Symbolic& S = c->S;
@@ -293,6 +321,28 @@ bool plan_levels(matex_ctx* c) {
       }
     }
     flush(cur, bt);
+    // longest tasks first (the block scheduler hands out CTAs in index order,
+    // so the level's tail is made of short tasks); duration ~ the length of one
+    // thread's dot product: a quarter of the panel extent for split tasks, the
+    // whole extent for packed ones (one thread per row or column)
+    auto sw = [&](int s) { return S.sup_first[s + 1] - S.sup_first[s]; };
+    auto sld = [&](int s) { return (int)(S.sup_rowptr[s + 1] - S.sup_rowptr[s]); };
+    auto fdur = [&](const int2& t) {
+      if (t.x >= 0) return std::min(sw(t.x), t.y + kRowBlock) / kSplitFor;
+      int d = 0;
+      for (int k = 0; k < t.y; ++k) d = std::max(d, sw(pack[-1 - t.x + k]));
+      return d;
+    };
+    auto bdur = [&](const int2& t) {
+      if (t.x >= 0) return (sld(t.x) - t.y) / kSplitFor;
+      int d = 0;
+      for (int k = 0; k < t.y; ++k) d = std::max(d, sld(pack[-1 - t.x + k]));
+      return d;
+    };
+    std::stable_sort(ft.begin() + fofs[l], ft.end(),
+                     [&](const int2& a, const int2& b) { return fdur(a) > fdur(b); });
+    std::stable_sort(bt.begin() + bofs[l], bt.end(),
+                     [&](const int2& a, const int2& b) { return bdur(a) > bdur(b); });
     L.nf = (int32_t)(ft.size() - fofs[l]);
     L.nb = (int32_t)(bt.size() - bofs[l]);
     L.max_w = std::max(mw, kPackRows);
@@ -423,11 +473,12 @@ RoundCols round_cols(matex_ctx* c, const Round& r) {
   rc.obeg = c->rc_obeg + r.begin;
   rc.nout = c->rc_nout + r.begin;
   rc.segid = c->rc_segid + r.begin;
+  rc.abort = c->d_count + 2;
   return rc;
 }
 
 matex_status read_count(matex_ctx* c, int* out) {
-  cudaMemcpyAsync(c->h_count, c->d_count, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(c->h_count, c->d_count, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "sync");
   *out = c->h_count[0];
   if (c->h_count[1] != 0)
@@ -487,15 +538,16 @@ void prof_collect(matex_ctx* c, const std::vector<int32_t>& m_seg) {
 }
 
 // Algorithmic work of one batched solve pair with K right-hand sides: a
-// multiply-add per stored panel entry and column in each direction, the
-// D^{-1} scaling; bytes: each panel read once per direction, D^{-1}, the row
+// multiply-add per strictly-lower nonzero of the supernodal L and column in
+// each direction, plus the D^{-1} scaling; bytes: the nonzeros of each panel
+// (L_ss^{-1} is lower triangular) read once per direction, D^{-1}, the row
 // lists, and the right-hand sides read and written once per direction.
 double solve_flops(const matex_ctx* c, int K) {
-  return (4.0 * (double)c->S.pan_off[c->S.nsup] + (double)c->n) * K;
+  return (4.0 * (double)c->S.nnz_L + 2.0 * (double)c->n) * K;
 }
 double solve_bytes(const matex_ctx* c, int K) {
-  return 16.0 * (double)c->S.pan_off[c->S.nsup] + 8.0 * c->n + 8.0 * (double)c->S.sup_rowptr[c->S.nsup] +
-         32.0 * (double)c->n * K;
+  return 16.0 * ((double)c->S.nnz_L + (double)c->n) + 8.0 * c->n +
+         8.0 * (double)c->S.sup_rowptr[c->S.nsup] + 32.0 * (double)c->n * K;
 }
 
 enum { P_SOLVE = 0, P_MOVE = 1, P_GS = 2, P_SMALL = 3, P_RECOMB = 4, P_OTHER = 5 };
@@ -510,7 +562,7 @@ enum { P_SOLVE = 0, P_MOVE = 1, P_GS = 2, P_SMALL = 3, P_RECOMB = 4, P_OTHER = 5
 std::string tune_key(matex_ctx* c) {
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, c->device);
-  char buf[256];
+  char buf[512];
   std::snprintf(buf, sizeof(buf), "n=%lld;nsup=%d;pan=%lld;lev=%d;ldy=%d;dev=%s", (long long)c->n,
                 c->S.nsup, (long long)c->S.pan_off[c->S.nsup], (int)c->levels.size(), c->ldy,
                 prop.name);
@@ -592,8 +644,13 @@ void autotune_solve(matex_ctx* c) {
   }
 }
 
-matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
-  const double t0 = now_ms();
+// One pass of the run (everything up to the output permutation) on c->st.
+// Plain (capture = false): the host reads every active-column count from the
+// device and appends it to kit_trace.  Recording (capture = true): the stream
+// is being captured into a CUDA graph; each count is taken from kit_trace and
+// followed by a guard kernel that raises the divergence flag (and keeps every
+// index in range) if the device count differs when the graph is replayed.
+matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
   cudaStream_t st = c->st;
   const int64_t n = c->n;
   const double nd = (double)n;
@@ -601,7 +658,20 @@ matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
   int launches = 0, sweepsM = 0, sweepsG = 0;
   int64_t solve_cols_total = 0;
   int e;
-  cudaMemsetAsync(c->d_count, 0, 2 * sizeof(int32_t), st);
+  size_t tpos = 0;
+  auto count = [&](int* out, int32_t* iter_now, const int32_t* vslot) -> matex_status {
+    if (!capture) {
+      const matex_status rs = read_count(c, out);
+      if (rs == MATEX_OK) c->kit_trace.push_back(*out);
+      return rs;
+    }
+    if (tpos >= c->kit_trace.size()) return fail(c, MATEX_ERR_STATE, "count trace too short");
+    *out = c->kit_trace[tpos++];
+    expect_count(c->d_count, *out, iter_now, c->iter_grp, vslot, c->d_count + 2, st);
+    launches++;
+    return MATEX_OK;
+  };
+  cudaMemsetAsync(c->d_count, 0, 4 * sizeof(int32_t), st);
   auto solve = [&](const DevFactor& F, int K) {
     e = prof_begin(c);
     const int l = solve_cols(c, F, K);
@@ -697,9 +767,9 @@ matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
     prof_end(c, e, P_SMALL, 1, 0.0, 0.0);
     launches += 2;
     int kit = 0;
-    if ((s = read_count(c, &kit)) != MATEX_OK) return s;
     int32_t* iter = c->iterA;
     int32_t* iter_next = c->iterB;
+    if ((s = count(&kit, iter, rc.vslot)) != MATEX_OK) return s;
     if (kit > 0) {
       e = prof_begin(c);
       basis_scale(c->Vb, vstride, rc.vslot, iter, kit, 0, c->ss.scale, n, st);
@@ -739,8 +809,8 @@ matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
                      c->iter_grp, c->d_count, st);
       prof_end(c, e, P_SMALL, 2, 0.0, 0.0);
       launches += 11;
-      if ((s = read_count(c, &kit)) != MATEX_OK) return s;
       std::swap(iter, iter_next);
+      if ((s = count(&kit, iter, rc.vslot)) != MATEX_OK) return s;
     }
     if (c->opts.tape) tape_small(c->ss, rc, K, c->THt, c->Tbeta, st);
     e = prof_begin(c);
@@ -757,21 +827,68 @@ matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
     launches += 4;
     if ((s = cuda_check(c, "round")) != MATEX_OK) return s;
   }
-  e = prof_begin(c);
-  permute_out(x_out, c->Xp, c->out_map, c->nrows_out, n, c->n_times, st);
-  prof_end(c, e, P_OTHER, 1, 0.0, 16.0 * (double)c->nrows_out * c->n_times);
-  launches++;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(c, "run sync");
-  if ((s = cuda_check(c, "run")) != MATEX_OK) return s;
-  {
-    int tmp = 0;
-    if ((s = read_count(c, &tmp)) != MATEX_OK) return s;
+  pc.launches = launches;
+  pc.sweepsM = sweepsM;
+  pc.sweepsG = sweepsG;
+  pc.solve_cols = solve_cols_total;
+  return MATEX_OK;
+}
+
+void drop_graph(matex_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->gexec = nullptr;
+  c->graph = nullptr;
+}
+
+// Record the run as a CUDA graph from the count trace of the plain run that
+// just finished.  Capture needs a stream other than the legacy default one, so
+// the pass is issued on the context's private capture stream.  On any failure
+// the context keeps running plainly.
+void capture_graph(matex_ctx* c) {
+  drop_graph(c);
+  const double t = now_ms();
+  if (!c->gst && cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->gst = nullptr;
+    return;
   }
-  // statistics from the per-segment records
+  cudaGetLastError();
+  cudaStream_t user = c->st;
+  c->st = c->gst;
+  cudaGraph_t g = nullptr;
+  PassCounts pc;
+  bool ok = cudaStreamBeginCapture(c->gst, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  const std::string saved_err = c->err;
+  const matex_status s = ok ? run_pass(c, true, pc) : MATEX_ERR_CUDA;
+  if (ok) ok = cudaStreamEndCapture(c->gst, &g) == cudaSuccess && s == MATEX_OK && g != nullptr;
+  c->st = user;
+  c->err = saved_err;
+  if (ok) ok = cudaGraphInstantiate(&c->gexec, g, 0) == cudaSuccess;
+  if (ok) {
+    c->graph = g;
+    c->graph_counts = pc;
+    c->graph_gen++;
+  } else {
+    if (g) cudaGraphDestroy(g);
+    c->gexec = nullptr;
+    cudaGetLastError();
+  }
+  c->graph_ms = now_ms() - t;
+}
+
+bool graph_allowed(const matex_ctx* c) { return c->opts.graph && !c->prof_on && !c->inject_wait; }
+
+// Statistics of the run that just completed (stream synchronised).
+matex_status finish_run(matex_ctx* c, const PassCounts& pc, double t0, bool replayed,
+                        matex_stats* stats) {
   std::vector<int32_t> m(c->n_segments), stt(c->n_segments);
   if (c->n_segments) {
-    cudaMemcpy(m.data(), c->m_rec, sizeof(int32_t) * c->n_segments, cudaMemcpyDeviceToHost);
-    cudaMemcpy(stt.data(), c->st_rec, sizeof(int32_t) * c->n_segments, cudaMemcpyDeviceToHost);
+    if (cudaMemcpy(m.data(), c->m_rec, sizeof(int32_t) * c->n_segments, cudaMemcpyDeviceToHost) !=
+            cudaSuccess ||
+        cudaMemcpy(stt.data(), c->st_rec, sizeof(int32_t) * c->n_segments, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+      return cuda_check(c, "run records");
   }
   matex_stats& o = c->last;
   o = c->setup_stats;
@@ -785,17 +902,58 @@ matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
     if (stt[i] == 3) o.nonconv++;
     if (stt[i] == 2) o.breakdowns++;
   }
-  o.sweeps_M = sweepsM;
-  o.sweeps_G = sweepsG;
-  o.solve_columns = solve_cols_total;
-  o.kernel_launches = launches;
-  o.rounds = (int32_t)rounds.size();
+  o.sweeps_M = pc.sweepsM;
+  o.sweeps_G = pc.sweepsG;
+  o.solve_columns = pc.solve_cols;
+  o.kernel_launches = pc.launches + 1;  // + the output permutation
+  o.rounds = (int32_t)(c->serial ? c->serial_rounds.size() : c->rounds.size());
+  o.graph_replay = replayed ? 1 : 0;
+  o.graph_capture_ms = c->graph_ms;
   c->taped = c->opts.tape && !c->serial;
-  prof_collect(c, m);
+  if (!replayed) prof_collect(c, m);
   if (stats) *stats = o;
   if (c->opts.strict && o.nonconv > 0)
     return fail(c, MATEX_ERR_NOCONV, "some segments reached m_max above tol");
   return MATEX_OK;
+}
+
+// Device flags after a replay: 0 = consistent, 1 = counts diverged; an
+// expired bounded wait is an error.
+matex_status replay_flags(matex_ctx* c, bool* diverged) {
+  cudaMemcpyAsync(c->h_count, c->d_count, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "replay sync");
+  if (c->h_count[1] != 0)
+    return fail(c, MATEX_ERR_TIMEOUT, "a bounded wait of the persistent solve expired");
+  *diverged = c->h_count[2] != 0;
+  return MATEX_OK;
+}
+
+matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
+  const double t0 = now_ms();
+  matex_status s;
+  if (graph_allowed(c) && c->gexec) {
+    if (cudaGraphLaunch(c->gexec, c->st) != cudaSuccess) return cuda_check(c, "graph launch");
+    permute_out(x_out, c->Xp, c->out_map, c->nrows_out, c->n, c->n_times, c->st);
+    if ((s = cuda_check(c, "graph run")) != MATEX_OK) return s;
+    bool diverged = false;
+    if ((s = replay_flags(c, &diverged)) != MATEX_OK) return s;
+    if (!diverged) return finish_run(c, c->graph_counts, t0, true, stats);
+    drop_graph(c);  // the counts changed: run plainly and record again
+  }
+  c->kit_trace.clear();
+  PassCounts pc;
+  if ((s = run_pass(c, false, pc)) != MATEX_OK) return s;
+  const int e = prof_begin(c);
+  permute_out(x_out, c->Xp, c->out_map, c->nrows_out, c->n, c->n_times, c->st);
+  prof_end(c, e, P_OTHER, 1, 0.0, 16.0 * (double)c->nrows_out * c->n_times);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "run sync");
+  if ((s = cuda_check(c, "run")) != MATEX_OK) return s;
+  {
+    int tmp = 0;
+    if ((s = read_count(c, &tmp)) != MATEX_OK) return s;
+  }
+  if (graph_allowed(c)) capture_graph(c);
+  return finish_run(c, pc, t0, false, stats);
 }
 
 // Reverse sweep over the forward's rounds (latest first); per round the
@@ -923,7 +1081,7 @@ matex_status matex_grad(matex_ctx* c, const double* xbar, double* dc, double* da
   if (!xbar || !dc || (c->n_src > 0 && !damp)) return fail(c, MATEX_ERR_ARG, "NULL argument");
   if (!c->opts.tape) return fail(c, MATEX_ERR_STATE, "matex_grad needs a context set up with tape = 1");
   if (!c->taped) return fail(c, MATEX_ERR_STATE, "matex_grad needs a preceding batched matex_run");
-  cudaMemsetAsync(c->d_count, 0, 2 * sizeof(int32_t), c->st);
+  cudaMemsetAsync(c->d_count, 0, 4 * sizeof(int32_t), c->st);
   return run_grad(c, xbar, dc, damp);
 }
 
@@ -935,6 +1093,7 @@ void matex_default_opts(matex_opts* o) {
   o->include_dc = 1;
   o->max_width = 1024;
   o->solve_mode = 2;
+  o->graph = 1;
 }
 
 const char* matex_status_string(matex_status s) {
@@ -1095,6 +1254,8 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     std::vector<Seg> segs;
     bool quiet = group_input_zero(gsrc[g], pwl_off, pwl_t, pwl_v, 0.0);
     if (!quiet) init_groups.push_back(g);
+    c->ginit_h.push_back(quiet ? 0 : 1);
+    c->glts_h.push_back(lts);
     for (size_t j = 0; j + 1 < lts.size(); ++j) {
       Seg sg;
       sg.g = g;
@@ -1123,9 +1284,15 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
       segs.push_back(sg);
     }
     max_segs = std::max(max_segs, segs.size());
+    std::vector<char> zf;
+    for (const Seg& sg : segs) zf.push_back(sg.zero ? 1 : 0);
+    c->gzero_h.push_back(std::move(zf));
     per_group.push_back(std::move(segs));
   }
   c->n_segments = segid;
+  c->gsrc_h = gsrc;
+  c->pwl_off_h.assign(pwl_off, pwl_off + n_src + 1);
+  c->pwl_t_h.assign(pwl_t, pwl_t + pwl_off[n_src]);
   std::vector<int32_t> h_group, h_seg, h_obeg, h_nout;
   std::vector<double> h_l0, h_len, h_hfirst, h_lprev;
   std::vector<int64_t> h_segid;
@@ -1210,7 +1377,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     bool k = c->upload(dinv, Nm.dinv.data(), Nm.dinv.size()) &&
              c->upload(pcm, Nm.pan_cm.data(), Nm.pan_cm.size()) &&
              c->upload(prm, Nm.pan_rm.data(), Nm.pan_rm.size());
-    F = DevFactor{sup_first, sup_parent, sup_rowptr, sup_rows, pan_off, dinv, pcm, prm, nullptr};
+    F = DevFactor{sup_first, sup_parent, sup_rowptr, sup_rows, pan_off, dinv, pcm, prm, nullptr, nullptr};
     return k;
   };
   ok = ok && up_factor(NM, c->fM) && up_factor(NG, c->fG);
@@ -1278,10 +1445,12 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
        c->alloc(c->ss.m, Kmax) && c->alloc(c->ss.status, Kmax) &&
        c->alloc(c->ss.hbuf, (size_t)Kmax * kMaxB) && c->alloc(c->ss.scale, Kmax) &&
        c->alloc(c->iterA, Kmax) && c->alloc(c->iterB, Kmax) && c->alloc(c->iter_grp, Kmax) &&
-       c->alloc(c->d_count, 2) && c->alloc(c->coef, (size_t)Kmax * c->n_times * kCoefLd) &&
+       c->alloc(c->d_count, 4) && c->alloc(c->coef, (size_t)Kmax * c->n_times * kCoefLd) &&
        c->alloc(c->yend, (size_t)Kmax * kMaxM) && c->alloc(c->m_rec, std::max<int64_t>(1, c->n_segments)) &&
        c->alloc(c->st_rec, std::max<int64_t>(1, c->n_segments));
-  if (ok && cudaMallocHost(&c->h_count, 2 * sizeof(int32_t)) != cudaSuccess) ok = false;
+  if (ok && cudaMallocHost(&c->h_count, 4 * sizeof(int32_t)) != cudaSuccess) ok = false;
+  if (ok && cudaMemset(c->d_count, 0, 4 * sizeof(int32_t)) != cudaSuccess) ok = false;
+  if (ok) c->fM.abort = c->fG.abort = c->d_count + 2;
   if (ok && o.tape) {
     const size_t R = (size_t)std::max<int64_t>(1, c->n_records);
     const size_t KM = (size_t)Kmax;
@@ -1353,11 +1522,40 @@ matex_status matex_set_caps(matex_ctx* c, const double* cap) {
   return MATEX_OK;
 }
 
+// True when the currents pwl_v keep zero every segment that setup skipped as
+// identically zero, and keep zero at t = 0 every group that starts from x = 0.
+static bool zero_pattern_kept(const matex_ctx* c, const double* pwl_v) {
+  const int32_t* off = c->pwl_off_h.data();
+  const double* pt = c->pwl_t_h.data();
+  for (size_t k = 0; k < c->sel_groups.size(); ++k) {
+    const std::vector<int32_t>& srcs = c->gsrc_h[c->sel_groups[k]];
+    const std::vector<double>& lts = c->glts_h[k];
+    bool quiet = group_input_zero(srcs, off, pt, pwl_v, 0.0);
+    if (!quiet && !c->ginit_h[k]) return false;
+    for (size_t j = 0; j + 1 < lts.size() && quiet; ++j) {
+      quiet = group_input_zero(srcs, off, pt, pwl_v, lts[j]) &&
+              group_input_zero(srcs, off, pt, pwl_v, lts[j + 1]);
+      if (!quiet && c->gzero_h[k][j]) return false;
+    }
+  }
+  return true;
+}
+
+static matex_status check_sources(matex_ctx* c, const double* pwl_v_host) {
+  for (size_t i = 0; i < c->pwl_v_host_shape.size(); ++i)
+    if (!std::isfinite(pwl_v_host[i])) return fail(c, MATEX_ERR_ARG, "non-finite PWL value");
+  if (!zero_pattern_kept(c, pwl_v_host))
+    return fail(c, MATEX_ERR_ARG,
+                "the new currents are non-zero on a segment that setup skipped as identically "
+                "zero; set up a new context");
+  return MATEX_OK;
+}
+
 matex_status matex_set_sources(matex_ctx* c, const double* pwl_v_host) {
   if (!c) return MATEX_ERR_ARG;
   if (!pwl_v_host) return fail(c, MATEX_ERR_ARG, "pwl_v is NULL");
-  for (size_t i = 0; i < c->pwl_v_host_shape.size(); ++i)
-    if (!std::isfinite(pwl_v_host[i])) return fail(c, MATEX_ERR_ARG, "non-finite PWL value");
+  matex_status cs = check_sources(c, pwl_v_host);
+  if (cs != MATEX_OK) return cs;
   cudaMemcpyAsync(c->pwl_v_d, pwl_v_host, sizeof(double) * c->pwl_v_host_shape.size(),
                   cudaMemcpyHostToDevice, c->st);
   c->taped = false;
@@ -1370,6 +1568,8 @@ matex_status matex_run_host(matex_ctx* c, const double* pwl_v_host, double* x_ou
   if (!x_out_host) return fail(c, MATEX_ERR_ARG, "x_out_host is NULL");
   const size_t bytes = sizeof(double) * (size_t)c->n_times * c->nrows_out;
   if (pwl_v_host) {
+    matex_status cs = check_sources(c, pwl_v_host);
+    if (cs != MATEX_OK) return cs;
     cudaMemcpyAsync(c->pwl_v_d, pwl_v_host, sizeof(double) * c->pwl_v_host_shape.size(),
                     cudaMemcpyHostToDevice, c->st);
   }
@@ -1399,7 +1599,7 @@ matex_status matex_solve(matex_ctx* c, int32_t which, int32_t ncols, const doubl
     return fail(c, MATEX_ERR_ARG, "bad solve arguments");
   const DevFactor& F = which == 0 ? c->fM : c->fG;
   const int64_t n = c->n;
-  cudaMemsetAsync(c->d_count, 0, 2 * sizeof(int32_t), c->st);
+  cudaMemsetAsync(c->d_count, 0, 4 * sizeof(int32_t), c->st);
   for (int32_t q0 = 0; q0 < ncols; q0 += c->ldy) {
     const int K = std::min<int>(c->ldy, ncols - q0);
     gather_cols(c->Y, c->ldy, K, b + (int64_t)q0 * n, n, nullptr, nullptr, c->perm, n, c->st);
@@ -1445,7 +1645,9 @@ matex_status matex_get_sizes(matex_ctx* c, int32_t* n_times, int32_t* n_rows, in
 
 matex_status matex_set_batching(matex_ctx* c, int32_t one_group_at_a_time) {
   if (!c) return MATEX_ERR_ARG;
-  c->serial = one_group_at_a_time != 0;
+  const bool serial = one_group_at_a_time != 0;
+  if (serial != c->serial) drop_graph(c);  // another launch sequence
+  c->serial = serial;
   return MATEX_OK;
 }
 
@@ -1678,3 +1880,169 @@ extern "C" matex_status matex_solve_noalloc(matex_ctx* c, int32_t which, int32_t
   if (flag) return fail(c, MATEX_ERR_TIMEOUT, "a bounded wait of the persistent solve expired");
   return MATEX_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batches of independent contexts (grids of different sizes) as one CUDA
+// graph launch: a start event, then one child-graph branch per context (its
+// recorded run), each followed by its own end event.  The branches share no
+// edges, so the GPU runs them concurrently.
+// ---------------------------------------------------------------------------
+struct matex_batch {
+  std::vector<matex_ctx*> ctxs;
+  std::vector<int64_t> gens;    // recording generation of each context in the built graph
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaEvent_t> ev;  // [0] batch start, [1 + i] end of context i's branch
+  cudaStream_t st = nullptr;
+  std::string err;
+  ~matex_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+matex_status batch_fail(matex_batch* b, matex_status s, const std::string& m) {
+  b->err = m;
+  return s;
+}
+
+// A plain run of context c into its own device buffer, which records its graph.
+matex_status batch_record(matex_batch* b, matex_ctx* c) {
+  if (!c->out_buf && !c->alloc(c->out_buf, (size_t)c->n_times * c->nrows_out))
+    return batch_fail(b, MATEX_ERR_OOM, "output buffer");
+  matex_status s = run_device(c, c->out_buf, nullptr);
+  if (s != MATEX_OK && s != MATEX_ERR_NOCONV) return batch_fail(b, s, c->err);
+  if (!c->graph) return batch_fail(b, MATEX_ERR_CUDA, "a context's run could not be recorded as a graph");
+  return MATEX_OK;
+}
+
+matex_status batch_build(matex_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  cudaGraph_t parent = nullptr;
+  if (cudaGraphCreate(&parent, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return batch_fail(b, MATEX_ERR_CUDA, "cudaGraphCreate failed");
+  }
+  cudaGraphNode_t start;
+  bool ok = cudaGraphAddEventRecordNode(&start, parent, nullptr, 0, b->ev[0]) == cudaSuccess;
+  for (size_t i = 0; ok && i < b->ctxs.size(); ++i) {
+    cudaGraphNode_t child, end;
+    ok = cudaGraphAddChildGraphNode(&child, parent, &start, 1, b->ctxs[i]->graph) == cudaSuccess &&
+         cudaGraphAddEventRecordNode(&end, parent, &child, 1, b->ev[1 + i]) == cudaSuccess;
+    b->gens[i] = b->ctxs[i]->graph_gen;
+  }
+  if (ok) ok = cudaGraphInstantiate(&b->exec, parent, 0) == cudaSuccess;
+  cudaGraphDestroy(parent);
+  if (!ok) {
+    b->exec = nullptr;
+    return batch_fail(b, MATEX_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(cudaGetLastError()));
+  }
+  return MATEX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+matex_status matex_batch_create(matex_batch** out, matex_ctx* const* ctxs, int32_t count) {
+  if (!out) return MATEX_ERR_ARG;
+  *out = nullptr;
+  if (!ctxs || count <= 0) return MATEX_ERR_ARG;
+  for (int32_t i = 0; i < count; ++i) {
+    if (!ctxs[i] || !ctxs[i]->opts.graph) return MATEX_ERR_ARG;
+    if (ctxs[i]->device != ctxs[0]->device) return MATEX_ERR_ARG;
+    for (int32_t k = 0; k < i; ++k)
+      if (ctxs[k] == ctxs[i]) return MATEX_ERR_ARG;
+  }
+  matex_batch* b = new (std::nothrow) matex_batch();
+  if (!b) return MATEX_ERR_OOM;
+  b->ctxs.assign(ctxs, ctxs + count);
+  b->gens.assign(count, -1);
+  b->st = ctxs[0]->st;
+  for (int32_t i = 0; i <= count; ++i) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      delete b;
+      return MATEX_ERR_CUDA;
+    }
+    b->ev.push_back(e);
+  }
+  matex_status s = MATEX_OK;
+  for (matex_ctx* c : b->ctxs)
+    if (!c->graph && (s = batch_record(b, c)) != MATEX_OK) break;
+  if (s == MATEX_OK) s = batch_build(b);
+  if (s != MATEX_OK) {
+    g_setup_err = b->err;
+    delete b;
+    return s;
+  }
+  *out = b;
+  return MATEX_OK;
+}
+
+matex_status matex_batch_run(matex_batch* b, double* const* x_outs, matex_stats* stats, float* grid_ms) {
+  if (!b) return MATEX_ERR_ARG;
+  const size_t nb = b->ctxs.size();
+  if (!x_outs) return batch_fail(b, MATEX_ERR_ARG, "x_outs is NULL");
+  for (size_t i = 0; i < nb; ++i)
+    if (!x_outs[i]) return batch_fail(b, MATEX_ERR_ARG, "an output pointer is NULL");
+  // contexts re-recorded (or dropped) since the batch graph was built
+  bool rebuild = !b->exec;
+  matex_status s;
+  for (size_t i = 0; i < nb; ++i) {
+    matex_ctx* c = b->ctxs[i];
+    if (c->prof_on || c->inject_wait)
+      return batch_fail(b, MATEX_ERR_STATE, "profiling or wait injection is on for a context");
+    if (!c->graph && (s = batch_record(b, c)) != MATEX_OK) return s;
+    if (c->graph_gen != b->gens[i]) rebuild = true;
+  }
+  if (rebuild && (s = batch_build(b)) != MATEX_OK) return s;
+  // work queued earlier on the contexts' own streams comes first
+  for (matex_ctx* c : b->ctxs)
+    if (c->st != b->st && cudaStreamSynchronize(c->st) != cudaSuccess)
+      return batch_fail(b, MATEX_ERR_CUDA, "context stream sync failed");
+  const double t0 = now_ms();
+  if (cudaGraphLaunch(b->exec, b->st) != cudaSuccess)
+    return batch_fail(b, MATEX_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(cudaGetLastError()));
+  for (size_t i = 0; i < nb; ++i) {
+    matex_ctx* c = b->ctxs[i];
+    permute_out(x_outs[i], c->Xp, c->out_map, c->nrows_out, c->n, c->n_times, b->st);
+    cudaMemcpyAsync(c->h_count, c->d_count, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, b->st);
+  }
+  if (cudaStreamSynchronize(b->st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return batch_fail(b, MATEX_ERR_CUDA, "batch run failed");
+  matex_status worst = MATEX_OK;
+  for (size_t i = 0; i < nb; ++i) {
+    matex_ctx* c = b->ctxs[i];
+    if (grid_ms) {
+      grid_ms[i] = 0.f;
+      cudaEventElapsedTime(&grid_ms[i], b->ev[0], b->ev[1 + i]);
+    }
+    if (c->h_count[1] != 0)
+      return batch_fail(b, MATEX_ERR_TIMEOUT, "a bounded wait of the persistent solve expired");
+    matex_stats* si = stats ? stats + i : nullptr;
+    if (c->h_count[2] != 0) {
+      // this grid's counts diverged from its recording: redo it plainly
+      drop_graph(c);
+      s = run_device(c, x_outs[i], si);
+    } else {
+      s = finish_run(c, c->graph_counts, t0, true, si);
+    }
+    if (s == MATEX_ERR_NOCONV) worst = s;
+    else if (s != MATEX_OK) return batch_fail(b, s, c->err);
+  }
+  return worst;
+}
+
+const char* matex_batch_last_error(const matex_batch* b) { return b ? b->err.c_str() : ""; }
+
+void matex_batch_destroy(matex_batch* b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  delete b;
+}
+
+}  // extern "C"

@@ -115,7 +115,11 @@ struct Small {
     double nrm = 0.0;
     for (int i = 0; i < (int)blockDim.x; ++i) nrm = fmax(nrm, w.red[i]);
     int s = 0;
-    if (nrm > kTheta13) s = (int)ceil(log2(nrm / kTheta13));
+    if (nrm > kTheta13) {
+      // bounded even for an infinite norm: 2^-1074 scales any finite matrix to zero
+      const double l = ceil(log2(nrm / kTheta13));
+      s = l < 1074.0 ? (int)l : 1074;
+    }
     w.s = s > 0 ? s : 0;
   }
   __syncthreads();

@@ -32,7 +32,7 @@ class MatexOpts(C.Structure):
                 ("n_rows", C.c_int32), ("rows", C.POINTER(C.c_int32)),
                 ("replay_m", C.POINTER(C.c_int32)), ("n_replay", C.c_int64),
                 ("max_width", C.c_int32), ("strict", C.c_int32), ("solve_mode", C.c_int32),
-                ("tape", C.c_int32)]
+                ("tape", C.c_int32), ("graph", C.c_int32)]
 
 
 class MatexStats(C.Structure):
@@ -42,7 +42,8 @@ class MatexStats(C.Structure):
                 ("krylov_segments", C.c_int32), ("sum_m", C.c_int32), ("max_m", C.c_int32),
                 ("nonconv", C.c_int32), ("breakdowns", C.c_int32), ("sweeps_M", C.c_int32),
                 ("sweeps_G", C.c_int32), ("solve_columns", C.c_int64),
-                ("kernel_launches", C.c_int32), ("rounds", C.c_int32)]
+                ("kernel_launches", C.c_int32), ("rounds", C.c_int32),
+                ("graph_replay", C.c_int32), ("graph_capture_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -65,7 +66,8 @@ EXPORTS = ["matex_default_opts", "matex_setup", "matex_run", "matex_run_host", "
            "matex_last_error", "matex_status_string", "matex_destroy", "matex_set_profiling",
            "matex_get_profile", "matex_host_factor_solve", "matex_set_batching",
            "matex_debug_inject_wait", "matex_solve_noalloc", "matex_grad", "matex_set_caps",
-           "matex_get_autotune"]
+           "matex_get_autotune", "matex_batch_create", "matex_batch_run", "matex_batch_last_error",
+           "matex_batch_destroy"]
 
 
 def _load():
@@ -119,6 +121,14 @@ def _load():
     lib.matex_get_profile.restype = C.c_int
     lib.matex_destroy.argtypes = [P]
     lib.matex_destroy.restype = None
+    lib.matex_batch_create.argtypes = [C.POINTER(P), C.POINTER(P), C.c_int32]
+    lib.matex_batch_create.restype = C.c_int
+    lib.matex_batch_run.argtypes = [P, C.POINTER(P), C.POINTER(MatexStats), C.POINTER(C.c_float)]
+    lib.matex_batch_run.restype = C.c_int
+    lib.matex_batch_last_error.argtypes = [P]
+    lib.matex_batch_last_error.restype = C.c_char_p
+    lib.matex_batch_destroy.argtypes = [P]
+    lib.matex_batch_destroy.restype = None
     return lib
 
 
@@ -297,8 +307,9 @@ class Sim:
 
     def __init__(self, p, col_block=0, group_select=-1, include_dc=True, rows=None,
                  replay_m=None, max_width=0, strict=False, stream=None, solve_mode=2,
-                 tape=False, **overrides):
+                 tape=False, graph=True, **overrides):
         o = matex_default_opts()
+        o.graph = int(bool(graph))
         o.col_block = col_block
         o.group_select = group_select
         o.include_dc = int(bool(include_dc))
@@ -387,6 +398,51 @@ class Sim:
         if getattr(self, "ctx", None):
             matex_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several Sims (independent grids) run as one CUDA graph launch
+    (matex_batch_create / matex_batch_run).  The Sims must outlive the batch."""
+
+    def __init__(self, sims):
+        self.sims = list(sims)
+        arr = (C.c_void_p * len(self.sims))(*[s.ctx.value for s in self.sims])
+        b = C.c_void_p()
+        st = _lib.matex_batch_create(C.byref(b), arr, len(self.sims))
+        if st != MATEX_OK:
+            msg = _lib.matex_last_error(None)
+            raise MatexError(st, msg.decode() if msg else "")
+        self.b = b
+
+    def run(self, outs=None):
+        """Returns (outputs, per-grid ms from the batch start to the end of each
+        grid's branch); per-Sim statistics land in each Sim's ``stats``."""
+        import torch
+        if outs is None:
+            outs = [torch.empty((s.n_times, s.n_rows), dtype=torch.float64, device="cuda")
+                    for s in self.sims]
+        k = len(self.sims)
+        ptrs = (C.c_void_p * k)(*[o.data_ptr() for o in outs])
+        stats = (MatexStats * k)()
+        ms = (C.c_float * k)()
+        st = _lib.matex_batch_run(self.b, ptrs, stats, ms)
+        if st not in (MATEX_OK, MATEX_ERR_NOCONV):
+            msg = _lib.matex_batch_last_error(self.b)
+            raise MatexError(st, msg.decode() if msg else "")
+        for s, x in zip(self.sims, stats):
+            s.stats = x
+        return outs, np.array(list(ms), dtype=np.float64)
+
+    def close(self):
+        if getattr(self, "b", None):
+            _lib.matex_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

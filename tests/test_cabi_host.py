@@ -129,3 +129,15 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     with pytest.raises(ImportError):
         M._load()
     importlib.reload(M)
+
+
+def test_default_options_layout():
+    """The binding's option and statistics structs line up with the header's
+    (matex_default_opts fills every field; a shifted field shows up here)."""
+    from paper_1511_04519_gb300 import build
+    build.build()
+    from paper_1511_04519_gb300 import matex as M
+    o = M.matex_default_opts()
+    assert (o.col_block, o.group_select, o.include_dc, o.n_rows, o.max_width, o.strict,
+            o.solve_mode, o.tape, o.graph) == (0, -1, 1, 0, 1024, 0, 2, 0, 1)
+    assert C.sizeof(M.MatexStats) == 3 * 8 + 8 + 4 * 12 + 8 + 4 * 4 + 8
