@@ -327,6 +327,16 @@ matex_status matex_host_factor_solve(int64_t n, const int64_t* rowptr, const int
                                      int32_t max_width, int32_t ncols, const double* b, double* x,
                                      int64_t* info);
 
+/*
+ * Measured FP64 throughput of the current device (no counterpart in the
+ * paper; the denominator of the ALU roofline the kernels are reported
+ * against): one kernel of independent fused multiply-add chains over every
+ * SM, timed with CUDA events; *tflops receives the best of `reps` launches
+ * (2 flops per FMA), *ms (host, may be NULL) its duration.  Synchronises the
+ * device; allocates 8 bytes of device memory for the call.
+ */
+matex_status matex_measure_fp64_peak(int32_t reps, double* tflops, double* ms);
+
 const char* matex_last_error(const matex_ctx* ctx);
 const char* matex_status_string(matex_status s);
 void matex_destroy(matex_ctx* ctx);

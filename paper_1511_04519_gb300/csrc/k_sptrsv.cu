@@ -18,6 +18,7 @@
 // four threads per panel row/column, each thread holding all KB columns.
 #include "kernels.h"
 
+#include <algorithm>
 #include <mutex>
 
 namespace matex {
@@ -26,6 +27,26 @@ namespace {
 
 constexpr int kSolveThreads = 128;
 constexpr int kSplit = kSolveThreads / kRowBlock;  // threads sharing one dot product
+
+// Sum of the kSplit partial dot products of every (row, column) pair of a
+// task through shared memory: each partial is added once, instead of a
+// shuffle butterfly whose adds run on every lane.  `part` (the task's staging
+// buffer, no longer read once the first barrier has passed) must hold
+// kSolveThreads * (KB + 1) doubles.  out(r, q, v) receives the sum of pair
+// (r, q), r < rows; consecutive threads take consecutive q of one row.
+template <int KB, typename Out>
+__device__ __forceinline__ void split_sum(const double (&acc)[KB], double* part, int rows, Out out) {
+  constexpr int ld = KB + 1;  // padded: the writes below hit distinct banks
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < KB; ++q) part[threadIdx.x * ld + q] = acc[q];
+  __syncthreads();
+  for (int o = threadIdx.x; o < rows * KB; o += blockDim.x) {
+    const int r = o / KB, q = o - r * KB;
+    const double* p = part + r * kSplit * ld + q;
+    out(r, q, (p[0] + p[ld]) + (p[2 * ld] + p[3 * ld]));
+  }
+}
 
 // Forward task: rows [i0, i0+32) of P_s b_s for KB right-hand sides.  Thread
 // (row, sub) accumulates all KB columns of its row over panel columns
@@ -77,22 +98,12 @@ __device__ __forceinline__ void fwd_task(const DevFactor& F, int s, int i0, int 
       for (int q = 0; q < KB; ++q) acc[q] = fma(p, sb[j * KB + q], acc[q]);
     }
   }
-#pragma unroll
-  for (int q = 0; q < KB; ++q)
-#pragma unroll
-    for (int off = kSplit / 2; off > 0; off >>= 1)
-      acc[q] += __shfl_down_sync(0xffffffffu, acc[q], off, kSplit);
-  if (sub == 0 && i < ld) {
-    if (i < w) {
-      double* __restrict__ dst = Y2 + (int64_t)(f + i) * ldy + c0;
-#pragma unroll
-      for (int q = 0; q < KB; ++q) dst[q] = acc[q];
-    } else {
-      double* __restrict__ dst = Y + (int64_t)F.sup_rows[rp + i] * ldy + c0;
-#pragma unroll
-      for (int q = 0; q < KB; ++q) atomicAdd(dst + q, -acc[q]);
-    }
-  }
+  const int32_t* __restrict__ rows = F.sup_rows + rp;
+  split_sum<KB>(acc, sb, min(kRowBlock, ld - i0), [&](int r, int q, double v) {
+    const int ir = i0 + r;
+    if (ir < w) Y2[(int64_t)(f + ir) * ldy + c0 + q] = v;
+    else atomicAdd(Y + (int64_t)rows[ir] * ldy + c0 + q, -v);
+  });
 }
 
 // Backward task: panel columns [j0, j0+32) of P_s^T [D_s^{-1} y_s; -x_R].
@@ -141,63 +152,85 @@ __device__ __forceinline__ void bwd_task(const DevFactor& F, int s, int j0, int 
       for (int q = 0; q < KB; ++q) acc[q] = fma(p, ub[i * KB + q], acc[q]);
     }
   }
-#pragma unroll
-  for (int q = 0; q < KB; ++q)
-#pragma unroll
-    for (int off = kSplit / 2; off > 0; off >>= 1)
-      acc[q] += __shfl_down_sync(0xffffffffu, acc[q], off, kSplit);
-  if (sub == 0 && j < w) {
-    double* __restrict__ dst = Y + (int64_t)(f + j) * ldy + c0;
-#pragma unroll
-    for (int q = 0; q < KB; ++q) dst[q] = acc[q];
+  split_sum<KB>(acc, ub, min(kRowBlock, w - j0), [&](int r, int q, double v) {
+    Y[(int64_t)(f + j0 + r) * ldy + c0 + q] = v;
+  });
+}
+
+// Descriptors of the supernodes of a packed task, staged in shared memory by
+// one parallel load (no per-thread walk over the list).
+struct PackDesc {
+  int f[kPackMax], w[kPackMax], ld[kPackMax];
+  int a[kPackMax], b[kPackMax];  // rows / columns of the earlier entries of the task
+  long long pan[kPackMax], rp[kPackMax];
+};
+
+__device__ __forceinline__ void load_pack(const DevFactor& F, int e0, int ne, PackDesc& d) {
+  for (int k = threadIdx.x; k < ne; k += blockDim.x) {
+    const int s = F.pack[e0 + k];
+    const int f = F.sup_first[s];
+    const long long rp = F.sup_rowptr[s];
+    d.f[k] = f;
+    d.w[k] = F.sup_first[s + 1] - f;
+    d.ld[k] = (int)(F.sup_rowptr[s + 1] - rp);
+    d.a[k] = F.pack_a[e0 + k];
+    d.b[k] = F.pack_b[e0 + k];
+    d.pan[k] = F.pan_off[s];
+    d.rp[k] = rp;
   }
+  __syncthreads();
+}
+
+// The entry k of a packed task with pre[k] <= x < pre[k + 1] (pre ascending, pre[0] = 0).
+__device__ __forceinline__ int pack_find(const int* pre, int ne, int x) {
+  int lo = 0, hi = ne - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
 }
 
 // Packed forward task: up to 128 panel rows of several small supernodes of
 // one level, one thread per row (no split: their panels are narrow).
 template <int KB>
-__device__ __forceinline__ void fwd_small(const DevFactor& F, const int32_t* __restrict__ ents,
-                                          int ne, int c0, double* __restrict__ Y,
-                                          double* __restrict__ Y2, int ldy, double* sb) {
-  int boff = 0;
-  for (int k = 0; k < ne; ++k) {
-    const int s = ents[k];
-    const int f = F.sup_first[s];
-    const int w = F.sup_first[s + 1] - f;
-    for (int e = threadIdx.x; e < w * KB; e += blockDim.x) {
+__device__ __forceinline__ void fwd_small(const DevFactor& F, int e0, int ne, int c0,
+                                          double* __restrict__ Y, double* __restrict__ Y2, int ldy,
+                                          double* sb, PackDesc& d) {
+  load_pack(F, e0, ne, d);
+  // right-hand sides b_s of every entry, one warp per entry
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int k = warp; k < ne; k += nwarps) {
+    const int f = d.f[k], cnt = d.w[k] * KB;
+    double* dst = sb + d.b[k] * KB;
+    for (int e = lane; e < cnt; e += 32) {
       const int j = e / KB, q = e - j * KB;
-      sb[boff + e] = __ldcg(Y + (int64_t)(f + j) * ldy + c0 + q);
+      dst[e] = __ldcg(Y + (int64_t)(f + j) * ldy + c0 + q);
     }
-    boff += w * KB;
   }
   __syncthreads();
-  // this thread's supernode and row
-  int k = 0, r = threadIdx.x, bo = 0, s = -1, w = 0, ld = 0;
-  for (; k < ne; ++k) {
-    s = ents[k];
-    w = F.sup_first[s + 1] - F.sup_first[s];
-    ld = (int)(F.sup_rowptr[s + 1] - F.sup_rowptr[s]);
-    if (r < ld) break;
-    r -= ld;
-    bo += w * KB;
-  }
-  if (k >= ne) return;
-  const int f = F.sup_first[s];
-  const double* __restrict__ P = F.pan_cm + F.pan_off[s];
+  const int x = threadIdx.x;
+  if (x >= d.a[ne - 1] + d.ld[ne - 1]) return;
+  const int k = pack_find(d.a, ne, x);
+  const int r = x - d.a[k], w = d.w[k], ld = d.ld[k], f = d.f[k];
+  const double* __restrict__ P = F.pan_cm + d.pan[k];
+  const double* bs = sb + d.b[k] * KB;
+  const int jend = r < w ? r + 1 : w;  // L_ss^{-1} is lower triangular
   double acc[KB];
 #pragma unroll
   for (int q = 0; q < KB; ++q) acc[q] = 0.0;
-  for (int j = 0; j < w; ++j) {
+  for (int j = 0; j < jend; ++j) {
     const double p = P[(int64_t)j * ld + r];
 #pragma unroll
-    for (int q = 0; q < KB; ++q) acc[q] = fma(p, sb[bo + j * KB + q], acc[q]);
+    for (int q = 0; q < KB; ++q) acc[q] = fma(p, bs[j * KB + q], acc[q]);
   }
   if (r < w) {
     double* __restrict__ dst = Y2 + (int64_t)(f + r) * ldy + c0;
 #pragma unroll
     for (int q = 0; q < KB; ++q) dst[q] = acc[q];
   } else {
-    double* __restrict__ dst = Y + (int64_t)F.sup_rows[F.sup_rowptr[s] + r] * ldy + c0;
+    double* __restrict__ dst = Y + (int64_t)F.sup_rows[d.rp[k] + r] * ldy + c0;
 #pragma unroll
     for (int q = 0; q < KB; ++q) atomicAdd(dst + q, -acc[q]);
   }
@@ -205,61 +238,54 @@ __device__ __forceinline__ void fwd_small(const DevFactor& F, const int32_t* __r
 
 // Packed backward task: up to 128 panel columns of several small supernodes.
 template <int KB>
-__device__ __forceinline__ void bwd_small(const DevFactor& F, const int32_t* __restrict__ ents,
-                                          int ne, int c0, double* __restrict__ Y,
-                                          const double* __restrict__ Y2, int ldy, double* ub) {
-  int uoff = 0;
-  for (int k = 0; k < ne; ++k) {
-    const int s = ents[k];
-    const int f = F.sup_first[s];
-    const int w = F.sup_first[s + 1] - f;
-    const int64_t rp = F.sup_rowptr[s];
-    const int ld = (int)(F.sup_rowptr[s + 1] - rp);
-    for (int e = threadIdx.x; e < ld * KB; e += blockDim.x) {
+__device__ __forceinline__ void bwd_small(const DevFactor& F, int e0, int ne, int c0,
+                                          double* __restrict__ Y, const double* __restrict__ Y2,
+                                          int ldy, double* ub, PackDesc& d) {
+  load_pack(F, e0, ne, d);
+  // u = [D_s^{-1} y_s; -x_R] of every entry, one warp per entry
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int k = warp; k < ne; k += nwarps) {
+    const int f = d.f[k], w = d.w[k], cnt = d.ld[k] * KB;
+    const int32_t* __restrict__ rows = F.sup_rows + d.rp[k];
+    double* dst = ub + d.a[k] * KB;
+    for (int e = lane; e < cnt; e += 32) {
       const int i = e / KB, q = e - i * KB;
-      ub[uoff + e] = i < w ? __ldcg(Y2 + (int64_t)(f + i) * ldy + c0 + q) * F.dinv[f + i]
-                           : -__ldcg(Y + (int64_t)F.sup_rows[rp + i] * ldy + c0 + q);
+      dst[e] = i < w ? __ldcg(Y2 + (int64_t)(f + i) * ldy + c0 + q) * F.dinv[f + i]
+                     : -__ldcg(Y + (int64_t)rows[i] * ldy + c0 + q);
     }
-    uoff += ld * KB;
   }
   __syncthreads();
-  int k = 0, c = threadIdx.x, uo = 0, s = -1, w = 0, ld = 0;
-  for (; k < ne; ++k) {
-    s = ents[k];
-    w = F.sup_first[s + 1] - F.sup_first[s];
-    ld = (int)(F.sup_rowptr[s + 1] - F.sup_rowptr[s]);
-    if (c < w) break;
-    c -= w;
-    uo += ld * KB;
-  }
-  if (k >= ne) return;
-  const int f = F.sup_first[s];
-  const double* __restrict__ P = F.pan_rm + F.pan_off[s];
+  const int x = threadIdx.x;
+  if (x >= d.b[ne - 1] + d.w[ne - 1]) return;
+  const int k = pack_find(d.b, ne, x);
+  const int j = x - d.b[k], w = d.w[k], ld = d.ld[k];
+  const double* __restrict__ P = F.pan_rm + d.pan[k];
+  const double* u = ub + d.a[k] * KB;
   double acc[KB];
 #pragma unroll
   for (int q = 0; q < KB; ++q) acc[q] = 0.0;
-  for (int i = 0; i < ld; ++i) {
-    const double p = P[(int64_t)i * w + c];
+  for (int i = j; i < ld; ++i) {  // column j of L_ss^{-1} is zero above row j
+    const double p = P[(int64_t)i * w + j];
 #pragma unroll
-    for (int q = 0; q < KB; ++q) acc[q] = fma(p, ub[uo + i * KB + q], acc[q]);
+    for (int q = 0; q < KB; ++q) acc[q] = fma(p, u[i * KB + q], acc[q]);
   }
-  double* __restrict__ dst = Y + (int64_t)(f + c) * ldy + c0;
+  double* __restrict__ dst = Y + (int64_t)(d.f[k] + j) * ldy + c0;
 #pragma unroll
   for (int q = 0; q < KB; ++q) dst[q] = acc[q];
 }
 
 template <int KB>
 __device__ __forceinline__ void run_fwd(const DevFactor& F, int2 tk, int c0, double* Y, double* Y2,
-                                        int ldy, double* sm) {
+                                        int ldy, double* sm, PackDesc& pd) {
   if (tk.x >= 0) fwd_task<KB>(F, tk.x, tk.y, c0, Y, Y2, ldy, sm);
-  else fwd_small<KB>(F, F.pack + (-1 - tk.x), tk.y, c0, Y, Y2, ldy, sm);
+  else fwd_small<KB>(F, -1 - tk.x, tk.y, c0, Y, Y2, ldy, sm, pd);
 }
 
 template <int KB>
 __device__ __forceinline__ void run_bwd(const DevFactor& F, int2 tk, int c0, double* Y,
-                                        const double* Y2, int ldy, double* sm) {
+                                        const double* Y2, int ldy, double* sm, PackDesc& pd) {
   if (tk.x >= 0) bwd_task<KB>(F, tk.x, tk.y, c0, Y, Y2, ldy, sm);
-  else bwd_small<KB>(F, F.pack + (-1 - tk.x), tk.y, c0, Y, Y2, ldy, sm);
+  else bwd_small<KB>(F, -1 - tk.x, tk.y, c0, Y, Y2, ldy, sm, pd);
 }
 
 template <int KB>
@@ -267,9 +293,10 @@ __global__ void __launch_bounds__(kSolveThreads)
 fwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* __restrict__ Y,
                  double* __restrict__ Y2, int ldy) {
   extern __shared__ double sb[];
+  __shared__ PackDesc pd;
   if (F.abort && *F.abort) return;
   const int2 tk = tasks[blockIdx.x / ncb];
-  run_fwd<KB>(F, tk, (blockIdx.x % ncb) * KB, Y, Y2, ldy, sb);
+  run_fwd<KB>(F, tk, (blockIdx.x % ncb) * KB, Y, Y2, ldy, sb, pd);
 }
 
 template <int KB>
@@ -277,9 +304,10 @@ __global__ void __launch_bounds__(kSolveThreads)
 bwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* __restrict__ Y,
                  const double* __restrict__ Y2, int ldy) {
   extern __shared__ double ub[];
+  __shared__ PackDesc pd;
   if (F.abort && *F.abort) return;
   const int2 tk = tasks[blockIdx.x / ncb];
-  run_bwd<KB>(F, tk, (blockIdx.x % ncb) * KB, Y, Y2, ldy, ub);
+  run_bwd<KB>(F, tk, (blockIdx.x % ncb) * KB, Y, Y2, ldy, ub, pd);
 }
 
 // ---------------------------------------------------------------------------
@@ -331,6 +359,7 @@ persistent_solve_kernel(DevFactor F, PersistSched ps, double* __restrict__ Y,
   extern __shared__ double sm[];
   __shared__ long long sh_t;
   __shared__ int sh_ok;
+  __shared__ PackDesc pd;
   if (F.abort && *F.abort) return;  // set before the launch: every CTA leaves, none waits
   const long long total = ps.nf_total + ps.nb_total;
   for (;;) {
@@ -386,17 +415,17 @@ persistent_solve_kernel(DevFactor F, PersistSched ps, double* __restrict__ Y,
       if (!sh_ok) { failed = true; break; }
       if (fwd) {
         switch (L.kb) {
-          case 1: run_fwd<1>(F, tk, c0, Y, Y2, ldy, sm); break;
-          case 2: run_fwd<2>(F, tk, c0, Y, Y2, ldy, sm); break;
-          case 4: run_fwd<4>(F, tk, c0, Y, Y2, ldy, sm); break;
-          default: run_fwd<8>(F, tk, c0, Y, Y2, ldy, sm); break;
+          case 1: run_fwd<1>(F, tk, c0, Y, Y2, ldy, sm, pd); break;
+          case 2: run_fwd<2>(F, tk, c0, Y, Y2, ldy, sm, pd); break;
+          case 4: run_fwd<4>(F, tk, c0, Y, Y2, ldy, sm, pd); break;
+          default: run_fwd<8>(F, tk, c0, Y, Y2, ldy, sm, pd); break;
         }
       } else {
         switch (L.kb) {
-          case 1: run_bwd<1>(F, tk, c0, Y, Y2, ldy, sm); break;
-          case 2: run_bwd<2>(F, tk, c0, Y, Y2, ldy, sm); break;
-          case 4: run_bwd<4>(F, tk, c0, Y, Y2, ldy, sm); break;
-          default: run_bwd<8>(F, tk, c0, Y, Y2, ldy, sm); break;
+          case 1: run_bwd<1>(F, tk, c0, Y, Y2, ldy, sm, pd); break;
+          case 2: run_bwd<2>(F, tk, c0, Y, Y2, ldy, sm, pd); break;
+          case 4: run_bwd<4>(F, tk, c0, Y, Y2, ldy, sm, pd); break;
+          default: run_bwd<8>(F, tk, c0, Y, Y2, ldy, sm, pd); break;
         }
       }
       __syncthreads();
@@ -425,12 +454,13 @@ template <int KB>
 void launch_level(bool fwd, const DevFactor& F, const LevelPlan& L, double* Y, double* Y2, int ldy,
                   int ncols, cudaStream_t st) {
   const int ncb = (ncols + KB - 1) / KB;
+  const size_t part = (size_t)kSolveThreads * (KB + 1);  // split_sum's partials
   if (fwd) {
-    const size_t smem = (size_t)L.max_w * KB * sizeof(double);
+    const size_t smem = std::max((size_t)L.max_w * KB, part) * sizeof(double);
     fwd_level_kernel<KB><<<(unsigned)(L.nf * ncb), kSolveThreads, smem, st>>>(F, L.ftasks, ncb, Y, Y2,
                                                                              ldy);
   } else {
-    const size_t smem = (size_t)L.max_wr * KB * sizeof(double);
+    const size_t smem = std::max((size_t)L.max_wr * KB, part) * sizeof(double);
     bwd_level_kernel<KB><<<(unsigned)(L.nb * ncb), kSolveThreads, smem, st>>>(F, L.btasks, ncb, Y, Y2,
                                                                              ldy);
   }

@@ -23,6 +23,8 @@ struct DevFactor {
   const double* pan_cm;
   const double* pan_rm;
   const int32_t* pack;   // supernode lists of packed tasks
+  const int32_t* pack_a; // per pack entry: panel rows (sum of w + r) of the task's earlier entries
+  const int32_t* pack_b; // per pack entry: panel columns (sum of w) of the task's earlier entries
   const int32_t* abort = nullptr;  // device flag or null: when set before a launch, its CTAs exit at once
                          // (a graph replay whose counts diverged; its result is discarded)
 };

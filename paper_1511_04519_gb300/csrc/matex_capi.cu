@@ -256,6 +256,7 @@ std::vector<double> group_lts(const std::vector<int32_t>& srcs, const int32_t* p
 // allocation failure.
 constexpr int kSolveSmemCap = 24 * 1024 + 512;  // keeps ~8 solve CTAs resident per SM
 constexpr int kSplitFor = 4;                    // threads sharing one panel row / column
+constexpr int kSolveThreadsFor = 128;           // threads of a solve CTA (partial sums per thread)
 
 bool plan_levels(matex_ctx* c) {
   const Symbolic& S = c->S;
@@ -270,12 +271,22 @@ bool plan_levels(matex_ctx* c) {
   // at most 16 wide, backward packs columns of panels at most 16 wide and 64
   // rows long (a longer panel keeps the 4-thread split dot of its own task)
   constexpr int kPackLd = 384;
+  std::vector<int32_t> pack_a, pack_b;  // per entry: rows / columns of the earlier entries
   auto flush = [&](std::vector<int32_t>& cur, std::vector<int2>& out) {
     if (cur.empty()) return;
     out.push_back(make_int2(-1 - (int)pack.size(), (int)cur.size()));
-    pack.insert(pack.end(), cur.begin(), cur.end());
+    int a = 0, b = 0;
+    for (int32_t s : cur) {
+      pack.push_back(s);
+      pack_a.push_back(a);
+      pack_b.push_back(b);
+      a += (int)(S.sup_rowptr[s + 1] - S.sup_rowptr[s]);
+      b += S.sup_first[s + 1] - S.sup_first[s];
+    }
     cur.clear();
   };
+  auto sup_w = [&](int s) { return S.sup_first[s + 1] - S.sup_first[s]; };
+  auto sup_ld = [&](int s) { return (int)(S.sup_rowptr[s + 1] - S.sup_rowptr[s]); };
   for (int l = 0; l < nlev; ++l) {
     LevelPlan& L = c->levels[l];
     fofs[l] = ft.size();
@@ -284,10 +295,18 @@ bool plan_levels(matex_ctx* c) {
     bool any_bpack = false;
     std::vector<int32_t> cur;
     int rows = 0;
-    for (int k = S.level_ptr[l]; k < S.level_ptr[l + 1]; ++k) {
-      const int s = S.level_sups[k];
-      const int w = S.sup_first[s + 1] - S.sup_first[s];
-      const int wr = (int)(S.sup_rowptr[s + 1] - S.sup_rowptr[s]);
+    // packed tasks run one thread per row (forward) or column (backward), and a
+    // warp takes as long as its longest thread: packing the level's supernodes
+    // in order of width (forward) or panel length (backward) keeps the threads
+    // of a warp alike
+    std::vector<int32_t> by_w(S.level_sups.begin() + S.level_ptr[l],
+                              S.level_sups.begin() + S.level_ptr[l + 1]);
+    std::vector<int32_t> by_ld = by_w;
+    std::stable_sort(by_w.begin(), by_w.end(), [&](int a, int b) { return sup_w(a) > sup_w(b); });
+    std::stable_sort(by_ld.begin(), by_ld.end(), [&](int a, int b) { return sup_ld(a) > sup_ld(b); });
+    for (const int s : by_w) {
+      const int w = sup_w(s);
+      const int wr = sup_ld(s);
       mw = std::max(mw, w);
       if (wr <= kPackRows && w <= 16) {
         if (rows + wr > kPackRows || (int)cur.size() == kPackMax) { flush(cur, ft); rows = 0; }
@@ -301,10 +320,9 @@ bool plan_levels(matex_ctx* c) {
     }
     flush(cur, ft);
     int cols = 0, ldsum = 0;
-    for (int k = S.level_ptr[l]; k < S.level_ptr[l + 1]; ++k) {
-      const int s = S.level_sups[k];
-      const int w = S.sup_first[s + 1] - S.sup_first[s];
-      const int wr = (int)(S.sup_rowptr[s + 1] - S.sup_rowptr[s]);
+    for (const int s : by_ld) {
+      const int w = sup_w(s);
+      const int wr = sup_ld(s);
       if (w <= 16 && wr <= 64) {
         if (cols + w > kPackRows || ldsum + wr > kPackLd || (int)cur.size() == kPackMax) {
           flush(cur, bt);
@@ -325,18 +343,16 @@ bool plan_levels(matex_ctx* c) {
     // so the level's tail is made of short tasks); duration ~ the length of one
     // thread's dot product: a quarter of the panel extent for split tasks, the
     // whole extent for packed ones (one thread per row or column)
-    auto sw = [&](int s) { return S.sup_first[s + 1] - S.sup_first[s]; };
-    auto sld = [&](int s) { return (int)(S.sup_rowptr[s + 1] - S.sup_rowptr[s]); };
     auto fdur = [&](const int2& t) {
-      if (t.x >= 0) return std::min(sw(t.x), t.y + kRowBlock) / kSplitFor;
+      if (t.x >= 0) return std::min(sup_w(t.x), t.y + kRowBlock) / kSplitFor;
       int d = 0;
-      for (int k = 0; k < t.y; ++k) d = std::max(d, sw(pack[-1 - t.x + k]));
+      for (int k = 0; k < t.y; ++k) d = std::max(d, sup_w(pack[-1 - t.x + k]));
       return d;
     };
     auto bdur = [&](const int2& t) {
-      if (t.x >= 0) return (sld(t.x) - t.y) / kSplitFor;
+      if (t.x >= 0) return (sup_ld(t.x) - t.y) / kSplitFor;
       int d = 0;
-      for (int k = 0; k < t.y; ++k) d = std::max(d, sld(pack[-1 - t.x + k]));
+      for (int k = 0; k < t.y; ++k) d = std::max(d, sup_ld(pack[-1 - t.x + k]));
       return d;
     };
     std::stable_sort(ft.begin() + fofs[l], ft.end(),
@@ -356,18 +372,25 @@ bool plan_levels(matex_ctx* c) {
     }
     while (kb > 1 && (size_t)ld_need * kb * sizeof(double) > (size_t)kSolveSmemCap) kb /= 2;
     L.kb = kb;
-    smem_need = std::max(smem_need, (int)(std::max(ld_need, L.max_w) * kb * sizeof(double)));
+    smem_need = std::max(smem_need, (int)(std::max(std::max(ld_need, L.max_w) * kb,
+                                                   kSolveThreadsFor * (kb + 1)) * sizeof(double)));
   }
   fofs[nlev] = ft.size();
   bofs[nlev] = bt.size();
   int2 *fd, *bd;
-  int32_t* pk;
-  if (pack.empty()) pack.push_back(0);
+  int32_t *pk, *pa, *pb;
+  if (pack.empty()) {
+    pack.push_back(0);
+    pack_a.push_back(0);
+    pack_b.push_back(0);
+  }
   if (!c->upload(fd, ft.data(), ft.size()) || !c->upload(bd, bt.data(), bt.size()) ||
-      !c->upload(pk, pack.data(), pack.size()))
+      !c->upload(pk, pack.data(), pack.size()) || !c->upload(pa, pack_a.data(), pack_a.size()) ||
+      !c->upload(pb, pack_b.data(), pack_b.size()))
     return false;
-  c->fM.pack = pk;
-  c->fG.pack = pk;
+  c->fM.pack = c->fG.pack = pk;
+  c->fM.pack_a = c->fG.pack_a = pa;
+  c->fM.pack_b = c->fG.pack_b = pb;
   for (int l = 0; l < nlev; ++l) {
     c->levels[l].ftasks = fd + fofs[l];
     c->levels[l].btasks = bd + bofs[l];
@@ -1377,7 +1400,8 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     bool k = c->upload(dinv, Nm.dinv.data(), Nm.dinv.size()) &&
              c->upload(pcm, Nm.pan_cm.data(), Nm.pan_cm.size()) &&
              c->upload(prm, Nm.pan_rm.data(), Nm.pan_rm.size());
-    F = DevFactor{sup_first, sup_parent, sup_rowptr, sup_rows, pan_off, dinv, pcm, prm, nullptr, nullptr};
+    F = DevFactor{sup_first, sup_parent, sup_rowptr, sup_rows, pan_off, dinv, pcm, prm,
+                  nullptr, nullptr, nullptr, nullptr};
     return k;
   };
   ok = ok && up_factor(NM, c->fM) && up_factor(NG, c->fG);

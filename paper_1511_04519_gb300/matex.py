@@ -67,7 +67,7 @@ EXPORTS = ["matex_default_opts", "matex_setup", "matex_run", "matex_run_host", "
            "matex_get_profile", "matex_host_factor_solve", "matex_set_batching",
            "matex_debug_inject_wait", "matex_solve_noalloc", "matex_grad", "matex_set_caps",
            "matex_get_autotune", "matex_batch_create", "matex_batch_run", "matex_batch_last_error",
-           "matex_batch_destroy"]
+           "matex_batch_destroy", "matex_measure_fp64_peak"]
 
 
 def _load():
@@ -129,6 +129,8 @@ def _load():
     lib.matex_batch_last_error.restype = C.c_char_p
     lib.matex_batch_destroy.argtypes = [P]
     lib.matex_batch_destroy.restype = None
+    lib.matex_measure_fp64_peak.argtypes = [C.c_int32, dp, dp]
+    lib.matex_measure_fp64_peak.restype = C.c_int
     return lib
 
 
@@ -404,6 +406,15 @@ class Sim:
             self.close()
         except Exception:
             pass
+
+
+def measure_fp64_peak(reps=5):
+    """(TFLOP/s, ms) of the FP64 FMA probe on the current device."""
+    tf, ms = C.c_double(), C.c_double()
+    st = _lib.matex_measure_fp64_peak(int(reps), C.byref(tf), C.byref(ms))
+    if st != MATEX_OK:
+        raise MatexError(st, "FP64 probe failed")
+    return tf.value, ms.value
 
 
 class Batch:
