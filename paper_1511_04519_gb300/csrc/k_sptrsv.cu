@@ -192,15 +192,21 @@ __device__ __forceinline__ int pack_find(const int* pre, int ne, int x) {
   return lo;
 }
 
-// Packed forward task: up to 128 panel rows of several small supernodes of
-// one level, one thread per row (no split: their panels are narrow).
+// Packed forward task: several small supernodes of one level.  Lanes are
+// (panel row, right-hand side) pairs: a warp takes 32 / KB consecutive rows of
+// the task at a time, the four warps taking turns, so every lane of a warp
+// runs a dot product of the same length w (packing in order of width keeps
+// neighbouring supernodes alike; a masked lane costs the FP64 pipe as much
+// as an active one).  The zero upper triangle of L_ss^{-1} is multiplied like
+// any other entry for that reason.
 template <int KB>
 __device__ __forceinline__ void fwd_small(const DevFactor& F, int e0, int ne, int c0,
                                           double* __restrict__ Y, double* __restrict__ Y2, int ldy,
                                           double* sb, PackDesc& d) {
+  constexpr int R = 32 / KB;
   load_pack(F, e0, ne, d);
-  // right-hand sides b_s of every entry, one warp per entry
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  // right-hand sides b_s of every entry, one warp per entry
   for (int k = warp; k < ne; k += nwarps) {
     const int f = d.f[k], cnt = d.w[k] * KB;
     double* dst = sb + d.b[k] * KB;
@@ -210,40 +216,35 @@ __device__ __forceinline__ void fwd_small(const DevFactor& F, int e0, int ne, in
     }
   }
   __syncthreads();
-  const int x = threadIdx.x;
-  if (x >= d.a[ne - 1] + d.ld[ne - 1]) return;
-  const int k = pack_find(d.a, ne, x);
-  const int r = x - d.a[k], w = d.w[k], ld = d.ld[k], f = d.f[k];
-  const double* __restrict__ P = F.pan_cm + d.pan[k];
-  const double* bs = sb + d.b[k] * KB;
-  const int jend = r < w ? r + 1 : w;  // L_ss^{-1} is lower triangular
-  double acc[KB];
-#pragma unroll
-  for (int q = 0; q < KB; ++q) acc[q] = 0.0;
-  for (int j = 0; j < jend; ++j) {
-    const double p = P[(int64_t)j * ld + r];
-#pragma unroll
-    for (int q = 0; q < KB; ++q) acc[q] = fma(p, bs[j * KB + q], acc[q]);
-  }
-  if (r < w) {
-    double* __restrict__ dst = Y2 + (int64_t)(f + r) * ldy + c0;
-#pragma unroll
-    for (int q = 0; q < KB; ++q) dst[q] = acc[q];
-  } else {
-    double* __restrict__ dst = Y + (int64_t)F.sup_rows[d.rp[k] + r] * ldy + c0;
-#pragma unroll
-    for (int q = 0; q < KB; ++q) atomicAdd(dst + q, -acc[q]);
+  const int rows_total = d.a[ne - 1] + d.ld[ne - 1];
+  const int rl = lane / KB, q = lane - rl * KB;
+  for (int x0 = warp * R; x0 < rows_total; x0 += nwarps * R) {
+    const int x = min(x0 + rl, rows_total - 1);  // past the task: a valid row, result dropped
+    const int k = pack_find(d.a, ne, x);
+    const int r = x - d.a[k], w = d.w[k], ld = d.ld[k], f = d.f[k];
+    const double* __restrict__ P = F.pan_cm + d.pan[k] + r;
+    const double* bs = sb + d.b[k] * KB + q;
+    double acc = 0.0;
+#pragma unroll 4
+    for (int j = 0; j < w; ++j) acc = fma(P[(int64_t)j * ld], bs[j * KB], acc);
+    if (x0 + rl < rows_total) {
+      if (r < w) Y2[(int64_t)(f + r) * ldy + c0 + q] = acc;
+      else atomicAdd(Y + (int64_t)F.sup_rows[d.rp[k] + r] * ldy + c0 + q, -acc);
+    }
   }
 }
 
-// Packed backward task: up to 128 panel columns of several small supernodes.
+// Packed backward task: several small supernodes.  Lanes are (panel column,
+// right-hand side) pairs, 32 / KB consecutive columns of the task per warp
+// step, each an ld-long dot product (packing in order of ld keeps them alike).
 template <int KB>
 __device__ __forceinline__ void bwd_small(const DevFactor& F, int e0, int ne, int c0,
                                           double* __restrict__ Y, const double* __restrict__ Y2,
                                           int ldy, double* ub, PackDesc& d) {
+  constexpr int R = 32 / KB;
   load_pack(F, e0, ne, d);
-  // u = [D_s^{-1} y_s; -x_R] of every entry, one warp per entry
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  // u = [D_s^{-1} y_s; -x_R] of every entry, one warp per entry
   for (int k = warp; k < ne; k += nwarps) {
     const int f = d.f[k], w = d.w[k], cnt = d.ld[k] * KB;
     const int32_t* __restrict__ rows = F.sup_rows + d.rp[k];
@@ -255,23 +256,19 @@ __device__ __forceinline__ void bwd_small(const DevFactor& F, int e0, int ne, in
     }
   }
   __syncthreads();
-  const int x = threadIdx.x;
-  if (x >= d.b[ne - 1] + d.w[ne - 1]) return;
-  const int k = pack_find(d.b, ne, x);
-  const int j = x - d.b[k], w = d.w[k], ld = d.ld[k];
-  const double* __restrict__ P = F.pan_rm + d.pan[k];
-  const double* u = ub + d.a[k] * KB;
-  double acc[KB];
-#pragma unroll
-  for (int q = 0; q < KB; ++q) acc[q] = 0.0;
-  for (int i = j; i < ld; ++i) {  // column j of L_ss^{-1} is zero above row j
-    const double p = P[(int64_t)i * w + j];
-#pragma unroll
-    for (int q = 0; q < KB; ++q) acc[q] = fma(p, u[i * KB + q], acc[q]);
+  const int cols_total = d.b[ne - 1] + d.w[ne - 1];
+  const int cl = lane / KB, q = lane - cl * KB;
+  for (int x0 = warp * R; x0 < cols_total; x0 += nwarps * R) {
+    const int x = min(x0 + cl, cols_total - 1);
+    const int k = pack_find(d.b, ne, x);
+    const int j = x - d.b[k], w = d.w[k], ld = d.ld[k];
+    const double* __restrict__ P = F.pan_rm + d.pan[k] + j;
+    const double* u = ub + d.a[k] * KB + q;
+    double acc = 0.0;
+#pragma unroll 4
+    for (int i = 0; i < ld; ++i) acc = fma(P[(int64_t)i * w], u[i * KB], acc);
+    if (x0 + cl < cols_total) Y[(int64_t)(d.f[k] + j) * ldy + c0 + q] = acc;
   }
-  double* __restrict__ dst = Y + (int64_t)(d.f[k] + j) * ldy + c0;
-#pragma unroll
-  for (int q = 0; q < KB; ++q) dst[q] = acc[q];
 }
 
 template <int KB>
