@@ -73,6 +73,48 @@ __device__ __forceinline__ void fwd_task(const DevFactor& F, int s, int i0, int 
   const int i = i0 + threadIdx.x / kSplit;
   // the same bound per warp (its 8 rows), uniform across the warp
   const int jw = min(jend, i0 + (int)(threadIdx.x / 32 + 1) * (32 / kSplit));
+  const int32_t* __restrict__ rows = F.sup_rows + rp;
+  if constexpr (KB >= 2 * kSplit) {
+    // enough right-hand sides to share them out: thread `sub` of a row takes
+    // KB / 4 of them (two or more independent FMA chains) over the whole row,
+    // so no partial sums need adding
+    constexpr int QS = KB / kSplit;
+    const int qa = sub * QS;
+    if (i >= ld) return;
+    const double* __restrict__ Pi = P + i;
+    const double* bq = sb + qa;
+    double acc[QS];
+#pragma unroll
+    for (int q = 0; q < QS; ++q) acc[q] = 0.0;
+    int j = 0;
+    for (; j + 3 < jw; j += 4) {
+      const double p0 = Pi[(int64_t)j * ld];
+      const double p1 = Pi[(int64_t)(j + 1) * ld];
+      const double p2 = Pi[(int64_t)(j + 2) * ld];
+      const double p3 = Pi[(int64_t)(j + 3) * ld];
+#pragma unroll
+      for (int q = 0; q < QS; ++q) {
+        double a = fma(p0, bq[j * KB + q], acc[q]);
+        a = fma(p1, bq[(j + 1) * KB + q], a);
+        a = fma(p2, bq[(j + 2) * KB + q], a);
+        acc[q] = fma(p3, bq[(j + 3) * KB + q], a);
+      }
+    }
+    for (; j < jw; ++j) {
+      const double p = Pi[(int64_t)j * ld];
+#pragma unroll
+      for (int q = 0; q < QS; ++q) acc[q] = fma(p, bq[j * KB + q], acc[q]);
+    }
+    if (i < w) {
+      double* __restrict__ dst = Y2 + (int64_t)(f + i) * ldy + c0 + qa;
+#pragma unroll
+      for (int q = 0; q < QS; ++q) dst[q] = acc[q];
+    } else {
+      double* __restrict__ dst = Y + (int64_t)rows[i] * ldy + c0 + qa;
+#pragma unroll
+      for (int q = 0; q < QS; ++q) atomicAdd(dst + q, -acc[q]);
+    }
+  } else {
   double acc[KB];
 #pragma unroll
   for (int q = 0; q < KB; ++q) acc[q] = 0.0;
@@ -98,12 +140,12 @@ __device__ __forceinline__ void fwd_task(const DevFactor& F, int s, int i0, int 
       for (int q = 0; q < KB; ++q) acc[q] = fma(p, sb[j * KB + q], acc[q]);
     }
   }
-  const int32_t* __restrict__ rows = F.sup_rows + rp;
   split_sum<KB>(acc, sb, min(kRowBlock, ld - i0), [&](int r, int q, double v) {
     const int ir = i0 + r;
     if (ir < w) Y2[(int64_t)(f + ir) * ldy + c0 + q] = v;
     else atomicAdd(Y + (int64_t)rows[ir] * ldy + c0 + q, -v);
   });
+  }
 }
 
 // Backward task: panel columns [j0, j0+32) of P_s^T [D_s^{-1} y_s; -x_R].
