@@ -262,6 +262,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serial", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-tr", action="store_true")
     ap.add_argument("--grids", type=int, default=0,
                     help="also run that many of the 96 uneven single-layer grids as one "
                          "batch graph launch and report their aggregate rate")
@@ -408,6 +409,21 @@ def main():
     e2e = {"value": world * units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(pin_v.nbytes),
            "d2h_bytes_per_step": int(pin_out.nbytes), "ms_per_step": e2e_s * 1e3}
 
+    # the paper's comparison method on the same solves: fixed-step trapezoidal
+    # integration with h = 10 ps (the output step), all sources at once
+    trap = None
+    if not args.no_tr:
+        sim.run(out)
+        xr = out.clone()
+        t0 = time.perf_counter()
+        xt, _ = sim.tr_run(1)                       # factor of C + h/2 G, recorded loop
+        first_s = time.perf_counter() - t0
+        tr_ms = min(sim.tr_run(1, xt)[1] for _ in range(2))
+        trap = {"h_ps": p.dt_out * 1e12, "steps": p.n_out - 1, "ms": tr_ms,
+                "rmatex_speedup": tr_ms / ms, "first_call_s": first_s,
+                "max_abs_diff_vs_rmatex_v": float((xt - xr).abs().max())}
+        del xt, xr
+
     # adjoint: the same grid with 256 observed nodes, IR-drop hinge loss; cost
     # of matex_grad relative to the forward run that taped it
     adjoint = None
@@ -458,7 +474,8 @@ def main():
                        "l2": "working set (factors, bases, 1.44 GB of outputs) > 129 MB L2"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "sptrsv": sptrsv, "one_group_at_a_time": serial,
-            "cpu_baseline": cpu, "adjoint": adjoint, "profile_ms_per_step": ms_prof,
+            "cpu_baseline": cpu, "adjoint": adjoint, "trapezoidal": trap,
+            "profile_ms_per_step": ms_prof,
             "profile": {k: {kk: v[kk] / args.steps for kk in ("ms", "launches", "flops", "bytes")}
                         for k, v in prof.items()},
             "run_stats": {k: stats[k] for k in ("n_segments", "krylov_segments", "sum_m", "max_m",

@@ -328,6 +328,21 @@ matex_status matex_host_factor_solve(int64_t n, const int64_t* rowptr, const int
                                      int64_t* info);
 
 /*
+ * Fixed-step trapezoidal integration of Eq. 1 (Eq. 2), the method the paper
+ * compares R-MATEX against, on the same batched triangular solves:
+ *   (C + h/2 G) x_{n+1} = (C - h/2 G) x_n + h/2 (b_n + b_{n+1}),
+ *   b(t) = B u(t) (+ dc_inject when opts.include_dc), all sources at once,
+ * from the DC state x_0 = G^{-1} b(0), with h = dt_out / substeps (substeps
+ * >= 1).  Writes the states at the output times t_o = o*dt_out into x_out
+ * (device, [N+1][n_rows], as matex_run) and, if ms_out (host) is not NULL,
+ * the device time of the integration (CUDA events; excludes the one-time host
+ * factorisation of C + h/2 G, redone when h changes).  The first call for a
+ * given substeps records the step loop as a CUDA graph; later calls replay
+ * it.  Uses the current source currents.  Synchronises the stream.
+ */
+matex_status matex_tr_run(matex_ctx* ctx, int32_t substeps, double* x_out, double* ms_out);
+
+/*
  * Measured FP64 throughput of the current device (no counterpart in the
  * paper; the denominator of the ALU roofline the kernels are reported
  * against): one kernel of independent fused multiply-add chains over every

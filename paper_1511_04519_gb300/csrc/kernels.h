@@ -121,6 +121,18 @@ struct SourceTable {
   const double* pwl_v;
 };
 
+// Trapezoidal baseline (k_trap.cu).  b = dc (or 0) + B u(t) over all sources;
+// Y[.][0] = c x - g G x + g (bp + bn) with G in CSR; x = Y[.][0] (and output
+// row `row` of Xp when row >= 0).  Permuted node order throughout.
+void tr_input(double* b, const double* dc, const SourceTable& src, int n_src, double t, int64_t n,
+              cudaStream_t st);
+void tr_rhs(double* Y, int ldy, const double* x, const int64_t* rowptr, const int32_t* col,
+            const double* val, const double* c, double g, const double* bp, const double* bn,
+            int64_t n, cudaStream_t st);
+void tr_store(double* x, const double* Y, int ldy, double* Xp, int64_t row, int64_t n,
+              cudaStream_t st);
+
+
 // Y[:, q] = B_k (u_k(l0+L) - u_k(l0)) / L, the input slope on the segment (Y zeroed here)
 void build_input_rhs(double* Y, int ldy, int K, const RoundCols& rc, const SourceTable& src,
                      int64_t n, cudaStream_t st);

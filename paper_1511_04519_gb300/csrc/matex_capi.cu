@@ -162,6 +162,18 @@ struct matex_ctx {
   PassCounts graph_counts;
   double graph_ms = 0.0;
   int64_t graph_gen = 0;           // bumped at every new recording
+  // trapezoidal baseline (matex_tr_run): factor of C + h/2 G for the last h
+  // (structure shared with the C + gamma G factor), G in CSR in the permuted
+  // order, state and input vectors, and the recorded loop
+  double tr_h = 0.0;
+  DevFactor fT{};
+  int64_t* trG_rowptr = nullptr;
+  int32_t* trG_col = nullptr;
+  double* trG_val = nullptr;
+  double *trX = nullptr, *trB0 = nullptr, *trB1 = nullptr;
+  cudaGraphExec_t tr_exec = nullptr;
+  int tr_substeps = 0;            // substeps the recorded loop was built for
+  double tr_factor_ms = 0.0;
   // profiling
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -174,6 +186,7 @@ struct matex_ctx {
     for (void* p : allocs) cudaFree(p);
     if (h_count) cudaFreeHost(h_count);
     if (gexec) cudaGraphExecDestroy(gexec);
+    if (tr_exec) cudaGraphExecDestroy(tr_exec);
     if (graph) cudaGraphDestroy(graph);
     if (gst) cudaStreamDestroy(gst);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
@@ -1902,6 +1915,150 @@ extern "C" matex_status matex_solve_noalloc(matex_ctx* c, int32_t which, int32_t
   if (cudaMemcpy(&flag, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return cuda_check(c, "solve_noalloc flag");
   if (flag) return fail(c, MATEX_ERR_TIMEOUT, "a bounded wait of the persistent solve expired");
+  return MATEX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-step trapezoidal integration (Eq. 2), the paper's comparison method,
+// on the same batched solves.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Factor C + h/2 G on the host with the context's symbolic structure and
+// upload it (panels allocated once, rewritten when h changes); G in CSR in
+// the permuted order on first use.
+matex_status tr_prepare(matex_ctx* c, double h) {
+  const int64_t n = c->n;
+  if (!c->trG_rowptr) {
+    const Symbolic& S = c->S;
+    std::vector<int64_t> rp(n + 1, 0);
+    for (int64_t k = 0; k < n; ++k) {
+      const int32_t o = S.perm[k];
+      rp[k + 1] = rp[k] + (c->g_rowptr_h[o + 1] - c->g_rowptr_h[o]);
+    }
+    std::vector<int32_t> col(rp[n]);
+    std::vector<double> val(rp[n]);
+    for (int64_t k = 0; k < n; ++k) {
+      const int32_t o = S.perm[k];
+      int64_t d = rp[k];
+      for (int64_t e = c->g_rowptr_h[o]; e < c->g_rowptr_h[o + 1]; ++e, ++d) {
+        col[d] = S.iperm[c->g_col_h[e]];
+        val[d] = c->g_val_h[e];
+      }
+    }
+    if (!c->upload(c->trG_rowptr, rp.data(), rp.size()) || !c->upload(c->trG_col, col.data(), col.size()) ||
+        !c->upload(c->trG_val, val.data(), val.size()) || !c->alloc(c->trX, n) ||
+        !c->alloc(c->trB0, n) || !c->alloc(c->trB1, n))
+      return fail(c, MATEX_ERR_OOM, "trapezoidal buffers");
+  }
+  if (c->tr_h == h) return MATEX_OK;
+  const double t0 = now_ms();
+  CsrSym A{n, c->g_rowptr_h.data(), c->g_col_h.data(), c->g_val_h.data()};
+  Numeric NT;
+  const std::string e = numeric_ldlt(A, c->c_host.data(), 0.5 * h, c->S, NT);
+  if (!e.empty()) return fail(c, MATEX_ERR_NOT_SPD, e);
+  if (!c->fT.dinv) {
+    double *d, *pc, *pr;
+    if (!c->alloc(d, NT.dinv.size()) || !c->alloc(pc, NT.pan_cm.size()) || !c->alloc(pr, NT.pan_rm.size()))
+      return fail(c, MATEX_ERR_OOM, "trapezoidal factor");
+    c->fT = c->fM;
+    c->fT.dinv = d;
+    c->fT.pan_cm = pc;
+    c->fT.pan_rm = pr;
+    c->fT.abort = nullptr;
+  }
+  if (cudaStreamSynchronize(c->st) != cudaSuccess ||
+      cudaMemcpy(const_cast<double*>(c->fT.dinv), NT.dinv.data(), sizeof(double) * NT.dinv.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(const_cast<double*>(c->fT.pan_cm), NT.pan_cm.data(), sizeof(double) * NT.pan_cm.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(const_cast<double*>(c->fT.pan_rm), NT.pan_rm.data(), sizeof(double) * NT.pan_rm.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return cuda_check(c, "trapezoidal factor upload");
+  c->tr_h = h;
+  c->tr_factor_ms = now_ms() - t0;
+  if (c->tr_exec) cudaGraphExecDestroy(c->tr_exec);
+  c->tr_exec = nullptr;
+  return MATEX_OK;
+}
+
+// The whole integration on c->st: DC start x_0 = G^{-1} b(0), then N*substeps
+// steps; the state at every output time goes to Xp.
+void tr_pass(matex_ctx* c, int substeps, double h) {
+  const int64_t n = c->n;
+  cudaStream_t st = c->st;
+  const double* dc = c->opts.include_dc ? c->dc_perm : nullptr;
+  double* bp = c->trB0;
+  double* bn = c->trB1;
+  tr_input(bp, dc, c->src, c->n_src, 0.0, n, st);
+  gather_cols(c->Y, c->ldy, 1, bp, 0, nullptr, nullptr, nullptr, n, st);
+  solve_cols(c, c->fG, 1);
+  tr_store(c->trX, c->Y, c->ldy, c->Xp, 0, n, st);
+  const int64_t steps = (int64_t)(c->n_times - 1) * substeps;
+  for (int64_t k = 1; k <= steps; ++k) {
+    tr_input(bn, dc, c->src, c->n_src, (double)k * h, n, st);
+    tr_rhs(c->Y, c->ldy, c->trX, c->trG_rowptr, c->trG_col, c->trG_val, c->c_perm, 0.5 * h, bp, bn,
+           n, st);
+    solve_cols(c, c->fT, 1);
+    tr_store(c->trX, c->Y, c->ldy, c->Xp, k % substeps == 0 ? k / substeps : -1, n, st);
+    std::swap(bp, bn);
+  }
+}
+
+}  // namespace
+
+extern "C" matex_status matex_tr_run(matex_ctx* c, int32_t substeps, double* x_out, double* ms_out) {
+  if (!c) return MATEX_ERR_ARG;
+  if (substeps < 1 || !x_out) return fail(c, MATEX_ERR_ARG, "substeps must be >= 1 and x_out set");
+  const double h = c->dt_out / substeps;
+  matex_status s = tr_prepare(c, h);
+  if (s != MATEX_OK) return s;
+  if (c->tr_substeps != substeps && c->tr_exec) {
+    cudaGraphExecDestroy(c->tr_exec);
+    c->tr_exec = nullptr;
+  }
+  // record the loop once (about 40 launches per step, no host decision in it)
+  if (!c->tr_exec && !c->inject_wait) {
+    if (!c->gst && cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      c->gst = nullptr;
+    }
+    if (c->gst) {
+      cudaStream_t user = c->st;
+      c->st = c->gst;
+      cudaGraph_t g = nullptr;
+      bool ok = cudaStreamBeginCapture(c->gst, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        tr_pass(c, substeps, h);
+        ok = cudaStreamEndCapture(c->gst, &g) == cudaSuccess && g != nullptr;
+      }
+      c->st = user;
+      if (ok) ok = cudaGraphInstantiate(&c->tr_exec, g, 0) == cudaSuccess;
+      if (g) cudaGraphDestroy(g);
+      if (!ok) c->tr_exec = nullptr;
+      cudaGetLastError();
+      c->tr_substeps = substeps;
+    }
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaMemsetAsync(c->d_count, 0, 4 * sizeof(int32_t), c->st);
+  cudaEventRecord(e0, c->st);
+  if (c->tr_exec) cudaGraphLaunch(c->tr_exec, c->st);
+  else tr_pass(c, substeps, h);
+  cudaEventRecord(e1, c->st);
+  permute_out(x_out, c->Xp, c->out_map, c->nrows_out, c->n, c->n_times, c->st);
+  const bool ok = cudaStreamSynchronize(c->st) == cudaSuccess;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok) return cuda_check(c, "trapezoidal run");
+  if ((s = cuda_check(c, "trapezoidal run")) != MATEX_OK) return s;
+  int tmp = 0;
+  if ((s = read_count(c, &tmp)) != MATEX_OK) return s;
+  if (ms_out) *ms_out = ms;
   return MATEX_OK;
 }
 

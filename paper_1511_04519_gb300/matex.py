@@ -67,7 +67,7 @@ EXPORTS = ["matex_default_opts", "matex_setup", "matex_run", "matex_run_host", "
            "matex_get_profile", "matex_host_factor_solve", "matex_set_batching",
            "matex_debug_inject_wait", "matex_solve_noalloc", "matex_grad", "matex_set_caps",
            "matex_get_autotune", "matex_batch_create", "matex_batch_run", "matex_batch_last_error",
-           "matex_batch_destroy", "matex_measure_fp64_peak"]
+           "matex_batch_destroy", "matex_measure_fp64_peak", "matex_tr_run"]
 
 
 def _load():
@@ -129,6 +129,8 @@ def _load():
     lib.matex_batch_last_error.restype = C.c_char_p
     lib.matex_batch_destroy.argtypes = [P]
     lib.matex_batch_destroy.restype = None
+    lib.matex_tr_run.argtypes = [P, C.c_int32, P, dp]
+    lib.matex_tr_run.restype = C.c_int
     lib.matex_measure_fp64_peak.argtypes = [C.c_int32, dp, dp]
     lib.matex_measure_fp64_peak.restype = C.c_int
     return lib
@@ -354,6 +356,17 @@ class Sim:
         pv = None if pwl_v is None else np.ascontiguousarray(pwl_v, dtype=np.float64)
         self.stats = matex_run_host(self.ctx, pv, out)
         return out
+
+    def tr_run(self, substeps=1, out=None):
+        """Fixed-step trapezoidal integration with h = dt_out / substeps on the
+        same solves (matex_tr_run); returns (voltages, device ms)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.n_times, self.n_rows), dtype=torch.float64, device="cuda")
+        ms = C.c_double()
+        _check(self.ctx, _lib.matex_tr_run(self.ctx, int(substeps), C.c_void_p(out.data_ptr()),
+                                           C.byref(ms)))
+        return out, ms.value
 
     def set_caps(self, c):
         matex_set_caps(self.ctx, c)
