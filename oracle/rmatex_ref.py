@@ -123,6 +123,20 @@ class Factors:
     def solve_G(self, b):
         return self.lu_G.solve(b)
 
+    def op(self, variant, v):
+        """The Arnoldi operator of each Krylov variant (Alg. 1 line
+        w = U\\(L\\(X2 v))):
+          'R' rational (Sec. 3.3.2):  X1 = C + gamma G, X2 = C: (C + gamma G)^{-1} C v
+          'I' inverted (Sec. 3.3.1):  X1 = G, X2 = C:            G^{-1} C v  (= -A^{-1} v)
+          'S' standard (Sec. 2.3, MEXP):                          -C^{-1} G v (= A v)"""
+        if variant == "R":
+            return self.solve_M(self.c * v)
+        if variant == "I":
+            return self.solve_G(self.c * v)
+        if variant == "S":
+            return -(self.G @ v) / self.c
+        raise ValueError(variant)
+
 
 def factorize(p, c=None):
     c = p.c if c is None else c
@@ -153,6 +167,20 @@ def rational_H(Ht_m, gamma):
     return (np.eye(m) - np.linalg.inv(Ht_m)) / gamma
 
 
+def krylov_H(Ht_m, gamma, variant="R"):
+    """The matrix whose exponential stands for e^{hA} on the Krylov space:
+    rational  (I - Htilde^{-1}) / gamma (Eq. 9);
+    inverted  H'^{-1}, where the Arnoldi of -A^{-1} gives Htilde = -H' (Sec. 3.3.1);
+    standard  the Arnoldi Hessenberg of A itself (Sec. 2.3)."""
+    if variant == "R":
+        return rational_H(Ht_m, gamma)
+    if variant == "I":
+        return -np.linalg.inv(Ht_m)
+    if variant == "S":
+        return Ht_m.copy()
+    raise ValueError(variant)
+
+
 def residual(beta, h_next, H, h):
     """Empirical posterior error of Sec. 3.3.3:
     ||v|| |htilde_{m+1,m} e_m^T e^{hH_m} e_1|."""
@@ -160,11 +188,21 @@ def residual(beta, h_next, H, h):
     return beta * abs(h_next) * abs(e[-1, 0])
 
 
-def arnoldi(fac, v, h_checks, tol, m_max, replay_m=None):
-    """Alg. 1 for the shift-and-invert operator w = (C+gamma G)^{-1} C v_j,
-    with modified Gram-Schmidt as written.  Stops at the first j whose
-    residual at every h in ``h_checks`` is below tol, at a happy breakdown,
-    at m_max, or exactly at ``replay_m`` when given."""
+def residual_scale(variant, gamma):
+    """The empirical residual of Sec. 3.3.3 uses h_{m+1,m} of the variant's own
+    Arnoldi: dimensionless for the rational operator, in seconds for the
+    inverted one, in 1/s for A itself.  So that one tolerance in volts serves
+    all three, h_{m+1,m} is scaled by the shift: the rational operator acts
+    on a stiff mode like the inverted one divided by gamma, and like A^{-1}
+    divided by -gamma."""
+    return {"R": 1.0, "I": 1.0 / gamma, "S": gamma}[variant]
+
+
+def arnoldi(fac, v, h_checks, tol, m_max, replay_m=None, variant="R"):
+    """Alg. 1 for the operator of ``variant`` (default the shift-and-invert
+    w = (C+gamma G)^{-1} C v_j), with modified Gram-Schmidt as written.  Stops
+    at the first j whose residual at every h in ``h_checks`` is below tol, at
+    a happy breakdown, at m_max, or exactly at ``replay_m`` when given."""
     beta = float(np.linalg.norm(v))
     n = v.shape[0]
     V = np.zeros((m_max + 1, n))
@@ -176,26 +214,27 @@ def arnoldi(fac, v, h_checks, tol, m_max, replay_m=None):
     breakdown = False
     limit = m_max if replay_m is None else replay_m
     for j in range(limit):
-        w = fac.solve_M(fac.c * V[j])            # a forward/backward substitution pair
+        w = fac.op(variant, V[j])                # R, I: a forward/backward substitution pair
         for i in range(j + 1):                   # modified Gram-Schmidt
             Ht[i, j] = w @ V[i]
             w = w - Ht[i, j] * V[i]
         Ht[j + 1, j] = np.linalg.norm(w)
         m = j + 1
-        if Ht[j + 1, j] <= BREAKDOWN_REL * Ht[0, 0]:
+        if Ht[j + 1, j] <= BREAKDOWN_REL * abs(Ht[0, 0]):   # |.|: h_11 < 0 for 'S'
             breakdown = True
             converged = True
             break
         V[j + 1] = w / Ht[j + 1, j]
         if replay_m is not None:
             continue
-        H = rational_H(Ht[:m, :m], fac.gamma)
-        rs = [residual(beta, Ht[m, m - 1], H, h) for h in h_checks]
+        H = krylov_H(Ht[:m, :m], fac.gamma, variant)
+        hs = residual_scale(variant, fac.gamma) * Ht[m, m - 1]
+        rs = [residual(beta, hs, H, h) for h in h_checks]
         res_log.append(max(rs))
         if max(rs) < tol:
             converged = True
             break
-    H = rational_H(Ht[:m, :m], fac.gamma)
+    H = krylov_H(Ht[:m, :m], fac.gamma, variant)
     return Basis(beta=beta, V=V[:m].copy(), Ht=Ht[:m + 1, :m].copy(), m=m, H=H,
                  converged=converged, breakdown=breakdown, residuals=res_log)
 
@@ -217,7 +256,8 @@ class GroupLog:
     breakdowns: int = 0
 
 
-def run_group(p, fac, k, X, t_out, nodes=None, replay_m=None, amp_scale=None, keep=None):
+def run_group(p, fac, k, X, t_out, nodes=None, replay_m=None, amp_scale=None, keep=None,
+              variant="R"):
     """Simulate group k (Alg. 2) and add its response at the output times
     into X (rows = output index, columns = ``nodes`` or all nodes)."""
     lts = local_transition_spots(p, k)
@@ -245,7 +285,8 @@ def run_group(p, fac, k, X, t_out, nodes=None, replay_m=None, amp_scale=None, ke
         else:
             h_first = hs[0] if hs.shape[0] else L
             rm = None if replay_m is None else replay_m[j]
-            basis = arnoldi(fac, v, (min(h_first, L), L), p.tol, p.m_max, replay_m=rm)
+            basis = arnoldi(fac, v, (min(h_first, L), L), p.tol, p.m_max, replay_m=rm,
+                            variant=variant)
             log.m.append(basis.m)
             log.nonconv += int(not basis.converged)
             log.breakdowns += int(basis.breakdown)
@@ -274,9 +315,11 @@ class RunResult:
 
 
 def rmatex(p, groups=None, nodes=None, replay_m=None, fac=None, amp_scale=None,
-           include_dc=True):
+           include_dc=True, variant="R"):
     """R-MATEX over every group (or the listed ones) with superposition:
-    X[o] = x_dc + sum_k x_k(t_o).  ``replay_m[k][j]`` forces m per segment."""
+    X[o] = x_dc + sum_k x_k(t_o).  ``replay_m[k][j]`` forces m per segment.
+    ``variant`` 'I' or 'S' runs the same circuit solver with the inverted
+    (I-MATEX) or standard (MEXP) Krylov space instead of the rational one."""
     fac = factorize(p) if fac is None else fac
     t_out = output_times(p)
     ncols = p.n if nodes is None else len(nodes)
@@ -287,7 +330,8 @@ def rmatex(p, groups=None, nodes=None, replay_m=None, fac=None, amp_scale=None,
     logs = []
     for k in (range(p.n_groups) if groups is None else groups):
         rm = None if replay_m is None else replay_m[k]
-        logs.append(run_group(p, fac, k, X, t_out, nodes=nodes, replay_m=rm, amp_scale=amp_scale))
+        logs.append(run_group(p, fac, k, X, t_out, nodes=nodes, replay_m=rm, amp_scale=amp_scale,
+                              variant=variant))
     return RunResult(X=X, logs=logs, x_dc=x_dc)
 
 

@@ -261,3 +261,53 @@ def test_config0_statistics():
     assert sum(lg.nonconv for lg in res.logs) == 0
     assert np.abs(res.x_dc - p.vdd).max() <= 1e-12
     assert 0 < (p.vdd - res.X).max() < 0.1
+
+
+# ---------------------------------------------------------------------------
+# The other two Krylov spaces of the circuit solver (Sec. 2.3 standard / MEXP,
+# Sec. 3.3.1 inverted / I-MATEX), on the same skeleton
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("variant", ["I", "S"])
+def test_variant_single_rc_node_closed_form(variant):
+    # one node: every Krylov space is the whole space at m = 1
+    p = one_node_problem()
+    res = R.rmatex(p, variant=variant)
+    ref = one_node_closed_form(p, R.output_times(p))
+    assert np.abs(res.X[:, 0] - ref).max() <= 1e-12 * p.vdd
+    assert all(m in (0, 1) for m in res.logs[0].m)
+
+
+@pytest.mark.parametrize("variant", ["I", "S"])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_variant_happy_breakdown_equals_dense_augmented_exponential(variant, seed):
+    p = small_random_rc(seed)
+    res = R.rmatex(p, variant=variant)
+    ref = R.dense_augmented(p, R.output_times(p))
+    assert np.abs(res.X - ref).max() <= 1e-10 * p.vdd
+
+
+def test_variant_maps_single_node():
+    # Htilde of -A^{-1} = G^{-1} C is c/g, so H'^{-1} = -g/c; the standard
+    # Hessenberg of A = -g/c is itself
+    c, g = 3e-13, 4.0
+    assert abs(R.krylov_H(np.array([[c / g]]), 1e-11, "I")[0, 0] - (-g / c)) <= 1e-12 * g / c
+    assert R.krylov_H(np.array([[-g / c]]), 1e-11, "S")[0, 0] == -g / c
+
+
+def test_variant_dimensions_follow_table1_trend():
+    """Table 1: on a stiff RC mesh the standard space (MEXP) needs far larger
+    bases than the inverted and rational ones for the same tolerance, and all
+    three agree with the dense solution to about tol."""
+    p = gridgen.small_mesh(31, nx=12, ny=12, layers=1, n_src=6, n_pads=4, t_end=0.3e-9,
+                           dt_out=5e-12, c_range=(1e-15, 1e-12), group_templates=[6])
+    p.m_max = 144
+    ref = R.dense_augmented(p, R.output_times(p))
+    stats = {}
+    for v in ("R", "I", "S"):
+        res = R.rmatex(p, variant=v)
+        ms = [m for lg in res.logs for m in lg.m if m > 0]
+        stats[v] = (np.mean(ms), max(ms), np.abs(res.X - ref).max())
+    assert stats["S"][0] > 4 * stats["R"][0] and stats["S"][0] > 4 * stats["I"][0], stats
+    for v in ("R", "I", "S"):
+        assert stats[v][2] <= 1e-5 * p.vdd, stats
