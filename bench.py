@@ -263,6 +263,9 @@ def main():
     ap.add_argument("--no-serial", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-tr", action="store_true")
+    ap.add_argument("--variants", action="store_true",
+                    help="also run the inverted (I-MATEX) and standard (MEXP) Krylov spaces "
+                         "on the bench grid (Table 1's comparison)")
     ap.add_argument("--grids", type=int, default=0,
                     help="also run that many of the 96 uneven single-layer grids as one "
                          "batch graph launch and report their aggregate rate")
@@ -424,6 +427,31 @@ def main():
                 "max_abs_diff_vs_rmatex_v": float((xt - xr).abs().max())}
         del xt, xr
 
+    # Table 1's comparison on the bench grid: the same circuit solver with the
+    # rational, inverted and standard Krylov spaces (m_max = 20)
+    variants = None
+    if args.variants:
+        sim.run(out)
+        xr = out.clone()
+        variants = {}
+        for name, key in (("rational", "R"), ("inverted", "I"), ("standard", "S")):
+            sv = M.Sim(p, stream=stream, krylov=key)
+            xv = sv.run()
+            sv.run(xv)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sv.run(xv)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st = sv.stats.as_dict()
+            ms_v = [int(m) for m in sv.m_sequence() if m > 0]
+            variants[name] = {"ms": e0.elapsed_time(e1), "m_avg": sum(ms_v) / max(1, len(ms_v)),
+                              "m_peak": max(ms_v) if ms_v else 0, "nonconv": st["nonconv"],
+                              "solve_columns": st["solve_columns"],
+                              "max_abs_diff_vs_rational_v": float((xv - xr).abs().max())}
+            del sv, xv
+        torch.cuda.empty_cache()
+
     # adjoint: the same grid with 256 observed nodes, IR-drop hinge loss; cost
     # of matex_grad relative to the forward run that taped it
     adjoint = None
@@ -475,6 +503,7 @@ def main():
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "sptrsv": sptrsv, "one_group_at_a_time": serial,
             "cpu_baseline": cpu, "adjoint": adjoint, "trapezoidal": trap,
+            "krylov_variants": variants,
             "profile_ms_per_step": ms_prof,
             "profile": {k: {kk: v[kk] / args.steps for kk in ("ms", "launches", "flops", "bytes")}
                         for k, v in prof.items()},

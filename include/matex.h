@@ -69,6 +69,12 @@ typedef struct matex_opts {
                               chosen per column count by the setup-time autotuner */
   int32_t tape;            /* 1: every run keeps each segment's Krylov basis, solve outputs and
                               Hessenberg on the device so that matex_grad can follow it */
+  int32_t krylov;          /* Krylov space of the circuit solver (Alg. 1): 0 (default) rational,
+                              X1 = C + gamma G (R-MATEX, Sec. 3.3.2); 1 inverted, X1 = G
+                              (I-MATEX, Sec. 3.3.1); 2 standard, w = A v = -C^{-1} G v (MEXP,
+                              Sec. 2.3; needs m far above 20 on stiff grids).  The residual's
+                              h_{m+1,m} is scaled by 1, 1/gamma, gamma so that tol (V) serves all
+                              three.  tape = 1 requires 0 */
   int32_t graph;           /* 1 (default): after a plain run, record the run's launches as a
                               CUDA graph and replay it in later runs while the device's
                               active-column counts match the recorded ones (checked on the

@@ -224,8 +224,8 @@ __device__ __forceinline__ void expm_dev(const double* M, double h, double* E, i
   SD::expm(M, h, E, m, w);
 }
 __device__ __forceinline__ void rational_H(const double* Ht, int m, double gamma, double* H,
-                                           ExpmWork& w) {
-  SD::rational_H(Ht, m, gamma, H, w);
+                                           ExpmWork& w, int variant) {
+  SD::rational_H(Ht, m, gamma, H, w, variant);
 }
 
 struct SmallShared {
@@ -248,7 +248,7 @@ residual_kernel(SmallState ss, RoundCols rc, const int32_t* __restrict__ iter, i
   if (threadIdx.x == 0) {
     ss.m[q] = m;
     int st = 0;
-    if (hnext <= 1e-13 * Ht[0]) st = 2;  // happy breakdown
+    if (hnext <= 1e-13 * fabs(Ht[0])) st = 2;  // happy breakdown (h_11 < 0 for A itself)
     else if (replay) st = (replay[rc.segid[q]] <= m) ? 1 : 0;
     sh.flag = st;
   }
@@ -261,14 +261,14 @@ residual_kernel(SmallState ss, RoundCols rc, const int32_t* __restrict__ iter, i
     }
     return;
   }
-  rational_H(Ht, m, gamma, sh.H, sh.w);
+  rational_H(Ht, m, gamma, sh.H, sh.w, ss.krylov);
   const double L = rc.len[q];
   const double hc = fmin(rc.hfirst[q], L);
   double rmax = 0.0;
   for (int pass = 0; pass < 2; ++pass) {
     expm_dev(sh.H, pass == 0 ? hc : L, sh.E, m, sh.w);
-    // r = ||v|| |htilde_{m+1,m} e_m^T e^{hH} e_1|
-    rmax = fmax(rmax, ss.beta[q] * fabs(hnext) * fabs(sh.E[(m - 1) * kLd + 0]));
+    // r = ||v|| |s h_{m+1,m} e_m^T e^{hH} e_1|, s making h_{m+1,m} dimensionless
+    rmax = fmax(rmax, ss.beta[q] * fabs(ss.rscale * hnext) * fabs(sh.E[(m - 1) * kLd + 0]));
   }
   if (threadIdx.x == 0) {
     int st = 0;
@@ -316,7 +316,7 @@ coef_kernel(SmallState ss, RoundCols rc, double gamma, double dt_out, double* __
   if (m <= 0) return;
   const double* Ht = ss.Ht + (int64_t)q * kMaxB * kMaxM;
   const double beta = ss.beta[q];
-  rational_H(Ht, m, gamma, sh.H, sh.w);
+  rational_H(Ht, m, gamma, sh.H, sh.w, ss.krylov);
   // segment end
   expm_dev(sh.H, rc.len[q], sh.E, m, sh.w);
   for (int i = threadIdx.x; i < m; i += blockDim.x) yend[(int64_t)q * kMaxM + i] = beta * sh.E[i * kLd];
@@ -423,6 +423,19 @@ void reduce_dots(const double* partials, int nchunks, int K, int nb, const int32
 }
 
 namespace {
+__global__ void apply_A_kernel(double* __restrict__ Vb, int64_t vstride,
+                               const int32_t* __restrict__ iter_grp, int jsrc, int jdst,
+                               const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                               const double* __restrict__ val, const double* __restrict__ c,
+                               int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double* __restrict__ v = Vb + (int64_t)iter_grp[blockIdx.y] * vstride + (int64_t)jsrc * n;
+  double gv = 0.0;
+  for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) gv = fma(val[k], v[col[k]], gv);
+  Vb[(int64_t)iter_grp[blockIdx.y] * vstride + (int64_t)jdst * n + i] = -gv / c[i];
+}
+
 __global__ void expect_count_kernel(const int32_t* __restrict__ count, int expected,
                                     int32_t* __restrict__ iter, int32_t* __restrict__ iter_grp,
                                     const int32_t* __restrict__ vslot, int32_t* __restrict__ flag) {
@@ -436,6 +449,14 @@ __global__ void expect_count_kernel(const int32_t* __restrict__ count, int expec
   }
 }
 }  // namespace
+
+void krylov_apply_A(double* Vb, int64_t vstride, const int32_t* iter_grp, int K, int jsrc, int jdst,
+                    const int64_t* rowptr, const int32_t* col, const double* val, const double* c,
+                    int64_t n, cudaStream_t st) {
+  if (K <= 0) return;
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)K);
+  apply_A_kernel<<<grid, 256, 0, st>>>(Vb, vstride, iter_grp, jsrc, jdst, rowptr, col, val, c, n);
+}
 
 void expect_count(const int32_t* count, int expected, int32_t* iter, int32_t* iter_grp,
                   const int32_t* vslot, int32_t* flag, cudaStream_t st) {

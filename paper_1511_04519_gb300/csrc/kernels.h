@@ -170,6 +170,8 @@ struct SmallState {
   int32_t* status;   // [ncol] 0 iterating, 1 converged, 2 breakdown, 3 m_max, 4 quiescent
   double* hbuf;      // [ncol][kMaxB] Gram-Schmidt coefficients of the current pass
   double* scale;     // [ncol] 1/norm for normalisation
+  int32_t krylov = 0;   // Krylov space: 0 rational, 1 inverted, 2 standard (exponent map)
+  double rscale = 1.0;  // factor on h_{m+1,m} in the residual: 1, 1/gamma, gamma
 };
 
 // finish the start vector: beta = sqrt(sum partials), scale = 1/beta, status;
@@ -187,6 +189,11 @@ void reduce_dots(const double* partials, int nchunks, int K, int nb, const int32
 // rest of the replay (whose result is then discarded) stays in range.
 void expect_count(const int32_t* count, int expected, int32_t* iter, int32_t* iter_grp,
                   const int32_t* vslot, int32_t* flag, cudaStream_t st);
+// w = A v = -C^{-1} G v for the standard Krylov space: column q of the batch
+// reads slot `jsrc` of its basis and writes slot `jdst` (G in CSR, permuted).
+void krylov_apply_A(double* Vb, int64_t vstride, const int32_t* iter_grp, int K, int jsrc, int jdst,
+                    const int64_t* rowptr, const int32_t* col, const double* val, const double* c,
+                    int64_t n, cudaStream_t st);
 void residual_check(SmallState ss, const RoundCols& rc, int K, int j, double gamma, double tol,
                     int m_max, const int32_t* replay, const int32_t* iter_in, int32_t* iter_out,
                     int32_t* iter_grp, int32_t* iter_count, cudaStream_t st);

@@ -680,6 +680,39 @@ void autotune_solve(matex_ctx* c) {
   }
 }
 
+// G in CSR in the factor's permuted order on the device (the trapezoidal
+// baseline and the standard Krylov space apply G itself).
+bool ensure_g_csr(matex_ctx* c) {
+  if (c->trG_rowptr) return true;
+  const int64_t n = c->n;
+  const Symbolic& S = c->S;
+  std::vector<int64_t> rp(n + 1, 0);
+  for (int64_t k = 0; k < n; ++k) {
+    const int32_t o = S.perm[k];
+    rp[k + 1] = rp[k] + (c->g_rowptr_h[o + 1] - c->g_rowptr_h[o]);
+  }
+  std::vector<int32_t> col(rp[n]);
+  std::vector<double> val(rp[n]);
+  for (int64_t k = 0; k < n; ++k) {
+    const int32_t o = S.perm[k];
+    int64_t d = rp[k];
+    for (int64_t e = c->g_rowptr_h[o]; e < c->g_rowptr_h[o + 1]; ++e, ++d) {
+      col[d] = S.iperm[c->g_col_h[e]];
+      val[d] = c->g_val_h[e];
+    }
+  }
+  int64_t* r = nullptr;
+  int32_t* cl = nullptr;
+  double* v = nullptr;
+  if (!c->upload(r, rp.data(), rp.size()) || !c->upload(cl, col.data(), col.size()) ||
+      !c->upload(v, val.data(), val.size()))
+    return false;
+  c->trG_rowptr = r;
+  c->trG_col = cl;
+  c->trG_val = v;
+  return true;
+}
+
 // One pass of the run (everything up to the output permutation) on c->st.
 // Plain (capture = false): the host reads every active-column count from the
 // device and appends it to kit_trace.  Recording (capture = true): the stream
@@ -813,19 +846,30 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
       launches++;
     }
     for (int j = 0; j < c->m_max && kit > 0; ++j) {
-      // w = (C + gamma G)^{-1} C v_j   (Alg. 1 with X1 = C + gamma G, X2 = C)
-      e = prof_begin(c);
-      gather_cols(c->Y, c->ldy, kit, c->Vb + (int64_t)j * n, vstride, c->iter_grp, c->c_perm,
-                  nullptr, n, st);
-      moved(e, 1, kit, true);
-      solve(c->fM, kit);
-      e = prof_begin(c);
-      scatter_cols(c->Y, c->ldy, kit, c->Vb + (int64_t)(j + 1) * n, vstride, c->iter_grp, nullptr,
-                   n, st);
-      if (c->opts.tape)  // keep a_k = (C + gamma G)^{-1} C q_k for the adjoint
-        scatter_cols(c->Y, c->ldy, kit, c->TA + (int64_t)j * n, (int64_t)kMaxM * n, c->iter_grp,
-                     nullptr, n, st);
-      moved(e, 1, kit, false);
+      if (c->opts.krylov == 2) {
+        // standard space (MEXP): w = A v_j = -C^{-1} G v_j, no solve
+        e = prof_begin(c);
+        krylov_apply_A(c->Vb, vstride, c->iter_grp, kit, j, j + 1, c->trG_rowptr, c->trG_col,
+                       c->trG_val, c->c_perm, n, st);
+        prof_end(c, e, P_SOLVE, 1, 2.0 * (double)c->g_col_h.size() * kit,
+                 (12.0 * (double)c->g_col_h.size() + 24.0 * nd) * kit);
+        launches++;
+      } else {
+        // w = X1^{-1} C v_j   (Alg. 1 with X2 = C; X1 = C + gamma G, or G for the
+        // inverted space)
+        e = prof_begin(c);
+        gather_cols(c->Y, c->ldy, kit, c->Vb + (int64_t)j * n, vstride, c->iter_grp, c->c_perm,
+                    nullptr, n, st);
+        moved(e, 1, kit, true);
+        solve(c->opts.krylov == 1 ? c->fG : c->fM, kit);
+        e = prof_begin(c);
+        scatter_cols(c->Y, c->ldy, kit, c->Vb + (int64_t)(j + 1) * n, vstride, c->iter_grp, nullptr,
+                     n, st);
+        if (c->opts.tape)  // keep a_k = (C + gamma G)^{-1} C q_k for the adjoint
+          scatter_cols(c->Y, c->ldy, kit, c->TA + (int64_t)j * n, (int64_t)kMaxM * n, c->iter_grp,
+                       nullptr, n, st);
+        moved(e, 1, kit, false);
+      }
       sweepsM++;
       // two classical Gram-Schmidt passes, then the norm and the normalisation
       e = prof_begin(c);
@@ -1215,6 +1259,8 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   if (o.max_width <= 0) o.max_width = 1024;
   if (o.tape && o.group_select >= 0) return bad("tape needs all groups (group_select = -1)");
   if (o.solve_mode < 0 || o.solve_mode > 2) return bad("solve_mode must be 0, 1 or 2");
+  if (o.krylov < 0 || o.krylov > 2) return bad("krylov must be 0, 1 or 2");
+  if (o.tape && o.krylov != 0) return bad("the adjoint tape follows the rational Krylov space only");
   if (o.col_block != 0 && o.col_block != 1 && o.col_block != 2 && o.col_block != 4 && o.col_block != 8)
     return bad("col_block must be 0, 1, 2, 4 or 8");
   if (o.group_select >= n_groups) return bad("group_select out of range");
@@ -1512,6 +1558,13 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     return MATEX_ERR_OOM;
   }
   set_small_smem_limits();
+  c->ss.krylov = o.krylov;
+  c->ss.rscale = o.krylov == 1 ? 1.0 / gamma : o.krylov == 2 ? gamma : 1.0;
+  if (o.krylov == 2 && !ensure_g_csr(c)) {
+    g_setup_err = "device allocation or upload failed";
+    delete c;
+    return MATEX_ERR_OOM;
+  }
   if (o.solve_mode == 2) autotune_solve(c);
   cudaMemset(c->Vb, 0, sizeof(double) * vslots * kMaxB * n);
   cudaMemset(c->Xb, 0, sizeof(double) * G * n);
@@ -1929,28 +1982,9 @@ namespace {
 // the permuted order on first use.
 matex_status tr_prepare(matex_ctx* c, double h) {
   const int64_t n = c->n;
-  if (!c->trG_rowptr) {
-    const Symbolic& S = c->S;
-    std::vector<int64_t> rp(n + 1, 0);
-    for (int64_t k = 0; k < n; ++k) {
-      const int32_t o = S.perm[k];
-      rp[k + 1] = rp[k] + (c->g_rowptr_h[o + 1] - c->g_rowptr_h[o]);
-    }
-    std::vector<int32_t> col(rp[n]);
-    std::vector<double> val(rp[n]);
-    for (int64_t k = 0; k < n; ++k) {
-      const int32_t o = S.perm[k];
-      int64_t d = rp[k];
-      for (int64_t e = c->g_rowptr_h[o]; e < c->g_rowptr_h[o + 1]; ++e, ++d) {
-        col[d] = S.iperm[c->g_col_h[e]];
-        val[d] = c->g_val_h[e];
-      }
-    }
-    if (!c->upload(c->trG_rowptr, rp.data(), rp.size()) || !c->upload(c->trG_col, col.data(), col.size()) ||
-        !c->upload(c->trG_val, val.data(), val.size()) || !c->alloc(c->trX, n) ||
-        !c->alloc(c->trB0, n) || !c->alloc(c->trB1, n))
-      return fail(c, MATEX_ERR_OOM, "trapezoidal buffers");
-  }
+  if (!ensure_g_csr(c) || (!c->trX && (!c->alloc(c->trX, n) || !c->alloc(c->trB0, n) ||
+                                        !c->alloc(c->trB1, n))))
+    return fail(c, MATEX_ERR_OOM, "trapezoidal buffers");
   if (c->tr_h == h) return MATEX_OK;
   const double t0 = now_ms();
   CsrSym A{n, c->g_rowptr_h.data(), c->g_col_h.data(), c->g_val_h.data()};

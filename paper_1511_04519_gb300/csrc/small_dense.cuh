@@ -168,8 +168,20 @@ struct Small {
   __syncthreads();
 }
 
-// H = (I - Ht_m^{-1}) / gamma  (Eq. 9); Ht is the column's (kMaxB x kMaxM) array.
-  static __device__ void rational_H(const double* Ht, int m, double gamma, double* H, Work& w) {
+// The exponent matrix of the Krylov space from its Arnoldi Hessenberg Ht (the
+// column's kMaxB x kMaxM array): variant 0 rational, H = (I - Ht_m^{-1}) / gamma
+// (Eq. 9); 1 inverted, H = -Ht_m^{-1} (the Arnoldi of G^{-1} C = -A^{-1},
+// Sec. 3.3.1); 2 standard, H = Ht_m (the Arnoldi of A, Sec. 2.3).
+  static __device__ void rational_H(const double* Ht, int m, double gamma, double* H, Work& w,
+                                    int variant = 0) {
+  if (variant == 2) {
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = e / m, j = e - i * m;
+      H[i * kLd + j] = Ht[i * kMaxM + j];
+    }
+    __syncthreads();
+    return;
+  }
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int i = e / m, j = e - i * m;
     w.V[i * kLd + j] = Ht[i * kMaxM + j];
@@ -177,10 +189,17 @@ struct Small {
   }
   __syncthreads();
   lu_solve(w.V, w.T, m, &w.piv);  // T = Ht_m^{-1}
-  const double ig = 1.0 / gamma;
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int i = e / m, j = e - i * m;
-    H[i * kLd + j] = ((i == j ? 1.0 : 0.0) - w.T[i * kLd + j]) * ig;
+  if (variant == 1) {
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = e / m, j = e - i * m;
+      H[i * kLd + j] = -w.T[i * kLd + j];
+    }
+  } else {
+    const double ig = 1.0 / gamma;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = e / m, j = e - i * m;
+      H[i * kLd + j] = ((i == j ? 1.0 : 0.0) - w.T[i * kLd + j]) * ig;
+    }
   }
   __syncthreads();
 }

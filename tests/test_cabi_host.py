@@ -139,5 +139,5 @@ def test_default_options_layout():
     from paper_1511_04519_gb300 import matex as M
     o = M.matex_default_opts()
     assert (o.col_block, o.group_select, o.include_dc, o.n_rows, o.max_width, o.strict,
-            o.solve_mode, o.tape, o.graph) == (0, -1, 1, 0, 1024, 0, 2, 0, 1)
+            o.solve_mode, o.tape, o.krylov, o.graph) == (0, -1, 1, 0, 1024, 0, 2, 0, 0, 1)
     assert C.sizeof(M.MatexStats) == 3 * 8 + 8 + 4 * 12 + 8 + 4 * 4 + 8
