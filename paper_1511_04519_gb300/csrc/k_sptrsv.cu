@@ -313,18 +313,104 @@ __device__ __forceinline__ void bwd_small(const DevFactor& F, int e0, int ne, in
   }
 }
 
+// Packed forward task, one thread per panel row (all rows of the task at
+// once; for levels whose packed work cannot fill the GPU, where the solve is
+// latency-bound): each thread holds KB accumulators over its row's w entries.
+template <int KB>
+__device__ __forceinline__ void fwd_small_rows(const DevFactor& F, int e0, int ne, int c0,
+                                               double* __restrict__ Y, double* __restrict__ Y2,
+                                               int ldy, double* sb, PackDesc& d) {
+  load_pack(F, e0, ne, d);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int k = warp; k < ne; k += nwarps) {
+    const int f = d.f[k], cnt = d.w[k] * KB;
+    double* dst = sb + d.b[k] * KB;
+    for (int e = lane; e < cnt; e += 32) {
+      const int j = e / KB, q = e - j * KB;
+      dst[e] = __ldcg(Y + (int64_t)(f + j) * ldy + c0 + q);
+    }
+  }
+  __syncthreads();
+  const int x = threadIdx.x;
+  if (x >= d.a[ne - 1] + d.ld[ne - 1]) return;
+  const int k = pack_find(d.a, ne, x);
+  const int r = x - d.a[k], w = d.w[k], ld = d.ld[k], f = d.f[k];
+  const double* __restrict__ P = F.pan_cm + d.pan[k];
+  const double* bs = sb + d.b[k] * KB;
+  const int jend = r < w ? r + 1 : w;  // L_ss^{-1} is lower triangular
+  double acc[KB];
+#pragma unroll
+  for (int q = 0; q < KB; ++q) acc[q] = 0.0;
+  for (int j = 0; j < jend; ++j) {
+    const double p = P[(int64_t)j * ld + r];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) acc[q] = fma(p, bs[j * KB + q], acc[q]);
+  }
+  if (r < w) {
+    double* __restrict__ dst = Y2 + (int64_t)(f + r) * ldy + c0;
+#pragma unroll
+    for (int q = 0; q < KB; ++q) dst[q] = acc[q];
+  } else {
+    double* __restrict__ dst = Y + (int64_t)F.sup_rows[d.rp[k] + r] * ldy + c0;
+#pragma unroll
+    for (int q = 0; q < KB; ++q) atomicAdd(dst + q, -acc[q]);
+  }
+}
+
+// Packed backward task, one thread per panel column.
+template <int KB>
+__device__ __forceinline__ void bwd_small_rows(const DevFactor& F, int e0, int ne, int c0,
+                                               double* __restrict__ Y,
+                                               const double* __restrict__ Y2, int ldy, double* ub,
+                                               PackDesc& d) {
+  load_pack(F, e0, ne, d);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int k = warp; k < ne; k += nwarps) {
+    const int f = d.f[k], w = d.w[k], cnt = d.ld[k] * KB;
+    const int32_t* __restrict__ rows = F.sup_rows + d.rp[k];
+    double* dst = ub + d.a[k] * KB;
+    for (int e = lane; e < cnt; e += 32) {
+      const int i = e / KB, q = e - i * KB;
+      dst[e] = i < w ? __ldcg(Y2 + (int64_t)(f + i) * ldy + c0 + q) * F.dinv[f + i]
+                     : -__ldcg(Y + (int64_t)rows[i] * ldy + c0 + q);
+    }
+  }
+  __syncthreads();
+  const int x = threadIdx.x;
+  if (x >= d.b[ne - 1] + d.w[ne - 1]) return;
+  const int k = pack_find(d.b, ne, x);
+  const int j = x - d.b[k], w = d.w[k], ld = d.ld[k];
+  const double* __restrict__ P = F.pan_rm + d.pan[k];
+  const double* u = ub + d.a[k] * KB;
+  double acc[KB];
+#pragma unroll
+  for (int q = 0; q < KB; ++q) acc[q] = 0.0;
+  for (int i = j; i < ld; ++i) {  // column j of L_ss^{-1} is zero above row j
+    const double p = P[(int64_t)i * w + j];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) acc[q] = fma(p, u[i * KB + q], acc[q]);
+  }
+  double* __restrict__ dst = Y + (int64_t)(d.f[k] + j) * ldy + c0;
+#pragma unroll
+  for (int q = 0; q < KB; ++q) dst[q] = acc[q];
+}
+
 template <int KB>
 __device__ __forceinline__ void run_fwd(const DevFactor& F, int2 tk, int c0, double* Y, double* Y2,
                                         int ldy, double* sm, PackDesc& pd) {
+  const int ne = tk.y & (kPackRowwise - 1);
   if (tk.x >= 0) fwd_task<KB>(F, tk.x, tk.y, c0, Y, Y2, ldy, sm);
-  else fwd_small<KB>(F, -1 - tk.x, tk.y, c0, Y, Y2, ldy, sm, pd);
+  else if (tk.y & kPackRowwise) fwd_small_rows<KB>(F, -1 - tk.x, ne, c0, Y, Y2, ldy, sm, pd);
+  else fwd_small<KB>(F, -1 - tk.x, ne, c0, Y, Y2, ldy, sm, pd);
 }
 
 template <int KB>
 __device__ __forceinline__ void run_bwd(const DevFactor& F, int2 tk, int c0, double* Y,
                                         const double* Y2, int ldy, double* sm, PackDesc& pd) {
+  const int ne = tk.y & (kPackRowwise - 1);
   if (tk.x >= 0) bwd_task<KB>(F, tk.x, tk.y, c0, Y, Y2, ldy, sm);
-  else bwd_small<KB>(F, -1 - tk.x, tk.y, c0, Y, Y2, ldy, sm, pd);
+  else if (tk.y & kPackRowwise) bwd_small_rows<KB>(F, -1 - tk.x, ne, c0, Y, Y2, ldy, sm, pd);
+  else bwd_small<KB>(F, -1 - tk.x, ne, c0, Y, Y2, ldy, sm, pd);
 }
 
 template <int KB>
@@ -431,7 +517,7 @@ persistent_solve_kernel(DevFactor F, PersistSched ps, double* __restrict__ Y,
       const int2 tk = fwd ? L.ftasks[task] : L.btasks[task];
       // supernodes of this task: one, or a packed list
       const int32_t* ents = tk.x >= 0 ? nullptr : F.pack + (-1 - tk.x);
-      const int ne = tk.x >= 0 ? 1 : tk.y;
+      const int ne = tk.x >= 0 ? 1 : (tk.y & (kPackRowwise - 1));
       if (threadIdx.x == 0) {
         bool ok = true;
         for (int k = 0; k < ne && ok; ++k) {

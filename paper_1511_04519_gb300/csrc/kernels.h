@@ -32,6 +32,9 @@ struct DevFactor {
 constexpr int kRowBlock = 32;  // panel rows (forward) / columns (backward) per task
 constexpr int kPackRows = 128; // rows (forward) / columns (backward) of a packed task
 constexpr int kPackMax = 64;   // supernodes per packed task
+// Flag in a packed task's count: one thread per panel row (forward) or column
+// (backward) instead of warp-wide (row or column, right-hand side) chunks.
+constexpr int kPackRowwise = 1 << 16;
 // A task is int2 {s, first row/column} for one supernode, or, for many small
 // supernodes of one level, int2 {-1 - e, count}: pack[e .. e+count) lists them
 // and the task runs one thread per panel row (forward) / column (backward).

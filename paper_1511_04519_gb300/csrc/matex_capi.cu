@@ -284,10 +284,17 @@ bool plan_levels(matex_ctx* c) {
   // at most 16 wide, backward packs columns of panels at most 16 wide and 64
   // rows long (a longer panel keeps the 4-thread split dot of its own task)
   constexpr int kPackLd = 384;
+  int dev_sms = 0;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int kPackTarget = 8 * std::max(dev_sms, 1);  // CTAs that keep every SM busy
   std::vector<int32_t> pack_a, pack_b;  // per entry: rows / columns of the earlier entries
-  auto flush = [&](std::vector<int32_t>& cur, std::vector<int2>& out) {
+  auto flush = [&](std::vector<int32_t>& cur, std::vector<int2>& out, int mode) {
     if (cur.empty()) return;
-    out.push_back(make_int2(-1 - (int)pack.size(), (int)cur.size()));
+    out.push_back(make_int2(-1 - (int)pack.size(), (int)cur.size() | mode));
     int a = 0, b = 0;
     for (int32_t s : cur) {
       pack.push_back(s);
@@ -317,12 +324,26 @@ bool plan_levels(matex_ctx* c) {
     std::vector<int32_t> by_ld = by_w;
     std::stable_sort(by_w.begin(), by_w.end(), [&](int a, int b) { return sup_w(a) > sup_w(b); });
     std::stable_sort(by_ld.begin(), by_ld.end(), [&](int a, int b) { return sup_ld(a) > sup_ld(b); });
+    // Packed tasks run their rows (columns) as warp-wide (row, right-hand
+    // side) chunks, every lane busy but each warp working through several
+    // chunks in turn; or one thread per row, lanes idle where rows of unequal
+    // width share a warp but every row at once.  The first wins when the
+    // level has enough packed work to fill the GPU, the second when it does
+    // not (small grids, upper levels: the solve is then latency-bound).
+    int prow = 0, pcol = 0;
+    for (const int s : by_w) {
+      if (sup_ld(s) <= kPackRows && sup_w(s) <= 16) prow += sup_ld(s);
+      if (sup_w(s) <= 16 && sup_ld(s) <= 64) pcol += sup_w(s);
+    }
+    const int cblocks = std::max(1, c->ldy / 8);
+    const int fmode = (prow / kPackRows) * cblocks >= kPackTarget ? 0 : kPackRowwise;
+    const int bmode = (pcol / kPackRows) * cblocks >= kPackTarget ? 0 : kPackRowwise;
     for (const int s : by_w) {
       const int w = sup_w(s);
       const int wr = sup_ld(s);
       mw = std::max(mw, w);
       if (wr <= kPackRows && w <= 16) {
-        if (rows + wr > kPackRows || (int)cur.size() == kPackMax) { flush(cur, ft); rows = 0; }
+        if (rows + wr > kPackRows || (int)cur.size() == kPackMax) { flush(cur, ft, fmode); rows = 0; }
         cur.push_back(s);
         rows += wr;
         fpacked[s] = 1;
@@ -331,14 +352,14 @@ bool plan_levels(matex_ctx* c) {
         for (int i0 = 0; i0 < wr; i0 += kRowBlock) ft.push_back(make_int2(s, i0));
       }
     }
-    flush(cur, ft);
+    flush(cur, ft, fmode);
     int cols = 0, ldsum = 0;
     for (const int s : by_ld) {
       const int w = sup_w(s);
       const int wr = sup_ld(s);
       if (w <= 16 && wr <= 64) {
         if (cols + w > kPackRows || ldsum + wr > kPackLd || (int)cur.size() == kPackMax) {
-          flush(cur, bt);
+          flush(cur, bt, bmode);
           cols = ldsum = 0;
         }
         cur.push_back(s);
@@ -351,7 +372,7 @@ bool plan_levels(matex_ctx* c) {
         for (int j0 = 0; j0 < w; j0 += kRowBlock) bt.push_back(make_int2(s, j0));
       }
     }
-    flush(cur, bt);
+    flush(cur, bt, bmode);
     // longest tasks first (the block scheduler hands out CTAs in index order,
     // so the level's tail is made of short tasks); duration ~ the length of one
     // thread's dot product: a quarter of the panel extent for split tasks, the
@@ -359,13 +380,13 @@ bool plan_levels(matex_ctx* c) {
     auto fdur = [&](const int2& t) {
       if (t.x >= 0) return std::min(sup_w(t.x), t.y + kRowBlock) / kSplitFor;
       int d = 0;
-      for (int k = 0; k < t.y; ++k) d = std::max(d, sup_w(pack[-1 - t.x + k]));
+      for (int k = 0; k < (t.y & (kPackRowwise - 1)); ++k) d = std::max(d, sup_w(pack[-1 - t.x + k]));
       return d;
     };
     auto bdur = [&](const int2& t) {
       if (t.x >= 0) return (sup_ld(t.x) - t.y) / kSplitFor;
       int d = 0;
-      for (int k = 0; k < t.y; ++k) d = std::max(d, sup_ld(pack[-1 - t.x + k]));
+      for (int k = 0; k < (t.y & (kPackRowwise - 1)); ++k) d = std::max(d, sup_ld(pack[-1 - t.x + k]));
       return d;
     };
     std::stable_sort(ft.begin() + fofs[l], ft.end(),
