@@ -251,6 +251,41 @@ def batch_grids(args, M, stream):
     return res
 
 
+def other_configs(M, stream):
+    """One recorded run, then one timed graph replay, of the single-group
+    1,024-node grid (about 190 sequential segments) and of the four-layer
+    1.44M-node grid with 256 uneven groups (64 sampled output rows)."""
+    import numpy as np
+    import torch
+
+    import gridgen
+    res = {}
+    for name, p, nrows in (("grid32x32_1group", gridgen.config0(), 0),
+                           ("mesh4x600x600_256groups", gridgen.config2(), 64)):
+        rows = None
+        if nrows:
+            rows = np.sort(np.random.default_rng(0).choice(p.n, nrows, replace=False)).astype(np.int32)
+        t0 = time.perf_counter()
+        sim = M.Sim(p, rows=rows, stream=stream)
+        setup_s = time.perf_counter() - t0
+        x = sim.run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.run(x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        st = sim.stats.as_dict()
+        res[name] = {"nodes": p.n, "groups": p.n_groups, "ms": ms,
+                     "value": p.n * (p.n_out - 1) * p.n_groups / (ms / 1e3), "unit": UNIT,
+                     "setup_s": setup_s, "graph_replay": st["graph_replay"],
+                     "rounds": st["rounds"], "solve_columns": st["solve_columns"],
+                     "nonconv": st["nonconv"], "nnz_L": st["nnz_L"]}
+        del sim, x
+        torch.cuda.empty_cache()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -263,6 +298,11 @@ def main():
     ap.add_argument("--no-serial", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-tr", action="store_true")
+    ap.add_argument("--lane-probe", action="store_true",
+                    help="also time the FP64 probe with 32, 16, 8 and 1 active lanes per warp")
+    ap.add_argument("--other-configs", action="store_true",
+                    help="also time one graph-replayed run of the 1,024-node single-group grid "
+                         "and of the 1.44M-node 256-group grid (several minutes)")
     ap.add_argument("--variants", action="store_true",
                     help="also run the inverted (I-MATEX) and standard (MEXP) Krylov spaces "
                          "on the bench grid (Table 1's comparison)")
@@ -485,7 +525,10 @@ def main():
                    "forward_taped_ms": fm, "grad_ms": gm, "grad_over_forward": gm / fm}
         del sim3
 
+    lanes = ({str(k): M.measure_fp64_lanes(k) for k in (32, 16, 8, 1)} if args.lane_probe
+             else None)
     grids = batch_grids(args, M, stream) if args.grids else None
+    others = other_configs(M, stream) if args.other_configs else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -511,7 +554,7 @@ def main():
                                                  "nonconv", "sweeps_M", "sweeps_G", "solve_columns",
                                                  "rounds", "kernel_launches", "graph_replay",
                                                  "graph_capture_ms")},
-            "batch_grids": grids,
+            "batch_grids": grids, "other_configs": others, "fp64_lane_probe_ms": lanes,
             "autotune": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in t.items()}
                          for t in tuning],
             "setup_ms": {"order": setup["setup_order_ms"], "factor": setup["setup_factor_ms"],

@@ -358,6 +358,14 @@ matex_status matex_tr_run(matex_ctx* ctx, int32_t substeps, double* x_out, doubl
  */
 matex_status matex_measure_fp64_peak(int32_t reps, double* tflops, double* ms);
 
+/*
+ * The same probe with only the first active_lanes (1..32) lanes of every warp
+ * running their chains (no counterpart in the paper): *ms (host) receives the
+ * best of `reps` launch times.  Equal times for 32, 16, 8 and 1 lanes show
+ * that a warp FP64 instruction costs the pipe the same with any mask.
+ */
+matex_status matex_measure_fp64_lanes(int32_t active_lanes, int32_t reps, double* ms);
+
 const char* matex_last_error(const matex_ctx* ctx);
 const char* matex_status_string(matex_status s);
 void matex_destroy(matex_ctx* ctx);

@@ -67,7 +67,8 @@ EXPORTS = ["matex_default_opts", "matex_setup", "matex_run", "matex_run_host", "
            "matex_get_profile", "matex_host_factor_solve", "matex_set_batching",
            "matex_debug_inject_wait", "matex_solve_noalloc", "matex_grad", "matex_set_caps",
            "matex_get_autotune", "matex_batch_create", "matex_batch_run", "matex_batch_last_error",
-           "matex_batch_destroy", "matex_measure_fp64_peak", "matex_tr_run"]
+           "matex_batch_destroy", "matex_measure_fp64_peak", "matex_tr_run",
+           "matex_measure_fp64_lanes"]
 
 
 def _load():
@@ -131,6 +132,8 @@ def _load():
     lib.matex_batch_destroy.restype = None
     lib.matex_tr_run.argtypes = [P, C.c_int32, P, dp]
     lib.matex_tr_run.restype = C.c_int
+    lib.matex_measure_fp64_lanes.argtypes = [C.c_int32, C.c_int32, dp]
+    lib.matex_measure_fp64_lanes.restype = C.c_int
     lib.matex_measure_fp64_peak.argtypes = [C.c_int32, dp, dp]
     lib.matex_measure_fp64_peak.restype = C.c_int
     return lib
@@ -429,6 +432,15 @@ def measure_fp64_peak(reps=5):
     if st != MATEX_OK:
         raise MatexError(st, "FP64 probe failed")
     return tf.value, ms.value
+
+
+def measure_fp64_lanes(active_lanes, reps=5):
+    """ms of the FP64 probe with only `active_lanes` lanes of each warp running."""
+    ms = C.c_double()
+    st = _lib.matex_measure_fp64_lanes(int(active_lanes), int(reps), C.byref(ms))
+    if st != MATEX_OK:
+        raise MatexError(st, "FP64 lane probe failed")
+    return ms.value
 
 
 class Batch:
