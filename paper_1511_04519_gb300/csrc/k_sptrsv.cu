@@ -13,9 +13,15 @@
 //             ancestors' rows, which a later level reads);
 //   backward: x_s = P_s^T [D_s^{-1} y_s; -x_R], pulling the ancestors' final
 //             x_R (solved one level up).
-// One launch covers one level of the supernodal elimination tree; a task is
-// (supernode, 32 panel rows or columns) x (column block of KB right-hand sides),
-// four threads per panel row/column, each thread holding all KB columns.
+// One launch covers one level of the supernodal elimination tree (or one
+// persistent launch covers all levels).  A task is (supernode, 32 panel rows
+// or columns) x (column block of KB right-hand sides) with four threads per
+// panel row/column, or a pack of small supernodes of one level.  In a split
+// task the four threads of a row either share its panel entries (each holds
+// all KB columns; partials added through shared memory) or, from KB = 8,
+// share out its columns (KB/4 each, no partial sums).  Packed tasks run one
+// thread per row/column or warp-wide (row, column-of-Y) chunks, chosen per
+// level at setup (the task's count carries the choice).
 #include "kernels.h"
 
 #include <algorithm>

@@ -9,6 +9,10 @@
 //              test of Sec. 3.3.3 per column; converged columns retire
 //     outputs  y(t_o) = beta e^{(t_o - l) H_m} e_1,  X[o] += V y + z + h z' - w
 //     hand-off x(l_{j+1}) for the next round.
+// After the first (plain) run the same pass is recorded as a CUDA graph and
+// replayed while the device's active-column counts match the recording.
+// Also here: batches of contexts as one graph, the trapezoidal baseline, the
+// other Krylov spaces' operators, and the allocation-free solve.
 #include <cuda_runtime.h>
 
 #include <algorithm>
