@@ -124,6 +124,14 @@ def dist_env():
     return world, rank, local
 
 
+def workload_config(p, world):
+    """The `config` of both arms' JSON lines."""
+    return {"workload": WORKLOAD, "nodes": p.n, "groups": p.n_groups,
+            "output_steps": p.n_out - 1, "sources": p.n_src,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "working set (factors, bases, 1.44 GB of outputs) > 129 MB L2"}
+
+
 def reference_arm(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -147,7 +155,7 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "working set > L2"},
+            "data": "synthetic", "config": workload_config(p, 1),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": env_threads, "kind": "oracle",
                              "sample": "each step: one of the 64 groups of the same grid through "
                                        "the FP64 oracle (SuperLU, MGS, scipy expm), all nodes "
@@ -539,10 +547,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nodes": p.n, "groups": p.n_groups,
-                       "output_steps": p.n_out - 1, "sources": p.n_src,
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "working set (factors, bases, 1.44 GB of outputs) > 129 MB L2"},
+            "config": workload_config(p, world),
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "sptrsv": sptrsv, "one_group_at_a_time": serial,
             "cpu_baseline": cpu, "adjoint": adjoint, "trapezoidal": trap,
