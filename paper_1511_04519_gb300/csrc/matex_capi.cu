@@ -1633,6 +1633,7 @@ matex_status matex_set_caps(matex_ctx* c, const double* cap) {
   if (!ok) return cuda_check(c, "set_caps upload");
   c->c_host.assign(cap, cap + c->n);
   c->taped = false;
+  c->tr_h = 0.0;  // the trapezoidal factor C + h/2 G is refactored on its next use
   c->setup_stats.setup_factor_ms = now_ms() - t;
   return MATEX_OK;
 }

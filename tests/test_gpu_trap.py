@@ -70,3 +70,18 @@ def test_trapezoidal_rows_and_new_sources(M):
     q.pwl_v = v2
     _, ref = R.trapezoidal(q, q.dt_out)
     assert np.abs(X.cpu().numpy() - ref[:, rows]).max() <= TOL_V * p.vdd
+
+
+def test_trapezoidal_follows_new_capacitances(M):
+    p = gridgen.small_mesh(23, nx=7, ny=7, layers=1, n_src=5, group_templates=[2, 3],
+                           t_end=0.3e-9, dt_out=10e-12)
+    sim = M.Sim(p)
+    sim.tr_run(1)
+    c2 = np.asarray(p.c) * np.random.default_rng(5).uniform(0.5, 2.0, p.n)
+    sim.set_caps(c2)
+    X, _ = sim.tr_run(1)
+    q = gridgen.small_mesh(23, nx=7, ny=7, layers=1, n_src=5, group_templates=[2, 3],
+                           t_end=0.3e-9, dt_out=10e-12)
+    q.c = c2
+    _, ref = R.trapezoidal(q, q.dt_out)
+    assert np.abs(X.cpu().numpy() - ref).max() <= TOL_V * p.vdd
