@@ -106,7 +106,7 @@ def segment_outputs(lts, t_out):
 
 
 # ---------------------------------------------------------------------------
-# Factorisations (the one-time serial part of Alg. 2, "LU_Decompose(X1)")
+# Factorisations (the one-time serial part of Alg. 2: X1 factored once)
 # ---------------------------------------------------------------------------
 
 @dataclass
@@ -124,8 +124,8 @@ class Factors:
         return self.lu_G.solve(b)
 
     def op(self, variant, v):
-        """The Arnoldi operator of each Krylov variant (Alg. 1 line
-        w = U\\(L\\(X2 v))):
+        """The Arnoldi operator of each Krylov variant (the solve step of
+        Alg. 1, X1^{-1} X2 v):
           'R' rational (Sec. 3.3.2):  X1 = C + gamma G, X2 = C: (C + gamma G)^{-1} C v
           'I' inverted (Sec. 3.3.1):  X1 = G, X2 = C:            G^{-1} C v  (= -A^{-1} v)
           'S' standard (Sec. 2.3, MEXP):                          -C^{-1} G v (= A v)"""
@@ -146,7 +146,7 @@ def factorize(p, c=None):
 
 
 # ---------------------------------------------------------------------------
-# Alg. 1 (MATEX_Arnoldi) with X1 = C + gamma G, X2 = C  (Sec. 3.3.2)
+# Alg. 1 (the Arnoldi process of the circuit solver) with X1 = C + gamma G, X2 = C  (Sec. 3.3.2)
 # ---------------------------------------------------------------------------
 
 @dataclass
@@ -264,7 +264,7 @@ def run_group(p, fac, k, X, t_out, nodes=None, replay_m=None, amp_scale=None, ke
     outs = segment_outputs(lts, t_out)
     log = GroupLog(lts=lts)
     sel = slice(None) if nodes is None else nodes
-    # Local_Initial_Solution: the group's own DC state at t = 0.
+    # the local initial solution of Alg. 2: the group's own DC state at t = 0.
     x = fac.solve_G(input_vector(p, k, lts[0], amp_scale))
     X[0] += x[sel]
     for j in range(lts.shape[0] - 1):

@@ -1,5 +1,5 @@
 // Host setup, part 1: fill-reducing ordering and supernodal symbolic analysis
-// of the SPD matrices that Alg. 2 factors once ("LU_Decompose(X1)"): for
+// of the SPD matrices that Alg. 2 factors once, X1 = C + gamma G and G: for
 // R-MATEX X1 = C + gamma G (Sec. 3.3.2), and G itself for F, P and the DC
 // state (Eq. 6).  C is diagonal, so both share one sparsity pattern and one
 // symbolic analysis.

@@ -1,4 +1,4 @@
-// Basis recombination and superposition (Alg. 1 last line, Alg. 2 snapshots,
+// Basis recombination and superposition (the final step of Alg. 1, Alg. 2 snapshots,
 // and the scheduler's sum of group responses, Sec. 3.2):
 //   x_k(t_o) = V_k y_k(t_o) + z_k + (t_o - l_j) z'_k - w_k     (Eq. 6 with -P)
 //   X[o]    += sum over the round's groups whose segment holds t_o.

@@ -1,6 +1,7 @@
 // Multi-right-hand-side supernodal triangular solves with the once-factorised
-// M = L D L^T (Alg. 1: "a pair of forward and backward substitutions",
-// w = U \ (L \ (X2 v_j)); here X1 = C + gamma G or G, both SPD, so U = D L^T).
+// M = L D L^T: the operator apply of Alg. 1, one forward and one backward
+// substitution per Arnoldi step (here X1 = C + gamma G or G, both SPD, so the
+// upper factor is D L^T).
 //
 // Layout: the right-hand sides live node-major in Y[n][ldy] (permuted node
 // order), so the K columns of one row are contiguous.  The forward result y

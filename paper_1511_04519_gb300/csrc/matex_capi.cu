@@ -806,7 +806,7 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
     cudaMemsetAsync(c->m_rec, 0, sizeof(int32_t) * std::max<int64_t>(1, c->n_segments), st);
     cudaMemsetAsync(c->st_rec, 0, sizeof(int32_t) * std::max<int64_t>(1, c->n_segments), st);
   }
-  // each group's own DC state at t = 0 (Local_Initial_Solution); groups with
+  // each group's own DC state at t = 0 (Alg. 2's local initial solution); groups with
   // zero input at t = 0 start from x = 0
   const int ng = (int)c->init_groups.size();
   for (int g0 = 0; g0 < ng; g0 += c->ldy) {
