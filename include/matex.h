@@ -80,6 +80,15 @@ typedef struct matex_opts {
                               active-column counts match the recorded ones (checked on the
                               device; on a mismatch the run is redone plainly and re-recorded);
                               0: every run is issued launch by launch */
+  double tail_eps;         /* 0 (default): exact.  eps > 0 (V): a group's term of an output
+                              (Eq. 6 with -P) is shortened once it stays small for the rest of
+                              its segment: past the last output where ||y||_2 > eps/2 its V y
+                              part is left out (|V y|_inf <= ||y||_2 for an orthonormal V), and
+                              the whole term when also max|z - w| + L max|z'| <= eps/2.  Each
+                              output entry then differs from the exact run by at most
+                              eps x (number of groups), plus rounding.  Changes the work done,
+                              so such runs are timed apart from exact ones.  tape = 1 requires
+                              0.  Negative or non-finite: MATEX_ERR_ARG */
 } matex_opts;
 
 /* Counters and timings of the last matex_run (or of setup for the setup_* fields). */

@@ -303,17 +303,38 @@ __global__ void record_kernel(SmallState ss, RoundCols rc, int K, int32_t* m_rec
 
 __global__ void __launch_bounds__(kSmallThreads)
 coef_kernel(SmallState ss, RoundCols rc, double gamma, double dt_out, double* __restrict__ coef,
-            int ldo, double* __restrict__ yend) {
+            int ldo, double* __restrict__ yend, double tail_eps, const double* __restrict__ pbound,
+            int32_t* __restrict__ tcut) {
   extern __shared__ double smem_raw[];
   SmallShared& sh = *reinterpret_cast<SmallShared*>(smem_raw);
   const int q = blockIdx.x;
   const int m = ss.m[q];
   const int no = rc.nout[q];
   double* cq = coef + (int64_t)q * ldo * kCoefLd;
+  // tail cut (thread 0): outputs up to the last one whose ||y||_2 exceeds
+  // tail_eps/2 keep V y; a NaN norm or bound counts as large
+  const bool cut = pbound != nullptr && tail_eps > 0.0;
+  const double e2 = 0.25 * tail_eps * tail_eps;
+  int last = -1;
+  auto put_cut = [&]() {
+    if (tcut == nullptr || threadIdx.x != 0) return;
+    tcut[2 * q] = cut ? last + 1 : no;
+    tcut[2 * q + 1] =
+        cut && pbound[2 * q] + rc.len[q] * pbound[2 * q + 1] <= 0.5 * tail_eps ? 1 : 0;
+  };
+  auto note_norm = [&](int o) {
+    if (!cut || threadIdx.x != 0) return;
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) s = fma(sh.y[k], sh.y[k], s);
+    if (!(s <= e2)) last = o;
+  };
   // step of the -P term at every output: h = t_o - l_j with t_o = o * dt_out
   for (int o = threadIdx.x; o < no; o += blockDim.x)
     cq[(int64_t)o * kCoefLd + kMaxM] = (double)(rc.obeg[q] + o) * dt_out - rc.l0[q];
-  if (m <= 0) return;
+  if (m <= 0 || no <= 0) {
+    put_cut();
+    if (m <= 0) return;
+  }
   const double* Ht = ss.Ht + (int64_t)q * kMaxB * kMaxM;
   const double beta = ss.beta[q];
   rational_H(Ht, m, gamma, sh.H, sh.w, ss.krylov);
@@ -329,19 +350,23 @@ coef_kernel(SmallState ss, RoundCols rc, double gamma, double dt_out, double* __
     cq[i] = sh.y[i];
   }
   __syncthreads();
-  if (no == 1) return;
-  expm_dev(sh.H, dt_out, sh.E, m, sh.w);
-  for (int o = 1; o < no; ++o) {
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      double s = 0.0;
-      for (int k = 0; k < m; ++k) s = fma(sh.E[i * kLd + k], sh.y[k], s);
-      sh.y2[i] = s;
-      cq[(int64_t)o * kCoefLd + i] = s;
+  note_norm(0);
+  if (no > 1) {
+    expm_dev(sh.H, dt_out, sh.E, m, sh.w);
+    for (int o = 1; o < no; ++o) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < m; ++k) s = fma(sh.E[i * kLd + k], sh.y[k], s);
+        sh.y2[i] = s;
+        cq[(int64_t)o * kCoefLd + i] = s;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < m; i += blockDim.x) sh.y[i] = sh.y2[i];
+      __syncthreads();
+      note_norm(o);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) sh.y[i] = sh.y2[i];
-    __syncthreads();
   }
+  put_cut();
 }
 
 __global__ void __launch_bounds__(kSmallThreads)
@@ -478,9 +503,11 @@ void record_segments(const SmallState& ss, const RoundCols& rc, int K, int32_t* 
 }
 
 void output_coefficients(SmallState ss, const RoundCols& rc, int K, double gamma, double dt_out,
-                         double* coef, int ldo, double* yend, cudaStream_t st) {
+                         double* coef, int ldo, double* yend, cudaStream_t st, double tail_eps,
+                         const double* pbound, int32_t* tcut) {
   const size_t smem = sizeof(SmallShared);
-  coef_kernel<<<K, kSmallThreads, smem, st>>>(ss, rc, gamma, dt_out, coef, ldo, yend);
+  coef_kernel<<<K, kSmallThreads, smem, st>>>(ss, rc, gamma, dt_out, coef, ldo, yend, tail_eps,
+                                              pbound, tcut);
 }
 
 void expm_batch(int batch, int m, const double* A, const double* h, double* E, cudaStream_t st) {

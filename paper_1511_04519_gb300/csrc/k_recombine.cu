@@ -61,7 +61,7 @@ recombine_kernel(double* __restrict__ Xp, int64_t n, const double* __restrict__ 
                  const double* __restrict__ Z, const double* __restrict__ Zp,
                  const double* __restrict__ W, int64_t gstride, RoundCols rc,
                  const int32_t* __restrict__ mcol, const double* __restrict__ coef, int ldo, int K,
-                 int obeg_min, double dt_out) {
+                 int obeg_min, double dt_out, const int32_t* __restrict__ tcut) {
   const int64_t i = (int64_t)blockIdx.x * kRecThreads + threadIdx.x;
   const int o0 = obeg_min + blockIdx.y * kOT;
   if (i >= n || (rc.abort && *rc.abort)) return;
@@ -74,13 +74,18 @@ recombine_kernel(double* __restrict__ Xp, int64_t n, const double* __restrict__ 
     const int ob = rc.obeg[q], no = rc.nout[q];
     const int lo = max(ob, o0), hi = min(ob + no, o0 + kOT);
     if (lo >= hi) continue;
+    int mq = mcol[q];
+    if (tcut && o0 >= ob + tcut[2 * q]) {  // the tile lies past the column's tail cut
+      if (tcut[2 * q + 1]) continue;
+      mq = 0;
+    }
     covered |= ((1u << (hi - lo)) - 1u) << (lo - o0);
     const int64_t g = rc.group[q];
     const double* __restrict__ vcol = Vb + (int64_t)rc.vslot[q] * vstride + i;
     const double z = Z[g * gstride + i], zp = Zp[g * gstride + i], w = W[g * gstride + i];
     const double l0 = rc.l0[q];
     const double* __restrict__ cq = coef + (int64_t)q * ldo * kCoefLd;
-    switch (mcol[q]) {
+    switch (mq) {
 #define MATEX_GT(MM) \
   case MM: group_tile<MM>(acc, asum, zsum, vcol, n, z, zp, w, l0, cq, o0, ob, lo, hi); break;
       MATEX_GT(0) MATEX_GT(1) MATEX_GT(2) MATEX_GT(3) MATEX_GT(4) MATEX_GT(5) MATEX_GT(6)
@@ -96,6 +101,43 @@ recombine_kernel(double* __restrict__ Xp, int64_t n, const double* __restrict__ 
       const double to = (double)(o0 + t) * dt_out;
       Xp[(int64_t)(o0 + t) * n + i] += acc[t] + fma(to, zsum, asum);
     }
+}
+
+// Per column, the largest |z - w| and |z'| of its group over a chunk of nodes,
+// folded into pbound by an atomic max.  Both are >= 0 (or NaN with the sign
+// bit clear), so their bit patterns order like the values and a NaN, whose
+// pattern is above +inf's, is kept.
+constexpr int kPbThreads = 256;
+constexpr int kPbPer = 8;  // nodes per thread
+
+__global__ void __launch_bounds__(kPbThreads)
+p_bound_kernel(const double* __restrict__ Z, const double* __restrict__ Zp,
+               const double* __restrict__ W, int64_t gstride, RoundCols rc, int64_t n,
+               unsigned long long* __restrict__ pbound) {
+  const int q = blockIdx.y;
+  const int64_t g = rc.group[q];
+  const double* __restrict__ z = Z + g * gstride;
+  const double* __restrict__ zp = Zp + g * gstride;
+  const double* __restrict__ w = W + g * gstride;
+  unsigned long long a = 0, b = 0;
+  const int64_t base = (int64_t)blockIdx.x * kPbThreads * kPbPer + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < kPbPer; ++k) {
+    const int64_t i = base + (int64_t)k * kPbThreads;
+    if (i < n) {
+      a = max(a, (unsigned long long)__double_as_longlong(fabs(z[i] - w[i])));
+      b = max(b, (unsigned long long)__double_as_longlong(fabs(zp[i])));
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a = max(a, __shfl_xor_sync(0xffffffffu, a, off));
+    b = max(b, __shfl_xor_sync(0xffffffffu, b, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(pbound + 2 * q, a);
+    atomicMax(pbound + 2 * q + 1, b);
+  }
 }
 
 __global__ void next_state_kernel(double* __restrict__ X, const double* __restrict__ Vb,
@@ -145,13 +187,24 @@ __global__ void permute_out_kernel(double* __restrict__ out, const double* __res
 void recombine(double* Xp, int64_t n, int n_times, const double* Vbase, int64_t vstride,
                const double* Z, const double* Zp, const double* W, int64_t gstride,
                const RoundCols& rc, const int32_t* mcol, const double* coef, int ldo, int K,
-               int obeg_min, int oend_max, double dt_out, cudaStream_t st) {
+               int obeg_min, int oend_max, double dt_out, cudaStream_t st,
+               const int32_t* tcut) {
   (void)n_times;
   if (K <= 0 || oend_max <= obeg_min) return;
   dim3 grid((unsigned)((n + kRecThreads - 1) / kRecThreads),
             (unsigned)((oend_max - obeg_min + kOT - 1) / kOT));
   recombine_kernel<<<grid, kRecThreads, 0, st>>>(Xp, n, Vbase, vstride, Z, Zp, W, gstride, rc, mcol,
-                                                  coef, ldo, K, obeg_min, dt_out);
+                                                  coef, ldo, K, obeg_min, dt_out, tcut);
+}
+
+void p_bound(const double* Z, const double* Zp, const double* W, int64_t gstride,
+             const RoundCols& rc, int K, int64_t n, double* pbound, cudaStream_t st) {
+  if (K <= 0) return;
+  cudaMemsetAsync(pbound, 0, sizeof(double) * 2 * (size_t)K, st);
+  const int64_t per = (int64_t)kPbThreads * kPbPer;
+  dim3 grid((unsigned)((n + per - 1) / per), (unsigned)K);
+  p_bound_kernel<<<grid, kPbThreads, 0, st>>>(Z, Zp, W, gstride, rc, n,
+                                              reinterpret_cast<unsigned long long*>(pbound));
 }
 
 void next_state(double* X, const double* Vbase, int64_t vstride, const double* Z, const double* Zp,

@@ -204,20 +204,35 @@ void residual_check(SmallState ss, const RoundCols& rc, int K, int j, double gam
 void record_segments(const SmallState& ss, const RoundCols& rc, int K, int32_t* m_rec,
                      int32_t* st_rec, cudaStream_t st);
 // coefficient vectors beta e^{h H} e_1 for every output of the segment and
-// for the segment end; coef [K][ldo][kCoefLd] (slot kMaxM holds h), yend [K][kMaxM]
+// for the segment end; coef [K][ldo][kCoefLd] (slot kMaxM holds h), yend [K][kMaxM].
+// With tail_eps > 0 it also writes each column's tail cut: tcut[2q] = outputs,
+// from the segment's first, up to the last one with ||y||_2 > tail_eps/2;
+// tcut[2q+1] = 1 when pbound[q] <= tail_eps/2 as well (the -P term is dropped
+// past the cut too).  With tail_eps = 0, tcut[2q] = the column's output count.
 void output_coefficients(SmallState ss, const RoundCols& rc, int K, double gamma, double dt_out,
-                         double* coef, int ldo, double* yend, cudaStream_t st);
+                         double* coef, int ldo, double* yend, cudaStream_t st,
+                         double tail_eps = 0.0, const double* pbound = nullptr,
+                         int32_t* tcut = nullptr);
+// pbound[2q] = max_i |z_i - w_i| and pbound[2q+1] = max_i |z'_i| over the
+// column's group, so that pbound[2q] + L pbound[2q+1] bounds its -P term
+// z + h z' - w for every h in [0, L] (a NaN anywhere makes the bound NaN)
+void p_bound(const double* Z, const double* Zp, const double* W, int64_t gstride,
+             const RoundCols& rc, int K, int64_t n, double* pbound, cudaStream_t st);
 size_t small_shared_bytes();
 void set_small_smem_limits();
 // batched expm for the public test entry point
 void expm_batch(int batch, int m, const double* A, const double* h, double* E, cudaStream_t st);
 
 // Recombination + superposition: Xp[o][i] += sum over columns whose segment
-// holds o of (V y_o + z + h z' - w)   (h = t_o - l0)
+// holds o of (V y_o + z + h z' - w)   (h = t_o - l0).  With tcut (the tail
+// cuts of output_coefficients), an output tile that starts at or past a
+// column's cut takes the column without V y, or not at all when the column's
+// -P term is dropped as well.
 void recombine(double* Xp, int64_t n, int n_times, const double* Vbase, int64_t vstride,
                const double* Z, const double* Zp, const double* W, int64_t gstride,
                const RoundCols& rc, const int32_t* mcol, const double* coef, int ldo, int K,
-               int obeg_min, int oend_max, double dt_out, cudaStream_t st);
+               int obeg_min, int oend_max, double dt_out, cudaStream_t st,
+               const int32_t* tcut = nullptr);
 // next state x_k = V y_end + z + L z' - w
 void next_state(double* X, const double* Vbase, int64_t vstride, const double* Z, const double* Zp,
                 const double* W, int64_t gstride, const RoundCols& rc, const int32_t* mcol,

@@ -150,6 +150,8 @@ struct matex_ctx {
   int32_t* h_count = nullptr;  // pinned
   double* coef = nullptr;
   double* yend = nullptr;
+  int32_t* tcut = nullptr;   // [Kmax][2] tail cut of each column (tail_eps > 0)
+  double* pbound = nullptr;  // [Kmax][2] bounds on the column's -P term (tail_eps > 0)
   int32_t *m_rec = nullptr, *st_rec = nullptr;
   double* out_buf = nullptr;   // device output for matex_run_host
   // host copies of the round tables (profiling arithmetic)
@@ -919,11 +921,21 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
     }
     if (c->opts.tape) tape_small(c->ss, rc, K, c->THt, c->Tbeta, st);
     e = prof_begin(c);
-    output_coefficients(c->ss, rc, K, c->gamma, c->dt_out, c->coef, c->n_times, c->yend, st);
+    const double teps = c->opts.tail_eps;
+    if (teps > 0.0) {
+      e = prof_begin(c);
+      p_bound(c->Zb, c->Zpb, c->Wb, n, rc, K, n, c->pbound, st);
+      prof_end(c, e, P_OTHER, 1, 3.0 * nd * K, 24.0 * nd * K);
+      launches++;
+    }
+    e = prof_begin(c);
+    output_coefficients(c->ss, rc, K, c->gamma, c->dt_out, c->coef, c->n_times, c->yend, st,
+                        teps, teps > 0.0 ? c->pbound : nullptr, c->tcut);
     prof_end(c, e, P_SMALL, 1, 0.0, 0.0);
     e = prof_begin(c);
     recombine(c->Xp, n, c->n_times, c->Vb, vstride, c->Zb, c->Zpb, c->Wb, n, rc, c->ss.m, c->coef,
-              c->n_times, K, r.obeg_min, r.oend_max, c->dt_out, st);
+              c->n_times, K, r.obeg_min, r.oend_max, c->dt_out, st,
+              teps > 0.0 ? c->tcut : nullptr);
     prof_end(c, e, P_RECOMB, 1, 0.0, 0.0, (int)ri);
     e = prof_begin(c);
     next_state(c->Xb, c->Vb, vstride, c->Zb, c->Zpb, c->Wb, n, rc, c->ss.m, c->yend, K, n, st);
@@ -1286,6 +1298,8 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   if (o.solve_mode < 0 || o.solve_mode > 2) return bad("solve_mode must be 0, 1 or 2");
   if (o.krylov < 0 || o.krylov > 2) return bad("krylov must be 0, 1 or 2");
   if (o.tape && o.krylov != 0) return bad("the adjoint tape follows the rational Krylov space only");
+  if (!std::isfinite(o.tail_eps) || o.tail_eps < 0.0) return bad("tail_eps must be finite and >= 0");
+  if (o.tape && o.tail_eps > 0.0) return bad("the adjoint tape follows exact runs only (tail_eps 0)");
   if (o.col_block != 0 && o.col_block != 1 && o.col_block != 2 && o.col_block != 4 && o.col_block != 8)
     return bad("col_block must be 0, 1, 2, 4 or 8");
   if (o.group_select >= n_groups) return bad("group_select out of range");
@@ -1554,7 +1568,8 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
        c->alloc(c->ss.hbuf, (size_t)Kmax * kMaxB) && c->alloc(c->ss.scale, Kmax) &&
        c->alloc(c->iterA, Kmax) && c->alloc(c->iterB, Kmax) && c->alloc(c->iter_grp, Kmax) &&
        c->alloc(c->d_count, 4) && c->alloc(c->coef, (size_t)Kmax * c->n_times * kCoefLd) &&
-       c->alloc(c->yend, (size_t)Kmax * kMaxM) && c->alloc(c->m_rec, std::max<int64_t>(1, c->n_segments)) &&
+       c->alloc(c->yend, (size_t)Kmax * kMaxM) &&
+       c->alloc(c->tcut, (size_t)Kmax * 2) && c->alloc(c->pbound, (size_t)Kmax * 2) && c->alloc(c->m_rec, std::max<int64_t>(1, c->n_segments)) &&
        c->alloc(c->st_rec, std::max<int64_t>(1, c->n_segments));
   if (ok && cudaMallocHost(&c->h_count, 4 * sizeof(int32_t)) != cudaSuccess) ok = false;
   if (ok && cudaMemset(c->d_count, 0, 4 * sizeof(int32_t)) != cudaSuccess) ok = false;

@@ -32,7 +32,8 @@ class MatexOpts(C.Structure):
                 ("n_rows", C.c_int32), ("rows", C.POINTER(C.c_int32)),
                 ("replay_m", C.POINTER(C.c_int32)), ("n_replay", C.c_int64),
                 ("max_width", C.c_int32), ("strict", C.c_int32), ("solve_mode", C.c_int32),
-                ("tape", C.c_int32), ("krylov", C.c_int32), ("graph", C.c_int32)]
+                ("tape", C.c_int32), ("krylov", C.c_int32), ("graph", C.c_int32),
+                ("tail_eps", C.c_double)]
 
 
 class MatexStats(C.Structure):
@@ -314,9 +315,10 @@ class Sim:
 
     def __init__(self, p, col_block=0, group_select=-1, include_dc=True, rows=None,
                  replay_m=None, max_width=0, strict=False, stream=None, solve_mode=2,
-                 tape=False, graph=True, krylov="R", **overrides):
+                 tape=False, graph=True, krylov="R", tail_eps=0.0, **overrides):
         o = matex_default_opts()
         o.graph = int(bool(graph))
+        o.tail_eps = float(tail_eps)
         o.krylov = {"R": 0, "I": 1, "S": 2}[krylov]
         o.col_block = col_block
         o.group_select = group_select

@@ -139,5 +139,13 @@ def test_default_options_layout():
     from paper_1511_04519_gb300 import matex as M
     o = M.matex_default_opts()
     assert (o.col_block, o.group_select, o.include_dc, o.n_rows, o.max_width, o.strict,
-            o.solve_mode, o.tape, o.krylov, o.graph) == (0, -1, 1, 0, 1024, 0, 2, 0, 0, 1)
+            o.solve_mode, o.tape, o.krylov, o.graph, o.tail_eps) == (0, -1, 1, 0, 1024, 0, 2, 0,
+                                                                     0, 1, 0.0)
+    # the library writes exactly sizeof(matex_opts) bytes: a sentinel-filled
+    # buffer keeps every byte past the binding's struct
+    size = C.sizeof(M.MatexOpts)
+    buf = (C.c_ubyte * (size + 64))(*([0xA5] * (size + 64)))
+    M._lib.matex_default_opts(C.cast(buf, C.POINTER(M.MatexOpts)))
+    assert bytes(buf[size:]) == b"\xa5" * 64
+    assert M.MatexOpts.from_buffer(buf).tail_eps == 0.0
     assert C.sizeof(M.MatexStats) == 3 * 8 + 8 + 4 * 12 + 8 + 4 * 4 + 8
