@@ -14,44 +14,54 @@ namespace {
 constexpr int kRecThreads = 128;
 constexpr int kOT = 16;  // output times per thread
 
-// One group's contribution to a thread's node over the tile's output times.
-// M is the group's Krylov dimension, so every FP64 instruction issued is
-// useful work.  When the group's segment covers the whole tile (`full`,
-// warp-uniform), its -P term z + (t_o - l_j) z' - w = (z - w - l_j z') + t_o z'
-// is folded into two per-tile sums (a, zsum) applied once per output after all
-// groups, leaving M FMAs per (node, output, group); a partially covering
-// group adds its -P term per output.
-template <int M>
+// One group's contribution to a thread's node over the tile's output times,
+// from its basis vectors J0..J1-1 (and its -P term when P).  A group of
+// Krylov dimension M takes one call <0, M, true>, or for M > kSplitM two calls
+// (<0, kSplitM, true> and <kSplitM, M, false>) so that no instance holds more
+// than kSplitM basis values in registers.  Every FP64 instruction issued is
+// useful work.  When the group's segment covers the whole tile (warp-uniform),
+// its -P term z + (t_o - l_j) z' - w = (z - w - l_j z') + t_o z' is folded into
+// two per-tile sums (asum, zsum) applied once per output after all groups,
+// leaving one FMA per (node, output, group, basis vector).  A partially
+// covering group runs a loop over its covered outputs only (trip count
+// uniform across the block) and adds its term, -P included, into the
+// thread's slots of a shared-memory accumulator (`part`, stride kRecThreads),
+// which a register array could not take at a run-time index.
+constexpr int kSplitM = 10;
+
+template <int J0, int J1, bool P>
 __device__ __forceinline__ void group_tile(double (&acc)[kOT], double& asum, double& zsum,
+                                           double* __restrict__ part,
                                            const double* __restrict__ vcol, int64_t n, double z,
                                            double zp, double w, double l0,
                                            const double* __restrict__ cq, int o0, int ob, int lo,
                                            int hi) {
-  double v[M > 0 ? M : 1];
-#pragma unroll
-  for (int j = 0; j < M; ++j) v[j] = vcol[(int64_t)j * n];
+  constexpr int M = J1 - J0;
   const double zmw = z - w;
   if (lo == o0 && hi == o0 + kOT) {
-    asum += fma(-l0, zp, zmw);
-    zsum += zp;
+    double v[M > 0 ? M : 1];
+#pragma unroll
+    for (int j = 0; j < M; ++j) v[j] = vcol[(int64_t)(J0 + j) * n];
+    if (P) {
+      asum += fma(-l0, zp, zmw);
+      zsum += zp;
+    }
 #pragma unroll
     for (int t = 0; t < kOT; ++t) {
-      const double* __restrict__ y = cq + (int64_t)(o0 + t - ob) * kCoefLd;
+      const double* __restrict__ y = cq + (int64_t)(o0 + t - ob) * kCoefLd + J0;
       double a = acc[t];
 #pragma unroll
       for (int j = 0; j < M; ++j) a = fma(v[j], y[j], a);
       acc[t] = a;
     }
   } else {
-#pragma unroll
-    for (int t = 0; t < kOT; ++t) {
-      const int o = o0 + t;
-      if (o < lo || o >= hi) continue;
+#pragma unroll 1
+    for (int o = lo; o < hi; ++o) {
       const double* __restrict__ y = cq + (int64_t)(o - ob) * kCoefLd;
-      double a = fma(y[kMaxM], zp, acc[t]) + zmw;
+      double a = P ? fma(y[kMaxM], zp, zmw) : 0.0;
 #pragma unroll
-      for (int j = 0; j < M; ++j) a = fma(v[j], y[j], a);
-      acc[t] = a;
+      for (int j = J0; j < J1; ++j) a = fma(vcol[(int64_t)j * n], y[j], a);  // L1 after the first o
+      part[(o - o0) * kRecThreads] += a;
     }
   }
 }
@@ -62,12 +72,17 @@ recombine_kernel(double* __restrict__ Xp, int64_t n, const double* __restrict__ 
                  const double* __restrict__ W, int64_t gstride, RoundCols rc,
                  const int32_t* __restrict__ mcol, const double* __restrict__ coef, int ldo, int K,
                  int obeg_min, double dt_out, const int32_t* __restrict__ tcut) {
+  __shared__ double part_s[kOT * kRecThreads];
   const int64_t i = (int64_t)blockIdx.x * kRecThreads + threadIdx.x;
   const int o0 = obeg_min + blockIdx.y * kOT;
   if (i >= n || (rc.abort && *rc.abort)) return;
+  double* __restrict__ part = part_s + threadIdx.x;  // this thread's slots only: no barrier
   double acc[kOT];
 #pragma unroll
-  for (int t = 0; t < kOT; ++t) acc[t] = 0.0;
+  for (int t = 0; t < kOT; ++t) {
+    acc[t] = 0.0;
+    part[t * kRecThreads] = 0.0;
+  }
   double asum = 0.0, zsum = 0.0;
   unsigned covered = 0;
   for (int q = 0; q < K; ++q) {
@@ -86,12 +101,23 @@ recombine_kernel(double* __restrict__ Xp, int64_t n, const double* __restrict__ 
     const double l0 = rc.l0[q];
     const double* __restrict__ cq = coef + (int64_t)q * ldo * kCoefLd;
     switch (mq) {
-#define MATEX_GT(MM) \
-  case MM: group_tile<MM>(acc, asum, zsum, vcol, n, z, zp, w, l0, cq, o0, ob, lo, hi); break;
+#define MATEX_GT(MM)                                                                           \
+  case MM:                                                                                     \
+    group_tile<0, MM, true>(acc, asum, zsum, part, vcol, n, z, zp, w, l0, cq, o0, ob, lo, hi); \
+    break;
+#define MATEX_GT2(MM)                                                                          \
+  case MM:                                                                                     \
+    group_tile<0, kSplitM, true>(acc, asum, zsum, part, vcol, n, z, zp, w, l0, cq, o0, ob, lo, \
+                                 hi);                                                          \
+    group_tile<kSplitM, MM, false>(acc, asum, zsum, part, vcol, n, z, zp, w, l0, cq, o0, ob,   \
+                                   lo, hi);                                                    \
+    break;
       MATEX_GT(0) MATEX_GT(1) MATEX_GT(2) MATEX_GT(3) MATEX_GT(4) MATEX_GT(5) MATEX_GT(6)
-      MATEX_GT(7) MATEX_GT(8) MATEX_GT(9) MATEX_GT(10) MATEX_GT(11) MATEX_GT(12) MATEX_GT(13)
-      MATEX_GT(14) MATEX_GT(15) MATEX_GT(16) MATEX_GT(17) MATEX_GT(18) MATEX_GT(19) MATEX_GT(20)
+      MATEX_GT(7) MATEX_GT(8) MATEX_GT(9) MATEX_GT(10) MATEX_GT2(11) MATEX_GT2(12) MATEX_GT2(13)
+      MATEX_GT2(14) MATEX_GT2(15) MATEX_GT2(16) MATEX_GT2(17) MATEX_GT2(18) MATEX_GT2(19)
+      MATEX_GT2(20)
 #undef MATEX_GT
+#undef MATEX_GT2
       default: break;
     }
   }
@@ -99,7 +125,7 @@ recombine_kernel(double* __restrict__ Xp, int64_t n, const double* __restrict__ 
   for (int t = 0; t < kOT; ++t)
     if (covered & (1u << t)) {
       const double to = (double)(o0 + t) * dt_out;
-      Xp[(int64_t)(o0 + t) * n + i] += acc[t] + fma(to, zsum, asum);
+      Xp[(int64_t)(o0 + t) * n + i] += (acc[t] + part[t * kRecThreads]) + fma(to, zsum, asum);
     }
 }
 
