@@ -81,7 +81,7 @@ def test_host_factorisation_rejects_indefinite(lib):
     assert st == 2  # MATEX_ERR_NOT_SPD
 
 
-def _setup_status(lib, p, **kw):
+def _setup_status(lib, p, opts=None, **kw):
     f = lib.matex_setup
     f.restype = C.c_int
     ctx = C.c_void_p()
@@ -95,7 +95,7 @@ def _setup_status(lib, p, **kw):
            _P(arrs["pwl_off"], C.c_int32), _P(arrs["pwl_t"], C.c_double),
            _P(arrs["pwl_v"], C.c_double), _P(arrs["src_group"], C.c_int32),
            C.c_int32(p.n_groups), C.c_double(p.gamma), C.c_double(p.tol), C.c_int32(p.m_max),
-           C.c_double(p.t_end), C.c_double(p.dt_out), None, None)
+           C.c_double(p.t_end), C.c_double(p.dt_out), opts, None)
     lib.matex_last_error.restype = C.c_char_p
     return st, lib.matex_last_error(None).decode()
 
@@ -118,6 +118,27 @@ def test_setup_rejects_bad_inputs_before_gpu(lib, mutation):
     elif mutation == "bad_col":
         cidx = p.g_col.copy(); cidx[0] = -3; kw["g_col"] = cidx
     st, msg = _setup_status(lib, p, **kw)
+    assert st == 1, (st, msg)
+    assert msg
+
+
+@pytest.mark.parametrize("field,value", [("tail_eps", -1e-9), ("tail_eps", float("nan")),
+                                         ("tail_eps", float("inf")), ("krylov", 3),
+                                         ("solve_mode", 5), ("tape_tail", 1e-9),
+                                         ("tape_krylov", 1)])
+def test_setup_rejects_bad_options_before_gpu(lib, field, value):
+    """Option checks run on the host before any device work: the status is
+    MATEX_ERR_ARG with a message, on a machine without a GPU as well."""
+    from paper_1511_04519_gb300 import matex as M
+    p = gridgen.small_mesh(4, nx=5, ny=5, n_src=3)
+    o = M.matex_default_opts()
+    if field == "tape_tail":
+        o.tape, o.tail_eps = 1, value
+    elif field == "tape_krylov":
+        o.tape, o.krylov = 1, value
+    else:
+        setattr(o, field, value)
+    st, msg = _setup_status(lib, p, opts=C.byref(o))
     assert st == 1, (st, msg)
     assert msg
 
