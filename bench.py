@@ -30,6 +30,52 @@ WORKLOAD = "rmatex_mesh2x300x300_180k_nodes_2000src_64groups_10ns_10ps"
 TAIL_EPS = 1e-12  # per group, in units of Vdd: 64 groups stay 64x inside the 1e-9 Vdd bound
 
 
+def work_model(p, m_seq):
+    """Whole-run work model (the terms of Eq. 11-12) from the Krylov
+    dimension of every (group, segment) of a run, groups in order and
+    segments in time order (segments that built no basis have m = 0):
+
+    * solve_columns: sum over Krylov segments of (m + 2) (m shift-and-invert
+      solves, plus the G-solves of z' and w);
+    * critical_path_sweeps: the longest per-group chain, max_k sum (m + 2):
+      what one compute node per group would run in sequence;
+    * batched_sweeps: the segment-aligned rounds run here, sum over rounds
+      of (largest m in the round + 2);
+    * recombine_vy_gflop: 2 n sum over segments of nout * m, the V y part of
+      the recombination (an output t_o belongs to the segment with
+      l_j < t_o <= l_{j+1})."""
+    import numpy as np
+    n_steps = int(round(p.t_end / p.dt_out))
+    T = n_steps * p.dt_out
+    t_out = np.arange(n_steps + 1, dtype=np.float64) * p.dt_out
+    m_seq = np.asarray(m_seq)
+    pos = cols = chain = 0
+    round_max = {}
+    vy = 0.0
+    for k in range(p.n_groups):
+        pts = {0.0, T}
+        for s in np.nonzero(p.src_group == k)[0]:
+            pts.update(float(t) for t in p.pwl_t[p.pwl_off[s]:p.pwl_off[s + 1]] if 0.0 < t < T)
+        lts = sorted(pts)
+        ms = m_seq[pos:pos + len(lts) - 1]
+        pos += len(lts) - 1
+        own = 0
+        for j, m in enumerate(int(v) for v in ms):
+            if m <= 0:
+                continue
+            own += m + 2
+            round_max[j] = max(round_max.get(j, 0), m)
+            nout = int(np.count_nonzero((t_out > lts[j]) & (t_out <= lts[j + 1])))
+            vy += 2.0 * p.n * nout * m
+        cols += own
+        chain = max(chain, own)
+    if pos != m_seq.shape[0]:
+        raise ValueError(f"m sequence has {m_seq.shape[0]} entries, the schedule {pos}")
+    return {"solve_columns": cols, "critical_path_sweeps": chain,
+            "batched_sweeps": sum(m + 2 for m in round_max.values()),
+            "recombine_vy_gflop": vy / 1e9}
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm, src = 6800.0, "fallback"
@@ -478,6 +524,22 @@ def main():
                 "max_abs_diff_vs_rmatex_v": float((xt - xr).abs().max())}
         del xt, xr
 
+    # the work model beside the measured counts and times (auxiliary: a
+    # failure here is reported in the line, never fatal)
+    try:
+        wm = work_model(p, sim.m_sequence())
+        rec_s = prof["recombine"]["ms"] / args.steps / 1e3
+        wm["measured"] = {"solve_columns": stats["solve_columns"],
+                          "sweeps": stats["sweeps_M"] + stats["sweeps_G"],
+                          "solve_ms": prof["solve"]["ms"] / args.steps,
+                          "recombine_ms": rec_s * 1e3,
+                          "recombine_vy_tflops": wm["recombine_vy_gflop"] / 1e3 / rec_s
+                          if rec_s > 0 else None}
+        wm["note"] = ("measured solve columns and sweeps also count the one G-solve of the "
+                      "pads' DC state")
+    except Exception as exc:  # noqa: BLE001
+        wm = {"error": f"{type(exc).__name__}: {exc}"}
+
     # tail skipping (opt-in, changes the work): a group's term of an output
     # loses V y once ||y||_2 stays below eps/2, and vanishes when its -P term
     # is below eps/2 too; every entry stays within n_groups * eps of the exact run
@@ -584,7 +646,7 @@ def main():
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "sptrsv": sptrsv, "one_group_at_a_time": serial,
             "cpu_baseline": cpu, "adjoint": adjoint, "trapezoidal": trap,
-            "krylov_variants": variants, "tail_skip": tail,
+            "krylov_variants": variants, "tail_skip": tail, "work_model": wm,
             "profile_ms_per_step": ms_prof,
             "profile": {k: {kk: v[kk] / args.steps for kk in ("ms", "launches", "flops", "bytes")}
                         for k, v in prof.items()},
