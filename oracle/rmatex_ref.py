@@ -21,7 +21,7 @@ Rational (shift-and-invert) Krylov, Sec. 3.3.2: Arnoldi on
 with the empirical residual of Sec. 3.3.3
     r_m(h) = ||v|| * |htilde_{m+1,m} e_m^T e^{h H_m} e_1|.
 
-Readings where the paper is silent (each is listed in the design doc):
+Readings where the paper is silent:
   * residual checked at h_c = first output offset in the segment and at the
     segment length; both must be below tol (the basis is reused for every
     step inside the segment, Alg. 2, and Fig. 4 says error falls with h);

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
-Bar (BASELINE the benchmark spec): max node-voltage error <= 1e-9 * Vdd.  When the
+Bar: max node-voltage error <= 1e-9 * Vdd.  When the
 adaptive Krylov dimension picked on the GPU differs from the oracle's on some
 segment (a residual within rounding of tol), the run is repeated in replay
 mode with the oracle's m sequence and must meet the bar there.
