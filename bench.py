@@ -138,30 +138,87 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def cpu_oracle_sample(n_groups_sample: int) -> dict:
-    """The oracle as it stands on the first groups of the workload (single
-    thread: BLAS pinned to one thread by the parent's environment)."""
+_POOL = {}
+
+
+def _oracle_group(g):
+    """One group of the workload through the oracle, in a pool worker (the
+    problem and its factors are inherited from the parent at fork)."""
+    from oracle import rmatex_ref as R
+    t0 = time.perf_counter()
+    R.rmatex(_POOL["p"], fac=_POOL["fac"], groups=[int(g)])
+    return time.perf_counter() - t0
+
+
+def oracle_pool(workers):
+    """The bench grid factorised once by the oracle, then a pool of `workers`
+    processes forked from this process (which never touches the GPU), one
+    BLAS thread each; returns (problem, pool)."""
+    import multiprocessing as mp
+
     import gridgen
     from oracle import rmatex_ref as R
     p = gridgen.config1()
-    fac = R.factorize(p)
+    _POOL["p"] = p
+    _POOL["fac"] = R.factorize(p)
+    return p, mp.get_context("fork").Pool(workers)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_sample(workers: int) -> dict:
+    """The oracle as it stands on `workers` groups of the workload, one group
+    per worker process running at once (factorisation excluded)."""
+    p, pool = oracle_pool(workers)
+    groups = list(range(min(workers, p.n_groups)))
     t0 = time.perf_counter()
-    R.rmatex(p, fac=fac, groups=list(range(n_groups_sample)), nodes=None)
+    per = pool.map(_oracle_group, groups, chunksize=1)
     dt = time.perf_counter() - t0
-    units = p.n * (p.n_out - 1) * n_groups_sample
-    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n_groups_sample} of 64 groups of the same grid, all 180,000 nodes, "
-                      f"1,000 output steps; factorisation excluded; {dt:.1f} s"}
+    pool.close()
+    pool.join()
+    units = p.n * (p.n_out - 1) * len(groups)
+    return {"value": units / dt, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"{len(groups)} of 64 groups of the same grid, all 180,000 nodes, "
+                      f"1,000 output steps, one group per worker process on {workers} host "
+                      f"cores at once; factorisation excluded; {dt:.1f} s wall, "
+                      f"{sum(per):.1f} s of CPU work"}
 
 
-def run_cpu_sample(n_groups_sample: int) -> dict:
+def run_cpu_sample(workers: int) -> dict:
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
     out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-oracle-sample",
-                          str(n_groups_sample)], env=env, stdout=subprocess.PIPE, text=True,
+                          str(workers)], env=env, stdout=subprocess.PIPE, text=True,
                          check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def measured_traffic():
+    """DRAM bytes per batched solve call from the committed ncu summary of the
+    bench step, valid only while the solve kernels' source is the one the
+    counters were taken on (else None, with the reason)."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "traffic_solve_mesh2x300x300.md")
+    src = os.path.join(ROOT, "paper_1511_04519_gb300", "csrc", "k_sptrsv.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError as exc:
+        return None, f"no summary: {exc}"
+    m_b = re.search(r"traffic_per_solve_call_bytes:\s*([0-9.eE+]+)", text)
+    m_s = re.search(r"k_sptrsv_cu_sha256_16:\s*([0-9a-f]+)", text)
+    if not m_b or not m_s:
+        return None, "summary without the traffic line"
+    if m_s.group(1) != sha:
+        return None, "the solve kernels changed since the counters were taken"
+    return float(m_b.group(1)), f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {path}"
 
 
 def dist_env():
@@ -180,33 +237,43 @@ def workload_config(p, world):
 
 
 def reference_arm(args):
+    """The oracle as it stands on the host's cores: each step runs one group
+    per core at once (a forked pool; this process never touches the GPU),
+    cycling through the 64 groups."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    env_threads = 1
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    import gridgen
-    from oracle import rmatex_ref as R
-    p = gridgen.config1()
-    fac = R.factorize(p)
-    times = []
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    workers = host_cores()
+    p, pool = oracle_pool(workers)
+    times, cpu_s = [], 0.0
+    g0 = 0
     for i in range(args.warmup + args.steps):
-        g = i % p.n_groups
+        groups = [(g0 + k) % p.n_groups for k in range(min(workers, p.n_groups))]
+        g0 += len(groups)
         t0 = time.perf_counter()
-        R.rmatex(p, fac=fac, groups=[g])
+        per = pool.map(_oracle_group, groups, chunksize=1)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
+            cpu_s += sum(per)
+    pool.close()
+    pool.join()
     step_s = sum(times) / len(times)
-    value = p.n * (p.n_out - 1) * 1 / step_s
+    per_step = min(workers, p.n_groups)
+    value = p.n * (p.n_out - 1) * per_step / step_s
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(p, 1),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": env_threads, "kind": "oracle",
-                             "sample": "each step: one of the 64 groups of the same grid through "
-                                       "the FP64 oracle (SuperLU, MGS, scipy expm), all nodes "
-                                       "and outputs; factorisation excluded"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                             "sample": f"each step: {per_step} of the 64 groups of the same "
+                                       f"grid through the FP64 oracle (SuperLU, MGS, scipy "
+                                       f"expm), all nodes and outputs, one group per worker "
+                                       f"process on {workers} host cores at once; "
+                                       f"factorisation excluded; {cpu_s:.1f} s of CPU work "
+                                       f"over the timed steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -231,6 +298,20 @@ def ncu_case(what: str) -> int:
     off = np.concatenate([[0], np.cumsum(np.diff(p.pwl_off)[sel])]).astype(np.int32)
     q = gridgen.with_sources(p, p.src_node[sel], off, p.pwl_t.reshape(-1, 3)[sel].ravel(),
                              p.pwl_v.reshape(-1, 3)[sel].ravel(), p.src_group[sel], groups)
+    if what == "ksweep":
+        # the whole bench grid, level-by-level launches: one bare solve pair of
+        # 1, 4 and 64 right-hand sides (each after its own warm-up call)
+        sim = M.Sim(p, solve_mode=1)
+        for k in (1, 4, 64):
+            sim.time_solve(0, k, reps=1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for k in (1, 4, 64):
+            sim.time_solve(0, k, reps=1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"ncu_case": what, "max_memory_gb": torch.cuda.max_memory_allocated() / 1e9}))
+        return 0
     sim = M.Sim(q, solve_mode={"solve": 0, "levels": 1}.get(what, 2))
     if what in ("solve", "levels"):
         k = 16 if what == "solve" else 64
@@ -348,15 +429,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-oracle-sample", type=int, default=0)
-    ap.add_argument("--cpu-groups", type=int, default=3)
+    ap.add_argument("--cpu-workers", type=int, default=0,
+                    help="oracle worker processes for cpu_baseline (0: every host core)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serial", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-tr", action="store_true")
     ap.add_argument("--no-tail", action="store_true",
                     help="skip the separately reported tail-skipping run (tail_eps > 0)")
-    ap.add_argument("--lane-probe", action="store_true",
-                    help="also time the FP64 probe with 32, 16, 8 and 1 active lanes per warp")
     ap.add_argument("--other-configs", action="store_true",
                     help="also time one graph-replayed run of the 1,024-node single-group grid "
                          "and of the 1.44M-node 256-group grid (several minutes)")
@@ -368,7 +448,7 @@ def main():
                          "batch graph launch and report their aggregate rate")
     ap.add_argument("--profile-step", action="store_true",
                     help="warm up, run one step inside cudaProfilerStart/Stop, print its stats")
-    ap.add_argument("--ncu-case", choices=["solve", "levels", "run"], default=None,
+    ap.add_argument("--ncu-case", choices=["solve", "levels", "run", "ksweep"], default=None,
                     help="reduced case for full ncu captures: the same grid with 8 groups; "
                          "one warm call, then one call inside cudaProfilerStart/Stop")
     args = ap.parse_args()
@@ -468,14 +548,39 @@ def main():
         roof = {"bound": "hbm", "achieved": d["bytes"] / (d["ms"] / 1e3) / 1e9, "peak": hbm_peak,
                 "unit": "GB/s", "peak_source": f"{hbm_src} copy bandwidth"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
     roof["kernel"] = dom
     roof["per_launch_ms"] = per_launch_ms
+    roof["algorithmic_per_launch"] = (d["flops"] if roof["unit"] == "TFLOP/s" else d["bytes"]) / max(
+        1, d["units"])
+    roof["algorithmic_bytes_per_launch"] = d["bytes"] / max(1, d["units"])
+    traffic, traffic_src = measured_traffic() if dom == "solve" else (None, "not the solve class")
+    roof["traffic"] = traffic
+    roof["traffic_source"] = traffic_src
     s = prof["solve"]
     sptrsv = {"achieved_gbs": s["bytes"] / (s["ms"] / 1e3) / 1e9 if s["ms"] else None,
               "achieved_tflops": s["flops"] / (s["ms"] / 1e3) / 1e12 if s["ms"] else None,
               "frac_hbm": (s["bytes"] / (s["ms"] / 1e3) / 1e9) / hbm_peak if s["ms"] else None,
-              "frac_fp64": (s["flops"] / (s["ms"] / 1e3) / 1e12) / fp64_peak if s["ms"] else None}
+              "frac_fp64": (s["flops"] / (s["ms"] / 1e3) / 1e12) / fp64_peak if s["ms"] else None,
+              "work_from": "exact fill of L (nnz_L_exact), not the amalgamated panels"}
+    # The solve pair alone, per column count: where bytes dominate (one or two
+    # right-hand sides) its roofline is HBM, above that the FP64 pipe.
+    nnz = float(setup["nnz_L_exact"])
+    by_k = []
+    for K in (1, 2, 4, 8, 16, 32, 64):
+        try:
+            best, mean = sim.time_solve(0, K, reps=20)
+        except M.MatexError:   # wider than the context's column buffer
+            break
+        byt = 2.0 * (12.0 * nnz + 4.0 * (p.n + 1)) + 8.0 * p.n + 32.0 * p.n * K
+        fl = (4.0 * nnz + 2.0 * p.n) * K
+        by_k.append({"ncols": K, "ms": best, "mean_ms": mean,
+                     "gbs": byt / (best / 1e3) / 1e9, "frac_hbm": byt / (best / 1e3) / 1e9 / hbm_peak,
+                     "tflops": fl / (best / 1e3) / 1e12,
+                     "frac_fp64": fl / (best / 1e3) / 1e12 / fp64_peak})
+    sptrsv["by_ncols"] = by_k
+    sptrsv["k1"] = dict(by_k[0], algorithmic_bytes=2.0 * (12.0 * nnz + 4.0 * (p.n + 1)) + 40.0 * p.n,
+                        note="one right-hand side: the column count where the solve's bytes "
+                             "dominate (0.2 flop/byte), so its roofline is HBM")
 
     # one group at a time: the same kernels, one column per launch
     serial = None
@@ -628,14 +733,12 @@ def main():
                    "forward_taped_ms": fm, "grad_ms": gm, "grad_over_forward": gm / fm}
         del sim3
 
-    lanes = ({str(k): M.measure_fp64_lanes(k) for k in (32, 16, 8, 1)} if args.lane_probe
-             else None)
     grids = batch_grids(args, M, stream) if args.grids else None
     others = other_configs(M, stream) if args.other_configs else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = run_cpu_sample(args.cpu_groups)
+        cpu = run_cpu_sample(args.cpu_workers or host_cores())
 
     if rank == 0:
         line = {
@@ -654,7 +757,7 @@ def main():
                                                  "nonconv", "sweeps_M", "sweeps_G", "solve_columns",
                                                  "rounds", "kernel_launches", "graph_replay",
                                                  "graph_capture_ms")},
-            "batch_grids": grids, "other_configs": others, "fp64_lane_probe_ms": lanes,
+            "batch_grids": grids, "other_configs": others,
             "autotune": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in t.items()}
                          for t in tuning],
             "setup_ms": {"order": setup["setup_order_ms"], "factor": setup["setup_factor_ms"],

@@ -113,6 +113,8 @@ typedef struct matex_stats {
   int32_t rounds;          /* segment rounds (max segments over the selected groups) */
   int32_t graph_replay;    /* 1: the last run replayed the captured CUDA graph */
   double graph_capture_ms; /* host time of the last graph capture + instantiation */
+  int64_t nnz_L_exact;     /* strictly lower nonzeros of L for the ordering, without the
+                              explicit zeros of relaxed amalgamation that nnz_L counts */
 } matex_stats;
 
 void matex_default_opts(matex_opts* opts);
@@ -209,8 +211,13 @@ matex_status matex_set_batching(matex_ctx* ctx, int32_t one_group_at_a_time);
  *   xbar   device, [N+1][n_rows], dL/dx_out for the run's output rows,
  * writes
  *   dc     device [n], dL/dc_i (original node order), and
- *   damp   device [n_src], dL/da_s for a scale a_s multiplying source s's currents
- *          (evaluated at a_s = 1, i.e. d/da of the current pwl_v).
+ *   damp   device [n_src], dL/da_s, where a_s scales source s's currents as given
+ *          at matex_setup (u_s = a_s * u_s,setup): evaluated at the currents the
+ *          run used, so after matex_set_sources(a_s * u_s,setup) it is dL/da_s at
+ *          that a (a_s = 0 included).  Like dc it is the derivative of the run as
+ *          computed: a group whose sources are all at zero builds no Krylov
+ *          basis (a zero start vector), so its gradient then has no part from
+ *          the exponential term.
  * The Krylov dimensions are those of the last run (as if replayed).  Requires
  * a context set up with opts.tape = 1 and a preceding matex_run.  Reuses the
  * forward's factors (both matrices are symmetric).  Synchronises the stream.
@@ -243,6 +250,21 @@ matex_status matex_set_sources(matex_ctx* ctx, const double* pwl_v_host);
 matex_status matex_solve(matex_ctx* ctx, int32_t which, int32_t ncols, const double* b, double* x);
 
 /*
+ * Device time of the bare batched solve pair (forward and backward
+ * substitution of Alg. 1's operator apply, Sec. 3.3.2) on the context's own
+ * column buffer, without the moves matex_solve adds around it (no
+ * counterpart in the paper; the measurement behind the solve's roofline):
+ * which as for matex_solve; 1 <= ncols <= the buffer width (the largest
+ * segment round, rounded up to 8, at least 8); one warm-up, then reps timed
+ * solves with CUDA events on the context's stream, in the launch mode the
+ * context uses for ncols.  *best_ms receives the fastest, *mean_ms (may be
+ * NULL) the mean.  The buffer's values are whatever the last call left.
+ * Synchronises the stream.
+ */
+matex_status matex_time_solve(matex_ctx* ctx, int32_t which, int32_t ncols, int32_t reps,
+                              float* best_ms, float* mean_ms);
+
+/*
  * Same solve as matex_solve, for callers that are not allowed to allocate
  * device memory (no counterpart in the paper).  Code running inside another
  * library's allocator or memory-pool callback, or in a process whose device
@@ -250,17 +272,22 @@ matex_status matex_solve(matex_ctx* ctx, int32_t which, int32_t ncols, const dou
  * still solve with a context built earlier.  This call allocates nothing and
  * uses none of the context's work buffers: its right-hand-side buffers and
  * dependency counters live in one static 16 MiB device array inside the
- * library (held on every GPU that loads the library until the process exits).
+ * library, held on every device where a context was set up until the process
+ * exits.
  *   which, ncols, b, x  as for matex_solve (device pointers, [ncols][n]).
  * Limits: n <= 917,504 nodes and at most 174,761 supernodes in the factor;
  * larger factors get MATEX_ERR_ARG with the limit in matex_last_error().
- * Right-hand sides are processed in chunks that fit the array.  The first
- * call on each device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
- * Every call shares the one array, and its contents after a call are those of
- * the last chunk: calls that overlap on the GPU (other streams, other host
- * threads, other contexts on the same device) race with each other and must
- * be serialised by the caller.  Synchronises the context's stream.
+ * Right-hand sides are processed in chunks that fit the array (fewer columns
+ * per chunk for larger n).  Each chunk runs the launch mode the context uses
+ * for that column count (per tree level, or one persistent launch).
+ * matex_setup does the set-up this call needs on its device: it looks up the
+ * array's device address (cudaGetSymbolAddress, which also loads the module
+ * that holds the array) and loads every solve kernel, so the first call
+ * triggers no lazy module loading either.  Every call shares the one array,
+ * and its contents after a call are those of the last chunk: calls that
+ * overlap on the GPU (other streams, other host threads, other contexts on
+ * the same device) race with each other and must be serialised by the
+ * caller.  Synchronises the context's stream.
  */
 matex_status matex_solve_noalloc(matex_ctx* ctx, int32_t which, int32_t ncols, const double* b,
                                  double* x);
@@ -334,8 +361,8 @@ matex_status matex_get_setup_stats(matex_ctx* ctx, matex_stats* stats);
  * (A host CSR as for G; dshift host[n] or NULL), then a CPU forward/backward
  * substitution with exactly the factor panels the GPU kernels read, for
  * ncols right-hand sides b (host [ncols][n], original order) into x (host,
- * same layout).  info (host, may be NULL) receives
- * {nnz_L, n_supernodes, n_levels, max_width_seen}.
+ * same layout).  info (host [5], may be NULL) receives
+ * {nnz_L, n_supernodes, n_levels, max_width_seen, nnz_L_exact}.
  */
 matex_status matex_host_factor_solve(int64_t n, const int64_t* rowptr, const int32_t* col,
                                      const double* val, const double* dshift, double alpha,
@@ -366,14 +393,6 @@ matex_status matex_tr_run(matex_ctx* ctx, int32_t substeps, double* x_out, doubl
  * device; allocates 8 bytes of device memory for the call.
  */
 matex_status matex_measure_fp64_peak(int32_t reps, double* tflops, double* ms);
-
-/*
- * The same probe with only the first active_lanes (1..32) lanes of every warp
- * running their chains (no counterpart in the paper): *ms (host) receives the
- * best of `reps` launch times.  Equal times for 32, 16, 8 and 1 lanes show
- * that a warp FP64 instruction costs the pipe the same with any mask.
- */
-matex_status matex_measure_fp64_lanes(int32_t active_lanes, int32_t reps, double* ms);
 
 const char* matex_last_error(const matex_ctx* ctx);
 const char* matex_status_string(matex_status s);

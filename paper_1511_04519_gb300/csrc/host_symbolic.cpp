@@ -268,6 +268,9 @@ std::string symbolic_analysis(const CsrSym& A, const std::vector<int32_t>& nd_pe
       }
     }
   }
+  // the fill of L itself: what the method needs, before amalgamation pads it
+  S.nnz_L_exact = 0;
+  for (int64_t j = 0; j < n; ++j) S.nnz_L_exact += cc[j] - 1;
   // supernodes: j joins j-1 when parent[j-1] == j and the structures nest
   S.sup_first.clear();
   for (int64_t j = 0; j < n; ++j) {

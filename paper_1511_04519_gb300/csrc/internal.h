@@ -31,7 +31,10 @@ struct Symbolic {
   std::vector<int64_t> pan_off;     // nsup+1, offsets of the (w+r) x w solve panels
   std::vector<int32_t> level_ptr;   // levels of the supernodal tree, leaves first
   std::vector<int32_t> level_sups;
-  int64_t nnz_L = 0;                // strictly lower nonzeros of L (dense panels)
+  int64_t nnz_L = 0;                // strictly lower entries of the dense panels (after
+                                    // relaxed amalgamation, explicit zeros included)
+  int64_t nnz_L_exact = 0;          // strictly lower nonzeros of L itself for this ordering
+                                    // (column counts before any amalgamation)
   double flops_factor = 0.0;
 };
 

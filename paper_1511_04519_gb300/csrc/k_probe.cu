@@ -16,8 +16,7 @@ constexpr int kProbeThreads = 256;
 constexpr int kProbeIters = 2048;
 
 __global__ void __launch_bounds__(kProbeThreads)
-fp64_fma_probe(double mul, double add, double* __restrict__ sink, int active) {
-  if ((int)(threadIdx.x & 31) >= active) return;  // lanes past `active` sit out
+fp64_fma_probe(double mul, double add, double* __restrict__ sink) {
   double a0 = threadIdx.x * 1e-3, a1 = a0 + 0.1, a2 = a0 + 0.2, a3 = a0 + 0.3;
   double a4 = a0 + 0.4, a5 = a0 + 0.5, a6 = a0 + 0.6, a7 = a0 + 0.7;
 #pragma unroll 4
@@ -37,10 +36,8 @@ fp64_fma_probe(double mul, double add, double* __restrict__ sink, int active) {
 
 }  // namespace
 
-namespace {
-
-// Best-of-reps time of the probe with `active` lanes of every warp running.
-matex_status probe_time(int active, int32_t reps, float* best_ms, double* flops) {
+extern "C" matex_status matex_measure_fp64_peak(int32_t reps, double* tflops, double* ms) {
+  if (!tflops || reps <= 0) return MATEX_ERR_ARG;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -57,12 +54,12 @@ matex_status probe_time(int active, int32_t reps, float* best_ms, double* flops)
     return MATEX_ERR_CUDA;
   }
   const int blocks = sms * 16;
-  *flops = 2.0 * 8.0 * kProbeIters * (double)blocks * kProbeThreads * active / 32.0;
-  fp64_fma_probe<<<blocks, kProbeThreads>>>(0.999999, 1e-7, sink, active);  // warm-up
+  const double flops = 2.0 * 8.0 * kProbeIters * (double)blocks * kProbeThreads;
+  fp64_fma_probe<<<blocks, kProbeThreads>>>(0.999999, 1e-7, sink);  // warm-up
   float best = 1e30f;
   for (int r = 0; r < reps; ++r) {
     cudaEventRecord(e0);
-    fp64_fma_probe<<<blocks, kProbeThreads>>>(0.999999, 1e-7, sink, active);
+    fp64_fma_probe<<<blocks, kProbeThreads>>>(0.999999, 1e-7, sink);
     cudaEventRecord(e1);
     cudaEventSynchronize(e1);
     float t = 0.f;
@@ -74,28 +71,7 @@ matex_status probe_time(int active, int32_t reps, float* best_ms, double* flops)
   cudaEventDestroy(e1);
   cudaFree(sink);
   if (!ok) return MATEX_ERR_CUDA;
-  *best_ms = best;
-  return MATEX_OK;
-}
-
-}  // namespace
-
-extern "C" matex_status matex_measure_fp64_peak(int32_t reps, double* tflops, double* ms) {
-  if (!tflops || reps <= 0) return MATEX_ERR_ARG;
-  float best = 0.f;
-  double flops = 0.0;
-  const matex_status s = probe_time(32, reps, &best, &flops);
-  if (s != MATEX_OK) return s;
   *tflops = flops / (best * 1e-3) / 1e12;
   if (ms) *ms = best;
   return MATEX_OK;
-}
-
-extern "C" matex_status matex_measure_fp64_lanes(int32_t active_lanes, int32_t reps, double* ms) {
-  if (!ms || reps <= 0 || active_lanes < 1 || active_lanes > 32) return MATEX_ERR_ARG;
-  float best = 0.f;
-  double flops = 0.0;
-  const matex_status s = probe_time(active_lanes, reps, &best, &flops);
-  if (s == MATEX_OK) *ms = best;
-  return s;
 }

@@ -699,6 +699,23 @@ int persistent_blocks_per_sm(size_t smem) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_solve_kernel, kSolveThreads, smem);
   return nb;
 }
+bool preload_solve_kernels() {
+  cudaFuncAttributes a;
+  bool ok = cudaFuncGetAttributes(&a, persistent_solve_kernel) == cudaSuccess &&
+            cudaFuncGetAttributes(&a, gather_cols_kernel) == cudaSuccess &&
+            cudaFuncGetAttributes(&a, scatter_cols_kernel) == cudaSuccess &&
+            cudaFuncGetAttributes(&a, fwd_level_kernel<1>) == cudaSuccess &&
+            cudaFuncGetAttributes(&a, fwd_level_kernel<2>) == cudaSuccess &&
+            cudaFuncGetAttributes(&a, fwd_level_kernel<4>) == cudaSuccess &&
+            cudaFuncGetAttributes(&a, fwd_level_kernel<8>) == cudaSuccess &&
+            cudaFuncGetAttributes(&a, bwd_level_kernel<1>) == cudaSuccess &&
+            cudaFuncGetAttributes(&a, bwd_level_kernel<2>) == cudaSuccess &&
+            cudaFuncGetAttributes(&a, bwd_level_kernel<4>) == cudaSuccess &&
+            cudaFuncGetAttributes(&a, bwd_level_kernel<8>) == cudaSuccess;
+  if (!ok) cudaGetLastError();
+  return ok;
+}
+
 void set_solve_smem_limit(int bytes) {
   std::lock_guard<std::mutex> lk(g_smem_mu);
   int& cur = g_solve_smem[cur_device_slot()];

@@ -29,6 +29,7 @@ struct DevFactor {
                          // (a graph replay whose counts diverged; its result is discarded)
 };
 
+constexpr int kMaxColBlock = 8;  // largest column block KB of the solve kernels (a power of two)
 constexpr int kRowBlock = 32;  // panel rows (forward) / columns (backward) per task
 constexpr int kPackRows = 128; // rows (forward) / columns (backward) of a packed task
 constexpr int kPackMax = 64;   // supernodes per packed task
@@ -81,6 +82,11 @@ struct PersistSched {
 void persistent_solve(const DevFactor& F, const PersistSched& ps, int grid, size_t smem,
                       double* Y, double* Y2, int ldy, cudaStream_t st);
 int persistent_blocks_per_sm(size_t smem);
+// Loads every kernel a solve can launch (level kernels of every column block,
+// the persistent kernel, the gathers and scatters) on the current device, so
+// that a later solve triggers no lazy module loading (which allocates device
+// memory for the code).  Returns false on a CUDA error.
+bool preload_solve_kernels();
 // adds one to *p on the stream (failure-injection hook of the tests)
 void bump_counter(int* p, cudaStream_t st);
 

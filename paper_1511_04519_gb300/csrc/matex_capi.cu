@@ -47,6 +47,10 @@ struct Round {
   int32_t obeg_min, oend_max;
 };
 
+// Device address of the allocation-free solve's static scratch array on
+// device `dev` (defined with matex_solve_noalloc below).
+matex_status noalloc_scratch(int dev, void** out, std::string& err);
+
 // Launch and sweep counts of one pass of the run.
 struct PassCounts {
   int launches = 0, sweepsM = 0, sweepsG = 0;
@@ -600,17 +604,19 @@ void prof_collect(matex_ctx* c, const std::vector<int32_t>& m_seg) {
   c->ev_used = 0;
 }
 
-// Algorithmic work of one batched solve pair with K right-hand sides: a
-// multiply-add per strictly-lower nonzero of the supernodal L and column in
-// each direction, plus the D^{-1} scaling; bytes: the nonzeros of each panel
-// (L_ss^{-1} is lower triangular) read once per direction, D^{-1}, the row
-// lists, and the right-hand sides read and written once per direction.
+// Algorithmic work of one batched solve pair with K right-hand sides, from
+// the exact fill of L (the explicit zeros of relaxed amalgamation are the
+// implementation's choice, not work the method needs): a multiply-add per
+// strictly-lower nonzero of L and column in each direction, plus the D^{-1}
+// scaling; bytes: L in compressed form (8-byte value and 4-byte row index per
+// nonzero, 4-byte column pointers) read once per direction, D^{-1}, and the
+// right-hand sides read and written once per direction.
 double solve_flops(const matex_ctx* c, int K) {
-  return (4.0 * (double)c->S.nnz_L + 2.0 * (double)c->n) * K;
+  return (4.0 * (double)c->S.nnz_L_exact + 2.0 * (double)c->n) * K;
 }
 double solve_bytes(const matex_ctx* c, int K) {
-  return 16.0 * ((double)c->S.nnz_L + (double)c->n) + 8.0 * c->n +
-         8.0 * (double)c->S.sup_rowptr[c->S.nsup] + 32.0 * (double)c->n * K;
+  return 2.0 * (12.0 * (double)c->S.nnz_L_exact + 4.0 * ((double)c->n + 1.0)) + 8.0 * c->n +
+         32.0 * (double)c->n * K;
 }
 
 enum { P_SOLVE = 0, P_MOVE = 1, P_GS = 2, P_SMALL = 3, P_RECOMB = 4, P_OTHER = 5 };
@@ -1353,6 +1359,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   if (!e.empty()) { g_setup_err = e; delete c; return MATEX_ERR_NOT_SPD; }
   c->setup_stats.setup_factor_ms = now_ms() - t;
   c->setup_stats.nnz_L = c->S.nnz_L;
+  c->setup_stats.nnz_L_exact = c->S.nnz_L_exact;
   c->setup_stats.n_supernodes = c->S.nsup;
   c->setup_stats.n_levels = (int32_t)c->S.level_ptr.size() - 1;
 
@@ -1606,6 +1613,17 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     return MATEX_ERR_OOM;
   }
   if (o.solve_mode == 2) autotune_solve(c);
+  {
+    // Load, here, everything matex_solve_noalloc touches on this device: the
+    // module that holds its static scratch array (under lazy module loading
+    // the array is allocated when its module is first loaded) and every solve
+    // kernel.  Its first call then allocates nothing.  A failure here is left
+    // for that call to report.
+    void* scratch = nullptr;
+    std::string serr;
+    if (noalloc_scratch(c->device, &scratch, serr) != MATEX_OK) cudaGetLastError();
+    preload_solve_kernels();
+  }
   cudaMemset(c->Vb, 0, sizeof(double) * vslots * kMaxB * n);
   cudaMemset(c->Xb, 0, sizeof(double) * G * n);
   if (cudaDeviceSynchronize() != cudaSuccess) {
@@ -1744,6 +1762,41 @@ matex_status matex_solve(matex_ctx* c, int32_t which, int32_t ncols, const doubl
   return read_count(c, &tmp);
 }
 
+matex_status matex_time_solve(matex_ctx* c, int32_t which, int32_t ncols, int32_t reps,
+                              float* best_ms, float* mean_ms) {
+  if (!c) return MATEX_ERR_ARG;
+  if ((which != 0 && which != 1) || ncols < 1 || ncols > c->ldy || reps < 1 || !best_ms)
+    return fail(c, MATEX_ERR_ARG, "bad time_solve arguments (1 <= ncols <= column buffer width)");
+  const DevFactor& F = which == 0 ? c->fM : c->fG;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_check(c, "time_solve events");
+  }
+  cudaMemsetAsync(c->d_count, 0, 4 * sizeof(int32_t), c->st);
+  solve_cols(c, F, ncols);  // warm-up
+  float best = 1e30f, sum = 0.f;
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(e0, c->st);
+    solve_cols(c, F, ncols);
+    cudaEventRecord(e1, c->st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, ms);
+    sum += ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  matex_status s = cuda_check(c, "time_solve");
+  if (s != MATEX_OK) return s;
+  int tmp = 0;
+  if ((s = read_count(c, &tmp)) != MATEX_OK) return s;
+  *best_ms = best;
+  if (mean_ms) *mean_ms = sum / (float)reps;
+  return MATEX_OK;
+}
+
 matex_status matex_expm(matex_ctx* c, int32_t batch, int32_t m, const double* A, const double* h,
                         double* E) {
   if (!c) return MATEX_ERR_ARG;
@@ -1855,6 +1908,7 @@ extern "C" matex_status matex_host_factor_solve(int64_t n, const int64_t* rowptr
     info[1] = S.nsup;
     info[2] = (int64_t)S.level_ptr.size() - 1;
     info[3] = maxw;
+    info[4] = S.nnz_L_exact;
   }
   std::vector<double> y(n), tmp;
   for (int32_t q = 0; q < ncols; ++q) {
@@ -1956,6 +2010,12 @@ extern "C" matex_status matex_solve_noalloc(matex_ctx* c, int32_t which, int32_t
                                       std::to_string((kNoAllocCounterBytes - 16) / 12) +
                                       " supernodes (its static scratch limit)");
   const size_t rhs_doubles = (kNoAllocBytes - kNoAllocCounterBytes) / sizeof(double);
+  // Leading dimension of a chunk of kc columns.  Every solve kernel works on
+  // column blocks of KB columns, KB a power of two up to kMaxColBlock, halved
+  // while KB / 2 >= kc (run_level and the persistent schedule): the blocks of
+  // a chunk then end at kc rounded up to KB, which ld_for(kc) covers.
+  static_assert(kMaxColBlock <= 8 && (kMaxColBlock & (kMaxColBlock - 1)) == 0,
+                "ld_for holds the column blocks only for power-of-two blocks up to 8");
   auto ld_for = [](int kc) { return kc <= 1 ? 1 : kc <= 2 ? 2 : kc <= 4 ? 4 : (kc + 7) & ~7; };
   // widest column chunk whose Y and Y2 fit the static scratch
   int kc = std::min<int>(ncols, c->ldy);
@@ -1983,6 +2043,14 @@ extern "C" matex_status matex_solve_noalloc(matex_ctx* c, int32_t which, int32_t
     const int ldy = ld_for(K);
     double* Y2 = Y + (size_t)n * ldy;
     gather_cols(Y, ldy, K, b + (int64_t)q0 * n, n, nullptr, nullptr, c->perm, n, st);
+    int mode = c->opts.solve_mode;
+    if (mode == 2) mode = c->mode_by_ncols.empty() ? 0 : c->mode_by_ncols[std::min(K, c->ldy)];
+    if (mode == 1) {
+      // one launch per tree level: no counters, only the two column buffers
+      solve_inplace(F, c->levels.data(), nlev, Y, Y2, ldy, K, st);
+      scatter_cols(Y, ldy, K, x + (int64_t)q0 * n, n, nullptr, c->perm, n, st);
+      continue;
+    }
     PersistSched ps;
     ps.lev = c->plev_d + (size_t)(K - 1) * nlev;
     ps.nlev = nlev;

@@ -44,7 +44,8 @@ class MatexStats(C.Structure):
                 ("nonconv", C.c_int32), ("breakdowns", C.c_int32), ("sweeps_M", C.c_int32),
                 ("sweeps_G", C.c_int32), ("solve_columns", C.c_int64),
                 ("kernel_launches", C.c_int32), ("rounds", C.c_int32),
-                ("graph_replay", C.c_int32), ("graph_capture_ms", C.c_double)]
+                ("graph_replay", C.c_int32), ("graph_capture_ms", C.c_double),
+                ("nnz_L_exact", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -69,7 +70,7 @@ EXPORTS = ["matex_default_opts", "matex_setup", "matex_run", "matex_run_host", "
            "matex_debug_inject_wait", "matex_solve_noalloc", "matex_grad", "matex_set_caps",
            "matex_get_autotune", "matex_batch_create", "matex_batch_run", "matex_batch_last_error",
            "matex_batch_destroy", "matex_measure_fp64_peak", "matex_tr_run",
-           "matex_measure_fp64_lanes"]
+           "matex_time_solve"]
 
 
 def _load():
@@ -95,6 +96,9 @@ def _load():
     lib.matex_solve.restype = C.c_int
     lib.matex_solve_noalloc.argtypes = [P, C.c_int32, C.c_int32, P, P]
     lib.matex_solve_noalloc.restype = C.c_int
+    lib.matex_time_solve.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_float),
+                                     C.POINTER(C.c_float)]
+    lib.matex_time_solve.restype = C.c_int
     lib.matex_expm.argtypes = [P, C.c_int32, C.c_int32, P, P, P]
     lib.matex_expm.restype = C.c_int
     lib.matex_get_m.argtypes = [P, i32p, C.c_int64, i64p]
@@ -133,8 +137,6 @@ def _load():
     lib.matex_batch_destroy.restype = None
     lib.matex_tr_run.argtypes = [P, C.c_int32, P, dp]
     lib.matex_tr_run.restype = C.c_int
-    lib.matex_measure_fp64_lanes.argtypes = [C.c_int32, C.c_int32, dp]
-    lib.matex_measure_fp64_lanes.restype = C.c_int
     lib.matex_measure_fp64_peak.argtypes = [C.c_int32, dp, dp]
     lib.matex_measure_fp64_peak.restype = C.c_int
     return lib
@@ -401,6 +403,14 @@ class Sim:
         torch.cuda.synchronize()
         return x
 
+    def time_solve(self, which, ncols, reps=10):
+        """(best ms, mean ms) of the bare batched solve pair with ncols
+        right-hand sides (matex_time_solve)."""
+        best, mean = C.c_float(), C.c_float()
+        _check(self.ctx, _lib.matex_time_solve(self.ctx, int(which), int(ncols), int(reps),
+                                               C.byref(best), C.byref(mean)))
+        return best.value, mean.value
+
     def one_group_at_a_time(self, on=True):
         matex_set_batching(self.ctx, on)
 
@@ -434,15 +444,6 @@ def measure_fp64_peak(reps=5):
     if st != MATEX_OK:
         raise MatexError(st, "FP64 probe failed")
     return tf.value, ms.value
-
-
-def measure_fp64_lanes(active_lanes, reps=5):
-    """ms of the FP64 probe with only `active_lanes` lanes of each warp running."""
-    ms = C.c_double()
-    st = _lib.matex_measure_fp64_lanes(int(active_lanes), int(reps), C.byref(ms))
-    if st != MATEX_OK:
-        raise MatexError(st, "FP64 lane probe failed")
-    return ms.value
 
 
 class Batch:

@@ -42,7 +42,7 @@ def host_factor_solve(lib, p, dshift, alpha, b, max_width=128):
     f = lib.matex_host_factor_solve
     f.restype = C.c_int
     x = np.zeros_like(b)
-    info = np.zeros(4, np.int64)
+    info = np.zeros(5, np.int64)
     st = f(C.c_int64(p.n), _P(p.g_rowptr, C.c_int64), _P(p.g_col, C.c_int32),
            _P(p.g_val, C.c_double), _P(dshift, C.c_double), C.c_double(alpha),
            C.c_int32(max_width), C.c_int32(b.shape[0]), _P(b, C.c_double), _P(x, C.c_double),
@@ -70,6 +70,11 @@ def test_host_factorisation_solves(lib, case, width):
         assert info[3] <= width
         # fill is modest: nested dissection on a mesh
         assert info[0] <= 40 * p.n
+        # the dense panels hold the exact fill plus amalgamation's explicit
+        # zeros; unit-width supernodes (no amalgamation) hold the fill alone
+        assert info[4] <= info[0]
+        if width == 1:
+            assert info[4] == info[0]
 
 
 def test_host_factorisation_rejects_indefinite(lib):
@@ -169,4 +174,4 @@ def test_default_options_layout():
     M._lib.matex_default_opts(C.cast(buf, C.POINTER(M.MatexOpts)))
     assert bytes(buf[size:]) == b"\xa5" * 64
     assert M.MatexOpts.from_buffer(buf).tail_eps == 0.0
-    assert C.sizeof(M.MatexStats) == 3 * 8 + 8 + 4 * 12 + 8 + 4 * 4 + 8
+    assert C.sizeof(M.MatexStats) == 3 * 8 + 8 + 4 * 12 + 8 + 4 * 4 + 8 + 8

@@ -24,17 +24,18 @@ def M():
     return matex
 
 
-def oracle_m(res):
-    return np.concatenate([np.asarray(lg.m, np.int32) for lg in res.logs])
+from tests.parity_util import check_adaptive, oracle_m  # noqa: E402,F401
 
 
-def parity(M, p, rows=None):
-    ref = R.rmatex(p, nodes=rows)
-    sim = M.Sim(p, rows=rows)
+def parity(M, p, rows=None, **kw):
+    ref = R.rmatex(p, nodes=rows, fac=kw.pop("fac", None),
+                   groups=None if kw.get("group_select", -1) < 0 else [kw["group_select"]],
+                   include_dc=kw.get("include_dc", True))
+    sim = M.Sim(p, rows=rows, **kw)
     X = sim.run().cpu().numpy()
-    if not np.array_equal(sim.m_sequence(), oracle_m(ref)):
-        X = M.Sim(p, rows=rows, replay_m=oracle_m(ref)).run().cpu().numpy()
-    return np.abs(X - ref.X).max(), sim.stats
+    err = check_adaptive(p.meta.get("label", "case"), p, X, sim.m_sequence(), ref,
+                         lambda m: M.Sim(p, rows=rows, replay_m=m, **kw).run().cpu().numpy())
+    return err, sim.stats
 
 
 @pytest.mark.parametrize("seed", [0, 1])

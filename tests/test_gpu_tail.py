@@ -10,6 +10,7 @@ import pytest
 
 import gridgen
 from oracle import rmatex_ref as R
+from tests.parity_util import check_adaptive  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -66,12 +67,11 @@ def test_within_bound_of_exact_run(M, eps_vdd):
 def test_small_eps_keeps_oracle_parity(M):
     p = uneven_groups()
     ref = R.rmatex(p)
-    ms = np.concatenate([np.asarray(lg.m, np.int32) for lg in ref.logs])
     sim = M.Sim(p, tail_eps=1e-12 * p.vdd)
     X = sim.run().cpu().numpy()
-    if not np.array_equal(sim.m_sequence(), ms):
-        X = M.Sim(p, tail_eps=1e-12 * p.vdd, replay_m=ms).run().cpu().numpy()
-    assert np.abs(X - ref.X).max() <= TOL_V * p.vdd
+    err = check_adaptive("uneven_groups_tail_eps_1e-12", p, X, sim.m_sequence(), ref,
+                         lambda m: M.Sim(p, tail_eps=1e-12 * p.vdd, replay_m=m).run().cpu().numpy())
+    assert err <= TOL_V * p.vdd
 
 
 def test_bench_grid_sampled_rows(M):

@@ -23,6 +23,9 @@ def M():
     return matex
 
 
+from tests.parity_util import check_adaptive  # noqa: E402
+
+
 def per_group(res):
     return [list(lg.m) for lg in res.logs]
 
@@ -31,10 +34,10 @@ def parity(M, p, variant):
     ref = R.rmatex(p, variant=variant)
     sim = M.Sim(p, krylov=variant)
     X = sim.run().cpu().numpy()
-    ms = np.concatenate([np.asarray(m, np.int32) for m in per_group(ref)])
-    if not np.array_equal(sim.m_sequence(), ms):
-        X = M.Sim(p, krylov=variant, replay_m=ms).run().cpu().numpy()
-    return np.abs(X - ref.X).max(), sim
+    err = check_adaptive(f"{p.meta.get('label', 'case')}_krylov_{variant}", p, X,
+                         sim.m_sequence(), ref,
+                         lambda m: M.Sim(p, krylov=variant, replay_m=m).run().cpu().numpy())
+    return err, sim
 
 
 def test_inverted_space_matches_oracle_small_mesh(M):
@@ -74,10 +77,10 @@ def test_inverted_space_on_bench_grid_groups(M):
         ref = R.rmatex(p, groups=[k], nodes=rows, variant="I")
         sim = M.Sim(p, krylov="I", group_select=k, rows=rows)
         X = sim.run().cpu().numpy()
-        ms = np.asarray(ref.logs[0].m, np.int32)
-        if not np.array_equal(sim.m_sequence(), ms):
-            X = M.Sim(p, krylov="I", group_select=k, rows=rows, replay_m=ms).run().cpu().numpy()
-        assert np.abs(X - ref.X).max() <= TOL_V * p.vdd
+        err = check_adaptive(f"mesh2x300x300_group{k}_krylov_I", p, X, sim.m_sequence(), ref,
+                             lambda m: M.Sim(p, krylov="I", group_select=k, rows=rows,
+                                             replay_m=m).run().cpu().numpy())
+        assert err <= TOL_V * p.vdd
 
 
 def test_standard_space_needs_far_larger_bases(M):
