@@ -67,8 +67,14 @@ typedef struct matex_opts {
   int32_t solve_mode;      /* 0: one persistent launch per triangular-solve pair, tasks ordered
                               by dependency counters; 1: one launch per tree level; 2 (default):
                               chosen per column count by the setup-time autotuner */
-  int32_t tape;            /* 1: every run keeps each segment's Krylov basis, solve outputs and
-                              Hessenberg on the device so that matex_grad can follow it */
+  int32_t tape;            /* what every run keeps on the device so that matex_grad can follow
+                              it: 0 nothing; 1 the full tape, each segment's Krylov basis,
+                              solve outputs and Hessenberg (memory ~ segments x m x n);
+                              2 checkpoints, each group's state x and carried input solution
+                              z at the start of every tape_window-th segment round (memory ~
+                              segments x n / tape_window); matex_grad then recomputes each
+                              window's segments from its checkpoint, tape_block groups at a
+                              time, with the run's Krylov dimensions, and reverses them */
   int32_t krylov;          /* Krylov space of the circuit solver (Alg. 1): 0 (default) rational,
                               X1 = C + gamma G (R-MATEX, Sec. 3.3.2); 1 inverted, X1 = G
                               (I-MATEX, Sec. 3.3.1); 2 standard, w = A v = -C^{-1} G v (MEXP,
@@ -89,6 +95,12 @@ typedef struct matex_opts {
                               eps x (number of groups), plus rounding.  Changes the work done,
                               so such runs are timed apart from exact ones.  tape = 1 requires
                               0.  Negative or non-finite: MATEX_ERR_ARG */
+  int32_t tape_window;     /* tape = 2: segment rounds per checkpoint window; 0 (default): the
+                              setup chooses it, with tape_block, from the free device memory
+                              (the largest block that fits, then the window with the least
+                              memory) */
+  int32_t tape_block;      /* tape = 2: groups recomputed together (columns of the recompute
+                              and reverse launches); 0 (default): chosen at setup */
 } matex_opts;
 
 /* Counters and timings of the last matex_run (or of setup for the setup_* fields). */
@@ -115,6 +127,10 @@ typedef struct matex_stats {
   double graph_capture_ms; /* host time of the last graph capture + instantiation */
   int64_t nnz_L_exact;     /* strictly lower nonzeros of L for the ordering, without the
                               explicit zeros of relaxed amalgamation that nnz_L counts */
+  int32_t tape_window;     /* tape = 2: rounds per checkpoint window and groups per recompute */
+  int32_t tape_block;      /*   block as set up (0 otherwise) */
+  int64_t tape_bytes;      /* device bytes of the adjoint's tape (tape 1) or of its checkpoints,
+                              window tape and reverse work buffers (tape 2) */
 } matex_stats;
 
 void matex_default_opts(matex_opts* opts);
@@ -219,7 +235,10 @@ matex_status matex_set_batching(matex_ctx* ctx, int32_t one_group_at_a_time);
  *          basis (a zero start vector), so its gradient then has no part from
  *          the exponential term.
  * The Krylov dimensions are those of the last run (as if replayed).  Requires
- * a context set up with opts.tape = 1 and a preceding matex_run.  Reuses the
+ * a context set up with opts.tape = 1 or 2 and a preceding matex_run.  With
+ * tape = 2 the segments are recomputed from the run's checkpoints first (the
+ * recomputed Krylov process follows the run's dimensions; MATEX_ERR_STATE if
+ * a recomputed segment retires its column at another step).  Reuses the
  * forward's factors (both matrices are symmetric).  Synchronises the stream.
  */
 matex_status matex_grad(matex_ctx* ctx, const double* xbar, double* dc, double* damp);

@@ -139,10 +139,16 @@ class Factors:
 
 
 def factorize(p, c=None):
+    """SuperLU factors of X1 = C + gamma G and of G.  Both are symmetric, so the
+    column ordering is the minimum degree ordering of A^T + A (SuperLU's
+    choice for a symmetric nonzero structure) rather than its default COLAMD,
+    which orders for an unsymmetric LU and triples the fill on these grids;
+    the solves are the same linear solves either way."""
     c = p.c if c is None else c
     G = p.G().tocsc()
     M = (sp.diags(c) + p.gamma * G).tocsc()
-    return Factors(G=G, c=c, gamma=p.gamma, lu_M=spla.splu(M), lu_G=spla.splu(G))
+    return Factors(G=G, c=c, gamma=p.gamma, lu_M=spla.splu(M, permc_spec="MMD_AT_PLUS_A"),
+                   lu_G=spla.splu(G, permc_spec="MMD_AT_PLUS_A"))
 
 
 # ---------------------------------------------------------------------------

@@ -47,9 +47,11 @@ def hinge_ir_drop_loss(X, vdd, theta, dt):
     return (w[:, None] * a * a).sum()
 
 
-def make_sim(p, rows, **kw):
-    """A tape-enabled Sim for ``IRDrop`` with the problem's base currents."""
-    sim = M.Sim(p, rows=rows, tape=True, **kw)
+def make_sim(p, rows, tape=True, **kw):
+    """A Sim that keeps what ``IRDrop``'s backward needs (tape: True or
+    "full" for the full tape, "checkpoint" for checkpoints recomputed per
+    window), with the problem's base currents."""
+    sim = M.Sim(p, rows=rows, tape=tape, **kw)
     sim.base_pwl_v = np.asarray(p.pwl_v, dtype=np.float64).copy()
     sim.pwl_source = np.repeat(np.arange(p.n_src), np.diff(np.asarray(p.pwl_off)))
     sim._caps = np.asarray(p.c, dtype=np.float64).copy()

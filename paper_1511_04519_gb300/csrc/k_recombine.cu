@@ -183,6 +183,24 @@ __global__ void next_state_kernel(double* __restrict__ X, const double* __restri
   X[g * gstride + i] = s;
 }
 
+// Checkpoint of column q: CK[q] = {X[group q], Z[group q]} (save), or back (restore).
+__global__ void checkpoint_kernel(double* __restrict__ CK, double* __restrict__ X,
+                                  double* __restrict__ Z, const int32_t* __restrict__ groups,
+                                  int64_t n, int restore) {
+  const int q = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t g = groups[q];
+  double* ck = CK + (int64_t)q * 2 * n;
+  if (restore) {
+    X[g * n + i] = ck[i];
+    Z[g * n + i] = ck[n + i];
+  } else {
+    ck[i] = X[g * n + i];
+    ck[n + i] = Z[g * n + i];
+  }
+}
+
 __global__ void fill_rows_kernel(double* __restrict__ Xp, const double* __restrict__ base,
                                  int64_t n, int n_times) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -239,6 +257,13 @@ void next_state(double* X, const double* Vbase, int64_t vstride, const double* Z
   if (K <= 0) return;
   dim3 grid((unsigned)((n + 255) / 256), (unsigned)K);
   next_state_kernel<<<grid, 256, 0, st>>>(X, Vbase, vstride, Z, Zp, W, gstride, rc, mcol, yend, n);
+}
+
+void checkpoint_states(double* CK, double* X, double* Z, const int32_t* groups, int K, int64_t n,
+                       bool restore, cudaStream_t st) {
+  if (K <= 0) return;
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)K);
+  checkpoint_kernel<<<grid, 256, 0, st>>>(CK, X, Z, groups, n, restore ? 1 : 0);
 }
 
 void fill_rows(double* Xp, const double* base, int64_t n, int n_times, cudaStream_t st) {

@@ -55,14 +55,62 @@ __device__ __forceinline__ void split_sum(const double (&acc)[KB], double* part,
   }
 }
 
-// Forward task: rows [i0, i0+32) of P_s b_s for KB right-hand sides.  Thread
-// (row, sub) accumulates all KB columns of its row over panel columns
-// j = sub, sub+4, ..., so each panel entry is loaded once per task.  Loads of
-// Y go through L2 only (__ldcg): other CTAs of a persistent launch write them.
+// One CTA's share of a split task: chunk c of n over the task's reduction,
+// with the scratch slot of its (task, column block) when n > 1.
+struct Chunk {
+  int c = 0, n = 1;
+  double* part = nullptr;
+  int* cnt = nullptr;
+  int slot = 0;
+};
+
+// [a, b) = chunk ch of the range [lo, hi), chunk widths rounded up to 16 so
+// that the four-load steps of the dot products stay whole
+__device__ __forceinline__ void chunk_range(const Chunk& ch, int lo, int hi, int& a, int& b) {
+  if (ch.n == 1) { a = lo; b = hi; return; }
+  const int span = ((hi - lo + ch.n - 1) / ch.n + 15) & ~15;
+  a = min(hi, lo + ch.c * span);
+  b = min(hi, a + span);
+}
+
+// Partial sums of the task's `rows` x KB outputs are in part[slot][chunk];
+// every thread has written its share.  The CTA that completes the slot's
+// count adds the chunks in order and hands each sum to out(r, q, v).
+template <int KB, typename Out>
+__device__ __forceinline__ void chunk_finish(const Chunk& ch, int rows, Out out) {
+  __shared__ int sh_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int old = atomicAdd(ch.cnt + ch.slot, 1);
+    sh_last = old == ch.n - 1;
+  }
+  __syncthreads();
+  if (!sh_last) return;
+  __threadfence();
+  const double* base = ch.part + (int64_t)ch.slot * ch.n * kRowBlock * KB;
+  for (int e = threadIdx.x; e < rows * KB; e += blockDim.x) {
+    const int r = e / KB, q = e - r * KB;
+    double v = 0.0;
+    for (int c = 0; c < ch.n; ++c) v += __ldcg(base + ((int64_t)c * kRowBlock + r) * KB + q);
+    out(r, q, v);
+  }
+  if (threadIdx.x == 0) ch.cnt[ch.slot] = 0;
+}
+
+__device__ __forceinline__ double* chunk_part(const Chunk& ch, int KB, int r, int q) {
+  return ch.part + (((int64_t)ch.slot * ch.n + ch.c) * kRowBlock + r) * KB + q;
+}
+
+// Forward task: rows [i0, i0+32) of P_s b_s for KB right-hand sides, over the
+// panel columns of chunk ch.  Thread (row, sub) accumulates all KB columns of
+// its row over panel columns j = sub, sub+4, ..., so each panel entry is
+// loaded once per task.  Loads of Y go through L2 only (__ldcg): other CTAs
+// of a persistent launch write them.
 template <int KB>
 __device__ __forceinline__ void fwd_task(const DevFactor& F, int s, int i0, int c0,
                                          double* __restrict__ Y, double* __restrict__ Y2, int ldy,
-                                         double* sb) {
+                                         double* sb, const Chunk& ch) {
   const int f = F.sup_first[s];
   const int w = F.sup_first[s + 1] - f;
   const int64_t rp = F.sup_rowptr[s];
@@ -70,63 +118,75 @@ __device__ __forceinline__ void fwd_task(const DevFactor& F, int s, int i0, int 
   // L_ss^{-1} is lower triangular: rows below i0 + 32 of the diagonal block
   // have no entries right of column i0 + 32, so the block stops there
   const int jend = min(w, i0 + kRowBlock);
-  for (int e = threadIdx.x; e < jend * KB; e += blockDim.x) {
+  int ja, jb;
+  chunk_range(ch, 0, jend, ja, jb);
+  for (int e = threadIdx.x; e < (jb - ja) * KB; e += blockDim.x) {
     const int j = e / KB, q = e - j * KB;
-    sb[e] = __ldcg(Y + (int64_t)(f + j) * ldy + c0 + q);
+    sb[e] = __ldcg(Y + (int64_t)(f + ja + j) * ldy + c0 + q);
   }
   __syncthreads();
   const double* __restrict__ P = F.pan_cm + F.pan_off[s];
   const int sub = threadIdx.x % kSplit;
   const int i = i0 + threadIdx.x / kSplit;
   // the same bound per warp (its 8 rows), uniform across the warp
-  const int jw = min(jend, i0 + (int)(threadIdx.x / 32 + 1) * (32 / kSplit));
+  const int jw = min(jb, i0 + (int)(threadIdx.x / 32 + 1) * (32 / kSplit));
   const int32_t* __restrict__ rows = F.sup_rows + rp;
+  const int ndiag = max(0, min(kRowBlock, w - i0));  // rows of the block in the diagonal block
   if constexpr (KB >= 2 * kSplit) {
     // enough right-hand sides to share them out: thread `sub` of a row takes
     // KB / 4 of them (two or more independent FMA chains) over the whole row,
     // so no partial sums need adding
     constexpr int QS = KB / kSplit;
     const int qa = sub * QS;
-    if (i >= ld) return;
-    const double* __restrict__ Pi = P + i;
-    const double* bq = sb + qa;
+    const double* bq = sb + qa - ja * KB;
     double acc[QS];
 #pragma unroll
     for (int q = 0; q < QS; ++q) acc[q] = 0.0;
-    int j = 0;
-    for (; j + 3 < jw; j += 4) {
-      const double p0 = Pi[(int64_t)j * ld];
-      const double p1 = Pi[(int64_t)(j + 1) * ld];
-      const double p2 = Pi[(int64_t)(j + 2) * ld];
-      const double p3 = Pi[(int64_t)(j + 3) * ld];
+    if (i < ld) {
+      const double* __restrict__ Pi = P + i;
+      int j = ja;
+      for (; j + 3 < jw; j += 4) {
+        const double p0 = Pi[(int64_t)j * ld];
+        const double p1 = Pi[(int64_t)(j + 1) * ld];
+        const double p2 = Pi[(int64_t)(j + 2) * ld];
+        const double p3 = Pi[(int64_t)(j + 3) * ld];
 #pragma unroll
-      for (int q = 0; q < QS; ++q) {
-        double a = fma(p0, bq[j * KB + q], acc[q]);
-        a = fma(p1, bq[(j + 1) * KB + q], a);
-        a = fma(p2, bq[(j + 2) * KB + q], a);
-        acc[q] = fma(p3, bq[(j + 3) * KB + q], a);
+        for (int q = 0; q < QS; ++q) {
+          double a = fma(p0, bq[j * KB + q], acc[q]);
+          a = fma(p1, bq[(j + 1) * KB + q], a);
+          a = fma(p2, bq[(j + 2) * KB + q], a);
+          acc[q] = fma(p3, bq[(j + 3) * KB + q], a);
+        }
+      }
+      for (; j < jw; ++j) {
+        const double p = Pi[(int64_t)j * ld];
+#pragma unroll
+        for (int q = 0; q < QS; ++q) acc[q] = fma(p, bq[j * KB + q], acc[q]);
+      }
+      if (i >= w) {
+        double* __restrict__ dst = Y + (int64_t)rows[i] * ldy + c0 + qa;
+#pragma unroll
+        for (int q = 0; q < QS; ++q) atomicAdd(dst + q, -acc[q]);
+      } else if (ch.n == 1) {
+        double* __restrict__ dst = Y2 + (int64_t)(f + i) * ldy + c0 + qa;
+#pragma unroll
+        for (int q = 0; q < QS; ++q) dst[q] = acc[q];
+      } else {
+#pragma unroll
+        for (int q = 0; q < QS; ++q) *chunk_part(ch, KB, i - i0, qa + q) = acc[q];
       }
     }
-    for (; j < jw; ++j) {
-      const double p = Pi[(int64_t)j * ld];
-#pragma unroll
-      for (int q = 0; q < QS; ++q) acc[q] = fma(p, bq[j * KB + q], acc[q]);
-    }
-    if (i < w) {
-      double* __restrict__ dst = Y2 + (int64_t)(f + i) * ldy + c0 + qa;
-#pragma unroll
-      for (int q = 0; q < QS; ++q) dst[q] = acc[q];
-    } else {
-      double* __restrict__ dst = Y + (int64_t)rows[i] * ldy + c0 + qa;
-#pragma unroll
-      for (int q = 0; q < QS; ++q) atomicAdd(dst + q, -acc[q]);
-    }
+    if (ch.n > 1 && ndiag > 0)
+      chunk_finish<KB>(ch, ndiag, [&](int r, int q, double v) {
+        Y2[(int64_t)(f + i0 + r) * ldy + c0 + q] = v;
+      });
   } else {
   double acc[KB];
 #pragma unroll
   for (int q = 0; q < KB; ++q) acc[q] = 0.0;
   if (i < ld) {
-    int j = sub;
+    int j = ja + sub;
+    const double* sbj = sb - ja * KB;
     // four panel loads in flight per thread, then their FMAs
     for (; j + 3 * kSplit < jw; j += 4 * kSplit) {
       const double p0 = P[(int64_t)j * ld + i];
@@ -135,31 +195,37 @@ __device__ __forceinline__ void fwd_task(const DevFactor& F, int s, int i0, int 
       const double p3 = P[(int64_t)(j + 3 * kSplit) * ld + i];
 #pragma unroll
       for (int q = 0; q < KB; ++q) {
-        double a = fma(p0, sb[j * KB + q], acc[q]);
-        a = fma(p1, sb[(j + kSplit) * KB + q], a);
-        a = fma(p2, sb[(j + 2 * kSplit) * KB + q], a);
-        acc[q] = fma(p3, sb[(j + 3 * kSplit) * KB + q], a);
+        double a = fma(p0, sbj[j * KB + q], acc[q]);
+        a = fma(p1, sbj[(j + kSplit) * KB + q], a);
+        a = fma(p2, sbj[(j + 2 * kSplit) * KB + q], a);
+        acc[q] = fma(p3, sbj[(j + 3 * kSplit) * KB + q], a);
       }
     }
     for (; j < jw; j += kSplit) {
       const double p = P[(int64_t)j * ld + i];
 #pragma unroll
-      for (int q = 0; q < KB; ++q) acc[q] = fma(p, sb[j * KB + q], acc[q]);
+      for (int q = 0; q < KB; ++q) acc[q] = fma(p, sbj[j * KB + q], acc[q]);
     }
   }
   split_sum<KB>(acc, sb, min(kRowBlock, ld - i0), [&](int r, int q, double v) {
     const int ir = i0 + r;
-    if (ir < w) Y2[(int64_t)(f + ir) * ldy + c0 + q] = v;
-    else atomicAdd(Y + (int64_t)rows[ir] * ldy + c0 + q, -v);
+    if (ir >= w) atomicAdd(Y + (int64_t)rows[ir] * ldy + c0 + q, -v);
+    else if (ch.n == 1) Y2[(int64_t)(f + ir) * ldy + c0 + q] = v;
+    else *chunk_part(ch, KB, r, q) = v;
   });
+  if (ch.n > 1 && ndiag > 0)
+    chunk_finish<KB>(ch, ndiag, [&](int r, int q, double v) {
+      Y2[(int64_t)(f + i0 + r) * ldy + c0 + q] = v;
+    });
   }
 }
 
-// Backward task: panel columns [j0, j0+32) of P_s^T [D_s^{-1} y_s; -x_R].
+// Backward task: panel columns [j0, j0+32) of P_s^T [D_s^{-1} y_s; -x_R], over
+// the panel rows of chunk ch.
 template <int KB>
 __device__ __forceinline__ void bwd_task(const DevFactor& F, int s, int j0, int c0,
                                          double* __restrict__ Y, const double* __restrict__ Y2,
-                                         int ldy, double* ub) {
+                                         int ldy, double* ub, const Chunk& ch) {
   const int f = F.sup_first[s];
   const int w = F.sup_first[s + 1] - f;
   const int64_t rp = F.sup_rowptr[s];
@@ -167,8 +233,10 @@ __device__ __forceinline__ void bwd_task(const DevFactor& F, int s, int j0, int 
   const int32_t* __restrict__ rows = F.sup_rows + rp;
   // column j of the lower-triangular L_ss^{-1} is zero above row j, so the
   // panel rows of this block of columns start at j0
-  for (int e = j0 * KB + threadIdx.x; e < ld * KB; e += blockDim.x) {
-    const int i = e / KB, q = e - i * KB;
+  int ia, ib;
+  chunk_range(ch, j0, ld, ia, ib);
+  for (int e = threadIdx.x; e < (ib - ia) * KB; e += blockDim.x) {
+    const int i = ia + e / KB, q = e % KB;
     ub[e] = i < w ? __ldcg(Y2 + (int64_t)(f + i) * ldy + c0 + q) * F.dinv[f + i]
                   : -__ldcg(Y + (int64_t)rows[i] * ldy + c0 + q);
   }
@@ -176,34 +244,41 @@ __device__ __forceinline__ void bwd_task(const DevFactor& F, int s, int j0, int 
   const double* __restrict__ P = F.pan_rm + F.pan_off[s];
   const int sub = threadIdx.x % kSplit;
   const int j = j0 + threadIdx.x / kSplit;
+  const double* ubi = ub - ia * KB;
   double acc[KB];
 #pragma unroll
   for (int q = 0; q < KB; ++q) acc[q] = 0.0;
   if (j < w) {
     // the warp's 8 columns start at j0 + 8 * warp: rows above are zero for all of them
-    int i = j0 + (int)(threadIdx.x / 32) * (32 / kSplit) + sub;
-    for (; i + 3 * kSplit < ld; i += 4 * kSplit) {
+    int i = max(ia, j0 + (int)(threadIdx.x / 32) * (32 / kSplit)) + sub;
+    for (; i + 3 * kSplit < ib; i += 4 * kSplit) {
       const double p0 = P[(int64_t)i * w + j];
       const double p1 = P[(int64_t)(i + kSplit) * w + j];
       const double p2 = P[(int64_t)(i + 2 * kSplit) * w + j];
       const double p3 = P[(int64_t)(i + 3 * kSplit) * w + j];
 #pragma unroll
       for (int q = 0; q < KB; ++q) {
-        double a = fma(p0, ub[i * KB + q], acc[q]);
-        a = fma(p1, ub[(i + kSplit) * KB + q], a);
-        a = fma(p2, ub[(i + 2 * kSplit) * KB + q], a);
-        acc[q] = fma(p3, ub[(i + 3 * kSplit) * KB + q], a);
+        double a = fma(p0, ubi[i * KB + q], acc[q]);
+        a = fma(p1, ubi[(i + kSplit) * KB + q], a);
+        a = fma(p2, ubi[(i + 2 * kSplit) * KB + q], a);
+        acc[q] = fma(p3, ubi[(i + 3 * kSplit) * KB + q], a);
       }
     }
-    for (; i < ld; i += kSplit) {
+    for (; i < ib; i += kSplit) {
       const double p = P[(int64_t)i * w + j];
 #pragma unroll
-      for (int q = 0; q < KB; ++q) acc[q] = fma(p, ub[i * KB + q], acc[q]);
+      for (int q = 0; q < KB; ++q) acc[q] = fma(p, ubi[i * KB + q], acc[q]);
     }
   }
-  split_sum<KB>(acc, ub, min(kRowBlock, w - j0), [&](int r, int q, double v) {
-    Y[(int64_t)(f + j0 + r) * ldy + c0 + q] = v;
+  const int ncol = min(kRowBlock, w - j0);
+  split_sum<KB>(acc, ub, ncol, [&](int r, int q, double v) {
+    if (ch.n == 1) Y[(int64_t)(f + j0 + r) * ldy + c0 + q] = v;
+    else *chunk_part(ch, KB, r, q) = v;
   });
+  if (ch.n > 1)
+    chunk_finish<KB>(ch, ncol, [&](int r, int q, double v) {
+      Y[(int64_t)(f + j0 + r) * ldy + c0 + q] = v;
+    });
 }
 
 // Descriptors of the supernodes of a packed task, staged in shared memory by
@@ -404,42 +479,65 @@ __device__ __forceinline__ void bwd_small_rows(const DevFactor& F, int e0, int n
 
 template <int KB>
 __device__ __forceinline__ void run_fwd(const DevFactor& F, int2 tk, int c0, double* Y, double* Y2,
-                                        int ldy, double* sm, PackDesc& pd) {
+                                        int ldy, double* sm, PackDesc& pd,
+                                        const Chunk& ch = Chunk()) {
   const int ne = tk.y & (kPackRowwise - 1);
-  if (tk.x >= 0) fwd_task<KB>(F, tk.x, tk.y, c0, Y, Y2, ldy, sm);
+  if (tk.x >= 0) fwd_task<KB>(F, tk.x, tk.y, c0, Y, Y2, ldy, sm, ch);
+  else if (ch.c > 0) return;  // packed tasks are not chunked: the first chunk's CTA runs them
   else if (tk.y & kPackRowwise) fwd_small_rows<KB>(F, -1 - tk.x, ne, c0, Y, Y2, ldy, sm, pd);
   else fwd_small<KB>(F, -1 - tk.x, ne, c0, Y, Y2, ldy, sm, pd);
 }
 
 template <int KB>
 __device__ __forceinline__ void run_bwd(const DevFactor& F, int2 tk, int c0, double* Y,
-                                        const double* Y2, int ldy, double* sm, PackDesc& pd) {
+                                        const double* Y2, int ldy, double* sm, PackDesc& pd,
+                                        const Chunk& ch = Chunk()) {
   const int ne = tk.y & (kPackRowwise - 1);
-  if (tk.x >= 0) bwd_task<KB>(F, tk.x, tk.y, c0, Y, Y2, ldy, sm);
+  if (tk.x >= 0) bwd_task<KB>(F, tk.x, tk.y, c0, Y, Y2, ldy, sm, ch);
+  else if (ch.c > 0) return;
   else if (tk.y & kPackRowwise) bwd_small_rows<KB>(F, -1 - tk.x, ne, c0, Y, Y2, ldy, sm, pd);
   else bwd_small<KB>(F, -1 - tk.x, ne, c0, Y, Y2, ldy, sm, pd);
 }
 
-template <int KB>
-__global__ void __launch_bounds__(kSolveThreads)
-fwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* __restrict__ Y,
-                 double* __restrict__ Y2, int ldy) {
-  extern __shared__ double sb[];
-  __shared__ PackDesc pd;
-  if (F.abort && *F.abort) return;
-  const int2 tk = tasks[blockIdx.x / ncb];
-  run_fwd<KB>(F, tk, (blockIdx.x % ncb) * KB, Y, Y2, ldy, sb, pd);
+// One CTA per (task, column block, chunk), chunks innermost: blockIdx.x =
+// (task * ncb + column block) * nchunk + chunk; the (task, column block) pair
+// is the chunks' scratch slot.
+__device__ __forceinline__ Chunk level_chunk(int ncb, int nchunk, const SplitScratch& sp,
+                                             int& task, int& cb) {
+  const int slot = blockIdx.x / nchunk;
+  task = slot / ncb;
+  cb = slot - task * ncb;
+  Chunk ch;
+  ch.c = blockIdx.x - slot * nchunk;
+  ch.n = nchunk;
+  ch.part = sp.part;
+  ch.cnt = sp.cnt;
+  ch.slot = slot;
+  return ch;
 }
 
 template <int KB>
 __global__ void __launch_bounds__(kSolveThreads)
-bwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, double* __restrict__ Y,
-                 const double* __restrict__ Y2, int ldy) {
+fwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, int nchunk,
+                 SplitScratch sp, double* __restrict__ Y, double* __restrict__ Y2, int ldy) {
+  extern __shared__ double sb[];
+  __shared__ PackDesc pd;
+  if (F.abort && *F.abort) return;
+  int task, cb;
+  const Chunk ch = level_chunk(ncb, nchunk, sp, task, cb);
+  run_fwd<KB>(F, tasks[task], cb * KB, Y, Y2, ldy, sb, pd, ch);
+}
+
+template <int KB>
+__global__ void __launch_bounds__(kSolveThreads)
+bwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, int nchunk,
+                 SplitScratch sp, double* __restrict__ Y, const double* __restrict__ Y2, int ldy) {
   extern __shared__ double ub[];
   __shared__ PackDesc pd;
   if (F.abort && *F.abort) return;
-  const int2 tk = tasks[blockIdx.x / ncb];
-  run_bwd<KB>(F, tk, (blockIdx.x % ncb) * KB, Y, Y2, ldy, ub, pd);
+  int task, cb;
+  const Chunk ch = level_chunk(ncb, nchunk, sp, task, cb);
+  run_bwd<KB>(F, tasks[task], cb * KB, Y, Y2, ldy, ub, pd, ch);
 }
 
 // ---------------------------------------------------------------------------
@@ -584,29 +682,43 @@ persistent_solve_kernel(DevFactor F, PersistSched ps, double* __restrict__ Y,
 
 template <int KB>
 void launch_level(bool fwd, const DevFactor& F, const LevelPlan& L, double* Y, double* Y2, int ldy,
-                  int ncols, cudaStream_t st) {
+                  int ncols, cudaStream_t st, const SplitScratch* split) {
   const int ncb = (ncols + KB - 1) / KB;
   const size_t part = (size_t)kSolveThreads * (KB + 1);  // split_sum's partials
+  // Chunks: when the level's (task, column block) pairs leave most of the GPU
+  // idle and its split tasks have long reductions, each such task runs as
+  // several CTAs over slices of its reduction (at least kSplitMinWidth long).
+  const int tasks = fwd ? L.nf : L.nb;
+  const int extent = fwd ? L.split_w : L.split_ld;
+  int nchunk = 1;
+  SplitScratch sp;
+  if (split && split->part && extent >= 2 * kSplitMinWidth && (long long)tasks * ncb < kSplitSlots) {
+    const int want = (kSplitTarget + tasks * ncb - 1) / (tasks * ncb);
+    nchunk = std::max(1, std::min({want, extent / kSplitMinWidth, kSplitMaxChunks}));
+    // scratch holds 2 * kSplitSlots (slot, chunk) pairs
+    while (nchunk > 1 && (long long)tasks * ncb * nchunk > 2LL * kSplitSlots) --nchunk;
+    if (nchunk > 1) sp = *split;
+  }
+  const unsigned grid = (unsigned)((long long)tasks * ncb * nchunk);
+  if (grid == 0) return;
   if (fwd) {
     const size_t smem = std::max((size_t)L.max_w * KB, part) * sizeof(double);
-    fwd_level_kernel<KB><<<(unsigned)(L.nf * ncb), kSolveThreads, smem, st>>>(F, L.ftasks, ncb, Y, Y2,
-                                                                             ldy);
+    fwd_level_kernel<KB><<<grid, kSolveThreads, smem, st>>>(F, L.ftasks, ncb, nchunk, sp, Y, Y2, ldy);
   } else {
     const size_t smem = std::max((size_t)L.max_wr * KB, part) * sizeof(double);
-    bwd_level_kernel<KB><<<(unsigned)(L.nb * ncb), kSolveThreads, smem, st>>>(F, L.btasks, ncb, Y, Y2,
-                                                                             ldy);
+    bwd_level_kernel<KB><<<grid, kSolveThreads, smem, st>>>(F, L.btasks, ncb, nchunk, sp, Y, Y2, ldy);
   }
 }
 
 void run_level(bool fwd, const DevFactor& F, const LevelPlan& L, double* Y, double* Y2, int ldy,
-               int ncols, cudaStream_t st) {
+               int ncols, cudaStream_t st, const SplitScratch* split) {
   int kb = L.kb;
   while (kb > 1 && kb / 2 >= ncols) kb /= 2;
   switch (kb) {
-    case 1: launch_level<1>(fwd, F, L, Y, Y2, ldy, ncols, st); break;
-    case 2: launch_level<2>(fwd, F, L, Y, Y2, ldy, ncols, st); break;
-    case 4: launch_level<4>(fwd, F, L, Y, Y2, ldy, ncols, st); break;
-    default: launch_level<8>(fwd, F, L, Y, Y2, ldy, ncols, st); break;
+    case 1: launch_level<1>(fwd, F, L, Y, Y2, ldy, ncols, st, split); break;
+    case 2: launch_level<2>(fwd, F, L, Y, Y2, ldy, ncols, st, split); break;
+    case 4: launch_level<4>(fwd, F, L, Y, Y2, ldy, ncols, st, split); break;
+    default: launch_level<8>(fwd, F, L, Y, Y2, ldy, ncols, st, split); break;
   }
 }
 
@@ -732,10 +844,10 @@ void set_solve_smem_limit(int bytes) {
 }
 
 int solve_inplace(const DevFactor& F, const LevelPlan* levels, int nlev, double* Y, double* Y2,
-                  int ldy, int ncols, cudaStream_t st) {
+                  int ldy, int ncols, cudaStream_t st, const SplitScratch* split) {
   if (ncols <= 0) return 0;
-  for (int l = 0; l < nlev; ++l) run_level(true, F, levels[l], Y, Y2, ldy, ncols, st);
-  for (int l = nlev - 1; l >= 0; --l) run_level(false, F, levels[l], Y, Y2, ldy, ncols, st);
+  for (int l = 0; l < nlev; ++l) run_level(true, F, levels[l], Y, Y2, ldy, ncols, st, split);
+  for (int l = nlev - 1; l >= 0; --l) run_level(false, F, levels[l], Y, Y2, ldy, ncols, st, split);
   return 2 * nlev;
 }
 

@@ -50,7 +50,28 @@ struct LevelPlan {
   int32_t max_w;         // widest supernode in the level
   int32_t max_wr;        // largest w + r in the level
   int32_t kb;            // column block: 1, 2, 4 or 8
+  int32_t split_w;       // widest supernode with split (non-packed) tasks, 0 if none: the
+                         // longest reduction of a forward task
+  int32_t split_ld;      // largest w + r of those: the longest reduction of a backward task
 };
+
+// Scratch of the chunked reduction.  A split task whose level would leave
+// the GPU mostly idle (few tasks x column blocks) runs as `nchunk` CTAs, each
+// over one slice of the task's reduction (panel columns forward, panel rows
+// backward).  Their partial sums of the rows that need a complete sum (the
+// diagonal block forward, every output backward) go to `part`; the CTA that
+// arrives last, counted in `cnt` (zero between launches: that CTA resets
+// it), adds them in chunk order and writes the result.  No CTA waits on
+// another.  Rows below the diagonal block take each chunk's partial by an
+// atomic subtraction, like the unchunked forward.
+struct SplitScratch {
+  double* part = nullptr;  // [kSplitSlots * 2][kRowBlock][kMaxColBlock]
+  int* cnt = nullptr;      // [kSplitSlots]
+};
+constexpr int kSplitTarget = 4 * 152;  // CTAs a level launch should reach (4 per SM)
+constexpr int kSplitSlots = kSplitTarget;
+constexpr int kSplitMaxChunks = 32;
+constexpr int kSplitMinWidth = 32;     // columns (rows) of one chunk at least
 void set_solve_smem_limit(int bytes);
 
 // Persistent (one launch per solve) schedule for a given column count.
@@ -94,7 +115,7 @@ void bump_counter(int* p, cudaStream_t st);
 // using Y2 (same shape) for the intermediate forward result.
 // Returns the number of kernels launched.
 int solve_inplace(const DevFactor& F, const LevelPlan* levels, int nlev, double* Y, double* Y2,
-                  int ldy, int ncols, cudaStream_t st);
+                  int ldy, int ncols, cudaStream_t st, const SplitScratch* split = nullptr);
 
 // Y[i][q] = (scale ? scale[i] : 1) * src[cols[q]*stride + rowmap[i]]
 // (cols == null: q; rowmap == null: i)
@@ -243,6 +264,10 @@ void recombine(double* Xp, int64_t n, int n_times, const double* Vbase, int64_t 
 void next_state(double* X, const double* Vbase, int64_t vstride, const double* Z, const double* Zp,
                 const double* W, int64_t gstride, const RoundCols& rc, const int32_t* mcol,
                 const double* yend, int K, int64_t n, cudaStream_t st);
+// Adjoint checkpoints: CK[q] = {X[groups[q]], Z[groups[q]]} ([K][2][n]), or the
+// reverse copy when restore is set (X, Z per group, [G][n]).
+void checkpoint_states(double* CK, double* X, double* Z, const int32_t* groups, int K, int64_t n,
+                       bool restore, cudaStream_t st);
 // Xp[o][i] = base[i] for all o
 void fill_rows(double* Xp, const double* base, int64_t n, int n_times, cudaStream_t st);
 // Xp[0][i] += sum_q Y[i][q]

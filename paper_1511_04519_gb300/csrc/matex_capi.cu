@@ -77,6 +77,7 @@ struct matex_ctx {
   // structure
   Symbolic S;
   std::vector<LevelPlan> levels;
+  SplitScratch split;              // chunked reductions of the level launches
   // persistent solve: per column count (1..ldy) one PersistLevel row per level
   PersistLevel* plev_d = nullptr;
   std::vector<long long> pf_total, pb_total;   // per column count
@@ -100,6 +101,14 @@ struct matex_ctx {
   double *YBO = nullptr, *YOUT = nullptr, *YBL = nullptr, *YL = nullptr, *HTB = nullptr;
   double *BETAB = nullptr, *D1 = nullptr, *HD = nullptr, *D0 = nullptr, *S1 = nullptr, *S2 = nullptr;
   int32_t *iota_d = nullptr, *mrec_d = nullptr, *act_d = nullptr;
+  // checkpointed adjoint (opts.tape = 2): windows of tape_W rounds, recompute
+  // blocks of tape_Kb groups; CK holds {x, z} of every column of each
+  // window's first round, window w's from slot ck_base[w]
+  int tape_W = 0, tape_Kb = 0;
+  int64_t tape_bytes = 0;
+  std::vector<int64_t> ck_base;
+  double* CK = nullptr;
+  std::vector<int32_t> h_group_all;
   std::vector<Round> rounds;          // batched: segment r of every group per round
   std::vector<Round> serial_rounds;   // one group at a time: one column per round
   bool serial = false;
@@ -348,10 +357,12 @@ bool plan_levels(matex_ctx* c) {
     const int cblocks = std::max(1, c->ldy / 8);
     const int fmode = (prow / kPackRows) * cblocks >= kPackTarget ? 0 : kPackRowwise;
     const int bmode = (pcol / kPackRows) * cblocks >= kPackTarget ? 0 : kPackRowwise;
+    L.split_w = L.split_ld = 0;
     for (const int s : by_w) {
       const int w = sup_w(s);
       const int wr = sup_ld(s);
       mw = std::max(mw, w);
+      if (!(w <= 16 && wr <= 64)) L.split_ld = std::max(L.split_ld, wr);
       if (wr <= kPackRows && w <= 16) {
         if (rows + wr > kPackRows || (int)cur.size() == kPackMax) { flush(cur, ft, fmode); rows = 0; }
         cur.push_back(s);
@@ -359,6 +370,7 @@ bool plan_levels(matex_ctx* c) {
         fpacked[s] = 1;
       } else {
         mwr = std::max(mwr, wr);
+        L.split_w = std::max(L.split_w, w);
         for (int i0 = 0; i0 < wr; i0 += kRowBlock) ft.push_back(make_int2(s, i0));
       }
     }
@@ -474,6 +486,10 @@ bool plan_levels(matex_ctx* c) {
     c->pb_total[nc] = bb;
   }
   if (!c->upload(c->plev_d, pl.data(), pl.size())) return false;
+  if (!c->alloc(c->split.part, (size_t)2 * kSplitSlots * kRowBlock * kMaxColBlock) ||
+      !c->alloc(c->split.cnt, (size_t)kSplitSlots) ||
+      cudaMemset(c->split.cnt, 0, sizeof(int) * kSplitSlots) != cudaSuccess)
+    return false;
   std::vector<int32_t> lev(S.nsup), nft(S.nsup), nbt(S.nsup), kids(S.nsup, 0);
   for (int l = 0; l < nlev; ++l)
     for (int k = S.level_ptr[l]; k < S.level_ptr[l + 1]; ++k) lev[S.level_sups[k]] = l;
@@ -504,7 +520,7 @@ int solve_cols(matex_ctx* c, const DevFactor& F, int ncols) {
   if (mode == 2) mode = c->mode_by_ncols.empty() ? 0 : c->mode_by_ncols[std::min(ncols, c->ldy)];
   if (mode == 1)
     return solve_inplace(F, c->levels.data(), (int)c->levels.size(), c->Y, c->Y2, c->ldy, ncols,
-                         c->st);
+                         c->st, &c->split);
   const int nlev = (int)c->levels.size();
   const int32_t nsup = c->S.nsup;
   PersistSched ps;
@@ -620,6 +636,55 @@ double solve_bytes(const matex_ctx* c, int K) {
 }
 
 enum { P_SOLVE = 0, P_MOVE = 1, P_GS = 2, P_SMALL = 3, P_RECOMB = 4, P_OTHER = 5 };
+
+// Sizes of the checkpointed adjoint.  Every segment is recomputed once
+// whatever the window, so the window only trades checkpoint memory (fewer
+// windows, fewer checkpoints) against window-tape memory (W x Kb segments'
+// bases, solve outputs and z'); the block Kb sets how many columns the
+// recompute and reverse launches carry.  Chosen: the widest block for which
+// some window fits the budget, with the window that needs the least memory.
+struct TapePlan {
+  int W = 0, Kb = 0;
+  double bytes = 0.0;
+};
+TapePlan plan_tape(const std::vector<Round>& rounds, int64_t n, int G, int Kmax, int n_times,
+                   int nrows, double budget, int W_fix, int Kb_fix) {
+  const double nd = (double)n;
+  auto ck = [&](int W) {
+    double s = 0.0;
+    for (size_t r = 0; r < rounds.size(); r += (size_t)W) s += rounds[r].K;
+    return s * 2.0 * nd * 8.0;
+  };
+  auto tape = [&](int W, int Kb) {
+    const double slots = (double)W * Kb;
+    return slots * (kMaxM + 1) * nd * 8.0 + std::max(0.0, slots - G) * kMaxB * nd * 8.0 +
+           (double)Kb * kWSlots * nd * 8.0 + 2.0 * Kb * n_times * kCoefLd * 8.0 +
+           2.0 * Kb * std::max(nrows, 1) * 8.0;
+  };
+  const int nr = std::max<int>(1, (int)rounds.size());
+  std::vector<int> kbs, ws;
+  if (Kb_fix > 0) kbs.push_back(std::min(Kb_fix, std::max(Kmax, 1)));
+  else
+    for (int k = std::max(Kmax, 1); k >= 1; k = k > 1 ? (k + 1) / 2 : 0) {
+      kbs.push_back(k);
+      if (k == 1) break;
+    }
+  if (W_fix > 0) ws.push_back(std::min(W_fix, nr));
+  else
+    for (int w = 1;; w *= 2) {
+      ws.push_back(std::min(w, nr));
+      if (w >= nr) break;
+    }
+  for (int kb : kbs) {
+    TapePlan best;
+    for (int w : ws) {
+      const double b = ck(w) + tape(w, kb);
+      if (b <= budget && (best.W == 0 || b < best.bytes)) best = TapePlan{w, kb, b};
+    }
+    if (best.W) return best;
+  }
+  return TapePlan{};
+}
 
 // Autotuner: for column counts 1, 2, 4, ..., ldy, time the batched solve with
 // one persistent launch and with one launch per tree level (CUDA events, best
@@ -845,13 +910,19 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
     // z' = G^{-1} B s_j and w = G^{-1} C z'   (Eq. 5/6)
     e = prof_begin(c);
     advance_z(c->Zb, c->Zpb, c->Xb, n, rc, K, n, st);
+    if (c->opts.tape == 2 && !c->serial && ri % (size_t)c->tape_W == 0) {
+      // adjoint checkpoint: x and z of every column at the start of the window
+      checkpoint_states(c->CK + c->ck_base[ri / c->tape_W] * 2 * n, c->Xb, c->Zb, rc.group, K, n,
+                        false, st);
+      launches++;
+    }
     build_input_rhs(c->Y, c->ldy, K, rc, c->src, n, st);
     prof_end(c, e, P_OTHER, 3, 2.0 * nd * K, 24.0 * nd * K + 8.0 * nd * c->ldy);
     launches += 3;
     solve(c->fG, K);
     e = prof_begin(c);
     scatter_cols(c->Y, c->ldy, K, c->Zpb, n, rc.group, nullptr, n, st);
-    if (c->opts.tape) scatter_cols(c->Y, c->ldy, K, c->TZp, n, rc.vslot, nullptr, n, st);
+    if (c->opts.tape == 1) scatter_cols(c->Y, c->ldy, K, c->TZp, n, rc.vslot, nullptr, n, st);
     gather_cols(c->Y, c->ldy, K, c->Zpb, n, rc.group, c->c_perm, nullptr, n, st);
     moved(e, 2, K, true);
     solve(c->fG, K);
@@ -898,7 +969,7 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
         e = prof_begin(c);
         scatter_cols(c->Y, c->ldy, kit, c->Vb + (int64_t)(j + 1) * n, vstride, c->iter_grp, nullptr,
                      n, st);
-        if (c->opts.tape)  // keep a_k = (C + gamma G)^{-1} C q_k for the adjoint
+        if (c->opts.tape == 1)  // keep a_k = (C + gamma G)^{-1} C q_k for the adjoint
           scatter_cols(c->Y, c->ldy, kit, c->TA + (int64_t)j * n, (int64_t)kMaxM * n, c->iter_grp,
                        nullptr, n, st);
         moved(e, 1, kit, false);
@@ -925,7 +996,7 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
       std::swap(iter, iter_next);
       if ((s = count(&kit, iter, rc.vslot)) != MATEX_OK) return s;
     }
-    if (c->opts.tape) tape_small(c->ss, rc, K, c->THt, c->Tbeta, st);
+    if (c->opts.tape == 1) tape_small(c->ss, rc, K, c->THt, c->Tbeta, st);
     e = prof_begin(c);
     const double teps = c->opts.tail_eps;
     if (teps > 0.0) {
@@ -1079,14 +1150,194 @@ matex_status run_device(matex_ctx* c, double* x_out, matex_stats* stats) {
   return finish_run(c, pc, t0, false, stats);
 }
 
+// Reverse of the columns [qa, qa + K) of round r, given their tape entries
+// (slots rec, device) and the run's Krylov dimension per column record
+// (mrec, host; c->mrec_d on the device).  The groups' carried adjoints (xbar
+// into the previous segment, zbar, dL/dc) are per group, so any subset of a
+// round's columns can be reversed on its own once the later rounds of the
+// same groups are.
+matex_status reverse_round(matex_ctx* c, const Round& r, int qa, int K, const int32_t* rec,
+                           const std::vector<int32_t>& mrec, const double* xbar, double* damp,
+                           const SourceTable& base) {
+  if (K <= 0) return MATEX_OK;
+  cudaStream_t st = c->st;
+  const int64_t n = c->n;
+  const int nrows = c->nrows_out;
+  const int64_t vstride = (int64_t)kMaxB * n;
+  const int b0 = r.begin + qa;
+  AdjWork aw{c->AW, (int64_t)kWSlots * n, c->XBg, c->CARRYg, c->CBg};
+  AdjRound ar;
+  ar.rec = rec;
+  ar.group = c->rc_group + b0;
+  ar.m = c->mrec_d + b0;
+  ar.obeg = c->rc_obeg + b0;
+  ar.nout = c->rc_nout + b0;
+  ar.seg = c->rc_seg + b0;
+  ar.l0 = c->rc_l0 + b0;
+  ar.len = c->rc_len + b0;
+  ar.hfirst = c->rc_hfirst + b0;
+  ar.V = c->Vb;
+  ar.vstride = vstride;
+  ar.A = c->TA;
+  ar.astride = (int64_t)kMaxM * n;
+  ar.Zp = c->TZp;
+  ar.Ht = c->THt;
+  ar.beta = c->Tbeta;
+  ar.n = n;
+  ar.dt = c->dt_out;
+  int mmax = 0;
+  for (int q = 0; q < K; ++q) mmax = std::max(mmax, mrec[b0 + q]);
+  // active column lists for k = 0..mmax-1, uploaded once
+  std::vector<int32_t> act;
+  std::vector<int> aoff(mmax + 1, 0);
+  for (int k = 0; k < mmax; ++k) {
+    aoff[k] = (int)act.size();
+    for (int q = 0; q < K; ++q)
+      if (mrec[b0 + q] > k) act.push_back(q);
+  }
+  aoff[mmax] = (int)act.size();
+  if (!act.empty())
+    cudaMemcpyAsync(c->act_d, act.data(), sizeof(int32_t) * act.size(), cudaMemcpyHostToDevice, st);
+  // output adjoints and the small dense reverse
+  if (mmax > 0) {
+    AdjDots d{c->XBg, n, ar.group, 0, c->Vb, vstride, ar.rec, 0, nullptr};
+    adj_dots(d, K, mmax, n, c->partials, c->nchunks, c->YBL, st);
+  }
+  adj_obs(ar, K, xbar, c->out_map, nrows, c->YBO, c->n_times, c->S1, c->S2, st);
+  adj_small(ar, K, c->gamma, c->YBO, c->n_times, c->YBL, c->YOUT, c->YL, c->HTB, c->BETAB, st);
+  adj_build(ar, aw, K, c->YL, xbar, c->out_map, nrows, c->YOUT, c->n_times, c->S1, c->S2, st);
+  // reverse Arnoldi steps
+  for (int k = mmax - 1; k >= 0; --k) {
+    const int Ka = aoff[k + 1] - aoff[k];
+    const int32_t* ak = c->act_d + aoff[k];
+    AdjDots d1{c->AW, (int64_t)kWSlots * n, c->iota_d, k + 1, c->Vb, vstride, ar.rec, k + 1, ak};
+    adj_dots(d1, Ka, 1, n, c->partials, c->nchunks, c->D1, st);
+    adj_rbar(ar, aw, ak, Ka, k, c->D1, c->HTB, st);
+    AdjDots dh{c->AW, (int64_t)kWSlots * n, c->iota_d, kWR, c->Vb, vstride, ar.rec, 0, ak};
+    adj_dots(dh, Ka, k + 1, n, c->partials, c->nchunks, c->HD, st);
+    adj_abar(ar, aw, ak, Ka, k, c->HD, c->HTB, st);
+    gather_cols(c->Y, c->ldy, Ka, c->AW + (int64_t)kWA * n, (int64_t)kWSlots * n, ak, nullptr,
+                nullptr, n, st);
+    solve_cols(c, c->fM, Ka);
+    adj_after_m(ar, aw, ak, Ka, k, c->Y, c->ldy, c->c_perm, st);
+  }
+  {
+    AdjDots d0{c->AW, (int64_t)kWSlots * n, c->iota_d, 0, c->Vb, vstride, ar.rec, 0, nullptr};
+    if (mmax > 0) adj_dots(d0, K, 1, n, c->partials, c->nchunks, c->D0, st);
+  }
+  adj_vbar(ar, aw, K, c->D0, c->BETAB, st);
+  // w = G^{-1}(c z'), then z' = G^{-1} B s
+  gather_cols(c->Y, c->ldy, K, c->AW + (int64_t)kWW * n, (int64_t)kWSlots * n, nullptr, nullptr,
+              nullptr, n, st);
+  solve_cols(c, c->fG, K);
+  adj_after_w(ar, aw, K, c->Y, c->ldy, c->c_perm, st);
+  gather_cols(c->Y, c->ldy, K, c->AW + (int64_t)kWZp * n, (int64_t)kWSlots * n, nullptr, nullptr,
+              nullptr, n, st);
+  solve_cols(c, c->fG, K);
+  adj_sources(ar, K, base, c->Y, c->ldy, damp, st);
+  return cuda_check(c, "grad round");
+}
+
+// Forward of rounds [r0, r1) for the columns [qa[i], qb[i]) of round r0 + i
+// (the block's groups) from the checkpoint of window w, keeping each
+// segment's basis, solve outputs, z', Hessenberg and norm in window-tape slot
+// i * Kb + (column - qa[i]).  The Krylov dimensions are the run's (replay of
+// m_rec); the active-column counts are known on the host, and guard kernels
+// check them on the device as in a graph replay (a mismatch raises the
+// divergence flag and keeps every index in range).
+matex_status recompute_window(matex_ctx* c, int w, int r0, int r1, const std::vector<int>& qa,
+                              const std::vector<int>& qb, int g0, int g1,
+                              const std::vector<int32_t>& mrec) {
+  cudaStream_t st = c->st;
+  const int64_t n = c->n;
+  const int64_t vstride = (int64_t)kMaxB * n;
+  const int Kb = c->tape_Kb;
+  const size_t gbytes = sizeof(double) * (size_t)(g1 - g0) * (size_t)n;
+  // the block's groups that have not started by the window start from zero
+  cudaMemsetAsync(c->Xb + (int64_t)g0 * n, 0, gbytes, st);
+  cudaMemsetAsync(c->Zb + (int64_t)g0 * n, 0, gbytes, st);
+  cudaMemsetAsync(c->Zpb + (int64_t)g0 * n, 0, gbytes, st);
+  {
+    const Round& R0 = c->rounds[r0];
+    checkpoint_states(c->CK + (c->ck_base[w] + qa[0]) * 2 * n, c->Xb, c->Zb,
+                      c->rc_group + R0.begin + qa[0], qb[0] - qa[0], n, true, st);
+  }
+  for (int r = r0; r < r1; ++r) {
+    const int i = r - r0;
+    const int K = qb[i] - qa[i];
+    if (K <= 0) continue;
+    const Round& R = c->rounds[r];
+    Round sub = R;
+    sub.begin = R.begin + qa[i];
+    sub.K = K;
+    RoundCols rc = round_cols(c, sub);
+    rc.vslot = c->iota_d + (int64_t)i * Kb;
+    const int b0 = sub.begin;
+    if (r != r0) advance_z(c->Zb, c->Zpb, c->Xb, n, rc, K, n, st);
+    build_input_rhs(c->Y, c->ldy, K, rc, c->src, n, st);
+    solve_cols(c, c->fG, K);
+    scatter_cols(c->Y, c->ldy, K, c->Zpb, n, rc.group, nullptr, n, st);
+    scatter_cols(c->Y, c->ldy, K, c->TZp, n, rc.vslot, nullptr, n, st);
+    gather_cols(c->Y, c->ldy, K, c->Zpb, n, rc.group, c->c_perm, nullptr, n, st);
+    solve_cols(c, c->fG, K);
+    scatter_cols(c->Y, c->ldy, K, c->Wb, n, rc.group, nullptr, n, st);
+    krylov_start(c->Vb, vstride, c->Xb, c->Zb, c->Wb, n, rc.group, rc.vslot, K, n, c->partials,
+                 c->nchunks, st);
+    start_finish(c->partials, c->nchunks, K, c->ss, rc.vslot, c->iterA, c->iter_grp, c->d_count,
+                 st);
+    int32_t* iter = c->iterA;
+    int32_t* iter_next = c->iterB;
+    auto active = [&](int above) {
+      int k = 0;
+      for (int q = 0; q < K; ++q) k += mrec[b0 + q] > above ? 1 : 0;
+      return k;
+    };
+    int kit = active(0);
+    expect_count(c->d_count, kit, iter, c->iter_grp, rc.vslot, c->d_count + 2, st);
+    if (kit > 0) basis_scale(c->Vb, vstride, rc.vslot, iter, kit, 0, c->ss.scale, n, st);
+    for (int j = 0; j < c->m_max && kit > 0; ++j) {
+      gather_cols(c->Y, c->ldy, kit, c->Vb + (int64_t)j * n, vstride, c->iter_grp, c->c_perm,
+                  nullptr, n, st);
+      solve_cols(c, c->fM, kit);
+      scatter_cols(c->Y, c->ldy, kit, c->Vb + (int64_t)(j + 1) * n, vstride, c->iter_grp, nullptr,
+                   n, st);
+      scatter_cols(c->Y, c->ldy, kit, c->TA + (int64_t)j * n, (int64_t)kMaxM * n, c->iter_grp,
+                   nullptr, n, st);
+      for (int pass = 0; pass < 2; ++pass) {
+        basis_dots(c->Vb, vstride, rc.vslot, iter, kit, 0, j + 1, j + 1, n, c->partials,
+                   c->nchunks, st);
+        reduce_dots(c->partials, c->nchunks, kit, j + 1, iter, c->ss, j, pass, st);
+        basis_update(c->Vb, vstride, rc.vslot, iter, kit, j + 1, j + 1, c->ss.hbuf, n, st);
+      }
+      basis_dots(c->Vb, vstride, rc.vslot, iter, kit, j + 1, 1, j + 1, n, c->partials, c->nchunks,
+                 st);
+      reduce_dots(c->partials, c->nchunks, kit, 1, iter, c->ss, j, 2, st);
+      basis_scale(c->Vb, vstride, rc.vslot, iter, kit, j + 1, c->ss.scale, n, st);
+      residual_check(c->ss, rc, kit, j, c->gamma, c->tol, c->m_max, c->m_rec, iter, iter_next,
+                     c->iter_grp, c->d_count, st);
+      std::swap(iter, iter_next);
+      kit = active(j + 1);
+      expect_count(c->d_count, kit, iter, c->iter_grp, rc.vslot, c->d_count + 2, st);
+    }
+    tape_small(c->ss, rc, K, c->THt, c->Tbeta, st);
+    output_coefficients(c->ss, rc, K, c->gamma, c->dt_out, c->coef, c->n_times, c->yend, st);
+    next_state(c->Xb, c->Vb, vstride, c->Zb, c->Zpb, c->Wb, n, rc, c->ss.m, c->yend, K, n, st);
+    matex_status s = cuda_check(c, "grad recompute");
+    if (s != MATEX_OK) return s;
+  }
+  return MATEX_OK;
+}
+
 // Reverse sweep over the forward's rounds (latest first); per round the
-// columns (groups) are handled together, like the forward.
+// columns (groups) are handled together, like the forward.  tape = 1 reads
+// the run's full tape; tape = 2 goes window by window (latest first) and
+// block by block, recomputing each block's segments of the window from the
+// window's checkpoint before reversing them.
 matex_status run_grad(matex_ctx* c, const double* xbar, double* dc, double* damp) {
   cudaStream_t st = c->st;
   const int64_t n = c->n;
   const int G = std::max(c->n_groups, 1);
   const int nrows = c->nrows_out;
-  const int64_t vstride = (int64_t)kMaxB * n;
   // Krylov dimension per record, from the forward's per-segment record
   std::vector<int32_t> mseg(std::max<int64_t>(1, c->n_segments)), mrec(c->n_records);
   if (cudaMemcpy(mseg.data(), c->m_rec, sizeof(int32_t) * mseg.size(), cudaMemcpyDeviceToHost) !=
@@ -1099,84 +1350,46 @@ matex_status run_grad(matex_ctx* c, const double* xbar, double* dc, double* damp
   cudaMemsetAsync(c->CARRYg, 0, sizeof(double) * G * n, st);
   cudaMemsetAsync(c->CBg, 0, sizeof(double) * G * n, st);
   cudaMemsetAsync(damp, 0, sizeof(double) * std::max(c->n_src, 1), st);
-  AdjWork aw{c->AW, (int64_t)kWSlots * n, c->XBg, c->CARRYg, c->CBg};
   SourceTable base = c->src;  // d(B u)/d a_s uses the currents given at setup
   base.pwl_v = c->pwl_base_d;
-  std::vector<int32_t> act;
-  for (size_t ri = c->rounds.size(); ri-- > 0;) {
-    const Round& r = c->rounds[ri];
-    const int K = r.K;
-    AdjRound ar;
-    ar.rec = c->rc_vslot + r.begin;
-    ar.group = c->rc_group + r.begin;
-    ar.m = c->mrec_d + r.begin;
-    ar.obeg = c->rc_obeg + r.begin;
-    ar.nout = c->rc_nout + r.begin;
-    ar.seg = c->rc_seg + r.begin;
-    ar.l0 = c->rc_l0 + r.begin;
-    ar.len = c->rc_len + r.begin;
-    ar.hfirst = c->rc_hfirst + r.begin;
-    ar.V = c->Vb;
-    ar.vstride = vstride;
-    ar.A = c->TA;
-    ar.astride = (int64_t)kMaxM * n;
-    ar.Zp = c->TZp;
-    ar.Ht = c->THt;
-    ar.beta = c->Tbeta;
-    ar.n = n;
-    ar.dt = c->dt_out;
-    int mmax = 0;
-    for (int q = 0; q < K; ++q) mmax = std::max(mmax, mrec[r.begin + q]);
-    // active column lists for k = 0..mmax-1, uploaded once
-    act.clear();
-    std::vector<int> aoff(mmax + 1, 0);
-    for (int k = 0; k < mmax; ++k) {
-      aoff[k] = (int)act.size();
-      for (int q = 0; q < K; ++q)
-        if (mrec[r.begin + q] > k) act.push_back(q);
+  matex_status s = MATEX_OK;
+  if (c->opts.tape == 1) {
+    for (size_t ri = c->rounds.size(); ri-- > 0;) {
+      const Round& r = c->rounds[ri];
+      s = reverse_round(c, r, 0, r.K, c->rc_vslot + r.begin, mrec, xbar, damp, base);
+      if (s != MATEX_OK) return s;
     }
-    aoff[mmax] = (int)act.size();
-    if (!act.empty())
-      cudaMemcpyAsync(c->act_d, act.data(), sizeof(int32_t) * act.size(), cudaMemcpyHostToDevice, st);
-    // output adjoints and the small dense reverse
-    if (mmax > 0) {
-      AdjDots d{c->XBg, n, ar.group, 0, c->Vb, vstride, ar.rec, 0, nullptr};
-      adj_dots(d, K, mmax, n, c->partials, c->nchunks, c->YBL, st);
+  } else {
+    const int W = c->tape_W, Kb = c->tape_Kb;
+    const int nr = (int)c->rounds.size();
+    const int nwin = (int)c->ck_base.size();
+    std::vector<int> qa, qb;
+    for (int w = nwin - 1; w >= 0; --w) {
+      const int r0 = w * W, r1 = std::min(nr, r0 + W);
+      for (int g0 = 0; g0 < G; g0 += Kb) {
+        const int g1 = std::min(G, g0 + Kb);
+        // the block's columns in each round of the window (columns are in group order)
+        qa.assign(r1 - r0, 0);
+        qb.assign(r1 - r0, 0);
+        bool any = false;
+        for (int r = r0; r < r1; ++r) {
+          const Round& R = c->rounds[r];
+          const int32_t* gb = c->h_group_all.data() + R.begin;
+          qa[r - r0] = (int)(std::lower_bound(gb, gb + R.K, g0) - gb);
+          qb[r - r0] = (int)(std::lower_bound(gb, gb + R.K, g1) - gb);
+          any = any || qb[r - r0] > qa[r - r0];
+        }
+        if (!any) continue;
+        s = recompute_window(c, w, r0, r1, qa, qb, g0, g1, mrec);
+        if (s != MATEX_OK) return s;
+        for (int r = r1 - 1; r >= r0; --r) {
+          const int i = r - r0;
+          s = reverse_round(c, c->rounds[r], qa[i], qb[i] - qa[i], c->iota_d + (int64_t)i * Kb,
+                            mrec, xbar, damp, base);
+          if (s != MATEX_OK) return s;
+        }
+      }
     }
-    adj_obs(ar, K, xbar, c->out_map, nrows, c->YBO, c->n_times, c->S1, c->S2, st);
-    adj_small(ar, K, c->gamma, c->YBO, c->n_times, c->YBL, c->YOUT, c->YL, c->HTB, c->BETAB, st);
-    adj_build(ar, aw, K, c->YL, xbar, c->out_map, nrows, c->YOUT, c->n_times, c->S1, c->S2, st);
-    // reverse Arnoldi steps
-    for (int k = mmax - 1; k >= 0; --k) {
-      const int Ka = aoff[k + 1] - aoff[k];
-      const int32_t* ak = c->act_d + aoff[k];
-      AdjDots d1{c->AW, (int64_t)kWSlots * n, c->iota_d, k + 1, c->Vb, vstride, ar.rec, k + 1, ak};
-      adj_dots(d1, Ka, 1, n, c->partials, c->nchunks, c->D1, st);
-      adj_rbar(ar, aw, ak, Ka, k, c->D1, c->HTB, st);
-      AdjDots dh{c->AW, (int64_t)kWSlots * n, c->iota_d, kWR, c->Vb, vstride, ar.rec, 0, ak};
-      adj_dots(dh, Ka, k + 1, n, c->partials, c->nchunks, c->HD, st);
-      adj_abar(ar, aw, ak, Ka, k, c->HD, c->HTB, st);
-      gather_cols(c->Y, c->ldy, Ka, c->AW + (int64_t)kWA * n, (int64_t)kWSlots * n, ak, nullptr,
-                  nullptr, n, st);
-      solve_cols(c, c->fM, Ka);
-      adj_after_m(ar, aw, ak, Ka, k, c->Y, c->ldy, c->c_perm, st);
-    }
-    {
-      AdjDots d0{c->AW, (int64_t)kWSlots * n, c->iota_d, 0, c->Vb, vstride, ar.rec, 0, nullptr};
-      if (mmax > 0) adj_dots(d0, K, 1, n, c->partials, c->nchunks, c->D0, st);
-    }
-    adj_vbar(ar, aw, K, c->D0, c->BETAB, st);
-    // w = G^{-1}(c z'), then z' = G^{-1} B s
-    gather_cols(c->Y, c->ldy, K, c->AW + (int64_t)kWW * n, (int64_t)kWSlots * n, nullptr, nullptr,
-                nullptr, n, st);
-    solve_cols(c, c->fG, K);
-    adj_after_w(ar, aw, K, c->Y, c->ldy, c->c_perm, st);
-    gather_cols(c->Y, c->ldy, K, c->AW + (int64_t)kWZp * n, (int64_t)kWSlots * n, nullptr, nullptr,
-                nullptr, n, st);
-    solve_cols(c, c->fG, K);
-    adj_sources(ar, K, base, c->Y, c->ldy, damp, st);
-    matex_status s = cuda_check(c, "grad round");
-    if (s != MATEX_OK) return s;
   }
   // initial states x(0) = G^{-1} B u(0) of the groups whose input is non-zero at t = 0
   const int ng = (int)c->init_groups.size();
@@ -1189,10 +1402,15 @@ matex_status run_grad(matex_ctx* c, const double* xbar, double* dc, double* damp
   }
   adj_csum(c->CBg, G, n, c->perm, dc, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(c, "grad sync");
-  matex_status s = cuda_check(c, "grad");
+  s = cuda_check(c, "grad");
   if (s != MATEX_OK) return s;
   int tmp = 0;
-  return read_count(c, &tmp);
+  if ((s = read_count(c, &tmp)) != MATEX_OK) return s;
+  if (c->opts.tape == 2 && c->h_count[2] != 0)
+    return fail(c, MATEX_ERR_STATE,
+                "matex_grad: a recomputed segment retired its column at another Krylov step than "
+                "the run did");
+  return MATEX_OK;
 }
 
 }  // namespace
@@ -1202,7 +1420,8 @@ extern "C" {
 matex_status matex_grad(matex_ctx* c, const double* xbar, double* dc, double* damp) {
   if (!c) return MATEX_ERR_ARG;
   if (!xbar || !dc || (c->n_src > 0 && !damp)) return fail(c, MATEX_ERR_ARG, "NULL argument");
-  if (!c->opts.tape) return fail(c, MATEX_ERR_STATE, "matex_grad needs a context set up with tape = 1");
+  if (!c->opts.tape)
+    return fail(c, MATEX_ERR_STATE, "matex_grad needs a context set up with tape = 1 or 2");
   if (!c->taped) return fail(c, MATEX_ERR_STATE, "matex_grad needs a preceding batched matex_run");
   cudaMemsetAsync(c->d_count, 0, 4 * sizeof(int32_t), c->st);
   return run_grad(c, xbar, dc, damp);
@@ -1300,6 +1519,8 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   matex_default_opts(&o);
   if (opts) o = *opts;
   if (o.max_width <= 0) o.max_width = 1024;
+  if (o.tape < 0 || o.tape > 2) return bad("tape must be 0, 1 or 2");
+  if (o.tape_window < 0 || o.tape_block < 0) return bad("tape_window and tape_block must be >= 0");
   if (o.tape && o.group_select >= 0) return bad("tape needs all groups (group_select = -1)");
   if (o.solve_mode < 0 || o.solve_mode > 2) return bad("solve_mode must be 0, 1 or 2");
   if (o.krylov < 0 || o.krylov > 2) return bad("krylov must be 0, 1 or 2");
@@ -1455,6 +1676,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   c->Kmax = Kmax;
   c->h_nout_all = h_nout;
   c->h_segid_all = h_segid;
+  c->h_group_all = h_group;
   for (const Round& rd : c->rounds) {
     std::vector<char> cov(c->n_times, 0);
     int cnt = 0;
@@ -1547,7 +1769,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   ok = ok && c->upload(c->sel_groups_d, c->sel_groups.data(), c->sel_groups.size());
   ok = ok && c->upload(c->init_groups_d, c->init_groups.data(), c->init_groups.size());
   std::vector<int32_t> h_vslot(h_group.size());
-  for (size_t r = 0; r < h_group.size(); ++r) h_vslot[r] = o.tape ? (int32_t)r : h_group[r];
+  for (size_t r = 0; r < h_group.size(); ++r) h_vslot[r] = o.tape == 1 ? (int32_t)r : h_group[r];
   ok = ok && c->upload(c->rc_vslot, h_vslot.data(), h_vslot.size());
   ok = ok && c->upload(c->rc_group, h_group.data(), h_group.size()) &&
        c->upload(c->rc_seg, h_seg.data(), h_seg.size()) &&
@@ -1565,7 +1787,35 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   c->nchunks = (int)((n + kChunk - 1) / kChunk);
   const size_t G = (size_t)std::max(n_groups, 1);
   c->n_records = (int64_t)h_group.size();
-  const size_t vslots = o.tape ? (size_t)std::max<int64_t>(1, c->n_records) : G;
+  if (ok && o.tape == 2) {
+    // what the run itself holds, then the plan within most of the rest
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const double nd = (double)n;
+    const double run_b = 8.0 * (2.0 * nd * c->ldy + (double)G * kMaxB * nd + 4.0 * G * nd +
+                                (double)c->n_times * nd + (double)Kmax * c->n_times * kCoefLd +
+                                (double)Kmax * kMaxB * c->nchunks);
+    const double budget = 0.85 * ((double)free_b - run_b);
+    const TapePlan tp = plan_tape(c->rounds, n, (int)G, Kmax, c->n_times, c->nrows_out, budget,
+                                  o.tape_window, o.tape_block);
+    if (!tp.W) {
+      g_setup_err = "tape = 2: no checkpoint window and block fit the free device memory";
+      delete c;
+      return MATEX_ERR_OOM;
+    }
+    c->tape_W = tp.W;
+    c->tape_Kb = tp.Kb;
+    int64_t slot = 0;
+    for (size_t r = 0; r < c->rounds.size(); r += (size_t)tp.W) {
+      c->ck_base.push_back(slot);
+      slot += c->rounds[r].K;
+    }
+    ok = c->alloc(c->CK, (size_t)std::max<int64_t>(1, slot) * 2 * n);
+    c->tape_bytes = (int64_t)tp.bytes;
+  }
+  const size_t vslots = o.tape == 1 ? (size_t)std::max<int64_t>(1, c->n_records)
+                        : o.tape == 2 ? std::max(G, (size_t)c->tape_W * c->tape_Kb)
+                                      : G;
   ok = ok && c->alloc(c->Y, (size_t)n * c->ldy) && c->alloc(c->Y2, (size_t)n * c->ldy) && c->alloc(c->Vb, vslots * kMaxB * n) &&
        c->alloc(c->Zb, G * n) && c->alloc(c->Zpb, G * n) && c->alloc(c->Wb, G * n) &&
        c->alloc(c->Xb, G * n) && c->alloc(c->Xp, (size_t)c->n_times * n) && c->alloc(c->xdc, n) &&
@@ -1582,9 +1832,14 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   if (ok && cudaMemset(c->d_count, 0, 4 * sizeof(int32_t)) != cudaSuccess) ok = false;
   if (ok) c->fM.abort = c->fG.abort = c->d_count + 2;
   if (ok && o.tape) {
-    const size_t R = (size_t)std::max<int64_t>(1, c->n_records);
-    const size_t KM = (size_t)Kmax;
-    std::vector<int32_t> iota(std::max(Kmax, 1));
+    // tape 1: one entry per record, reverse launches as wide as a round;
+    // tape 2: one entry per window-tape slot, launches as wide as a block
+    const size_t R = o.tape == 1 ? (size_t)std::max<int64_t>(1, c->n_records)
+                                 : (size_t)c->tape_W * c->tape_Kb;
+    const size_t KM = o.tape == 1 ? (size_t)Kmax : (size_t)c->tape_Kb;
+    if (o.tape == 1)
+      c->tape_bytes = (int64_t)(8.0 * (double)R * ((kMaxM + 1) * (double)n + kMaxB * (double)n));
+    std::vector<int32_t> iota(std::max<size_t>(std::max(Kmax, 1), R));
     for (int q = 0; q < (int)iota.size(); ++q) iota[q] = q;
     ok = c->alloc(c->TA, R * kMaxM * n) && c->alloc(c->TZp, R * n) &&
          c->alloc(c->THt, R * kMaxB * kMaxM) && c->alloc(c->Tbeta, R) &&
@@ -1595,7 +1850,8 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
          c->alloc(c->BETAB, KM) && c->alloc(c->D1, KM * kMaxB) && c->alloc(c->HD, KM * kMaxB) &&
          c->alloc(c->D0, KM * kMaxB) && c->alloc(c->S1, KM * c->nrows_out) &&
          c->alloc(c->S2, KM * c->nrows_out) && c->upload(c->iota_d, iota.data(), iota.size()) &&
-         c->alloc(c->mrec_d, R) && c->alloc(c->act_d, KM * (kMaxM + 1));
+         c->alloc(c->mrec_d, std::max<int64_t>(1, c->n_records)) &&
+         c->alloc(c->act_d, KM * (kMaxM + 1));
     adj_set_limits();
   }
   if (!ok) {
@@ -1632,6 +1888,9 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     return MATEX_ERR_CUDA;
   }
   c->setup_stats.setup_upload_ms = now_ms() - t;
+  c->setup_stats.tape_window = c->tape_W;
+  c->setup_stats.tape_block = c->tape_Kb;
+  c->setup_stats.tape_bytes = c->tape_bytes;
   *out = c;
   return MATEX_OK;
 }

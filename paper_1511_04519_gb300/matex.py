@@ -33,7 +33,7 @@ class MatexOpts(C.Structure):
                 ("replay_m", C.POINTER(C.c_int32)), ("n_replay", C.c_int64),
                 ("max_width", C.c_int32), ("strict", C.c_int32), ("solve_mode", C.c_int32),
                 ("tape", C.c_int32), ("krylov", C.c_int32), ("graph", C.c_int32),
-                ("tail_eps", C.c_double)]
+                ("tail_eps", C.c_double), ("tape_window", C.c_int32), ("tape_block", C.c_int32)]
 
 
 class MatexStats(C.Structure):
@@ -45,7 +45,8 @@ class MatexStats(C.Structure):
                 ("sweeps_G", C.c_int32), ("solve_columns", C.c_int64),
                 ("kernel_launches", C.c_int32), ("rounds", C.c_int32),
                 ("graph_replay", C.c_int32), ("graph_capture_ms", C.c_double),
-                ("nnz_L_exact", C.c_int64)]
+                ("nnz_L_exact", C.c_int64), ("tape_window", C.c_int32), ("tape_block", C.c_int32),
+                ("tape_bytes", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -317,7 +318,8 @@ class Sim:
 
     def __init__(self, p, col_block=0, group_select=-1, include_dc=True, rows=None,
                  replay_m=None, max_width=0, strict=False, stream=None, solve_mode=2,
-                 tape=False, graph=True, krylov="R", tail_eps=0.0, **overrides):
+                 tape=False, graph=True, krylov="R", tail_eps=0.0, tape_window=0, tape_block=0,
+                 **overrides):
         o = matex_default_opts()
         o.graph = int(bool(graph))
         o.tail_eps = float(tail_eps)
@@ -329,7 +331,9 @@ class Sim:
             o.max_width = max_width
         o.strict = int(bool(strict))
         o.solve_mode = int(solve_mode)
-        o.tape = int(bool(tape))
+        o.tape = {False: 0, True: 1, 0: 0, 1: 1, 2: 2, "full": 1, "checkpoint": 2}[tape]
+        o.tape_window = int(tape_window)
+        o.tape_block = int(tape_block)
         self._keep = []
         if rows is not None:
             r = np.ascontiguousarray(rows, dtype=np.int32)

@@ -78,10 +78,12 @@ def per_group_m(p, sim):
     return out
 
 
+@pytest.mark.parametrize("tape", ["full", "checkpoint"])
 @pytest.mark.parametrize("seed,layers", [(3, 1), (4, 2), (5, 1)])
-def test_gpu_adjoint_matches_cpu_adjoint(env, seed, layers):
+def test_gpu_adjoint_matches_cpu_adjoint(env, seed, layers, tape):
+    torch, M, AG = env
     p, obs, theta = small_case(seed, layers=layers)
-    L, dc, da, sim = gpu_loss_grad(env, p, obs, theta)
+    L, dc, da, sim = gpu_loss_grad(env, p, obs, theta, sim=AG.make_sim(p, obs, tape=tape))
     ms = per_group_m(p, sim)
     Lr, cbar, abar, _ = A.loss_and_grad(p, obs, theta, replay_m=ms)
     assert L > 0 and abs(L - Lr) <= 1e-9 * Lr
@@ -159,12 +161,44 @@ def test_amplitude_gradient_away_from_unit_amplitudes(env):
         fd_sim.set_sources(base * av[src_of])
         return float(AG.hinge_ir_drop_loss(fd_sim.run(), 0.0, theta, p.dt_out))
 
+    # Richardson-extrapolated central differences with a step far above the
+    # loss's rounding noise (at amp_s = 0 the gradient is small, so a 1e-6
+    # step resolves it only to 1e-5)
     for s in range(p.n_src):
-        h = 1e-6 * max(amp[s], 1.0)
-        ap = amp.copy(); ap[s] += h
-        am = amp.copy(); am[s] -= h
-        fd = (loss(ap) - loss(am)) / (2 * h)
+        def f(a_s):
+            av = amp.copy(); av[s] = a_s
+            return loss(av)
+        fd = richardson_derivative(f, amp[s], 1e-2 * max(amp[s], 1.0))
         assert abs(da[s] - fd) <= 1e-6 * abs(fd), (s, amp[s], da[s], fd)
+
+
+@pytest.mark.parametrize("window,block", [(1, 1), (2, 3), (3, 2), (0, 0)])
+def test_checkpointed_adjoint_equals_full_tape(env, window, block):
+    """Checkpoints every `window` segment rounds, segments recomputed `block`
+    groups at a time (0: the sizes chosen at setup): the same gradients as
+    the full tape, up to the order of the solves' FP64 atomic additions.
+    Six groups of uneven breakpoint counts, so windows and blocks have
+    ragged ends and groups that start or finish inside a window."""
+    torch, M, AG = env
+    p = gridgen.small_mesh(16, nx=12, ny=11, layers=2, n_src=14,
+                           group_templates=[1, 3, 2, 4, 1, 3], t_end=0.4e-9, dt_out=10e-12,
+                           c_range=(1e-14, 1e-12))
+    obs = np.sort(np.random.default_rng(16).choice(p.n, 11, replace=False)).astype(np.int32)
+    drop = p.vdd - R.rmatex(p, nodes=obs).X
+    theta = float(np.quantile(drop, 0.6))
+    full = AG.make_sim(p, obs, tape="full")
+    L1, dc1, da1, _ = gpu_loss_grad(env, p, obs, theta, sim=full)
+    ms = np.concatenate(per_group_m(p, full)).astype(np.int32)
+    ck = AG.make_sim(p, obs, tape="checkpoint", tape_window=window, tape_block=block,
+                     replay_m=ms)
+    st = ck.setup_stats()
+    assert st["tape_window"] >= 1 and st["tape_block"] >= 1 and st["tape_bytes"] > 0
+    if window:
+        assert (st["tape_window"], st["tape_block"]) == (window, block)
+    L2, dc2, da2, _ = gpu_loss_grad(env, p, obs, theta, sim=ck)
+    assert abs(L2 - L1) <= 1e-12 * L1
+    assert np.abs(dc2 - dc1).max() <= 1e-10 * np.abs(dc1).max()
+    assert np.abs(da2 - da1).max() <= 1e-10 * np.abs(da1).max()
 
 
 def test_grad_requires_tape_and_a_run(env):
@@ -193,14 +227,28 @@ def test_config3_adjoint_against_cpu_adjoint_and_differences(env, cfg3):
     torch, M, AG = env
     p = cfg3
     obs = p.observed.astype(np.int32)
-    sim = AG.make_sim(p, obs, include_dc=False)
+    sim = AG.make_sim(p, obs, include_dc=False, tape="checkpoint")
     X0 = sim.run().cpu().numpy()
+    st = sim.setup_stats()
+    # checkpoints per segment round, every group recomputed at once: x and z
+    # of the 192 segments plus one round's tape, not the 12 GB full tape
+    assert (st["tape_window"], st["tape_block"]) == (1, 64)
+    assert st["tape_bytes"] < 6e9
     drop = -X0                      # x_dc = Vdd on this grid: the load response is the drop
     theta = float(np.quantile(drop, 0.9))
     assert (drop > theta).mean() >= 0.09
     L, dc, da, sim = gpu_loss_grad(env, p, obs, theta, sim=sim, vdd=0.0)
     assert L > 0 and np.isfinite(dc).all() and np.isfinite(da).all()
     ms = per_group_m(p, sim)
+    # the full tape of the same run (same Krylov dimensions) gives the same gradients
+    full = AG.make_sim(p, obs, include_dc=False, tape="full",
+                       replay_m=np.concatenate(ms).astype(np.int32))
+    Lf, dcf, daf, _ = gpu_loss_grad(env, p, obs, theta, sim=full, vdd=0.0)
+    assert abs(Lf - L) <= 1e-12 * L
+    assert np.abs(dcf - dc).max() <= 1e-10 * np.abs(dc).max()
+    assert np.abs(daf - da).max() <= 1e-10 * np.abs(da).max()
+    full.close()
+    del full
     # CPU reverse of two groups, output adjoint from the GPU forward's rows
     Lr, G = A.hinge_loss(X0, 0.0, theta, p.dt_out)
     groups = [5, 41]

@@ -74,6 +74,36 @@ def test_solve_matches_sparse_direct(M, which, case, width):
             assert np.abs(A @ x[q] - b[q]).max() <= 1e-12 * np.abs(b[q]).max()
 
 
+@pytest.mark.parametrize("which", [0, 1])
+def test_chunked_level_solves_on_the_bench_grid(M, which):
+    """The 180k-node grid's top supernodes (up to 898 wide) are wide enough
+    for the level launches to split their reductions over several CTAs at
+    small column counts (and over fewer at large ones).  Level-by-level
+    solves of 1 to 64 right-hand sides against the sparse matrix (residual)
+    and against the same solves without chunks (the allocation-free entry
+    point runs them unchunked)."""
+    import torch
+    import scipy.sparse as sp
+    p = gridgen.config1()
+    sim = M.Sim(p, solve_mode=1)
+    A = sp.csr_matrix(sp.diags(p.c) + p.gamma * p.G()) if which == 0 else p.G()
+    rng = np.random.default_rng(21)
+    for ncols in (1, 2, 5, 16, 64):
+        b = torch.from_numpy(rng.standard_normal((ncols, p.n))).cuda()
+        x = sim.solve(which, b)
+        xu = torch.empty_like(b)
+        M.matex_solve_noalloc(sim.ctx, which, ncols, b.data_ptr(), xu.data_ptr())
+        torch.cuda.synchronize()
+        xn, bn, xun = x.cpu().numpy(), b.cpu().numpy(), xu.cpu().numpy()
+        for q in range(ncols):
+            # residual at the scale of backward-stable solves: eps |A| |x| with
+            # |A| ~ 200 S here (1e-11 leaves room; a wrong chunk sum is O(1))
+            r = np.abs(A @ xn[q] - bn[q]).max()
+            assert r <= 1e-11 * max(np.abs(bn[q]).max(), np.abs(A).max() * np.abs(xn[q]).max()), (ncols, q)
+            assert np.abs(xn[q] - xun[q]).max() <= 1e-12 * np.abs(xun[q]).max(), (ncols, q)
+    sim.close()
+
+
 def test_expm_matches_scipy(M):
     import torch
     import scipy.linalg as sla
