@@ -101,6 +101,12 @@ typedef struct matex_opts {
                               memory) */
   int32_t tape_block;      /* tape = 2: groups recomputed together (columns of the recompute
                               and reverse launches); 0 (default): chosen at setup */
+  int32_t recombine;       /* V y of the recombination (Eq. 6 at the outputs): 0 (default) on
+                              the tensor cores where it pays (exact runs, rounds of 16 to
+                              kdim_cap basis vectors), as an error-free decomposition of the
+                              FP64 operands into 6-bit bf16 slices whose products the FP32
+                              accumulators hold exactly (error of the order of an FP64 dot
+                              product); 1: FP64 FMAs only */
 } matex_opts;
 
 /* Counters and timings of the last matex_run (or of setup for the setup_* fields). */

@@ -66,7 +66,7 @@ struct Chunk {
 
 // [a, b) = chunk ch of the range [lo, hi), chunk widths rounded up to 16 so
 // that the four-load steps of the dot products stay whole
-__device__ __forceinline__ void chunk_range(const Chunk& ch, int lo, int hi, int& a, int& b) {
+__device__ __forceinline__ void chunk_range(Chunk ch, int lo, int hi, int& a, int& b) {
   if (ch.n == 1) { a = lo; b = hi; return; }
   const int span = ((hi - lo + ch.n - 1) / ch.n + 15) & ~15;
   a = min(hi, lo + ch.c * span);
@@ -77,7 +77,7 @@ __device__ __forceinline__ void chunk_range(const Chunk& ch, int lo, int hi, int
 // every thread has written its share.  The CTA that completes the slot's
 // count adds the chunks in order and hands each sum to out(r, q, v).
 template <int KB, typename Out>
-__device__ __forceinline__ void chunk_finish(const Chunk& ch, int rows, Out out) {
+__device__ __forceinline__ void chunk_finish(Chunk ch, int rows, Out out) {
   __shared__ int sh_last;
   __threadfence();
   __syncthreads();
@@ -98,7 +98,7 @@ __device__ __forceinline__ void chunk_finish(const Chunk& ch, int rows, Out out)
   if (threadIdx.x == 0) ch.cnt[ch.slot] = 0;
 }
 
-__device__ __forceinline__ double* chunk_part(const Chunk& ch, int KB, int r, int q) {
+__device__ __forceinline__ double* chunk_part(Chunk ch, int KB, int r, int q) {
   return ch.part + (((int64_t)ch.slot * ch.n + ch.c) * kRowBlock + r) * KB + q;
 }
 
@@ -110,7 +110,7 @@ __device__ __forceinline__ double* chunk_part(const Chunk& ch, int KB, int r, in
 template <int KB>
 __device__ __forceinline__ void fwd_task(const DevFactor& F, int s, int i0, int c0,
                                          double* __restrict__ Y, double* __restrict__ Y2, int ldy,
-                                         double* sb, const Chunk& ch) {
+                                         double* sb, Chunk ch) {
   const int f = F.sup_first[s];
   const int w = F.sup_first[s + 1] - f;
   const int64_t rp = F.sup_rowptr[s];
@@ -225,7 +225,7 @@ __device__ __forceinline__ void fwd_task(const DevFactor& F, int s, int i0, int 
 template <int KB>
 __device__ __forceinline__ void bwd_task(const DevFactor& F, int s, int j0, int c0,
                                          double* __restrict__ Y, const double* __restrict__ Y2,
-                                         int ldy, double* ub, const Chunk& ch) {
+                                         int ldy, double* ub, Chunk ch) {
   const int f = F.sup_first[s];
   const int w = F.sup_first[s + 1] - f;
   const int64_t rp = F.sup_rowptr[s];
@@ -480,7 +480,7 @@ __device__ __forceinline__ void bwd_small_rows(const DevFactor& F, int e0, int n
 template <int KB>
 __device__ __forceinline__ void run_fwd(const DevFactor& F, int2 tk, int c0, double* Y, double* Y2,
                                         int ldy, double* sm, PackDesc& pd,
-                                        const Chunk& ch = Chunk()) {
+                                        Chunk ch = Chunk()) {
   const int ne = tk.y & (kPackRowwise - 1);
   if (tk.x >= 0) fwd_task<KB>(F, tk.x, tk.y, c0, Y, Y2, ldy, sm, ch);
   else if (ch.c > 0) return;  // packed tasks are not chunked: the first chunk's CTA runs them
@@ -491,7 +491,7 @@ __device__ __forceinline__ void run_fwd(const DevFactor& F, int2 tk, int c0, dou
 template <int KB>
 __device__ __forceinline__ void run_bwd(const DevFactor& F, int2 tk, int c0, double* Y,
                                         const double* Y2, int ldy, double* sm, PackDesc& pd,
-                                        const Chunk& ch = Chunk()) {
+                                        Chunk ch = Chunk()) {
   const int ne = tk.y & (kPackRowwise - 1);
   if (tk.x >= 0) bwd_task<KB>(F, tk.x, tk.y, c0, Y, Y2, ldy, sm, ch);
   else if (ch.c > 0) return;
@@ -517,7 +517,7 @@ __device__ __forceinline__ Chunk level_chunk(int ncb, int nchunk, const SplitScr
 }
 
 template <int KB>
-__global__ void __launch_bounds__(kSolveThreads)
+__global__ void __launch_bounds__(kSolveThreads, 8)
 fwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, int nchunk,
                  SplitScratch sp, double* __restrict__ Y, double* __restrict__ Y2, int ldy) {
   extern __shared__ double sb[];
@@ -529,7 +529,7 @@ fwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, int nchun
 }
 
 template <int KB>
-__global__ void __launch_bounds__(kSolveThreads)
+__global__ void __launch_bounds__(kSolveThreads, 8)
 bwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, int nchunk,
                  SplitScratch sp, double* __restrict__ Y, const double* __restrict__ Y2, int ldy) {
   extern __shared__ double ub[];

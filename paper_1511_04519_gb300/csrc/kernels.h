@@ -264,6 +264,31 @@ void recombine(double* Xp, int64_t n, int n_times, const double* Vbase, int64_t 
 void next_state(double* X, const double* Vbase, int64_t vstride, const double* Z, const double* Zp,
                 const double* W, int64_t gstride, const RoundCols& rc, const int32_t* mcol,
                 const double* yend, int K, int64_t n, cudaStream_t st);
+// Tensor-core recombination of the V y part (k_recombine_tc.cu): error-free
+// 6-bit slices of V (per node) and of the coefficients (per output) in bf16,
+// tcgen05 MMAs into FP32 accumulators that stay exact integers, exact
+// integer combination, FP64 result added into Xp.  Scratch of a context,
+// sized at setup for rounds of up to kdim_cap basis vectors.
+constexpr int kTcMaxKdim = 2048;  // basis vectors of one round the scratch may be sized for
+constexpr int kTcMinKdim = 16;    // below this the FP64 kernel is cheaper
+struct TcScratch {
+  void* slices = nullptr;       // V and coefficient slices in the MMA tile layout
+  int64_t* kmap = nullptr;      // [kdim_cap] basis vector -> offset in Vbase
+  int32_t* kq = nullptr;        // [kdim_cap] basis vector -> (column << 5) | index
+  double* rowscale = nullptr;   // [n] power-of-two scale of each node's basis values
+  double* colscale = nullptr;   // [output tiles x 48] scale of each output's coefficients
+  int32_t* err = nullptr;       // raised when a bounded wait of the MMA kernel gives up
+  int kdim_cap = 0;
+};
+size_t tc_slices_bytes(int64_t n, int kdim, int nouts);
+void tc_set_limits();
+// Xp[o][i] += sum over the round's columns q and j < mcol[q] of V_q[j][i] y_q(o)[j]
+// for o in [obeg_min, oend_max) (the columns' own output ranges); kdim = sum
+// of mcol.  Returns the number of kernels launched.
+int recombine_tc(double* Xp, int64_t n, const double* Vbase, int64_t vstride, const RoundCols& rc,
+                 const int32_t* mcol, const double* coef, int ldo, int K, int kdim, int obeg_min,
+                 int oend_max, const TcScratch& ts, cudaStream_t st);
+
 // Adjoint checkpoints: CK[q] = {X[groups[q]], Z[groups[q]]} ([K][2][n]), or the
 // reverse copy when restore is set (X, Z per group, [G][n]).
 void checkpoint_states(double* CK, double* X, double* Z, const int32_t* groups, int K, int64_t n,

@@ -78,6 +78,8 @@ struct matex_ctx {
   Symbolic S;
   std::vector<LevelPlan> levels;
   SplitScratch split;              // chunked reductions of the level launches
+  TcScratch tc;                    // tensor-core recombination (kdim_cap 0: not used)
+  int32_t* m_zero = nullptr;       // [Kmax] zeros: the FP64 recombination with -P terms only
   // persistent solve: per column count (1..ldy) one PersistLevel row per level
   PersistLevel* plev_d = nullptr;
   std::vector<long long> pf_total, pb_total;   // per column count
@@ -949,7 +951,9 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
       prof_end(c, e, P_GS, 1, nd * kit, 16.0 * nd * kit);
       launches++;
     }
+    int kdim = 0;  // basis vectors of the round: each Arnoldi step adds one per active column
     for (int j = 0; j < c->m_max && kit > 0; ++j) {
+      kdim += kit;
       if (c->opts.krylov == 2) {
         // standard space (MEXP): w = A v_j = -C^{-1} G v_j, no solve
         e = prof_begin(c);
@@ -1010,10 +1014,20 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
                         teps, teps > 0.0 ? c->pbound : nullptr, c->tcut);
     prof_end(c, e, P_SMALL, 1, 0.0, 0.0);
     e = prof_begin(c);
-    recombine(c->Xp, n, c->n_times, c->Vb, vstride, c->Zb, c->Zpb, c->Wb, n, rc, c->ss.m, c->coef,
-              c->n_times, K, r.obeg_min, r.oend_max, c->dt_out, st,
-              teps > 0.0 ? c->tcut : nullptr);
-    prof_end(c, e, P_RECOMB, 1, 0.0, 0.0, (int)ri);
+    int rl = 1;
+    if (c->tc.kdim_cap && teps == 0.0 && kdim >= kTcMinKdim && kdim <= c->tc.kdim_cap) {
+      // V y on the tensor cores, then the -P terms alone in FP64
+      rl += recombine_tc(c->Xp, n, c->Vb, vstride, rc, c->ss.m, c->coef, c->n_times, K, kdim,
+                         r.obeg_min, r.oend_max, c->tc, st);
+      recombine(c->Xp, n, c->n_times, c->Vb, vstride, c->Zb, c->Zpb, c->Wb, n, rc, c->m_zero,
+                c->coef, c->n_times, K, r.obeg_min, r.oend_max, c->dt_out, st, nullptr);
+    } else {
+      recombine(c->Xp, n, c->n_times, c->Vb, vstride, c->Zb, c->Zpb, c->Wb, n, rc, c->ss.m, c->coef,
+                c->n_times, K, r.obeg_min, r.oend_max, c->dt_out, st,
+                teps > 0.0 ? c->tcut : nullptr);
+    }
+    prof_end(c, e, P_RECOMB, rl, 0.0, 0.0, (int)ri);
+    launches += rl - 1;
     e = prof_begin(c);
     next_state(c->Xb, c->Vb, vstride, c->Zb, c->Zpb, c->Wb, n, rc, c->ss.m, c->yend, K, n, st);
     record_segments(c->ss, rc, K, c->m_rec, c->st_rec, st);
@@ -1527,6 +1541,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   if (o.tape && o.krylov != 0) return bad("the adjoint tape follows the rational Krylov space only");
   if (!std::isfinite(o.tail_eps) || o.tail_eps < 0.0) return bad("tail_eps must be finite and >= 0");
   if (o.tape && o.tail_eps > 0.0) return bad("the adjoint tape follows exact runs only (tail_eps 0)");
+  if (o.recombine < 0 || o.recombine > 1) return bad("recombine must be 0 or 1");
   if (o.col_block != 0 && o.col_block != 1 && o.col_block != 2 && o.col_block != 4 && o.col_block != 8)
     return bad("col_block must be 0, 1, 2, 4 or 8");
   if (o.group_select >= n_groups) return bad("group_select out of range");
@@ -1861,6 +1876,32 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     return MATEX_ERR_OOM;
   }
   set_small_smem_limits();
+  if (o.recombine == 0 && o.tail_eps == 0.0) {
+    // tensor-core recombination scratch, sized once for rounds of up to
+    // kdim_cap basis vectors (never regrown: recorded graphs keep pointers)
+    int cap = std::min(Kmax * m_max, kTcMaxKdim);
+    cap = (cap + 31) & ~31;
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    while (cap > 32 && (double)tc_slices_bytes(n, cap, c->n_times) > 0.3 * (double)free_b) cap -= 32;
+    if (cap >= kTcMinKdim &&
+        (double)tc_slices_bytes(n, cap, c->n_times) <= 0.3 * (double)free_b) {
+      unsigned char* sl = nullptr;
+      int64_t* km = nullptr;
+      int32_t* kq = nullptr;
+      double *rsc = nullptr, *csc = nullptr;
+      const size_t ncol = ((size_t)c->n_times + 47) / 48 * 48;
+      if (c->alloc(sl, tc_slices_bytes(n, cap, c->n_times)) && c->alloc(km, cap) &&
+          c->alloc(kq, cap) && c->alloc(rsc, n) && c->alloc(csc, ncol) &&
+          c->alloc(c->m_zero, Kmax) &&
+          cudaMemset(c->m_zero, 0, sizeof(int32_t) * Kmax) == cudaSuccess) {
+        c->tc = TcScratch{sl, km, kq, rsc, csc, c->d_count + 1, cap};
+        tc_set_limits();
+      } else {
+        cudaGetLastError();  // no room: the FP64 recombination serves every round
+      }
+    }
+  }
   c->ss.krylov = o.krylov;
   c->ss.rscale = o.krylov == 1 ? 1.0 / gamma : o.krylov == 2 ? gamma : 1.0;
   if (o.krylov == 2 && !ensure_g_csr(c)) {

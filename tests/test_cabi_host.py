@@ -175,4 +175,4 @@ def test_default_options_layout():
     assert bytes(buf[size:]) == b"\xa5" * 64
     assert M.MatexOpts.from_buffer(buf).tail_eps == 0.0
     assert C.sizeof(M.MatexStats) == 3 * 8 + 8 + 4 * 12 + 8 + 4 * 4 + 8 + 8 + 4 * 2 + 8
-    assert (o.tape_window, o.tape_block) == (0, 0)
+    assert (o.tape_window, o.tape_block, o.recombine) == (0, 0, 0)

@@ -69,6 +69,52 @@ def test_uneven_grids_full_size_sampled(M):
         assert stats.nonconv == 0
 
 
+class _StoredOracle:
+    """The oracle's result for one group as stored by the golden script."""
+
+    def __init__(self, X, m):
+        self.X = X
+        self.logs = [type("Log", (), {"m": m})()]
+
+
+def test_uneven_groups_full_size_against_stored_oracle(M):
+    """The four-layer 600x600 grid (1.44M nodes; nnz(L) ~ 1.9e8, supernodes
+    thousands of nodes wide): two groups against the oracle at 32 nodes (16
+    random, 16 on the central line of every layer, where the top separators
+    lie) and every output time, from tests/golden (written by the committed
+    script beside it, which calls only the oracle); and the solves with both
+    factors at 1, 8 and 64 right-hand sides against the sparse matrices."""
+    import os
+    import torch
+    import scipy.sparse as sp
+    ref = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                               "mesh4x600x600_2groups_32rows.npz"))
+    p = gridgen.config2()
+    rows = ref["rows"].astype(np.int32)
+    for gi, g in enumerate(ref["groups"].tolist()):
+        kw = dict(group_select=int(g), rows=rows, include_dc=False)
+        sim = M.Sim(p, **kw)
+        X = sim.run().cpu().numpy()
+        stored = _StoredOracle(ref["X"][gi], ref["m"][gi])
+        err = check_adaptive(f"mesh4x600x600_group{g}_32rows", p, X, sim.m_sequence(), stored,
+                             lambda m: M.Sim(p, replay_m=m, **kw).run().cpu().numpy())
+        assert err <= TOL_V * p.vdd
+        assert np.abs(ref["X"][gi]).max() > 1e-4  # the group's loads do move these nodes
+        if gi == 0:
+            rng = np.random.default_rng(2)
+            for which in (0, 1):
+                A = sp.csr_matrix(sp.diags(p.c) + p.gamma * p.G()) if which == 0 else p.G()
+                amax = abs(A).max()
+                for ncols in (1, 8, 64):
+                    b = rng.standard_normal((ncols, p.n))
+                    x = sim.solve(which, torch.from_numpy(b).cuda()).cpu().numpy()
+                    for q in range(ncols):
+                        r = np.abs(A @ x[q] - b[q]).max()
+                        assert r <= 1e-11 * max(np.abs(b[q]).max(), amax * np.abs(x[q]).max())
+        sim.close()
+        torch.cuda.empty_cache()
+
+
 def test_uneven_groups_full_size_properties(M):
     """Config 2 at full size (1.44M nodes, 256 groups with 4..199 breakpoints):
     one batched run; every output finite, t = 0 equal to the DC state (Vdd),
