@@ -487,6 +487,7 @@ def main():
     sim = M.Sim(p, stream=stream)
     setup = sim.setup_stats()
     tuning = sim.autotune()
+    level_blocks = sim.level_blocks()
     out = torch.empty((sim.n_times, sim.n_rows), dtype=torch.float64, device="cuda")
     for _ in range(args.warmup):
         sim.run(out)
@@ -760,6 +761,8 @@ def main():
             "batch_grids": grids, "other_configs": others,
             "autotune": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in t.items()}
                          for t in tuning],
+            "autotune_level_blocks": [{k: (round(v, 4) if isinstance(v, float) else v)
+                                       for k, v in t.items()} for t in level_blocks],
             "setup_ms": {"order": setup["setup_order_ms"], "factor": setup["setup_factor_ms"],
                          "upload": setup["setup_upload_ms"], "nnz_L": setup["nnz_L"],
                          "supernodes": setup["n_supernodes"], "levels": setup["n_levels"]},

@@ -377,6 +377,19 @@ matex_status matex_get_profile(matex_ctx* ctx, matex_profile* out);
 matex_status matex_get_autotune(matex_ctx* ctx, int32_t* ncols, int32_t* mode, float* ms,
                                int32_t cap, int32_t* count);
 
+/*
+ * Column blocks of the level-by-level solve launches (no counterpart in the
+ * paper): for each of the *nlev levels of the supernodal tree (leaves first)
+ * the number of right-hand sides a thread block of the forward (kb_fwd) and
+ * backward (kb_bwd) substitution carries.  With solve_mode 2 and col_block 0
+ * the setup-time tuner times 1, 2, 4 and 8 per level and direction at the
+ * context's full column count and keeps the fastest; ms (host [2*cap] or
+ * NULL) receives the chosen blocks' times (forward, backward per level; -1
+ * when not tuned or read from the cache).  Writes at most cap levels.
+ */
+matex_status matex_get_level_blocks(matex_ctx* ctx, int32_t* kb_fwd, int32_t* kb_bwd, float* ms,
+                                    int32_t cap, int32_t* nlev);
+
 /* Setup statistics (ordering, factor sizes, timings). */
 matex_status matex_get_setup_stats(matex_ctx* ctx, matex_stats* stats);
 

@@ -711,8 +711,8 @@ void launch_level(bool fwd, const DevFactor& F, const LevelPlan& L, double* Y, d
 }
 
 void run_level(bool fwd, const DevFactor& F, const LevelPlan& L, double* Y, double* Y2, int ldy,
-               int ncols, cudaStream_t st, const SplitScratch* split) {
-  int kb = L.kb;
+               int ncols, cudaStream_t st, const SplitScratch* split, int force_kb = 0) {
+  int kb = force_kb > 0 ? force_kb : fwd ? L.kbf : L.kbb;
   while (kb > 1 && kb / 2 >= ncols) kb /= 2;
   switch (kb) {
     case 1: launch_level<1>(fwd, F, L, Y, Y2, ldy, ncols, st, split); break;
@@ -811,6 +811,30 @@ int persistent_blocks_per_sm(size_t smem) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_solve_kernel, kSolveThreads, smem);
   return nb;
 }
+float time_level(bool fwd, const DevFactor& F, const LevelPlan& L, int kb, double* Y, double* Y2,
+                 int ldy, int ncols, cudaStream_t st, const SplitScratch* split, int reps) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return -1.f;
+  }
+  run_level(fwd, F, L, Y, Y2, ldy, ncols, st, split, kb);
+  float best = 1e30f;
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(e0, st);
+    run_level(fwd, F, L, Y, Y2, ldy, ncols, st, split, kb);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return cudaGetLastError() == cudaSuccess ? best : -1.f;
+}
+
 bool preload_solve_kernels() {
   cudaFuncAttributes a;
   bool ok = cudaFuncGetAttributes(&a, persistent_solve_kernel) == cudaSuccess &&

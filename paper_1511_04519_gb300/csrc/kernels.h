@@ -49,7 +49,9 @@ struct LevelPlan {
   int32_t nf, nb;
   int32_t max_w;         // widest supernode in the level
   int32_t max_wr;        // largest w + r in the level
-  int32_t kb;            // column block: 1, 2, 4 or 8
+  int32_t kb;            // column block: 1, 2, 4 or 8 (occupancy rule; persistent schedule)
+  int32_t kbf, kbb;      // column blocks of the level launches, forward and backward
+                         // (set by the setup-time tuner, else kb)
   int32_t split_w;       // widest supernode with split (non-packed) tasks, 0 if none: the
                          // longest reduction of a forward task
   int32_t split_ld;      // largest w + r of those: the longest reduction of a backward task
@@ -108,6 +110,11 @@ int persistent_blocks_per_sm(size_t smem);
 // that a later solve triggers no lazy module loading (which allocates device
 // memory for the code).  Returns false on a CUDA error.
 bool preload_solve_kernels();
+// Device time (best of reps after a warm-up, CUDA events on st) of one level
+// launch with column block kb for ncols right-hand sides; -1 on an error.
+float time_level(bool fwd, const DevFactor& F, const LevelPlan& L, int kb, double* Y, double* Y2,
+                 int ldy, int ncols, cudaStream_t st, const SplitScratch* split, int reps);
+constexpr int kSolveSmemTune = 100 * 1024;  // largest staging buffer a tuned column block may use
 // adds one to *p on the stream (failure-injection hook of the tests)
 void bump_counter(int* p, cudaStream_t st);
 

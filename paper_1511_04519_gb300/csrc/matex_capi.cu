@@ -93,6 +93,7 @@ struct matex_ctx {
   // autotuned solve launch mode per column count (0 persistent, 1 per level)
   std::vector<int8_t> mode_by_ncols;
   std::vector<int32_t> tune_reps, tune_modes;
+  std::vector<float> level_tune_ms;  // per level and direction: best time of the chosen block
   std::vector<float> tune_ms;
   // adjoint tape (opts.tape): per record (non-zero segment) basis slot = record
   int64_t n_records = 0;
@@ -430,6 +431,7 @@ bool plan_levels(matex_ctx* c) {
     }
     while (kb > 1 && (size_t)ld_need * kb * sizeof(double) > (size_t)kSolveSmemCap) kb /= 2;
     L.kb = kb;
+    L.kbf = L.kbb = kb;
     smem_need = std::max(smem_need, (int)(std::max(std::max(ld_need, L.max_w) * kb,
                                                    kSolveThreadsFor * (kb + 1)) * sizeof(double)));
   }
@@ -453,7 +455,7 @@ bool plan_levels(matex_ctx* c) {
     c->levels[l].ftasks = fd + fofs[l];
     c->levels[l].btasks = bd + bofs[l];
   }
-  set_solve_smem_limit(std::max(smem_need, 48 * 1024));
+  set_solve_smem_limit(std::max(smem_need, kSolveSmemTune));
   // persistent schedules for every column count 1..ldy
   std::vector<PersistLevel> pl((size_t)c->ldy * nlev);
   c->pf_total.assign(c->ldy + 1, 0);
@@ -705,6 +707,74 @@ std::string tune_key(matex_ctx* c) {
   for (char* p = buf; *p; ++p)
     if (*p == ' ') *p = '_';
   return buf;
+}
+
+// Column block of every level launch, per direction: the tree's levels
+// differ (thousands of small supernodes at the bottom, one wide supernode at
+// the top), so each level's forward and backward kernel is timed with
+// KB = 1, 2, 4 and 8 right-hand sides per thread block at the context's full
+// column count (best of three after a warm-up; zero right-hand sides) and
+// keeps the fastest.  Blocks whose staging buffer would exceed
+// kSolveSmemTune are not tried.  Cached with the launch-mode choice.
+void autotune_levels(matex_ctx* c) {
+  const std::string key = "kb:" + tune_key(c);
+  const char* cache = std::getenv("MATEX_AUTOTUNE_CACHE");
+  const int nlev = (int)c->levels.size();
+  if (cache) {
+    FILE* f = std::fopen(cache, "r");
+    if (f) {
+      char line[8192];
+      bool found = false;
+      while (!found && std::fgets(line, sizeof(line), f)) {
+        std::string l(line);
+        if (l.compare(0, key.size() + 1, key + " ") != 0) continue;
+        std::vector<int> v;
+        for (size_t i = key.size() + 1; i < l.size(); ++i)
+          if (l[i] >= '1' && l[i] <= '8') v.push_back(l[i] - '0');
+        if ((int)v.size() == 2 * nlev) {
+          for (int k = 0; k < nlev; ++k) {
+            c->levels[k].kbf = v[2 * k];
+            c->levels[k].kbb = v[2 * k + 1];
+          }
+          found = true;
+        }
+      }
+      std::fclose(f);
+      if (found) return;
+    }
+  }
+  cudaMemsetAsync(c->Y, 0, sizeof(double) * (size_t)c->n * c->ldy, c->st);
+  cudaMemsetAsync(c->Y2, 0, sizeof(double) * (size_t)c->n * c->ldy, c->st);
+  c->level_tune_ms.assign(2 * nlev, -1.f);
+  for (int l = 0; l < nlev; ++l) {
+    LevelPlan& L = c->levels[l];
+    for (int dir = 0; dir < 2; ++dir) {
+      const bool fwd = dir == 0;
+      const int ext = fwd ? L.max_w : L.max_wr;
+      int best_kb = fwd ? L.kbf : L.kbb;
+      float best = 1e30f;
+      for (int kb = 1; kb <= kMaxColBlock; kb *= 2) {
+        if ((size_t)ext * kb * sizeof(double) > (size_t)kSolveSmemTune) break;
+        const float ms = time_level(fwd, c->fM, L, kb, c->Y, c->Y2, c->ldy, c->ldy, c->st,
+                                    &c->split, 3);
+        if (ms > 0.f && ms < best) {
+          best = ms;
+          best_kb = kb;
+        }
+      }
+      (fwd ? L.kbf : L.kbb) = best_kb;
+      c->level_tune_ms[2 * l + dir] = best < 1e29f ? best : -1.f;
+    }
+  }
+  if (cache) {
+    FILE* f = std::fopen(cache, "a");
+    if (f) {
+      std::fprintf(f, "%s ", key.c_str());
+      for (int l = 0; l < nlev; ++l) std::fprintf(f, "%d%d", c->levels[l].kbf, c->levels[l].kbb);
+      std::fprintf(f, "\n");
+      std::fclose(f);
+    }
+  }
 }
 
 void autotune_solve(matex_ctx* c) {
@@ -1909,6 +1979,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     delete c;
     return MATEX_ERR_OOM;
   }
+  if (o.solve_mode == 2 && o.col_block == 0) autotune_levels(c);
   if (o.solve_mode == 2) autotune_solve(c);
   {
     // Load, here, everything matex_solve_noalloc touches on this device: the
@@ -2153,6 +2224,24 @@ matex_status matex_get_autotune(matex_ctx* c, int32_t* ncols, int32_t* mode, flo
       const bool have = 2 * (size_t)i + 1 < c->tune_ms.size();
       ms[2 * i] = have ? c->tune_ms[2 * i] : -1.f;
       ms[2 * i + 1] = have ? c->tune_ms[2 * i + 1] : -1.f;
+    }
+  }
+  return MATEX_OK;
+}
+
+matex_status matex_get_level_blocks(matex_ctx* c, int32_t* kb_fwd, int32_t* kb_bwd, float* ms,
+                                    int32_t cap, int32_t* nlev) {
+  if (!c) return MATEX_ERR_ARG;
+  if (!nlev || cap < 0 || (cap > 0 && (!kb_fwd || !kb_bwd))) return fail(c, MATEX_ERR_ARG, "NULL argument");
+  const int L = (int)c->levels.size();
+  *nlev = L;
+  for (int l = 0; l < L && l < cap; ++l) {
+    kb_fwd[l] = c->levels[l].kbf;
+    kb_bwd[l] = c->levels[l].kbb;
+    if (ms) {
+      const bool tuned = c->level_tune_ms.size() == (size_t)(2 * L);
+      ms[2 * l] = tuned ? c->level_tune_ms[2 * l] : -1.f;
+      ms[2 * l + 1] = tuned ? c->level_tune_ms[2 * l + 1] : -1.f;
     }
   }
   return MATEX_OK;

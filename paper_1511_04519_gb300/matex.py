@@ -72,7 +72,7 @@ EXPORTS = ["matex_default_opts", "matex_setup", "matex_run", "matex_run_host", "
            "matex_debug_inject_wait", "matex_solve_noalloc", "matex_grad", "matex_set_caps",
            "matex_get_autotune", "matex_batch_create", "matex_batch_run", "matex_batch_last_error",
            "matex_batch_destroy", "matex_measure_fp64_peak", "matex_tr_run",
-           "matex_time_solve"]
+           "matex_time_solve", "matex_get_level_blocks"]
 
 
 def _load():
@@ -98,6 +98,8 @@ def _load():
     lib.matex_solve.restype = C.c_int
     lib.matex_solve_noalloc.argtypes = [P, C.c_int32, C.c_int32, P, P]
     lib.matex_solve_noalloc.restype = C.c_int
+    lib.matex_get_level_blocks.argtypes = [P, i32p, i32p, C.POINTER(C.c_float), C.c_int32, i32p]
+    lib.matex_get_level_blocks.restype = C.c_int
     lib.matex_time_solve.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_float),
                                      C.POINTER(C.c_float)]
     lib.matex_time_solve.restype = C.c_int
@@ -416,6 +418,21 @@ class Sim:
         _check(self.ctx, _lib.matex_time_solve(self.ctx, int(which), int(ncols), int(reps),
                                                C.byref(best), C.byref(mean)))
         return best.value, mean.value
+
+    def level_blocks(self):
+        """Per tree level: the column blocks of the forward and backward level
+        launches and their tuned times (matex_get_level_blocks)."""
+        n = C.c_int32()
+        _check(self.ctx, _lib.matex_get_level_blocks(self.ctx, None, None, None, 0, C.byref(n)))
+        L = n.value
+        f = np.zeros(L, np.int32)
+        b = np.zeros(L, np.int32)
+        ms = np.zeros(2 * L, np.float32)
+        _check(self.ctx, _lib.matex_get_level_blocks(
+            self.ctx, f.ctypes.data_as(C.POINTER(C.c_int32)), b.ctypes.data_as(C.POINTER(C.c_int32)),
+            ms.ctypes.data_as(C.POINTER(C.c_float)), L, C.byref(n)))
+        return [{"level": l, "kb_fwd": int(f[l]), "kb_bwd": int(b[l]),
+                 "fwd_ms": float(ms[2 * l]), "bwd_ms": float(ms[2 * l + 1])} for l in range(L)]
 
     def one_group_at_a_time(self, on=True):
         matex_set_batching(self.ctx, on)
