@@ -107,6 +107,17 @@ typedef struct matex_opts {
                               FP64 operands into 6-bit bf16 slices whose products the FP32
                               accumulators hold exactly (error of the order of an FP64 dot
                               product); 1: FP64 FMAs only */
+  int32_t decompose;       /* 0 (default): the groups as given (Sec. 3.1's bump groups);
+                              1: every group's input is split further into single ramps: on
+                              [0, T] a source is its value at t = 0 plus, at each of its
+                              breakpoints tau in [0, T), a ramp ds max(0, t - tau) (ds: change
+                              of slope at tau), and every (group, tau) becomes a column of its
+                              own (a group's non-zero starting values one more).  A ramp
+                              starts from zero state, so its Krylov basis needs no earlier
+                              segment and all ramps are independent; the responses sum to the
+                              same outputs.  Order of the columns (matex_get_m): by group,
+                              its constant part first, then its ramps by tau.  Requires
+                              group_select -1 and tape 0; new currents need a new context */
 } matex_opts;
 
 /* Counters and timings of the last matex_run (or of setup for the setup_* fields). */

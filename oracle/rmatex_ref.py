@@ -94,6 +94,81 @@ def full_input_vector(p, t, amp_scale=None):
     return u
 
 
+def _slope_right(ts, vs, x):
+    """Slope of a PWL waveform just right of x (0 before its first and from
+    its last breakpoint on: the value is held there)."""
+    if x < ts[0] or x >= ts[-1]:
+        return 0.0
+    j = int(np.searchsorted(ts, x, side="right")) - 1
+    return (vs[j + 1] - vs[j]) / (ts[j + 1] - ts[j])
+
+
+def _slope_left(ts, vs, x):
+    """Slope of a PWL waveform just left of x."""
+    if x <= ts[0] or x > ts[-1]:
+        return 0.0
+    j = int(np.searchsorted(ts, x, side="left")) - 1
+    return (vs[j + 1] - vs[j]) / (ts[j + 1] - ts[j])
+
+
+def ramp_decomposition(p):
+    """The decomposition of Sec. 3.1 carried down to single ramps.
+
+    On [0, T] a source's PWL input equals its value at t = 0 plus, for each of
+    its breakpoints tau in (0, T), the ramp ds * max(0, t - tau), ds the change
+    of slope at tau (slope right of tau minus slope left of it), plus a ramp at
+    tau = 0 with the slope right of 0.  Every (group, tau) pair becomes a group
+    of its own whose sources are those ramps (one per source of the group
+    whose slope changes at tau), so its only local transition spot inside
+    (0, T) is tau; a group whose sources start from non-zero values gets one
+    more group holding those constant values.  By superposition the groups'
+    responses sum to the original problem's.  A ramp starts from zero at tau
+    with x(tau) = 0, so its Krylov basis starts from w = G^{-1} C G^{-1} B ds,
+    which does not depend on any earlier state: all ramps are independent.
+
+    Group order: by original group, then its constant part, then ramps by
+    tau; sources of a new group in the original order.  Each ramp source's
+    PWL has the points (tau, 0) and (T, ds (T - tau))."""
+    import copy
+    T = sim_end(p)
+    entries = {}  # (k, kind, tau) -> list of (source, points)
+    for s in range(p.n_src):
+        o0, o1 = int(p.pwl_off[s]), int(p.pwl_off[s + 1])
+        ts = np.asarray(p.pwl_t[o0:o1], np.float64)
+        vs = np.asarray(p.pwl_v[o0:o1], np.float64)
+        k = int(p.src_group[s])
+        u0 = float(np.interp(0.0, ts, vs))
+        if u0 != 0.0:
+            entries.setdefault((k, 0, 0.0), []).append((s, [(0.0, u0)]))
+        s0 = _slope_right(ts, vs, 0.0)
+        if s0 != 0.0:
+            entries.setdefault((k, 1, 0.0), []).append((s, [(0.0, 0.0), (T, s0 * T)]))
+        for tau in ts:
+            tau = float(tau)
+            if not (0.0 < tau < T):
+                continue
+            ds = _slope_right(ts, vs, tau) - _slope_left(ts, vs, tau)
+            if ds != 0.0:
+                entries.setdefault((k, 1, tau), []).append((s, [(tau, 0.0), (T, ds * (T - tau))]))
+    node, off, tt, vv, grp = [], [0], [], [], []
+    for g, key in enumerate(sorted(entries)):
+        for s, pts in entries[key]:
+            node.append(int(p.src_node[s]))
+            grp.append(g)
+            for t, v in pts:
+                tt.append(t)
+                vv.append(v)
+            off.append(len(tt))
+    q = copy.copy(p)
+    q.src_node = np.asarray(node, np.int32)
+    q.pwl_off = np.asarray(off, np.int32)
+    q.pwl_t = np.asarray(tt, np.float64)
+    q.pwl_v = np.asarray(vv, np.float64)
+    q.src_group = np.asarray(grp, np.int32)
+    q.n_groups = len(entries)
+    return q
+
+
 def segment_outputs(lts, t_out):
     """For each segment [l_j, l_{j+1}] the output indices o with
     l_j < t_o <= l_{j+1} (an output on a breakpoint belongs to the segment

@@ -286,6 +286,82 @@ std::vector<double> group_lts(const std::vector<int32_t>& srcs, const int32_t* p
   return pts;
 }
 
+// Ramp decomposition (Sec. 3.1's source decomposition carried to single
+// ramps).  On [0, T] a PWL source equals its value at 0 plus, at each of its
+// breakpoints tau in (0, T), ds max(0, t - tau) with ds the change of slope
+// at tau, plus a ramp at tau = 0 with the slope right of 0.  Each (group,
+// kind, tau) with kind 0 = starting values, 1 = ramp becomes a group; groups
+// are ordered by (group, kind, tau), their sources by original index.  A
+// ramp source's PWL is (tau, 0), (T, ds (T - tau)); a starting value's is
+// (0, u(0)).
+struct RampProblem {
+  std::vector<int32_t> node, off, grp;
+  std::vector<double> t, v;
+  int32_t ngroups = 0;
+};
+
+double slope_right(const double* t, const double* v, int np, double x) {
+  if (x < t[0] || x >= t[np - 1]) return 0.0;
+  const int j = (int)(std::upper_bound(t, t + np, x) - t) - 1;
+  return (v[j + 1] - v[j]) / (t[j + 1] - t[j]);
+}
+
+double slope_left(const double* t, const double* v, int np, double x) {
+  if (x <= t[0] || x > t[np - 1]) return 0.0;
+  const int j = (int)(std::lower_bound(t, t + np, x) - t) - 1;
+  return (v[j + 1] - v[j]) / (t[j + 1] - t[j]);
+}
+
+void ramp_transform(int32_t n_src, const int32_t* src_node, const int32_t* pwl_off,
+                    const double* pwl_t, const double* pwl_v, const int32_t* src_group, double T,
+                    RampProblem& out) {
+  struct E {
+    int32_t k, kind;
+    double tau;
+    int32_t s;
+    int npts;
+    double t0, v0, t1, v1;
+  };
+  std::vector<E> es;
+  for (int32_t s = 0; s < n_src; ++s) {
+    const int o = pwl_off[s], np = pwl_off[s + 1] - o;
+    const double* t = pwl_t + o;
+    const double* v = pwl_v + o;
+    const int32_t k = src_group[s];
+    const double u0 = pwl_value(t, v, np, 0.0);
+    if (u0 != 0.0) es.push_back(E{k, 0, 0.0, s, 1, 0.0, u0, 0.0, 0.0});
+    const double s0 = slope_right(t, v, np, 0.0);
+    if (s0 != 0.0) es.push_back(E{k, 1, 0.0, s, 2, 0.0, 0.0, T, s0 * T});
+    for (int j = 0; j < np; ++j) {
+      const double tau = t[j];
+      if (!(tau > 0.0 && tau < T)) continue;
+      const double ds = slope_right(t, v, np, tau) - slope_left(t, v, np, tau);
+      if (ds != 0.0) es.push_back(E{k, 1, tau, s, 2, tau, 0.0, T, ds * (T - tau)});
+    }
+  }
+  std::stable_sort(es.begin(), es.end(), [](const E& a, const E& b) {
+    if (a.k != b.k) return a.k < b.k;
+    if (a.kind != b.kind) return a.kind < b.kind;
+    return a.tau < b.tau;
+  });
+  out = RampProblem();
+  out.off.push_back(0);
+  for (size_t i = 0; i < es.size(); ++i) {
+    const E& e = es[i];
+    if (i == 0 || e.k != es[i - 1].k || e.kind != es[i - 1].kind || e.tau != es[i - 1].tau)
+      out.ngroups++;
+    out.node.push_back(src_node[e.s]);
+    out.grp.push_back(out.ngroups - 1);
+    out.t.push_back(e.t0);
+    out.v.push_back(e.v0);
+    if (e.npts == 2) {
+      out.t.push_back(e.t1);
+      out.v.push_back(e.v1);
+    }
+    out.off.push_back((int32_t)out.t.size());
+  }
+}
+
 // Per tree level: forward tasks (supernode, 32 panel rows), backward tasks
 // (supernode, 32 panel columns) and the column block.  Returns false on an
 // allocation failure.
@@ -1612,6 +1688,9 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   if (!std::isfinite(o.tail_eps) || o.tail_eps < 0.0) return bad("tail_eps must be finite and >= 0");
   if (o.tape && o.tail_eps > 0.0) return bad("the adjoint tape follows exact runs only (tail_eps 0)");
   if (o.recombine < 0 || o.recombine > 1) return bad("recombine must be 0 or 1");
+  if (o.decompose < 0 || o.decompose > 1) return bad("decompose must be 0 or 1");
+  if (o.decompose == 1 && (o.tape || o.group_select >= 0))
+    return bad("decompose = 1 (ramps) needs tape = 0 and group_select = -1");
   if (o.col_block != 0 && o.col_block != 1 && o.col_block != 2 && o.col_block != 4 && o.col_block != 8)
     return bad("col_block must be 0, 1, 2, 4 or 8");
   if (o.group_select >= n_groups) return bad("group_select out of range");
@@ -1635,6 +1714,20 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   if (N < 1) { delete c; return bad("t_end / dt_out must be >= 1"); }
   c->n_times = N + 1;
   c->T = (double)N * dt_out;
+  RampProblem ramps;
+  if (o.decompose == 1 && n_src > 0) {
+    // from here on the problem is the ramp-decomposed one
+    ramp_transform(n_src, src_node, pwl_off, pwl_t, pwl_v, src_group, c->T, ramps);
+    n_src = (int32_t)ramps.node.size();
+    src_node = ramps.node.data();
+    pwl_off = ramps.off.data();
+    pwl_t = ramps.t.data();
+    pwl_v = ramps.v.data();
+    src_group = ramps.grp.data();
+    n_groups = ramps.ngroups;
+    c->n_src = n_src;
+    c->n_groups = n_groups;
+  }
   if (o.n_rows > 0) c->rows.assign(o.rows, o.rows + o.n_rows);
   c->nrows_out = o.n_rows > 0 ? o.n_rows : (int32_t)n;
   c->opts.rows = nullptr;
@@ -1872,6 +1965,20 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   c->nchunks = (int)((n + kChunk - 1) / kChunk);
   const size_t G = (size_t)std::max(n_groups, 1);
   c->n_records = (int64_t)h_group.size();
+  if (ok && o.decompose == 1) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const double need = 8.0 * (double)G * (kMaxB + 4.0) * (double)n;
+    if (need > 0.9 * (double)free_b) {
+      char msg[256];
+      std::snprintf(msg, sizeof(msg),
+                    "decompose = 1: %d ramps need %.1f GB of Krylov bases and states, %.1f GB free",
+                    (int)G, need / 1e9, (double)free_b / 1e9);
+      g_setup_err = msg;
+      delete c;
+      return MATEX_ERR_OOM;
+    }
+  }
   if (ok && o.tape == 2) {
     // what the run itself holds, then the plan within most of the rest
     size_t free_b = 0, total_b = 0;
@@ -2074,6 +2181,8 @@ static matex_status check_sources(matex_ctx* c, const double* pwl_v_host) {
 matex_status matex_set_sources(matex_ctx* c, const double* pwl_v_host) {
   if (!c) return MATEX_ERR_ARG;
   if (!pwl_v_host) return fail(c, MATEX_ERR_ARG, "pwl_v is NULL");
+  if (c->opts.decompose == 1)
+    return fail(c, MATEX_ERR_STATE, "decompose = 1 (ramps): set up a new context for new currents");
   matex_status cs = check_sources(c, pwl_v_host);
   if (cs != MATEX_OK) return cs;
   cudaMemcpyAsync(c->pwl_v_d, pwl_v_host, sizeof(double) * c->pwl_v_host_shape.size(),
@@ -2086,6 +2195,8 @@ matex_status matex_run_host(matex_ctx* c, const double* pwl_v_host, double* x_ou
                             matex_stats* stats) {
   if (!c) return MATEX_ERR_ARG;
   if (!x_out_host) return fail(c, MATEX_ERR_ARG, "x_out_host is NULL");
+  if (pwl_v_host && c->opts.decompose == 1)
+    return fail(c, MATEX_ERR_STATE, "decompose = 1 (ramps): set up a new context for new currents");
   const size_t bytes = sizeof(double) * (size_t)c->n_times * c->nrows_out;
   if (pwl_v_host) {
     matex_status cs = check_sources(c, pwl_v_host);

@@ -34,7 +34,7 @@ class MatexOpts(C.Structure):
                 ("max_width", C.c_int32), ("strict", C.c_int32), ("solve_mode", C.c_int32),
                 ("tape", C.c_int32), ("krylov", C.c_int32), ("graph", C.c_int32),
                 ("tail_eps", C.c_double), ("tape_window", C.c_int32), ("tape_block", C.c_int32),
-                ("recombine", C.c_int32)]
+                ("recombine", C.c_int32), ("decompose", C.c_int32)]
 
 
 class MatexStats(C.Structure):
@@ -322,7 +322,7 @@ class Sim:
     def __init__(self, p, col_block=0, group_select=-1, include_dc=True, rows=None,
                  replay_m=None, max_width=0, strict=False, stream=None, solve_mode=2,
                  tape=False, graph=True, krylov="R", tail_eps=0.0, tape_window=0, tape_block=0,
-                 recombine="auto", **overrides):
+                 recombine="auto", decompose="groups", **overrides):
         o = matex_default_opts()
         o.graph = int(bool(graph))
         o.tail_eps = float(tail_eps)
@@ -336,6 +336,7 @@ class Sim:
         o.solve_mode = int(solve_mode)
         o.tape = {False: 0, True: 1, 0: 0, 1: 1, 2: 2, "full": 1, "checkpoint": 2}[tape]
         o.recombine = {"auto": 0, "tensor": 0, "fp64": 1}[recombine]
+        o.decompose = {"groups": 0, "ramps": 1}[decompose]
         o.tape_window = int(tape_window)
         o.tape_block = int(tape_block)
         self._keep = []

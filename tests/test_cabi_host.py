@@ -130,7 +130,9 @@ def test_setup_rejects_bad_inputs_before_gpu(lib, mutation):
 @pytest.mark.parametrize("field,value", [("tail_eps", -1e-9), ("tail_eps", float("nan")),
                                          ("tail_eps", float("inf")), ("krylov", 3),
                                          ("solve_mode", 5), ("tape_tail", 1e-9),
-                                         ("tape_krylov", 1)])
+                                         ("tape_krylov", 1), ("decompose", 2),
+                                         ("decompose_tape", 1), ("recombine", 2),
+                                         ("tape", 3), ("tape_window", -1)])
 def test_setup_rejects_bad_options_before_gpu(lib, field, value):
     """Option checks run on the host before any device work: the status is
     MATEX_ERR_ARG with a message, on a machine without a GPU as well."""
@@ -141,6 +143,8 @@ def test_setup_rejects_bad_options_before_gpu(lib, field, value):
         o.tape, o.tail_eps = 1, value
     elif field == "tape_krylov":
         o.tape, o.krylov = 1, value
+    elif field == "decompose_tape":
+        o.tape, o.decompose = 1, value
     else:
         setattr(o, field, value)
     st, msg = _setup_status(lib, p, opts=C.byref(o))
@@ -175,4 +179,4 @@ def test_default_options_layout():
     assert bytes(buf[size:]) == b"\xa5" * 64
     assert M.MatexOpts.from_buffer(buf).tail_eps == 0.0
     assert C.sizeof(M.MatexStats) == 3 * 8 + 8 + 4 * 12 + 8 + 4 * 4 + 8 + 8 + 4 * 2 + 8
-    assert (o.tape_window, o.tape_block, o.recombine) == (0, 0, 0)
+    assert (o.tape_window, o.tape_block, o.recombine, o.decompose) == (0, 0, 0, 0)

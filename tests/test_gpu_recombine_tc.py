@@ -44,7 +44,7 @@ def both_paths(M, p, **kw):
 @pytest.mark.parametrize("seed", [0, 1])
 def test_ragged_tiles_match_fp64_and_oracle(M, seed):
     # 37 x 29 x 2 = 2146 nodes (16 full tiles of 128 + 98), 201 outputs (4 tiles of 48 + 9)
-    p = gridgen.small_mesh(40 + seed, nx=37, ny=29, layers=2, n_src=40,
+    p = gridgen.small_mesh(40 + seed, nx=37, ny=29, layers=2, n_src=48,
                            group_templates=[2, 3, 1, 4, 2, 3, 1, 2, 3, 2] * 2, t_end=2e-9,
                            dt_out=10e-12)
     Xa, Xb, sim = both_paths(M, p)
