@@ -24,7 +24,7 @@ __global__ void input_rhs_kernel(double* __restrict__ Y, int ldy, int K, RoundCo
                                  SourceTable src) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= K) return;
-  const int g = rc.group[q];
+  const int g = rc.sgroup ? rc.sgroup[q] : rc.group[q];
   const double l0 = rc.l0[q], L = rc.len[q], l1 = l0 + L;
   for (int p = src.grp_ptr[g]; p < src.grp_ptr[g + 1]; ++p) {
     const int s = src.grp_src[p];

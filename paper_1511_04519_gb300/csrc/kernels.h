@@ -147,7 +147,10 @@ struct RoundCols {
   const int32_t* nout;     // outputs in the segment
   const int64_t* segid;    // global (group, segment) index
   const int32_t* abort = nullptr;  // device flag or null: set, the recombination exits at once
+  const int32_t* sgroup = nullptr; // group whose sources drive the column (group holds its
+                                   // state slot; the two differ only for batched ramps)
 };
+constexpr int kRampBatch = 256;  // ramp columns per batch when there are more
 
 struct SourceTable {
   const int32_t* grp_ptr;  // [n_groups+1] into grp_src

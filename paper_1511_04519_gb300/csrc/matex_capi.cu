@@ -113,6 +113,16 @@ struct matex_ctx {
   double* CK = nullptr;
   std::vector<int32_t> h_group_all;
   std::vector<Round> rounds;          // batched: segment r of every group per round
+  // Batches of groups run one after another, each with its own rounds and
+  // initial states; per-group state and basis slots are reused from batch to
+  // batch (state slot = rc_group, source group = rc_sgroup).  One batch with
+  // slot = group except for ramp columns beyond kRampBatch, which hand no
+  // state to later segments.
+  struct Batch { int32_t r0, r1, i0, ni; };  // rounds [r0, r1), initial states [i0, i0 + ni)
+  std::vector<Batch> batches;
+  int32_t g_slots = 1;                // per-group state and basis slots
+  int32_t* rc_sgroup = nullptr;
+  int32_t* init_slots_d = nullptr;    // state slot of each entry of init_groups
   std::vector<Round> serial_rounds;   // one group at a time: one column per round
   bool serial = false;
   std::vector<int32_t> serial_cover;
@@ -636,6 +646,7 @@ RoundCols round_cols(matex_ctx* c, const Round& r) {
   rc.obeg = c->rc_obeg + r.begin;
   rc.nout = c->rc_nout + r.begin;
   rc.segid = c->rc_segid + r.begin;
+  rc.sgroup = c->rc_sgroup + r.begin;
   rc.abort = c->d_count + 2;
   return rc;
 }
@@ -1020,36 +1031,49 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
   }
   // per-run state starts at zero: x, z, z' of every group, the segment records
   {
-    const size_t gb = sizeof(double) * (size_t)std::max(c->n_groups, 1) * (size_t)n;
+    const size_t gb = sizeof(double) * (size_t)c->g_slots * (size_t)n;
     cudaMemsetAsync(c->Xb, 0, gb, st);
     cudaMemsetAsync(c->Zb, 0, gb, st);
     cudaMemsetAsync(c->Zpb, 0, gb, st);
     cudaMemsetAsync(c->m_rec, 0, sizeof(int32_t) * std::max<int64_t>(1, c->n_segments), st);
     cudaMemsetAsync(c->st_rec, 0, sizeof(int32_t) * std::max<int64_t>(1, c->n_segments), st);
   }
+  matex_status s = MATEX_OK;
+  const std::vector<Round>& rounds = c->serial ? c->serial_rounds : c->rounds;
+  const size_t nbatch = c->serial ? 1 : c->batches.size();
+  for (size_t bi = 0; bi < nbatch; ++bi) {
+  const int r0 = c->serial ? 0 : c->batches[bi].r0;
+  const int r1 = c->serial ? (int)rounds.size() : c->batches[bi].r1;
+  const int i0 = c->serial ? 0 : c->batches[bi].i0;
+  const int ng = c->serial ? (int)c->init_groups.size() : c->batches[bi].ni;
+  if (bi > 0) {
+    // the batch's groups take over the previous batch's state slots
+    const size_t gb = sizeof(double) * (size_t)c->g_slots * (size_t)n;
+    cudaMemsetAsync(c->Xb, 0, gb, st);
+    cudaMemsetAsync(c->Zb, 0, gb, st);
+    cudaMemsetAsync(c->Zpb, 0, gb, st);
+  }
   // each group's own DC state at t = 0 (Alg. 2's local initial solution); groups with
   // zero input at t = 0 start from x = 0
-  const int ng = (int)c->init_groups.size();
   for (int g0 = 0; g0 < ng; g0 += c->ldy) {
     const int K = std::min(c->ldy, ng - g0);
     e = prof_begin(c);
-    build_initial_rhs(c->Y, c->ldy, K, c->src, c->init_groups_d + g0, n, st);
+    build_initial_rhs(c->Y, c->ldy, K, c->src, c->init_groups_d + i0 + g0, n, st);
     prof_end(c, e, P_OTHER, 2, 0.0, 8.0 * nd * c->ldy);
     launches += 2;
     solve(c->fG, K);
     sweepsG++;
     e = prof_begin(c);
-    scatter_cols(c->Y, c->ldy, K, c->Xb, n, c->init_groups_d + g0, nullptr, n, st);
+    scatter_cols(c->Y, c->ldy, K, c->Xb, n, c->init_slots_d + i0 + g0, nullptr, n, st);
     moved(e, 1, K, false);
     e = prof_begin(c);
     add_row_sum(c->Xp, c->Y, c->ldy, K, n, st);
     prof_end(c, e, P_OTHER, 1, nd * K, 8.0 * nd * (K + 2));
     launches++;
   }
-  matex_status s = cuda_check(c, "initial states");
+  s = cuda_check(c, "initial states");
   if (s != MATEX_OK) return s;
-  const std::vector<Round>& rounds = c->serial ? c->serial_rounds : c->rounds;
-  for (size_t ri = 0; ri < rounds.size(); ++ri) {
+  for (size_t ri = (size_t)r0; ri < (size_t)r1; ++ri) {
     const Round& r = rounds[ri];
     const int K = r.K;
     RoundCols rc = round_cols(c, r);
@@ -1180,6 +1204,7 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
     prof_end(c, e, P_OTHER, 2, 0.0, 0.0);
     launches += 4;
     if ((s = cuda_check(c, "round")) != MATEX_OK) return s;
+  }
   }
   pc.launches = launches;
   pc.sweepsM = sweepsM;
@@ -1496,7 +1521,7 @@ matex_status recompute_window(matex_ctx* c, int w, int r0, int r1, const std::ve
 matex_status run_grad(matex_ctx* c, const double* xbar, double* dc, double* damp) {
   cudaStream_t st = c->st;
   const int64_t n = c->n;
-  const int G = std::max(c->n_groups, 1);
+  const int G = c->g_slots;
   const int nrows = c->nrows_out;
   // Krylov dimension per record, from the forward's per-segment record
   std::vector<int32_t> mseg(std::max<int64_t>(1, c->n_segments)), mrec(c->n_records);
@@ -1820,19 +1845,46 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   c->gsrc_h = gsrc;
   c->pwl_off_h.assign(pwl_off, pwl_off + n_src + 1);
   c->pwl_t_h.assign(pwl_t, pwl_t + pwl_off[n_src]);
-  std::vector<int32_t> h_group, h_seg, h_obeg, h_nout;
+  std::vector<int32_t> h_group, h_sgroup, h_seg, h_obeg, h_nout;
   std::vector<double> h_l0, h_len, h_hfirst, h_lprev;
   std::vector<int64_t> h_segid;
   int Kmax = 1;
-  for (size_t r = 0; r < max_segs; ++r) {
+  const int nsel = (int)per_group.size();
+  int bsize = std::max(nsel, 1);
+  if (o.decompose == 1 && nsel > kRampBatch) {
+    // ramp columns in batches whose state and basis slots fit in memory
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const double per_slot = 8.0 * (kMaxB + 4.0) * (double)n;
+    bsize = (int)std::min<double>(kRampBatch, std::max(8.0, 0.35 * (double)free_b / per_slot));
+    bsize = std::max(8, bsize & ~7);
+  }
+  std::vector<int32_t> init_slots;
+  std::vector<int32_t> init_src;
+  for (int b0 = 0; b0 < nsel; b0 += bsize) {
+    const int b1 = std::min(nsel, b0 + bsize);
+    matex_ctx::Batch bt;
+    bt.r0 = (int32_t)c->rounds.size();
+    bt.i0 = (int32_t)init_src.size();
+    for (int k = b0; k < b1; ++k)
+      if (c->ginit_h[k]) {
+        init_src.push_back(c->sel_groups[k]);
+        init_slots.push_back(bsize < nsel ? k - b0 : c->sel_groups[k]);
+      }
+    bt.ni = (int32_t)init_src.size() - bt.i0;
+    size_t bmax = 0;
+    for (int k = b0; k < b1; ++k) bmax = std::max(bmax, per_group[k].size());
+  for (size_t r = 0; r < bmax; ++r) {
     Round rd;
     rd.begin = (int32_t)h_group.size();
     rd.obeg_min = c->n_times;
     rd.oend_max = 0;
-    for (auto& segs : per_group) {
+    for (int k = b0; k < b1; ++k) {
+      const std::vector<Seg>& segs = per_group[k];
       if (r >= segs.size() || segs[r].zero) continue;
       const Seg& sg = segs[r];
-      h_group.push_back(sg.g);
+      h_group.push_back(bsize < nsel ? k - b0 : sg.g);
+      h_sgroup.push_back(sg.g);
       h_seg.push_back(sg.j);
       h_obeg.push_back(sg.obeg);
       h_nout.push_back(sg.nout);
@@ -1850,6 +1902,11 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     Kmax = std::max(Kmax, rd.K);
     if (rd.K > 0) c->rounds.push_back(rd);
   }
+    bt.r1 = (int32_t)c->rounds.size();
+    c->batches.push_back(bt);
+  }
+  c->g_slots = bsize < nsel ? bsize : std::max(n_groups, 1);
+  init_groups = init_src;
   c->init_groups = init_groups;
   c->Kmax = Kmax;
   c->h_nout_all = h_nout;
@@ -1868,7 +1925,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   {
     std::vector<std::vector<int32_t>> by_group(n_groups);
     for (const Round& rd : c->rounds)
-      for (int q = 0; q < rd.K; ++q) by_group[h_group[rd.begin + q]].push_back(rd.begin + q);
+      for (int q = 0; q < rd.K; ++q) by_group[h_sgroup[rd.begin + q]].push_back(rd.begin + q);
     for (int32_t g = 0; g < n_groups; ++g)
       for (int32_t rec : by_group[g]) {
         Round one;
@@ -1946,6 +2003,8 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   }
   ok = ok && c->upload(c->sel_groups_d, c->sel_groups.data(), c->sel_groups.size());
   ok = ok && c->upload(c->init_groups_d, c->init_groups.data(), c->init_groups.size());
+  ok = ok && c->upload(c->init_slots_d, init_slots.data(), init_slots.size());
+  ok = ok && c->upload(c->rc_sgroup, h_sgroup.data(), h_sgroup.size());
   std::vector<int32_t> h_vslot(h_group.size());
   for (size_t r = 0; r < h_group.size(); ++r) h_vslot[r] = o.tape == 1 ? (int32_t)r : h_group[r];
   ok = ok && c->upload(c->rc_vslot, h_vslot.data(), h_vslot.size());
@@ -1963,7 +2022,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   c->ldy = roundup8(std::max({Kmax, 8, std::min<int>(n_groups, 256)}));
   ok = ok && plan_levels(c);
   c->nchunks = (int)((n + kChunk - 1) / kChunk);
-  const size_t G = (size_t)std::max(n_groups, 1);
+  const size_t G = (size_t)c->g_slots;
   c->n_records = (int64_t)h_group.size();
   if (ok && o.decompose == 1) {
     size_t free_b = 0, total_b = 0;
@@ -2310,6 +2369,8 @@ matex_status matex_get_sizes(matex_ctx* c, int32_t* n_times, int32_t* n_rows, in
 }
 
 matex_status matex_set_batching(matex_ctx* c, int32_t one_group_at_a_time) {
+  if (c && one_group_at_a_time && c->batches.size() > 1)
+    return fail(c, MATEX_ERR_STATE, "one group at a time is not available for batched ramp columns");
   if (!c) return MATEX_ERR_ARG;
   const bool serial = one_group_at_a_time != 0;
   if (serial != c->serial) drop_graph(c);  // another launch sequence

@@ -77,3 +77,18 @@ def test_ramps_refuse_new_currents(M):
     with pytest.raises(M.MatexError) as ei:
         sim.set_sources(np.asarray(p.pwl_v) * 2.0)
     assert ei.value.status == 7  # MATEX_ERR_STATE
+
+
+def test_ramp_columns_in_batches_match_oracle(M):
+    """100 single-template groups give 300 ramp columns, more than one batch
+    of 256: the second batch reuses the first one's state and basis slots
+    (ramps hand no state to later segments)."""
+    p = gridgen.small_mesh(35, nx=20, ny=20, layers=2, n_src=100, group_templates=[1] * 100,
+                           t_end=0.5e-9, dt_out=5e-12)
+    rows = np.sort(np.random.default_rng(35).choice(p.n, 40, replace=False)).astype(np.int32)
+    q = R.ramp_decomposition(p)
+    assert q.n_groups > 256
+    err, sim = ramp_parity(M, p, "ramps_two_batches", rows=rows)
+    assert err <= TOL_V * p.vdd
+    with pytest.raises(M.MatexError):
+        sim.one_group_at_a_time(True)
