@@ -435,6 +435,8 @@ def main():
     ap.add_argument("--no-serial", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-tr", action="store_true")
+    ap.add_argument("--no-ramps", action="store_true",
+                    help="skip the ramp-decomposition run of the bench grid")
     ap.add_argument("--no-tail", action="store_true",
                     help="skip the separately reported tail-skipping run (tail_eps > 0)")
     ap.add_argument("--other-configs", action="store_true",
@@ -701,8 +703,38 @@ def main():
             del sv, xv
         torch.cuda.empty_cache()
 
+    # the paper's source decomposition carried to single ramps (opts.decompose
+    # = 1): every ramp's basis in one batched round, no segment chain; same
+    # superposed outputs (to the Krylov tolerance), timed like the headline
+    ramps = None
+    if not args.no_ramps:
+        sim.run(out)
+        xr = out.clone()
+        sr = M.Sim(p, stream=stream, decompose="ramps")
+        xq = torch.empty_like(out)
+        for _ in range(args.warmup):
+            sr.run(xq)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            sr.run(xq)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_r = ev0.elapsed_time(ev1) / args.steps
+        st_r = sr.stats.as_dict()
+        ramps = {"ms_per_step": ms_r, "value": world * units / (ms_r / 1e3), "unit": UNIT,
+                 "speedup_vs_groups": ms / ms_r, "columns": int(sr.n_segments),
+                 "rounds": st_r["rounds"], "solve_columns": st_r["solve_columns"],
+                 "sum_m": st_r["sum_m"], "graph_replay": st_r["graph_replay"],
+                 "max_abs_diff_vs_groups_v": float((xq - xr).abs().max()),
+                 "note": "both decompositions meet tol = 1e-7 V per Krylov segment"}
+        del sr, xq, xr
+        torch.cuda.empty_cache()
+
     # adjoint: the same grid with 256 observed nodes, IR-drop hinge loss; cost
-    # of matex_grad relative to the forward run that taped it
+    # of matex_grad relative to the forward run that keeps what it needs:
+    # checkpoints of x and z per segment round (segments recomputed in the
+    # reverse sweep), and the full tape of every basis for comparison
     adjoint = None
     if not args.no_adjoint:
         from paper_1511_04519_gb300 import autograd as AG
@@ -710,29 +742,34 @@ def main():
         torch.cuda.empty_cache()
         p3 = gridgen.config3(seed=gridgen.SEED_BASE + 1 + 1000 * rank)
         obs = p3.observed.astype(np.int32)
-        sim3 = AG.make_sim(p3, obs, include_dc=False, stream=stream)
-        X3 = sim3.run()
-        theta = float(torch.quantile((-X3).flatten(), 0.9))
-        Xr = X3.detach().clone().requires_grad_(True)
-        AG.hinge_ir_drop_loss(Xr, 0.0, theta, p3.dt_out).backward()
-        xbar = Xr.grad.detach()
-        f_ms, g_ms = [], []
-        for it in range(args.warmup + args.steps):
-            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            e0.record(stream)
-            sim3.run(X3)
-            e1.record(stream)
-            sim3.grad(xbar)
-            e2.record(stream)
-            torch.cuda.synchronize()
-            if it >= args.warmup:
-                f_ms.append(e0.elapsed_time(e1))
-                g_ms.append(e1.elapsed_time(e2))
-        fm, gm = sum(f_ms) / len(f_ms), sum(g_ms) / len(g_ms)
         adjoint = {"workload": "mesh2x300x300_256_observed_nodes_hinge_loss",
-                   "params": {"caps": p3.n, "amplitudes": p3.n_src},
-                   "forward_taped_ms": fm, "grad_ms": gm, "grad_over_forward": gm / fm}
-        del sim3
+                   "params": {"caps": p3.n, "amplitudes": p3.n_src}}
+        for mode in ("checkpoint", "full"):
+            sim3 = AG.make_sim(p3, obs, include_dc=False, stream=stream, tape=mode)
+            X3 = sim3.run()
+            theta = float(torch.quantile((-X3).flatten(), 0.9))
+            Xr = X3.detach().clone().requires_grad_(True)
+            AG.hinge_ir_drop_loss(Xr, 0.0, theta, p3.dt_out).backward()
+            xbar = Xr.grad.detach()
+            f_ms, g_ms = [], []
+            for it in range(args.warmup + args.steps):
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+                sim3.run(X3)
+                e1.record(stream)
+                sim3.grad(xbar)
+                e2.record(stream)
+                torch.cuda.synchronize()
+                if it >= args.warmup:
+                    f_ms.append(e0.elapsed_time(e1))
+                    g_ms.append(e1.elapsed_time(e2))
+            fm, gm = sum(f_ms) / len(f_ms), sum(g_ms) / len(g_ms)
+            st3 = sim3.setup_stats()
+            adjoint[mode] = {"forward_ms": fm, "grad_ms": gm, "grad_over_forward": gm / fm,
+                             "tape_bytes": st3["tape_bytes"], "tape_window": st3["tape_window"],
+                             "tape_block": st3["tape_block"]}
+            del sim3, X3, Xr, xbar
+            torch.cuda.empty_cache()
 
     grids = batch_grids(args, M, stream) if args.grids else None
     others = other_configs(M, stream) if args.other_configs else None
@@ -750,7 +787,8 @@ def main():
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "sptrsv": sptrsv, "one_group_at_a_time": serial,
             "cpu_baseline": cpu, "adjoint": adjoint, "trapezoidal": trap,
-            "krylov_variants": variants, "tail_skip": tail, "work_model": wm,
+            "krylov_variants": variants, "tail_skip": tail, "ramp_decomposition": ramps,
+            "work_model": wm,
             "profile_ms_per_step": ms_prof,
             "profile": {k: {kk: v[kk] / args.steps for kk in ("ms", "launches", "flops", "bytes")}
                         for k, v in prof.items()},

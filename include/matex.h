@@ -148,6 +148,8 @@ typedef struct matex_stats {
   int32_t tape_block;      /*   block as set up (0 otherwise) */
   int64_t tape_bytes;      /* device bytes of the adjoint's tape (tape 1) or of its checkpoints,
                               window tape and reverse work buffers (tape 2) */
+  int32_t tc_rounds;       /* segment rounds of the last run whose V y ran on the tensor cores */
+  int32_t reserved0;
 } matex_stats;
 
 void matex_default_opts(matex_opts* opts);

@@ -516,12 +516,22 @@ __device__ __forceinline__ Chunk level_chunk(int ncb, int nchunk, const SplitScr
   return ch;
 }
 
+// Level launches are chained with programmatic dependent launch: each lets
+// the next level's grid be scheduled as soon as all of its own CTAs run
+// (launch_dependents), and waits for the previous grid to complete and its
+// writes to be visible (griddepcontrol.wait) before reading anything.
+__device__ __forceinline__ void level_chain_wait() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 template <int KB>
 __global__ void __launch_bounds__(kSolveThreads, 8)
 fwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, int nchunk,
                  SplitScratch sp, double* __restrict__ Y, double* __restrict__ Y2, int ldy) {
   extern __shared__ double sb[];
   __shared__ PackDesc pd;
+  level_chain_wait();
   if (F.abort && *F.abort) return;
   int task, cb;
   const Chunk ch = level_chunk(ncb, nchunk, sp, task, cb);
@@ -534,6 +544,7 @@ bwd_level_kernel(DevFactor F, const int2* __restrict__ tasks, int ncb, int nchun
                  SplitScratch sp, double* __restrict__ Y, const double* __restrict__ Y2, int ldy) {
   extern __shared__ double ub[];
   __shared__ PackDesc pd;
+  level_chain_wait();
   if (F.abort && *F.abort) return;
   int task, cb;
   const Chunk ch = level_chunk(ncb, nchunk, sp, task, cb);
@@ -701,12 +712,22 @@ void launch_level(bool fwd, const DevFactor& F, const LevelPlan& L, double* Y, d
   }
   const unsigned grid = (unsigned)((long long)tasks * ncb * nchunk);
   if (grid == 0) return;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kSolveThreads);
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   if (fwd) {
-    const size_t smem = std::max((size_t)L.max_w * KB, part) * sizeof(double);
-    fwd_level_kernel<KB><<<grid, kSolveThreads, smem, st>>>(F, L.ftasks, ncb, nchunk, sp, Y, Y2, ldy);
+    cfg.dynamicSmemBytes = std::max((size_t)L.max_w * KB, part) * sizeof(double);
+    cudaLaunchKernelEx(&cfg, fwd_level_kernel<KB>, F, L.ftasks, ncb, nchunk, sp, Y, Y2, ldy);
   } else {
-    const size_t smem = std::max((size_t)L.max_wr * KB, part) * sizeof(double);
-    bwd_level_kernel<KB><<<grid, kSolveThreads, smem, st>>>(F, L.btasks, ncb, nchunk, sp, Y, Y2, ldy);
+    cfg.dynamicSmemBytes = std::max((size_t)L.max_wr * KB, part) * sizeof(double);
+    cudaLaunchKernelEx(&cfg, bwd_level_kernel<KB>, F, L.btasks, ncb, nchunk, sp, Y,
+                       (const double*)Y2, ldy);
   }
 }
 

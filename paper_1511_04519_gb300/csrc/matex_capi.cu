@@ -53,7 +53,7 @@ matex_status noalloc_scratch(int dev, void** out, std::string& err);
 
 // Launch and sweep counts of one pass of the run.
 struct PassCounts {
-  int launches = 0, sweepsM = 0, sweepsG = 0;
+  int launches = 0, sweepsM = 0, sweepsG = 0, tc_rounds = 0;
   int64_t solve_cols = 0;
 };
 
@@ -1189,6 +1189,7 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
       // V y on the tensor cores, then the -P terms alone in FP64
       rl += recombine_tc(c->Xp, n, c->Vb, vstride, rc, c->ss.m, c->coef, c->n_times, K, kdim,
                          r.obeg_min, r.oend_max, c->tc, st);
+      pc.tc_rounds++;
       recombine(c->Xp, n, c->n_times, c->Vb, vstride, c->Zb, c->Zpb, c->Wb, n, rc, c->m_zero,
                 c->coef, c->n_times, K, r.obeg_min, r.oend_max, c->dt_out, st, nullptr);
     } else {
@@ -1282,6 +1283,7 @@ matex_status finish_run(matex_ctx* c, const PassCounts& pc, double t0, bool repl
     if (stt[i] == 2) o.breakdowns++;
   }
   o.sweeps_M = pc.sweepsM;
+  o.tc_rounds = pc.tc_rounds;
   o.sweeps_G = pc.sweepsG;
   o.solve_columns = pc.solve_cols;
   o.kernel_launches = pc.launches + 1;  // + the output permutation

@@ -47,7 +47,7 @@ class MatexStats(C.Structure):
                 ("kernel_launches", C.c_int32), ("rounds", C.c_int32),
                 ("graph_replay", C.c_int32), ("graph_capture_ms", C.c_double),
                 ("nnz_L_exact", C.c_int64), ("tape_window", C.c_int32), ("tape_block", C.c_int32),
-                ("tape_bytes", C.c_int64)]
+                ("tape_bytes", C.c_int64), ("tc_rounds", C.c_int32), ("reserved0", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -178,5 +178,5 @@ def test_default_options_layout():
     M._lib.matex_default_opts(C.cast(buf, C.POINTER(M.MatexOpts)))
     assert bytes(buf[size:]) == b"\xa5" * 64
     assert M.MatexOpts.from_buffer(buf).tail_eps == 0.0
-    assert C.sizeof(M.MatexStats) == 3 * 8 + 8 + 4 * 12 + 8 + 4 * 4 + 8 + 8 + 4 * 2 + 8
+    assert C.sizeof(M.MatexStats) == 3 * 8 + 8 + 4 * 12 + 8 + 4 * 4 + 8 + 8 + 4 * 2 + 8 + 8
     assert (o.tape_window, o.tape_block, o.recombine, o.decompose) == (0, 0, 0, 0)

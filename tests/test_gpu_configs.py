@@ -79,16 +79,17 @@ class _StoredOracle:
 
 def test_uneven_groups_full_size_against_stored_oracle(M):
     """The four-layer 600x600 grid (1.44M nodes; nnz(L) ~ 1.9e8, supernodes
-    thousands of nodes wide): two groups against the oracle at 32 nodes (16
-    random, 16 on the central line of every layer, where the top separators
-    lie) and every output time, from tests/golden (written by the committed
-    script beside it, which calls only the oracle); and the solves with both
-    factors at 1, 8 and 64 right-hand sides against the sparse matrices."""
+    thousands of nodes wide): two groups against the oracle at their load
+    nodes and 32 more (16 random, 16 on the central line of every layer, where
+    the top separators lie), every output time, from tests/golden (written by
+    the committed script beside it, which calls only the oracle); and the
+    solves with both factors at 1, 8 and 64 right-hand sides against the
+    sparse matrices."""
     import os
     import torch
     import scipy.sparse as sp
     ref = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
-                               "mesh4x600x600_2groups_32rows.npz"))
+                               "mesh4x600x600_2groups.npz"))
     p = gridgen.config2()
     rows = ref["rows"].astype(np.int32)
     for gi, g in enumerate(ref["groups"].tolist()):
@@ -99,7 +100,7 @@ def test_uneven_groups_full_size_against_stored_oracle(M):
         err = check_adaptive(f"mesh4x600x600_group{g}_32rows", p, X, sim.m_sequence(), stored,
                              lambda m: M.Sim(p, replay_m=m, **kw).run().cpu().numpy())
         assert err <= TOL_V * p.vdd
-        assert np.abs(ref["X"][gi]).max() > 1e-4  # the group's loads do move these nodes
+        assert np.abs(ref["X"][gi]).max() > 1e-4  # the group's loads move their own nodes
         if gi == 0:
             rng = np.random.default_rng(2)
             for which in (0, 1):

@@ -36,8 +36,10 @@ def M():
 def both_paths(M, p, **kw):
     a = M.Sim(p, **kw)
     Xa = a.run().cpu().numpy()
+    assert a.stats.tc_rounds > 0
     b = M.Sim(p, recombine="fp64", replay_m=a.m_sequence(), **kw)
     Xb = b.run().cpu().numpy()
+    assert b.stats.tc_rounds == 0
     return Xa, Xb, a
 
 
@@ -96,7 +98,7 @@ def test_bench_grid_matches_fp64_recombination(M):
     a = M.Sim(p)
     Xa = a.run()
     a.run(Xa)
-    assert a.stats.graph_replay == 1
+    assert a.stats.graph_replay == 1 and a.stats.tc_rounds == a.stats.rounds
     b = M.Sim(p, recombine="fp64", replay_m=a.m_sequence())
     Xb = b.run()
     diff = float((Xa - Xb).abs().max())
