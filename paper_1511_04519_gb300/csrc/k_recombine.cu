@@ -183,6 +183,47 @@ __global__ void next_state_kernel(double* __restrict__ X, const double* __restri
   X[g * gstride + i] = s;
 }
 
+// The -P terms of a round alone, X[o] += sum over the columns whose segment
+// holds o of z + (t_o - l_j) z' - w = (z - w - l_j z') + t_o z'.  Which
+// columns hold o changes only where a column's output range starts or ends:
+// one thread per node sweeps the outputs in order, keeping the two running
+// sums A = sum (z - w - l_j z') and B = sum z' of the columns holding o and
+// updating them at those events (sorted by output: ev_o; ev_q = q + 1 when
+// column q enters, -(q + 1) when it leaves).  Each column's z, z', w are read
+// once per node, not once per output tile.
+__global__ void __launch_bounds__(128)
+recombine_p_kernel(double* __restrict__ Xp, int64_t n, const double* __restrict__ Z,
+                   const double* __restrict__ Zp, const double* __restrict__ W, int64_t gstride,
+                   RoundCols rc, const int32_t* __restrict__ ev_o, const int32_t* __restrict__ ev_q,
+                   int nev, int o_begin, int o_end, double dt_out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || (rc.abort && *rc.abort)) return;
+  double A = 0.0, B = 0.0;
+  int active = 0, e = 0;
+  for (int o = o_begin; o < o_end; ++o) {
+    for (; e < nev && ev_o[e] <= o; ++e) {
+      const int qs = ev_q[e];
+      const int q = (qs > 0 ? qs : -qs) - 1;
+      const int64_t g = rc.group[q];
+      const double zp = Zp[g * gstride + i];
+      const double a = fma(-rc.l0[q], zp, Z[g * gstride + i] - W[g * gstride + i]);
+      if (qs > 0) {
+        A += a;
+        B += zp;
+        active++;
+      } else {
+        A -= a;
+        B -= zp;
+        active--;
+      }
+    }
+    if (active > 0) {
+      double* x = Xp + (int64_t)o * n + i;
+      *x += fma((double)o * dt_out, B, A);
+    }
+  }
+}
+
 // Checkpoint of column q: CK[q] = {X[group q], Z[group q]} (save), or back (restore).
 __global__ void checkpoint_kernel(double* __restrict__ CK, double* __restrict__ X,
                                   double* __restrict__ Z, const int32_t* __restrict__ groups,
@@ -257,6 +298,14 @@ void next_state(double* X, const double* Vbase, int64_t vstride, const double* Z
   if (K <= 0) return;
   dim3 grid((unsigned)((n + 255) / 256), (unsigned)K);
   next_state_kernel<<<grid, 256, 0, st>>>(X, Vbase, vstride, Z, Zp, W, gstride, rc, mcol, yend, n);
+}
+
+void recombine_p(double* Xp, int64_t n, const double* Z, const double* Zp, const double* W,
+                 int64_t gstride, const RoundCols& rc, const int32_t* ev_o, const int32_t* ev_q,
+                 int nev, int o_begin, int o_end, double dt_out, cudaStream_t st) {
+  if (nev <= 0 || o_end <= o_begin) return;
+  recombine_p_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(Xp, n, Z, Zp, W, gstride, rc, ev_o,
+                                                                  ev_q, nev, o_begin, o_end, dt_out);
 }
 
 void checkpoint_states(double* CK, double* X, double* Z, const int32_t* groups, int K, int64_t n,

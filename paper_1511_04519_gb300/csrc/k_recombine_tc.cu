@@ -10,18 +10,19 @@
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication and its applications", Numer. Algorithms 59, 2012):
 //
-//   * every row i of V is scaled by a power of two 2^e_i >= max_k |V[i][k]|
-//     and cut into S = 9 slices of 6 bits, V[i][k] = 2^e_i sum_p a_p 64^-(p+1)
-//     with integers a_0 in [-64, 64], a_p in [-32, 32] (p >= 1), exact in bf16;
-//     every column o of Y likewise with 2^f_o and integers b_q;
+//   * every row i of V is scaled by a power of two 2^e_i > max_k |V[i][k]|
+//     and cut into S = 9 base-64 digits, V[i][k] = 2^e_i sum_p a_p 64^-(p+1)
+//     with a_p = sign(V[i][k]) d_p, d_p in [0, 63] the digits of the
+//     magnitude (truncated after the ninth), exact in bf16; every column o of
+//     Y likewise with 2^f_o and digits b_q;
 //   * C_d = sum_{p+q=d} A_p B_q (d = 0..8) on the tensor cores: each product
-//     of two slices is at most 2^12, so a sum over at most 455 basis vectors
-//     and up to nine slice pairs stays below 2^24, an integer that the FP32
+//     of two digits is below 2^12, so a sum over at most 455 basis vectors
+//     and up to nine digit pairs stays below 2^24, an integer that the FP32
 //     accumulator holds exactly (no assumption on its rounding);
 //   * X = 2^(e_i + f_o - 12) sum_d 64^-d C_d, combined in 64-bit integers and
-//     converted to FP64 once.  The pairs with p + q > 8 are left out: they
-//     are below 2^-54 of max|V[i][:]| max|Y[:][o]| per term, the size of the
-//     rounding of an FP64 dot product.
+//     converted to FP64 once.  The digits past the ninth and the pairs with
+//     p + q > 8 are left out: together below 2^-52 of max|V[i][:]|
+//     max|Y[:][o]| per term, the size of the rounding of an FP64 dot product.
 //
 // Kernels: tc_kmap (basis-vector table of the round), tc_split_rows (V
 // slices in the MMA tile layout), tc_split_cols (Y slices), tc_gemm (bulk
@@ -56,15 +57,16 @@ __device__ __forceinline__ int tc_off(int r, int k) {
   return (r >> 3) * kTcSbo + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-// The nine 6-bit slices of r in (-1, 1): r = sum_p s[p] 64^-(p+1) + O(2^-55).
+// The nine base-64 digits of r in (-1, 1), signed like r:
+// r = sum_p s[p] 64^-(p+1) + e, |e| < 2^-54.  |r| 2^54 is scaled exactly (a
+// power of two) and truncated to an integer below 2^54 once; the digits are
+// its 6-bit fields, taken with integer operations (the FP64 pipe does one
+// multiply and one conversion per value).
 __device__ __forceinline__ void slice9(double r, float (&s)[kTcS]) {
+  const unsigned long long q = __double2ull_rz(fabs(r) * 0x1p54);
+  const float sg = r < 0.0 ? -1.f : 1.f;
 #pragma unroll
-  for (int p = 0; p < kTcS; ++p) {
-    r *= 64.0;
-    const double a = rint(r);
-    s[p] = (float)a;
-    r -= a;  // exact: |r - a| <= 1/2 and both are multiples of the same ulp
-  }
+  for (int p = 0; p < kTcS; ++p) s[p] = sg * (float)(unsigned)((q >> (6 * (kTcS - 1 - p))) & 63ull);
 }
 
 // Power of two 2^e with max < 2^e (1 for max = 0).

@@ -299,6 +299,15 @@ int recombine_tc(double* Xp, int64_t n, const double* Vbase, int64_t vstride, co
                  const int32_t* mcol, const double* coef, int ldo, int K, int kdim, int obeg_min,
                  int oend_max, const TcScratch& ts, cudaStream_t st);
 
+// The -P terms z + h z' - w of a round's columns at their outputs, added into
+// Xp by one sweep over the outputs per node; events ev_o / ev_q (nev, sorted
+// by output) mark where a column's output range starts (q + 1) or ends (-(q + 1)).
+void recombine_p(double* Xp, int64_t n, const double* Z, const double* Zp, const double* W,
+                 int64_t gstride, const RoundCols& rc, const int32_t* ev_o, const int32_t* ev_q,
+                 int nev, int o_begin, int o_end, double dt_out, cudaStream_t st);
+constexpr double kTcMinCover = 0.25;  // least share of a round's (column, output) pairs its
+                                      // columns cover for the dense tensor-core product to pay
+
 // Adjoint checkpoints: CK[q] = {X[groups[q]], Z[groups[q]]} ([K][2][n]), or the
 // reverse copy when restore is set (X, Z per group, [G][n]).
 void checkpoint_states(double* CK, double* X, double* Z, const int32_t* groups, int K, int64_t n,

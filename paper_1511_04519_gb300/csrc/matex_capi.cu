@@ -45,6 +45,8 @@ struct Round {
   int32_t begin;  // first column record
   int32_t K;      // columns
   int32_t obeg_min, oend_max;
+  double cover = 0.0;          // share of (column, output) pairs of the range the columns hold
+  int32_t ev_begin = 0, nev = 0;  // -P events of the round (recombine_p)
 };
 
 // Device address of the allocation-free solve's static scratch array on
@@ -79,7 +81,7 @@ struct matex_ctx {
   std::vector<LevelPlan> levels;
   SplitScratch split;              // chunked reductions of the level launches
   TcScratch tc;                    // tensor-core recombination (kdim_cap 0: not used)
-  int32_t* m_zero = nullptr;       // [Kmax] zeros: the FP64 recombination with -P terms only
+  int32_t *ev_o_d = nullptr, *ev_q_d = nullptr;  // -P events of all rounds
   // persistent solve: per column count (1..ldy) one PersistLevel row per level
   PersistLevel* plev_d = nullptr;
   std::vector<long long> pf_total, pb_total;   // per column count
@@ -1185,13 +1187,16 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
     prof_end(c, e, P_SMALL, 1, 0.0, 0.0);
     e = prof_begin(c);
     int rl = 1;
-    if (c->tc.kdim_cap && teps == 0.0 && kdim >= kTcMinKdim && kdim <= c->tc.kdim_cap) {
-      // V y on the tensor cores, then the -P terms alone in FP64
+    if (c->tc.kdim_cap && teps == 0.0 && kdim >= kTcMinKdim && kdim <= c->tc.kdim_cap &&
+        r.cover >= kTcMinCover) {
+      // V y on the tensor cores (a dense product over the round's output
+      // range, worth it when the columns hold most of that range), then the
+      // -P terms alone in one sweep over the outputs
       rl += recombine_tc(c->Xp, n, c->Vb, vstride, rc, c->ss.m, c->coef, c->n_times, K, kdim,
                          r.obeg_min, r.oend_max, c->tc, st);
       pc.tc_rounds++;
-      recombine(c->Xp, n, c->n_times, c->Vb, vstride, c->Zb, c->Zpb, c->Wb, n, rc, c->m_zero,
-                c->coef, c->n_times, K, r.obeg_min, r.oend_max, c->dt_out, st, nullptr);
+      recombine_p(c->Xp, n, c->Zb, c->Zpb, c->Wb, n, rc, c->ev_o_d + r.ev_begin,
+                  c->ev_q_d + r.ev_begin, r.nev, r.obeg_min, r.oend_max, c->dt_out, st);
     } else {
       recombine(c->Xp, n, c->n_times, c->Vb, vstride, c->Zb, c->Zpb, c->Wb, n, rc, c->ss.m, c->coef,
                 c->n_times, K, r.obeg_min, r.oend_max, c->dt_out, st,
@@ -1914,13 +1919,35 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   c->h_nout_all = h_nout;
   c->h_segid_all = h_segid;
   c->h_group_all = h_group;
-  for (const Round& rd : c->rounds) {
+  std::vector<int32_t> ev_o_h, ev_q_h;
+  for (Round& rd : c->rounds) {
     std::vector<char> cov(c->n_times, 0);
     int cnt = 0;
-    for (int q = 0; q < rd.K; ++q)
-      for (int o = h_obeg[rd.begin + q]; o < h_obeg[rd.begin + q] + h_nout[rd.begin + q]; ++o)
+    double held = 0.0;
+    std::vector<std::pair<int32_t, int32_t>> ev;
+    for (int q = 0; q < rd.K; ++q) {
+      const int ob = h_obeg[rd.begin + q], no = h_nout[rd.begin + q];
+      held += no;
+      if (no > 0) {
+        ev.push_back({ob, q + 1});
+        ev.push_back({ob + no, -(q + 1)});
+      }
+      for (int o = ob; o < ob + no; ++o)
         if (!cov[o]) { cov[o] = 1; cnt++; }
+    }
     c->round_cover.push_back(cnt);
+    const int span = rd.oend_max - rd.obeg_min;
+    rd.cover = span > 0 ? held / ((double)rd.K * span) : 0.0;
+    std::stable_sort(ev.begin(), ev.end(),
+                     [](const std::pair<int32_t, int32_t>& a, const std::pair<int32_t, int32_t>& b) {
+                       return a.first < b.first;
+                     });
+    rd.ev_begin = (int32_t)ev_o_h.size();
+    rd.nev = (int32_t)ev.size();
+    for (const auto& x : ev) {
+      ev_o_h.push_back(x.first);
+      ev_q_h.push_back(x.second);
+    }
   }
   c->offd_rows = c->S.sup_rowptr[c->S.nsup] - c->S.n;
   // the same column records, one group at a time in time order
@@ -2007,6 +2034,8 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   ok = ok && c->upload(c->init_groups_d, c->init_groups.data(), c->init_groups.size());
   ok = ok && c->upload(c->init_slots_d, init_slots.data(), init_slots.size());
   ok = ok && c->upload(c->rc_sgroup, h_sgroup.data(), h_sgroup.size());
+  ok = ok && c->upload(c->ev_o_d, ev_o_h.data(), ev_o_h.size()) &&
+       c->upload(c->ev_q_d, ev_q_h.data(), ev_q_h.size());
   std::vector<int32_t> h_vslot(h_group.size());
   for (size_t r = 0; r < h_group.size(); ++r) h_vslot[r] = o.tape == 1 ? (int32_t)r : h_group[r];
   ok = ok && c->upload(c->rc_vslot, h_vslot.data(), h_vslot.size());
@@ -2130,9 +2159,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
       double *rsc = nullptr, *csc = nullptr;
       const size_t ncol = ((size_t)c->n_times + 47) / 48 * 48;
       if (c->alloc(sl, tc_slices_bytes(n, cap, c->n_times)) && c->alloc(km, cap) &&
-          c->alloc(kq, cap) && c->alloc(rsc, n) && c->alloc(csc, ncol) &&
-          c->alloc(c->m_zero, Kmax) &&
-          cudaMemset(c->m_zero, 0, sizeof(int32_t) * Kmax) == cudaSuccess) {
+          c->alloc(kq, cap) && c->alloc(rsc, n) && c->alloc(csc, ncol)) {
         c->tc = TcScratch{sl, km, kq, rsc, csc, c->d_count + 1, cap};
         tc_set_limits();
       } else {

@@ -98,7 +98,9 @@ def test_bench_grid_matches_fp64_recombination(M):
     a = M.Sim(p)
     Xa = a.run()
     a.run(Xa)
-    assert a.stats.graph_replay == 1 and a.stats.tc_rounds == a.stats.rounds
+    # the long tails on the tensor cores; the rise and fall rounds (each column
+    # holding a few outputs of a wide range) stay on the FP64 kernel
+    assert a.stats.graph_replay == 1 and 1 <= a.stats.tc_rounds < a.stats.rounds
     b = M.Sim(p, recombine="fp64", replay_m=a.m_sequence())
     Xb = b.run()
     diff = float((Xa - Xb).abs().max())
