@@ -387,22 +387,27 @@ def batch_grids(args, M, stream):
     return res
 
 
-def other_configs(M, stream):
+def other_configs(M, stream, ramps_large=False):
     """One recorded run, then one timed graph replay, of the single-group
     1,024-node grid (about 190 sequential segments) and of the four-layer
-    1.44M-node grid with 256 uneven groups (64 sampled output rows)."""
+    1.44M-node grid with 256 uneven groups (64 sampled output rows), and with
+    ramps_large the same 1.44M-node grid decomposed into ramps (25,600
+    columns in batches of 256)."""
     import numpy as np
     import torch
 
     import gridgen
     res = {}
-    for name, p, nrows in (("grid32x32_1group", gridgen.config0(), 0),
-                           ("mesh4x600x600_256groups", gridgen.config2(), 64)):
+    cases = [("grid32x32_1group", gridgen.config0(), 0, "groups"),
+             ("mesh4x600x600_256groups", gridgen.config2(), 64, "groups")]
+    if ramps_large:
+        cases.append(("mesh4x600x600_256groups_ramps", gridgen.config2(), 64, "ramps"))
+    for name, p, nrows, dec in cases:
         rows = None
         if nrows:
             rows = np.sort(np.random.default_rng(0).choice(p.n, nrows, replace=False)).astype(np.int32)
         t0 = time.perf_counter()
-        sim = M.Sim(p, rows=rows, stream=stream)
+        sim = M.Sim(p, rows=rows, stream=stream, decompose=dec)
         setup_s = time.perf_counter() - t0
         x = sim.run()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -416,7 +421,9 @@ def other_configs(M, stream):
                      "value": p.n * (p.n_out - 1) * p.n_groups / (ms / 1e3), "unit": UNIT,
                      "setup_s": setup_s, "graph_replay": st["graph_replay"],
                      "rounds": st["rounds"], "solve_columns": st["solve_columns"],
-                     "nonconv": st["nonconv"], "nnz_L": st["nnz_L"]}
+                     "nonconv": st["nonconv"], "nnz_L": st["nnz_L"],
+                     "nnz_L_exact": st["nnz_L_exact"], "tc_rounds": st["tc_rounds"],
+                     "decompose": dec, "sum_m": st["sum_m"]}
         del sim, x
         torch.cuda.empty_cache()
     return res
@@ -442,6 +449,8 @@ def main():
     ap.add_argument("--other-configs", action="store_true",
                     help="also time one graph-replayed run of the 1,024-node single-group grid "
                          "and of the 1.44M-node 256-group grid (several minutes)")
+    ap.add_argument("--ramps-large", action="store_true",
+                    help="with --other-configs, also the 1.44M-node grid as ramps")
     ap.add_argument("--variants", action="store_true",
                     help="also run the inverted (I-MATEX) and standard (MEXP) Krylov spaces "
                          "on the bench grid (Table 1's comparison)")
@@ -772,7 +781,7 @@ def main():
             torch.cuda.empty_cache()
 
     grids = batch_grids(args, M, stream) if args.grids else None
-    others = other_configs(M, stream) if args.other_configs else None
+    others = other_configs(M, stream, args.ramps_large) if args.other_configs else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
