@@ -781,8 +781,8 @@ TapePlan plan_tape(const std::vector<Round>& rounds, int64_t n, int G, int Kmax,
 
 // Autotuner: for column counts 1, 2, 4, ..., ldy, time the batched solve with
 // one persistent launch and with one launch per tree level (CUDA events, best
-// of three after a warm-up) and keep the faster one for every column count up
-// to the next measured one.  The choice depends on the factor's tree (how
+// of five after a warm-up) and keep level launches unless the persistent one
+// is at least 10 % faster, for every column count up to the next measured one.  The choice depends on the factor's tree (how
 // many levels, how much work per level) and on the GPU, so it is measured
 // rather than fixed.  An optional cache file (MATEX_AUTOTUNE_CACHE) keyed by
 // the factor's shape and the device name avoids re-measuring.
@@ -905,7 +905,7 @@ void autotune_solve(matex_ctx* c) {
       for (int mode = 0; mode < 2; ++mode) {
         c->opts.solve_mode = mode;
         solve_cols(c, c->fM, r);
-        for (int rep = 0; rep < 3; ++rep) {
+        for (int rep = 0; rep < 5; ++rep) {
           cudaEventRecord(e0, c->st);
           solve_cols(c, c->fM, r);
           cudaEventRecord(e1, c->st);
@@ -915,7 +915,10 @@ void autotune_solve(matex_ctx* c) {
           best[mode] = std::min(best[mode], ms);
         }
       }
-      c->tune_modes.push_back(best[1] < best[0] ? 1 : 0);
+      // one persistent launch only when clearly faster: the two modes' times
+      // differ by a few percent from process to process, and level launches
+      // are the better-tested path (and the one the column-block tuner tuned)
+      c->tune_modes.push_back(best[0] < 0.9f * best[1] ? 0 : 1);
       c->tune_ms.push_back(best[0]);
       c->tune_ms.push_back(best[1]);
     }

@@ -230,7 +230,8 @@ def test_autotuner_measures_both_modes(M):
     assert [t["ncols"] for t in tab][:4] == [1, 2, 4, 8]
     for t in tab:
         assert t["mode"] in (0, 1) and t["persistent_ms"] > 0 and t["level_ms"] > 0
-        assert t["mode"] == (1 if t["level_ms"] < t["persistent_ms"] else 0)
+        # level launches unless the persistent one is at least 10 % faster
+        assert t["mode"] == (0 if t["persistent_ms"] < 0.9 * t["level_ms"] else 1)
 
 
 def test_m_max_one_and_replay(M):
