@@ -118,6 +118,17 @@ typedef struct matex_opts {
                               same outputs.  Order of the columns (matex_get_m): by group,
                               its constant part first, then its ramps by tau.  Requires
                               group_select -1 and tape 0; new currents need a new context */
+  int32_t resident;        /* segment rounds on small grids: 0 (default) chosen at setup, 1 off,
+                              2 on.  A resident round runs each column's whole segment (input
+                              solutions, Arnoldi with its residual test, output coefficients,
+                              next state) in one CTA, both triangular substitutions level by
+                              level in its shared memory; only the recombination is a launch of
+                              its own.  Possible when n <= 8192 (and 16 n + 34 KB fit one CTA's
+                              shared memory), krylov 0 or 1, tape 0 and tail_eps 0; 2 returns
+                              MATEX_ERR_ARG otherwise.  With 0 the setup times one such solve
+                              pair against the batched path's single-column pair and takes the
+                              resident rounds when they are at most twice as long (they also
+                              replace the ~12 other launches of every Arnoldi step) */
 } matex_opts;
 
 /* Counters and timings of the last matex_run (or of setup for the setup_* fields). */
@@ -149,7 +160,7 @@ typedef struct matex_stats {
   int64_t tape_bytes;      /* device bytes of the adjoint's tape (tape 1) or of its checkpoints,
                               window tape and reverse work buffers (tape 2) */
   int32_t tc_rounds;       /* segment rounds of the last run whose V y ran on the tensor cores */
-  int32_t reserved0;
+  int32_t resident;        /* 1: the segment rounds run as resident rounds (opts.resident) */
 } matex_stats;
 
 void matex_default_opts(matex_opts* opts);
@@ -288,11 +299,25 @@ matex_status matex_set_sources(matex_ctx* ctx, const double* pwl_v_host);
 matex_status matex_solve(matex_ctx* ctx, int32_t which, int32_t ncols, const double* b, double* x);
 
 /*
+ * The same solves through the resident rounds' substitution: one CTA per
+ * right-hand side runs both triangular sweeps level by level in its shared
+ * memory (one launch for all ncols, no atomics: results reproducible bit for
+ * bit).  which, ncols, b, x as for matex_solve (device, [ncols][n], original
+ * order; may alias).  MATEX_ERR_STATE when the context was set up without
+ * it (n > 8192 or the CTA's shared memory too small, krylov 2, tape,
+ * tail_eps > 0 or resident = 1).
+ */
+matex_status matex_solve_resident(matex_ctx* ctx, int32_t which, int32_t ncols, const double* b,
+                                  double* x);
+
+/*
  * Device time of the bare batched solve pair (forward and backward
  * substitution of Alg. 1's operator apply, Sec. 3.3.2) on the context's own
  * column buffer, without the moves matex_solve adds around it (no
  * counterpart in the paper; the measurement behind the solve's roofline):
- * which as for matex_solve; 1 <= ncols <= the buffer width (the largest
+ * which as for matex_solve, or 2 and 3 for the same factors through the
+ * resident substitution (one CTA per column; MATEX_ERR_STATE without it);
+ * 1 <= ncols <= the buffer width (the largest
  * segment round, rounded up to 8, at least 8); one warm-up, then reps timed
  * solves with CUDA events on the context's stream, in the launch mode the
  * context uses for ncols.  *best_ms receives the fastest, *mean_ms (may be

@@ -24,7 +24,7 @@ GENCODE = "arch=compute_103a,code=sm_103a"
 def _sources():
     cu = sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
     cpp = sorted(f for f in os.listdir(CSRC) if f.endswith(".cpp"))
-    hdr = sorted(f for f in os.listdir(CSRC) if f.endswith(".h"))
+    hdr = sorted(f for f in os.listdir(CSRC) if f.endswith((".h", ".cuh")))
     return cu, cpp, hdr
 
 
@@ -80,7 +80,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                 print(o)
     objs = [o for _, o in jobs]
     tmp = LIB + ".tmp"
-    _run([nvcc, "-shared", "-gencode", GENCODE, "-o", tmp] + objs + ["-lcudart", "-lpthread"])
+    # --no-undefined: a declared but missing function fails here, not at load time
+    _run([nvcc, "-shared", "-gencode", GENCODE, "-o", tmp] + objs +
+         ["-lcudart", "-lpthread", "-Xlinker", "--no-undefined"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -5,20 +5,11 @@
 // Sec. 3.3.3 and the coefficient vectors ||v|| e^{h H_m} e_1 at the output
 // times of a segment (Alg. 2, "snapshots" reuse the basis).
 #include "kernels.h"
-#include "small_dense.cuh"
+#include "column_steps.cuh"
 
 namespace matex {
 
 namespace {
-
-__device__ __forceinline__ double pwl_eval(const double* t, const double* v, int np, double x) {
-  if (x <= t[0]) return v[0];
-  if (x >= t[np - 1]) return v[np - 1];
-  int j = 0;
-  while (j + 1 < np && t[j + 1] <= x) ++j;
-  const double slope = (v[j + 1] - v[j]) / (t[j + 1] - t[j]);
-  return slope * (x - t[j]) + v[j];
-}
 
 __global__ void input_rhs_kernel(double* __restrict__ Y, int ldy, int K, RoundCols rc,
                                  SourceTable src) {
@@ -215,67 +206,12 @@ __global__ void reduce_dots_kernel(const double* __restrict__ partials, int nchu
   }
 }
 
-using SD = Small<kMaxM>;
-using ExpmWork = SD::Work;
-constexpr int kLd = SD::kLd;
-constexpr int kMat = SD::kMat;
-
-__device__ __forceinline__ void expm_dev(const double* M, double h, double* E, int m, ExpmWork& w) {
-  SD::expm(M, h, E, m, w);
-}
-__device__ __forceinline__ void rational_H(const double* Ht, int m, double gamma, double* H,
-                                           ExpmWork& w, int variant) {
-  SD::rational_H(Ht, m, gamma, H, w, variant);
-}
-
-struct SmallShared {
-  ExpmWork w;
-  double H[kMat];
-  double E[kMat];
-  double y[kMaxM], y2[kMaxM];
-  int flag;
-};
-
 __global__ void __launch_bounds__(kSmallThreads)
 residual_kernel(SmallState ss, RoundCols rc, const int32_t* __restrict__ iter, int j, double gamma,
                 double tol, int m_max, const int32_t* __restrict__ replay) {
   extern __shared__ double smem_raw[];
   SmallShared& sh = *reinterpret_cast<SmallShared*>(smem_raw);
-  const int q = iter[blockIdx.x];
-  const int m = j + 1;
-  const double* Ht = ss.Ht + (int64_t)q * kMaxB * kMaxM;
-  const double hnext = Ht[m * kMaxM + (m - 1)];
-  if (threadIdx.x == 0) {
-    ss.m[q] = m;
-    int st = 0;
-    if (hnext <= 1e-13 * fabs(Ht[0])) st = 2;  // happy breakdown (h_11 < 0 for A itself)
-    else if (replay) st = (replay[rc.segid[q]] <= m) ? 1 : 0;
-    sh.flag = st;
-  }
-  __syncthreads();
-  if (sh.flag != 0 || replay) {
-    if (threadIdx.x == 0) {
-      int st = sh.flag;
-      if (st == 0 && m >= m_max) st = 3;
-      ss.status[q] = st;
-    }
-    return;
-  }
-  rational_H(Ht, m, gamma, sh.H, sh.w, ss.krylov);
-  const double L = rc.len[q];
-  const double hc = fmin(rc.hfirst[q], L);
-  double rmax = 0.0;
-  for (int pass = 0; pass < 2; ++pass) {
-    expm_dev(sh.H, pass == 0 ? hc : L, sh.E, m, sh.w);
-    // r = ||v|| |s h_{m+1,m} e_m^T e^{hH} e_1|, s making h_{m+1,m} dimensionless
-    rmax = fmax(rmax, ss.beta[q] * fabs(ss.rscale * hnext) * fabs(sh.E[(m - 1) * kLd + 0]));
-  }
-  if (threadIdx.x == 0) {
-    int st = 0;
-    if (rmax < tol) st = 1;
-    else if (m >= m_max) st = 3;
-    ss.status[q] = st;
-  }
+  residual_column(ss, rc, iter[blockIdx.x], j, gamma, tol, m_max, replay, sh);
 }
 
 __global__ void compact_kernel(SmallState ss, const int32_t* __restrict__ groups,
@@ -307,66 +243,7 @@ coef_kernel(SmallState ss, RoundCols rc, double gamma, double dt_out, double* __
             int32_t* __restrict__ tcut) {
   extern __shared__ double smem_raw[];
   SmallShared& sh = *reinterpret_cast<SmallShared*>(smem_raw);
-  const int q = blockIdx.x;
-  const int m = ss.m[q];
-  const int no = rc.nout[q];
-  double* cq = coef + (int64_t)q * ldo * kCoefLd;
-  // tail cut (thread 0): outputs up to the last one whose ||y||_2 exceeds
-  // tail_eps/2 keep V y; a NaN norm or bound counts as large
-  const bool cut = pbound != nullptr && tail_eps > 0.0;
-  const double e2 = 0.25 * tail_eps * tail_eps;
-  int last = -1;
-  auto put_cut = [&]() {
-    if (tcut == nullptr || threadIdx.x != 0) return;
-    tcut[2 * q] = cut ? last + 1 : no;
-    tcut[2 * q + 1] =
-        cut && pbound[2 * q] + rc.len[q] * pbound[2 * q + 1] <= 0.5 * tail_eps ? 1 : 0;
-  };
-  auto note_norm = [&](int o) {
-    if (!cut || threadIdx.x != 0) return;
-    double s = 0.0;
-    for (int k = 0; k < m; ++k) s = fma(sh.y[k], sh.y[k], s);
-    if (!(s <= e2)) last = o;
-  };
-  // step of the -P term at every output: h = t_o - l_j with t_o = o * dt_out
-  for (int o = threadIdx.x; o < no; o += blockDim.x)
-    cq[(int64_t)o * kCoefLd + kMaxM] = (double)(rc.obeg[q] + o) * dt_out - rc.l0[q];
-  if (m <= 0 || no <= 0) {
-    put_cut();
-    if (m <= 0) return;
-  }
-  const double* Ht = ss.Ht + (int64_t)q * kMaxB * kMaxM;
-  const double beta = ss.beta[q];
-  rational_H(Ht, m, gamma, sh.H, sh.w, ss.krylov);
-  // segment end
-  expm_dev(sh.H, rc.len[q], sh.E, m, sh.w);
-  for (int i = threadIdx.x; i < m; i += blockDim.x) yend[(int64_t)q * kMaxM + i] = beta * sh.E[i * kLd];
-  if (no <= 0) return;
-  __syncthreads();
-  // first output, then the propagator e^{dt H} for the equally spaced rest
-  expm_dev(sh.H, rc.hfirst[q], sh.E, m, sh.w);
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    sh.y[i] = beta * sh.E[i * kLd];
-    cq[i] = sh.y[i];
-  }
-  __syncthreads();
-  note_norm(0);
-  if (no > 1) {
-    expm_dev(sh.H, dt_out, sh.E, m, sh.w);
-    for (int o = 1; o < no; ++o) {
-      for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < m; ++k) s = fma(sh.E[i * kLd + k], sh.y[k], s);
-        sh.y2[i] = s;
-        cq[(int64_t)o * kCoefLd + i] = s;
-      }
-      __syncthreads();
-      for (int i = threadIdx.x; i < m; i += blockDim.x) sh.y[i] = sh.y2[i];
-      __syncthreads();
-      note_norm(o);
-    }
-  }
-  put_cut();
+  coef_column(ss, rc, blockIdx.x, gamma, dt_out, coef, ldo, yend, tail_eps, pbound, tcut, sh);
 }
 
 __global__ void __launch_bounds__(kSmallThreads)

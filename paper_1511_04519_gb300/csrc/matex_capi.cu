@@ -80,6 +80,12 @@ struct matex_ctx {
   Symbolic S;
   std::vector<LevelPlan> levels;
   SplitScratch split;              // chunked reductions of the level launches
+  // resident rounds (opts.resident): per-level work lists, the choice, and
+  // the setup's timings of one solve pair both ways (ms, -1 if not taken)
+  ResidentPlan rplan;
+  bool resident_ok = false;  // plan built and shared-memory limits set
+  bool resident = false;
+  float res_pair_ms = -1.f, lvl_pair_ms = -1.f;
   TcScratch tc;                    // tensor-core recombination (kdim_cap 0: not used)
   int32_t *ev_o_d = nullptr, *ev_q_d = nullptr;  // -P events of all rounds
   // persistent solve: per column count (1..ldy) one PersistLevel row per level
@@ -606,6 +612,89 @@ bool plan_levels(matex_ctx* c) {
   return true;
 }
 
+// Work lists of the resident rounds (see ResidentPlan): per tree level,
+// leaves first, the forward rows and backward columns supernode by
+// supernode (consecutive threads read consecutive panel entries); the
+// level's below-diagonal rows numbered by target row, contributions in
+// supernode order; per level and direction the lanes per dot product.
+bool plan_resident(matex_ctx* c, int threads) {
+  const Symbolic& S = c->S;
+  const int nlev = (int)S.level_ptr.size() - 1;
+  if (nlev > kResidentMaxLevels) return false;
+  std::vector<ResRow> frow;
+  std::vector<ResCol> bc;
+  std::vector<int32_t> offs(kResOffN * (nlev + 1), 0), ftgt, fpp;
+  struct Upd { int32_t t, ord; size_t at; };
+  std::vector<Upd> up;
+  int uslots = 0;
+  auto lanes = [&](int items, int longest) {
+    // one pass over the level when possible, no more lanes than the longest
+    // dot product has groups of eight terms
+    int l = 1;
+    while (l < 8 && items * (2 * l) <= threads && 8 * l < longest) l *= 2;
+    return l;
+  };
+  for (int l = 0; l < nlev; ++l) {
+    const int r0 = (int)frow.size();
+    offs[kResOffR * (nlev + 1) + l] = r0;
+    offs[kResOffT * (nlev + 1) + l] = (int32_t)ftgt.size();
+    offs[kResOffC * (nlev + 1) + l] = (int32_t)bc.size();
+    up.clear();
+    int fmax = 1, bmax = 1;
+    for (int k = S.level_ptr[l]; k < S.level_ptr[l + 1]; ++k) {
+      const int s = S.level_sups[k];
+      const int f = S.sup_first[s];
+      const int w = S.sup_first[s + 1] - f;
+      const int64_t rp = S.sup_rowptr[s];
+      const int ld = (int)(S.sup_rowptr[s + 1] - rp);
+      const int64_t po = S.pan_off[s];
+      for (int i = 0; i < ld; ++i) {
+        frow.push_back(ResRow{po + i, f, i < w ? f + i : 0, i < w ? i + 1 : w, ld});
+        if (i >= w) up.push_back(Upd{S.sup_rows[rp + i], (int32_t)up.size(), frow.size() - 1});
+      }
+      for (int j = 0; j < w; ++j) bc.push_back(ResCol{po + j, rp, f, j, w, ld});
+      fmax = std::max(fmax, w);
+      bmax = std::max(bmax, ld);
+    }
+    std::sort(up.begin(), up.end(), [](const Upd& x, const Upd& y) {
+      return x.t != y.t ? x.t < y.t : x.ord < y.ord;
+    });
+    // target j takes the slots from the previous target's end (0 for the
+    // level's first) to fpp[j]
+    for (size_t e = 0; e < up.size(); ++e) {
+      frow[up[e].at].dst = -1 - (int32_t)e;  // scratch slot, in target order
+      if (e + 1 == up.size() || up[e + 1].t != up[e].t) {
+        ftgt.push_back(up[e].t);
+        fpp.push_back((int32_t)e + 1);
+      }
+    }
+    uslots = std::max(uslots, (int)up.size());
+    offs[kResOffFL * (nlev + 1) + l] = lanes((int)frow.size() - r0, fmax);
+    offs[kResOffBL * (nlev + 1) + l] =
+        lanes((int)bc.size() - offs[kResOffC * (nlev + 1) + l], bmax);
+  }
+  offs[kResOffR * (nlev + 1) + nlev] = (int32_t)frow.size();
+  offs[kResOffT * (nlev + 1) + nlev] = (int32_t)ftgt.size();
+  offs[kResOffC * (nlev + 1) + nlev] = (int32_t)bc.size();
+  ResidentPlan P;
+  ResRow* r1 = nullptr;
+  ResCol* c1 = nullptr;
+  int32_t *i1 = nullptr, *i2 = nullptr, *i3 = nullptr;
+  if (!c->upload(r1, frow.data(), frow.size()) || !c->upload(i1, ftgt.data(), ftgt.size()) ||
+      !c->upload(i2, fpp.data(), fpp.size()) || !c->upload(c1, bc.data(), bc.size()) ||
+      !c->upload(i3, offs.data(), offs.size()))
+    return false;
+  P.frow = r1;
+  P.ftgt = i1;
+  P.fpp = i2;
+  P.bcol = c1;
+  P.offs = i3;
+  P.nlev = nlev;
+  P.uslots = uslots;
+  c->rplan = P;
+  return true;
+}
+
 int solve_cols(matex_ctx* c, const DevFactor& F, int ncols) {
   if (ncols <= 0) return 0;
   int mode = c->opts.solve_mode;
@@ -662,6 +751,23 @@ matex_status read_count(matex_ctx* c, int* out) {
   return MATEX_OK;
 }
 
+// Algorithmic work of one batched solve pair with K right-hand sides, from
+// the exact fill of L (the explicit zeros of relaxed amalgamation are the
+// implementation's choice, not work the method needs): a multiply-add per
+// strictly-lower nonzero of L and column in each direction, plus the D^{-1}
+// scaling; bytes: L in compressed form (8-byte value and 4-byte row index per
+// nonzero, 4-byte column pointers) read once per direction, D^{-1}, and the
+// right-hand sides read and written once per direction.
+double solve_flops(const matex_ctx* c, int K) {
+  return (4.0 * (double)c->S.nnz_L_exact + 2.0 * (double)c->n) * K;
+}
+double solve_bytes(const matex_ctx* c, int K) {
+  return 2.0 * (12.0 * (double)c->S.nnz_L_exact + 4.0 * ((double)c->n + 1.0)) + 8.0 * c->n +
+         32.0 * (double)c->n * K;
+}
+
+enum { P_SOLVE = 0, P_MOVE = 1, P_GS = 2, P_SMALL = 3, P_RECOMB = 4, P_OTHER = 5 };
+
 // ---- profiling: CUDA events around timed units, summed after the run -------
 int prof_begin(matex_ctx* c) {
   if (!c->prof_on) return -1;
@@ -692,7 +798,14 @@ void prof_collect(matex_ctx* c, const std::vector<int32_t>& m_seg) {
     c->prof.units[p.cls] += 1;
     c->prof.launches[p.cls] += p.launches;
     double fl = p.flops, by = p.bytes;
-    if (p.round >= 0) {
+    if (p.round >= 0 && p.cls == P_SOLVE) {
+      // resident round: per column the two G solves and one solve per Arnoldi step
+      const Round& r = c->serial ? c->serial_rounds[p.round] : c->rounds[p.round];
+      double cols = 0.0;
+      for (int q = 0; q < r.K; ++q) cols += 2.0 + m_seg[c->h_segid_all[r.begin + q]];
+      fl = cols * solve_flops(c, 1);
+      by = cols * solve_bytes(c, 1);
+    } else if (p.round >= 0) {
       // recombination: per (node, output, group) m FMAs + the -P term and the sum
       const Round& r = c->serial ? c->serial_rounds[p.round] : c->rounds[p.round];
       const int cover = c->serial ? c->serial_cover[p.round] : c->round_cover[p.round];
@@ -713,22 +826,6 @@ void prof_collect(matex_ctx* c, const std::vector<int32_t>& m_seg) {
   c->ev_used = 0;
 }
 
-// Algorithmic work of one batched solve pair with K right-hand sides, from
-// the exact fill of L (the explicit zeros of relaxed amalgamation are the
-// implementation's choice, not work the method needs): a multiply-add per
-// strictly-lower nonzero of L and column in each direction, plus the D^{-1}
-// scaling; bytes: L in compressed form (8-byte value and 4-byte row index per
-// nonzero, 4-byte column pointers) read once per direction, D^{-1}, and the
-// right-hand sides read and written once per direction.
-double solve_flops(const matex_ctx* c, int K) {
-  return (4.0 * (double)c->S.nnz_L_exact + 2.0 * (double)c->n) * K;
-}
-double solve_bytes(const matex_ctx* c, int K) {
-  return 2.0 * (12.0 * (double)c->S.nnz_L_exact + 4.0 * ((double)c->n + 1.0)) + 8.0 * c->n +
-         32.0 * (double)c->n * K;
-}
-
-enum { P_SOLVE = 0, P_MOVE = 1, P_GS = 2, P_SMALL = 3, P_RECOMB = 4, P_OTHER = 5 };
 
 // Sizes of the checkpointed adjoint.  Every segment is recomputed once
 // whatever the window, so the window only trades checkpoint memory (fewer
@@ -1005,7 +1102,11 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
   cudaMemsetAsync(c->d_count, 0, 4 * sizeof(int32_t), st);
   auto solve = [&](const DevFactor& F, int K) {
     e = prof_begin(c);
-    const int l = solve_cols(c, F, K);
+    int l = 1;
+    // resident rounds: the DC and initial-state solves by the same one-CTA
+    // substitution (no atomics anywhere in such a run: reproducible)
+    if (c->resident) resident_solve(F, c->rplan, c->Y, c->Y, n, K, c->ldy, 1, nullptr, st);
+    else l = solve_cols(c, F, K);
     prof_end(c, e, P_SOLVE, l, solve_flops(c, K), solve_bytes(c, K));
     launches += l;
     solve_cols_total += K;
@@ -1082,6 +1183,47 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
     const Round& r = rounds[ri];
     const int K = r.K;
     RoundCols rc = round_cols(c, r);
+    if (c->resident) {
+      // every column's whole segment in one launch (one CTA each), then the
+      // recombination of the round's outputs
+      ResidentArgs ra{};
+      ra.F1 = c->opts.krylov == 1 ? c->fG : c->fM;
+      ra.FG = c->fG;
+      ra.plan = c->rplan;
+      ra.Vb = c->Vb;
+      ra.vstride = vstride;
+      ra.X = c->Xb;
+      ra.Z = c->Zb;
+      ra.Zp = c->Zpb;
+      ra.W = c->Wb;
+      ra.cperm = c->c_perm;
+      ra.src = c->src;
+      ra.rc = rc;
+      ra.ss = c->ss;
+      ra.coef = c->coef;
+      ra.ldo = c->n_times;
+      ra.yend = c->yend;
+      ra.m_rec = c->m_rec;
+      ra.st_rec = c->st_rec;
+      ra.replay = c->replay_d;
+      ra.gamma = c->gamma;
+      ra.tol = c->tol;
+      ra.dt_out = c->dt_out;
+      ra.m_max = c->m_max;
+      ra.n = n;
+      e = prof_begin(c);
+      resident_round(ra, K, st);
+      prof_end(c, e, P_SOLVE, 1, 0.0, 0.0, (int)ri);
+      e = prof_begin(c);
+      recombine(c->Xp, n, c->n_times, c->Vb, vstride, c->Zb, c->Zpb, c->Wb, n, rc, c->ss.m, c->coef,
+                c->n_times, K, r.obeg_min, r.oend_max, c->dt_out, st, nullptr);
+      prof_end(c, e, P_RECOMB, 1, 0.0, 0.0, (int)ri);
+      launches += 2;
+      sweepsG += 2;
+      solve_cols_total += 2 * (int64_t)K;
+      if ((s = cuda_check(c, "round")) != MATEX_OK) return s;
+      continue;
+    }
     // z = G^{-1} B u(l_j) carried forward (u is continuous and linear on every
     // segment: z_j = z_{j-1} + L_{j-1} z'_{j-1}, z_0 = x(0)); then
     // z' = G^{-1} B s_j and w = G^{-1} C z'   (Eq. 5/6)
@@ -1294,6 +1436,23 @@ matex_status finish_run(matex_ctx* c, const PassCounts& pc, double t0, bool repl
   o.tc_rounds = pc.tc_rounds;
   o.sweeps_G = pc.sweepsG;
   o.solve_columns = pc.solve_cols;
+  if (c->resident) {
+    // the Arnoldi steps were taken on the device: one solve column each
+    const std::vector<Round>& rr = c->serial ? c->serial_rounds : c->rounds;
+    int64_t sm = 0;
+    int32_t sweeps = 0;
+    for (const Round& r : rr) {
+      int mx = 0;
+      for (int q = 0; q < r.K; ++q) {
+        const int mq = m[c->h_segid_all[r.begin + q]];
+        sm += mq;
+        mx = std::max(mx, mq);
+      }
+      sweeps += mx;
+    }
+    o.solve_columns += sm;
+    o.sweeps_M = sweeps;
+  }
   o.kernel_launches = pc.launches + 1;  // + the output permutation
   o.rounds = (int32_t)(c->serial ? c->serial_rounds.size() : c->rounds.size());
   o.graph_replay = replayed ? 1 : 0;
@@ -1728,6 +1887,9 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     return bad("decompose = 1 (ramps) needs tape = 0 and group_select = -1");
   if (o.col_block != 0 && o.col_block != 1 && o.col_block != 2 && o.col_block != 4 && o.col_block != 8)
     return bad("col_block must be 0, 1, 2, 4 or 8");
+  if (o.resident < 0 || o.resident > 2) return bad("resident must be 0, 1 or 2");
+  if (o.resident == 2 && (o.krylov == 2 || o.tape || o.tail_eps > 0.0 || n > kResidentMaxN))
+    return bad("resident rounds need n <= 8192, krylov 0 or 1, tape 0 and tail_eps 0");
   if (o.group_select >= n_groups) return bad("group_select out of range");
   if (o.n_rows < 0 || (o.n_rows > 0 && !o.rows)) return bad("row list missing");
   for (int32_t r = 0; r < o.n_rows; ++r)
@@ -2179,6 +2341,43 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   }
   if (o.solve_mode == 2 && o.col_block == 0) autotune_levels(c);
   if (o.solve_mode == 2) autotune_solve(c);
+  if (o.resident != 1 && o.krylov != 2 && o.tape == 0 && o.tail_eps == 0.0 &&
+      n <= kResidentMaxN) {
+    // resident rounds: one CTA's solve pair against the batched path's
+    // single-column pair (in its tuned launch mode), best of five each
+    const DevFactor& F1 = o.krylov == 1 ? c->fG : c->fM;
+    if (plan_resident(c, kResidentThreads) && resident_fits(n, c->rplan.uslots) &&
+        resident_set_limits(n, c->rplan.uslots)) {
+      c->resident_ok = true;
+      cudaMemsetAsync(c->Y, 0, sizeof(double) * (size_t)n * c->ldy, c->st);
+      c->res_pair_ms = resident_time_solve(F1, c->rplan, c->Y, c->Y2, n, c->st, 5);
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      solve_cols(c, F1, 1);
+      float best = 1e30f;
+      for (int rep = 0; rep < 5; ++rep) {
+        cudaEventRecord(e0, c->st);
+        solve_cols(c, F1, 1);
+        cudaEventRecord(e1, c->st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best = std::min(best, ms);
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      c->lvl_pair_ms = best;
+      c->resident = c->res_pair_ms > 0.f && (o.resident == 2 || c->res_pair_ms <= 2.f * best);
+    }
+    cudaGetLastError();
+  }
+  if (o.resident == 2 && !c->resident) {
+    g_setup_err = "resident rounds do not fit this device (shared memory or launch failed)";
+    delete c;
+    return MATEX_ERR_ARG;
+  }
+  c->setup_stats.resident = c->resident ? 1 : 0;
   {
     // Load, here, everything matex_solve_noalloc touches on this device: the
     // module that holds its static scratch array (under lazy module loading
@@ -2335,23 +2534,44 @@ matex_status matex_solve(matex_ctx* c, int32_t which, int32_t ncols, const doubl
   return read_count(c, &tmp);
 }
 
+matex_status matex_solve_resident(matex_ctx* c, int32_t which, int32_t ncols, const double* b,
+                                  double* x) {
+  if (!c) return MATEX_ERR_ARG;
+  if ((which != 0 && which != 1) || ncols < 0 || (ncols > 0 && (!b || !x)))
+    return fail(c, MATEX_ERR_ARG, "bad solve arguments");
+  if (!c->resident_ok)
+    return fail(c, MATEX_ERR_STATE, "this context has no resident solve (grid too large, or "
+                                    "krylov 2, tape, tail_eps or resident = 1 at setup)");
+  const DevFactor& F = which == 0 ? c->fM : c->fG;
+  resident_solve(F, c->rplan, b, x, c->n, ncols, 1, c->n, c->perm, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "resident solve sync");
+  return cuda_check(c, "resident solve");
+}
+
 matex_status matex_time_solve(matex_ctx* c, int32_t which, int32_t ncols, int32_t reps,
                               float* best_ms, float* mean_ms) {
   if (!c) return MATEX_ERR_ARG;
-  if ((which != 0 && which != 1) || ncols < 1 || ncols > c->ldy || reps < 1 || !best_ms)
+  if (which < 0 || which > 3 || ncols < 1 || ncols > c->ldy || reps < 1 || !best_ms)
     return fail(c, MATEX_ERR_ARG, "bad time_solve arguments (1 <= ncols <= column buffer width)");
-  const DevFactor& F = which == 0 ? c->fM : c->fG;
+  if (which >= 2 && !c->resident_ok)
+    return fail(c, MATEX_ERR_STATE, "this context has no resident solve");
+  const DevFactor& F = which % 2 == 0 ? c->fM : c->fG;
+  // which 2, 3: the resident substitution, ncols columns of the buffer as n-vectors
+  auto one = [&]() {
+    if (which >= 2) resident_solve(F, c->rplan, c->Y, c->Y, c->n, ncols, 1, c->n, nullptr, c->st);
+    else solve_cols(c, F, ncols);
+  };
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
     return cuda_check(c, "time_solve events");
   }
   cudaMemsetAsync(c->d_count, 0, 4 * sizeof(int32_t), c->st);
-  solve_cols(c, F, ncols);  // warm-up
+  one();  // warm-up
   float best = 1e30f, sum = 0.f;
   for (int r = 0; r < reps; ++r) {
     cudaEventRecord(e0, c->st);
-    solve_cols(c, F, ncols);
+    one();
     cudaEventRecord(e1, c->st);
     cudaEventSynchronize(e1);
     float ms = 0.f;

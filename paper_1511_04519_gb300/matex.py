@@ -34,7 +34,7 @@ class MatexOpts(C.Structure):
                 ("max_width", C.c_int32), ("strict", C.c_int32), ("solve_mode", C.c_int32),
                 ("tape", C.c_int32), ("krylov", C.c_int32), ("graph", C.c_int32),
                 ("tail_eps", C.c_double), ("tape_window", C.c_int32), ("tape_block", C.c_int32),
-                ("recombine", C.c_int32), ("decompose", C.c_int32)]
+                ("recombine", C.c_int32), ("decompose", C.c_int32), ("resident", C.c_int32)]
 
 
 class MatexStats(C.Structure):
@@ -47,7 +47,7 @@ class MatexStats(C.Structure):
                 ("kernel_launches", C.c_int32), ("rounds", C.c_int32),
                 ("graph_replay", C.c_int32), ("graph_capture_ms", C.c_double),
                 ("nnz_L_exact", C.c_int64), ("tape_window", C.c_int32), ("tape_block", C.c_int32),
-                ("tape_bytes", C.c_int64), ("tc_rounds", C.c_int32), ("reserved0", C.c_int32)]
+                ("tape_bytes", C.c_int64), ("tc_rounds", C.c_int32), ("resident", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -72,7 +72,7 @@ EXPORTS = ["matex_default_opts", "matex_setup", "matex_run", "matex_run_host", "
            "matex_debug_inject_wait", "matex_solve_noalloc", "matex_grad", "matex_set_caps",
            "matex_get_autotune", "matex_batch_create", "matex_batch_run", "matex_batch_last_error",
            "matex_batch_destroy", "matex_measure_fp64_peak", "matex_tr_run",
-           "matex_time_solve", "matex_get_level_blocks"]
+           "matex_time_solve", "matex_get_level_blocks", "matex_solve_resident"]
 
 
 def _load():
@@ -98,6 +98,8 @@ def _load():
     lib.matex_solve.restype = C.c_int
     lib.matex_solve_noalloc.argtypes = [P, C.c_int32, C.c_int32, P, P]
     lib.matex_solve_noalloc.restype = C.c_int
+    lib.matex_solve_resident.argtypes = [P, C.c_int32, C.c_int32, P, P]
+    lib.matex_solve_resident.restype = C.c_int
     lib.matex_get_level_blocks.argtypes = [P, i32p, i32p, C.POINTER(C.c_float), C.c_int32, i32p]
     lib.matex_get_level_blocks.restype = C.c_int
     lib.matex_time_solve.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_float),
@@ -238,6 +240,12 @@ def matex_solve(ctx, which, ncols, b_ptr, x_ptr):
     _check(ctx, _lib.matex_solve(ctx, int(which), int(ncols), C.c_void_p(b_ptr), C.c_void_p(x_ptr)))
 
 
+def matex_solve_resident(ctx, which, ncols, b_ptr, x_ptr):
+    """matex_solve through the one-CTA substitution of the resident rounds."""
+    _check(ctx, _lib.matex_solve_resident(ctx, int(which), int(ncols), C.c_void_p(b_ptr),
+                                          C.c_void_p(x_ptr)))
+
+
 def matex_solve_noalloc(ctx, which, ncols, b_ptr, x_ptr):
     """matex_solve without any allocation (static device scratch; see matex.h)."""
     _check(ctx, _lib.matex_solve_noalloc(ctx, int(which), int(ncols), C.c_void_p(b_ptr),
@@ -322,7 +330,7 @@ class Sim:
     def __init__(self, p, col_block=0, group_select=-1, include_dc=True, rows=None,
                  replay_m=None, max_width=0, strict=False, stream=None, solve_mode=2,
                  tape=False, graph=True, krylov="R", tail_eps=0.0, tape_window=0, tape_block=0,
-                 recombine="auto", decompose="groups", **overrides):
+                 recombine="auto", decompose="groups", resident="auto", **overrides):
         o = matex_default_opts()
         o.graph = int(bool(graph))
         o.tail_eps = float(tail_eps)
@@ -337,6 +345,7 @@ class Sim:
         o.tape = {False: 0, True: 1, 0: 0, 1: 1, 2: 2, "full": 1, "checkpoint": 2}[tape]
         o.recombine = {"auto": 0, "tensor": 0, "fp64": 1}[recombine]
         o.decompose = {"groups": 0, "ramps": 1}[decompose]
+        o.resident = {"auto": 0, "off": 1, "on": 2, 0: 0, 1: 1, 2: 2}[resident]
         o.tape_window = int(tape_window)
         o.tape_block = int(tape_block)
         self._keep = []

@@ -132,7 +132,8 @@ def test_setup_rejects_bad_inputs_before_gpu(lib, mutation):
                                          ("solve_mode", 5), ("tape_tail", 1e-9),
                                          ("tape_krylov", 1), ("decompose", 2),
                                          ("decompose_tape", 1), ("recombine", 2),
-                                         ("tape", 3), ("tape_window", -1)])
+                                         ("tape", 3), ("tape_window", -1), ("resident", 3),
+                                         ("resident_krylov", 2), ("resident_tail", 1e-9)])
 def test_setup_rejects_bad_options_before_gpu(lib, field, value):
     """Option checks run on the host before any device work: the status is
     MATEX_ERR_ARG with a message, on a machine without a GPU as well."""
@@ -145,6 +146,10 @@ def test_setup_rejects_bad_options_before_gpu(lib, field, value):
         o.tape, o.krylov = 1, value
     elif field == "decompose_tape":
         o.tape, o.decompose = 1, value
+    elif field == "resident_krylov":
+        o.resident, o.krylov = 2, value
+    elif field == "resident_tail":
+        o.resident, o.tail_eps = 2, value
     else:
         setattr(o, field, value)
     st, msg = _setup_status(lib, p, opts=C.byref(o))
@@ -179,4 +184,4 @@ def test_default_options_layout():
     assert bytes(buf[size:]) == b"\xa5" * 64
     assert M.MatexOpts.from_buffer(buf).tail_eps == 0.0
     assert C.sizeof(M.MatexStats) == 3 * 8 + 8 + 4 * 12 + 8 + 4 * 4 + 8 + 8 + 4 * 2 + 8 + 8
-    assert (o.tape_window, o.tape_block, o.recombine, o.decompose) == (0, 0, 0, 0)
+    assert (o.tape_window, o.tape_block, o.recombine, o.decompose, o.resident) == (0, 0, 0, 0, 0)

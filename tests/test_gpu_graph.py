@@ -39,7 +39,7 @@ def uneven_groups(seed=0):
 
 def test_replay_matches_plain_run_and_oracle(M):
     p = uneven_groups()
-    sim = M.Sim(p)
+    sim = M.Sim(p, resident="off")
     X1 = sim.run().cpu().numpy()
     s1 = sim.stats.as_dict()
     assert s1["graph_replay"] == 0 and s1["graph_capture_ms"] > 0
@@ -50,13 +50,13 @@ def test_replay_matches_plain_run_and_oracle(M):
               "solve_columns", "rounds", "nonconv"):
         assert s1[k] == s2[k], k
     assert np.abs(X2 - X1).max() <= TOL_SAME * p.vdd
-    plain = M.Sim(p, graph=False)
+    plain = M.Sim(p, resident="off", graph=False)
     X3 = plain.run().cpu().numpy()
     assert plain.stats.graph_replay == 0
     assert np.abs(X3 - X1).max() <= TOL_SAME * p.vdd
     ref = R.rmatex(p)
     err = check_adaptive("uneven_groups_graph_replay", p, X2, sim.m_sequence(), ref,
-                         lambda m: M.Sim(p, replay_m=m).run().cpu().numpy())
+                         lambda m: M.Sim(p, resident="off", replay_m=m).run().cpu().numpy())
     assert err <= TOL_V * p.vdd
     # a third run replays again
     X4 = sim.run().cpu().numpy()
@@ -68,7 +68,7 @@ def test_changed_counts_fall_back_and_record_again(M):
     after fewer Arnoldi steps: the replay's guard sees other counts, the run is
     redone plainly, and the next run replays the new recording."""
     p = uneven_groups(1)
-    sim = M.Sim(p)
+    sim = M.Sim(p, resident="off")
     sim.run()
     sim.run()
     assert sim.stats.graph_replay == 1
@@ -80,7 +80,7 @@ def test_changed_counts_fall_back_and_record_again(M):
     assert not np.array_equal(sim.m_sequence(), m_before)
     q = uneven_groups(1)
     q.pwl_v = scaled
-    fresh = M.Sim(q, graph=False)
+    fresh = M.Sim(q, resident="off", graph=False)
     Xf = fresh.run().cpu().numpy()
     assert np.array_equal(fresh.m_sequence(), sim.m_sequence())
     assert np.abs(Xa - Xf).max() <= TOL_SAME * p.vdd
@@ -96,7 +96,7 @@ def test_replay_follows_new_capacitances_and_sources(M):
     p = uneven_groups()
     per_group = [list(lg.m) for lg in R.rmatex(p).logs]
     ms = np.concatenate([np.asarray(m, np.int32) for m in per_group])
-    sim = M.Sim(p, replay_m=ms)
+    sim = M.Sim(p, resident="off", replay_m=ms)
     sim.run()
     c2 = np.asarray(p.c) * np.random.default_rng(3).uniform(0.8, 1.25, p.n)
     v2 = np.asarray(p.pwl_v) * 1.5
@@ -107,7 +107,7 @@ def test_replay_follows_new_capacitances_and_sources(M):
     q = uneven_groups()
     q.c = c2
     q.pwl_v = v2
-    Xf = M.Sim(q, replay_m=ms, graph=False).run().cpu().numpy()
+    Xf = M.Sim(q, resident="off", replay_m=ms, graph=False).run().cpu().numpy()
     assert np.abs(X - Xf).max() <= TOL_SAME * p.vdd
     assert np.abs(X - R.rmatex(q, replay_m=per_group).X).max() <= TOL_V * p.vdd
 
@@ -117,7 +117,7 @@ def test_sources_breaking_the_zero_pattern_are_rejected(M):
     would make one of them non-zero are refused and change nothing."""
     p = gridgen.small_mesh(11, nx=8, ny=7, layers=1, n_src=6, group_templates=[2, 2, 2],
                            t_end=0.3e-9, dt_out=10e-12)
-    sim = M.Sim(p)
+    sim = M.Sim(p, resident="off")
     X0 = sim.run().cpu().numpy()
     bad = np.asarray(p.pwl_v).copy()
     first = np.asarray(p.pwl_off)[:-1]
@@ -130,7 +130,7 @@ def test_sources_breaking_the_zero_pattern_are_rejected(M):
 
 def test_batch_of_uneven_grids_matches_individual_runs(M):
     probs = gridgen.config4(count=6, side_range=(12, 40))
-    sims = [M.Sim(p) for p in probs]
+    sims = [M.Sim(p, resident="off") for p in probs]
     single = [s.run().cpu().numpy() for s in sims]
     batch = M.Batch(sims)
     outs, ms = batch.run()
@@ -143,7 +143,7 @@ def test_batch_of_uneven_grids_matches_individual_runs(M):
         ref = R.rmatex(probs[i])
         err = check_adaptive(f"uneven_grids_batch_grid{i}", probs[i], outs[i].cpu().numpy(),
                              sims[i].m_sequence(), ref,
-                             lambda m: M.Sim(probs[i], replay_m=m).run().cpu().numpy())
+                             lambda m: M.Sim(probs[i], resident="off", replay_m=m).run().cpu().numpy())
         assert err <= TOL_V * probs[i].vdd
     # one grid's counts change: only that grid is redone plainly
     sims[2].set_sources(np.asarray(probs[2].pwl_v) * 1e-4)
@@ -152,7 +152,7 @@ def test_batch_of_uneven_grids_matches_individual_runs(M):
     assert all(s.stats.graph_replay == 1 for k, s in enumerate(sims) if k != 2)
     q = gridgen.config4(count=6, side_range=(12, 40))[2]
     q.pwl_v = np.asarray(q.pwl_v) * 1e-4
-    Xq = M.Sim(q, graph=False).run().cpu().numpy()
+    Xq = M.Sim(q, resident="off", graph=False).run().cpu().numpy()
     assert np.abs(outs2[2].cpu().numpy() - Xq).max() <= TOL_SAME * q.vdd
     for k in (0, 1, 3, 4, 5):
         assert np.abs(outs2[k].cpu().numpy() - single[k]).max() <= TOL_SAME * probs[k].vdd
@@ -169,13 +169,13 @@ def test_contexts_of_different_sizes_coexist(M):
     replayed runs of the large one still work, and so does the batch)."""
     big_p = gridgen.config1()
     rows = np.arange(0, big_p.n, 997, dtype=np.int32)
-    big = M.Sim(big_p, rows=rows, group_select=5, graph=False)
+    big = M.Sim(big_p, resident="off", rows=rows, group_select=5, graph=False)
     X0 = big.run().cpu().numpy()
     small = M.Sim(gridgen.small_mesh(2, nx=6, ny=5, layers=1, n_src=4, group_templates=[2, 2],
                                      t_end=0.2e-9, dt_out=10e-12))
     Xs = small.run().cpu().numpy()
     for solve_mode in (0, 1):
-        again = M.Sim(big_p, rows=rows, group_select=5, solve_mode=solve_mode)
+        again = M.Sim(big_p, resident="off", rows=rows, group_select=5, solve_mode=solve_mode)
         tiny = M.Sim(gridgen.small_mesh(3, nx=5, ny=5, layers=1, n_src=3, group_templates=[3],
                                         t_end=0.2e-9, dt_out=10e-12), solve_mode=solve_mode)
         for _ in range(2):

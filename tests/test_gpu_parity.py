@@ -33,7 +33,9 @@ from tests.parity_util import check_adaptive, oracle_m  # noqa: E402
 def compare_run(M, p, ref=None, fac=None, case=None, **kw):
     """Run GPU (adaptive, then replay if m differs) and compare with the
     oracle; the adaptive run's m mismatches and error are bounded and
-    recorded (tests/parity_util.py)."""
+    recorded (tests/parity_util.py).  The batched path unless resident= is
+    given (the resident rounds have their own file)."""
+    kw.setdefault("resident", "off")
     if ref is None:
         ref = R.rmatex(p, fac=fac, groups=None if kw.get("group_select", -1) < 0 else [kw["group_select"]],
                        include_dc=kw.get("include_dc", True))
@@ -181,15 +183,15 @@ def test_group_select_rows_and_no_dc(M):
 def test_column_blocks_agree(M, col_block):
     p = gridgen.small_mesh(8, nx=20, ny=20, layers=2, n_src=24, group_templates=[2] * 12,
                            t_end=0.3e-9)
-    base = M.Sim(p, col_block=1).run().cpu().numpy()
-    X = M.Sim(p, col_block=col_block).run().cpu().numpy()
+    base = M.Sim(p, col_block=1, resident="off").run().cpu().numpy()
+    X = M.Sim(p, col_block=col_block, resident="off").run().cpu().numpy()
     assert np.abs(X - base).max() <= 1e-13
 
 
 def test_one_group_at_a_time_matches_batched(M):
     p = gridgen.small_mesh(12, nx=25, ny=20, layers=2, n_src=30, group_templates=[3, 1, 4, 1, 5, 6],
                            t_end=0.4e-9)
-    sim = M.Sim(p)
+    sim = M.Sim(p, resident="off")
     Xb = sim.run().cpu().numpy()
     mb = sim.m_sequence()
     sim.one_group_at_a_time(True)
@@ -202,7 +204,7 @@ def test_one_group_at_a_time_matches_batched(M):
 def test_persistent_and_level_solves_agree(M, mode):
     p = gridgen.small_mesh(13, nx=30, ny=30, layers=2, n_src=20, group_templates=[5] * 4, t_end=0.3e-9)
     ref = R.rmatex(p)
-    sim = M.Sim(p, solve_mode=mode, replay_m=oracle_m(ref))
+    sim = M.Sim(p, solve_mode=mode, replay_m=oracle_m(ref), resident="off")
     X = sim.run().cpu().numpy()
     assert np.abs(X - ref.X).max() <= TOL_V * p.vdd
 
@@ -210,7 +212,7 @@ def test_persistent_and_level_solves_agree(M, mode):
 def test_bounded_wait_reports_timeout_and_context_recovers(M):
     import time
     p = gridgen.small_mesh(14, nx=12, ny=12, n_src=4)
-    sim = M.Sim(p, solve_mode=0)  # the hook acts on the persistent solve
+    sim = M.Sim(p, solve_mode=0, resident="off")  # the hook acts on the persistent solve
     good = sim.run().cpu().numpy()
     M.matex_debug_inject_wait(sim.ctx, True)
     t0 = time.time()

@@ -28,10 +28,10 @@ def M():
 
 def ramp_parity(M, p, case, rows=None):
     ref = R.rmatex(R.ramp_decomposition(p), nodes=rows)
-    sim = M.Sim(p, decompose="ramps", rows=rows)
+    sim = M.Sim(p, resident="off", decompose="ramps", rows=rows)
     X = sim.run().cpu().numpy()
     err = check_adaptive(case, p, X, sim.m_sequence(), ref,
-                         lambda m: M.Sim(p, decompose="ramps", rows=rows,
+                         lambda m: M.Sim(p, resident="off", decompose="ramps", rows=rows,
                                          replay_m=m).run().cpu().numpy())
     return err, sim
 
@@ -54,7 +54,7 @@ def test_uneven_groups_four_layer_reduced_ramps(M):
                         max_tpl=14)
     err, sim = ramp_parity(M, p, "ramps_mesh4x24x24")
     assert err <= TOL_V * p.vdd
-    seg = M.Sim(p)
+    seg = M.Sim(p, resident="off")
     seg.run()
     assert sim.stats.rounds < seg.stats.rounds
 
@@ -65,14 +65,14 @@ def test_ramps_equal_groups_at_tight_tolerance(M):
     p = gridgen.small_mesh(33, nx=30, ny=30, layers=2, n_src=24, group_templates=[2] * 12,
                            t_end=0.6e-9, dt_out=5e-12)
     p.tol = 1e-12
-    Xg = M.Sim(p).run().cpu().numpy()
-    Xr = M.Sim(p, decompose="ramps").run().cpu().numpy()
+    Xg = M.Sim(p, resident="off").run().cpu().numpy()
+    Xr = M.Sim(p, resident="off", decompose="ramps").run().cpu().numpy()
     assert np.abs(Xg - Xr).max() <= TOL_V * p.vdd
 
 
 def test_ramps_refuse_new_currents(M):
     p = gridgen.small_mesh(34, nx=8, ny=8, n_src=4, group_templates=[2, 2])
-    sim = M.Sim(p, decompose="ramps")
+    sim = M.Sim(p, resident="off", decompose="ramps")
     sim.run()
     with pytest.raises(M.MatexError) as ei:
         sim.set_sources(np.asarray(p.pwl_v) * 2.0)

@@ -34,10 +34,10 @@ def M():
 
 
 def both_paths(M, p, **kw):
-    a = M.Sim(p, **kw)
+    a = M.Sim(p, resident="off", **kw)
     Xa = a.run().cpu().numpy()
     assert a.stats.tc_rounds > 0
-    b = M.Sim(p, recombine="fp64", replay_m=a.m_sequence(), **kw)
+    b = M.Sim(p, resident="off", recombine="fp64", replay_m=a.m_sequence(), **kw)
     Xb = b.run().cpu().numpy()
     assert b.stats.tc_rounds == 0
     return Xa, Xb, a
@@ -53,7 +53,7 @@ def test_ragged_tiles_match_fp64_and_oracle(M, seed):
     assert np.abs(Xa - Xb).max() <= TOL_SAME * p.vdd
     ref = R.rmatex(p)
     err = check_adaptive(f"tc_ragged_{seed}", p, Xa, sim.m_sequence(), ref,
-                         lambda m: M.Sim(p, replay_m=m).run().cpu().numpy())
+                         lambda m: M.Sim(p, resident="off", replay_m=m).run().cpu().numpy())
     assert err <= TOL_V * p.vdd
 
 
@@ -70,7 +70,7 @@ def test_more_than_one_exact_sum_window(M):
     assert np.abs(Xa - Xb).max() <= TOL_SAME * p.vdd
     ref = R.rmatex(p)
     err = check_adaptive("tc_two_windows", p, Xa, sim.m_sequence(), ref,
-                         lambda m: M.Sim(p, replay_m=m).run().cpu().numpy())
+                         lambda m: M.Sim(p, resident="off", replay_m=m).run().cpu().numpy())
     assert err <= TOL_V * p.vdd
 
 
@@ -80,11 +80,11 @@ def test_small_rounds_and_one_group_at_a_time(M):
     equal the FP64-only run."""
     p = gridgen.small_mesh(45, nx=20, ny=20, layers=1, n_src=12, group_templates=[2] * 6,
                            t_end=0.5e-9)
-    sim = M.Sim(p)
+    sim = M.Sim(p, resident="off")
     Xb = sim.run().cpu().numpy()
     sim.one_group_at_a_time(True)
     Xs = sim.run().cpu().numpy()
-    Xf = M.Sim(p, recombine="fp64", replay_m=sim.m_sequence()).run().cpu().numpy()
+    Xf = M.Sim(p, resident="off", recombine="fp64", replay_m=sim.m_sequence()).run().cpu().numpy()
     assert np.abs(Xb - Xf).max() <= TOL_SAME * p.vdd
     assert np.abs(Xs - Xf).max() <= TOL_SAME * p.vdd
 
@@ -95,13 +95,13 @@ def test_bench_grid_matches_fp64_recombination(M):
     time."""
     import torch
     p = gridgen.config1()
-    a = M.Sim(p)
+    a = M.Sim(p, resident="off")
     Xa = a.run()
     a.run(Xa)
     # the long tails on the tensor cores; the rise and fall rounds (each column
     # holding a few outputs of a wide range) stay on the FP64 kernel
     assert a.stats.graph_replay == 1 and 1 <= a.stats.tc_rounds < a.stats.rounds
-    b = M.Sim(p, recombine="fp64", replay_m=a.m_sequence())
+    b = M.Sim(p, resident="off", recombine="fp64", replay_m=a.m_sequence())
     Xb = b.run()
     diff = float((Xa - Xb).abs().max())
     assert diff <= TOL_SAME * p.vdd, diff

@@ -32,11 +32,11 @@ def per_group(res):
 
 def parity(M, p, variant):
     ref = R.rmatex(p, variant=variant)
-    sim = M.Sim(p, krylov=variant)
+    sim = M.Sim(p, resident="off", krylov=variant)
     X = sim.run().cpu().numpy()
     err = check_adaptive(f"{p.meta.get('label', 'case')}_krylov_{variant}", p, X,
                          sim.m_sequence(), ref,
-                         lambda m: M.Sim(p, krylov=variant, replay_m=m).run().cpu().numpy())
+                         lambda m: M.Sim(p, resident="off", krylov=variant, replay_m=m).run().cpu().numpy())
     return err, sim
 
 
@@ -75,10 +75,10 @@ def test_inverted_space_on_bench_grid_groups(M):
     rows = np.sort(np.random.default_rng(7).choice(p.n, 17, replace=False)).astype(np.int32)
     for k in (3, 40):
         ref = R.rmatex(p, groups=[k], nodes=rows, variant="I")
-        sim = M.Sim(p, krylov="I", group_select=k, rows=rows)
+        sim = M.Sim(p, resident="off", krylov="I", group_select=k, rows=rows)
         X = sim.run().cpu().numpy()
         err = check_adaptive(f"mesh2x300x300_group{k}_krylov_I", p, X, sim.m_sequence(), ref,
-                             lambda m: M.Sim(p, krylov="I", group_select=k, rows=rows,
+                             lambda m: M.Sim(p, resident="off", krylov="I", group_select=k, rows=rows,
                                              replay_m=m).run().cpu().numpy())
         assert err <= TOL_V * p.vdd
 
@@ -92,7 +92,7 @@ def test_standard_space_needs_far_larger_bases(M):
                            dt_out=5e-12, c_range=(1e-15, 1e-12), group_templates=[6])
     out = {}
     for v in ("R", "I", "S"):
-        sim = M.Sim(p, krylov=v)
+        sim = M.Sim(p, resident="off", krylov=v)
         X = sim.run().cpu().numpy()
         out[v] = (X, sim.stats.as_dict())
     assert out["R"][1]["nonconv"] == 0 and out["I"][1]["nonconv"] == 0
@@ -104,4 +104,4 @@ def test_standard_space_needs_far_larger_bases(M):
 def test_tape_requires_rational_space(M):
     p = gridgen.small_mesh(42, nx=5, ny=5, layers=1, n_src=3, group_templates=[3])
     with pytest.raises(M.MatexError):
-        M.Sim(p, krylov="I", tape=True)
+        M.Sim(p, resident="off", krylov="I", tape=True)
