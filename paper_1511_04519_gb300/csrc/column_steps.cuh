@@ -42,6 +42,12 @@ struct SmallShared {
   double E[kMat];
   double y[kMaxM], y2[kMaxM];
   int flag;
+  // the last residual test's H (for Krylov dimension cm) and its two
+  // exponentials e^{ch[i] H} (ce[i]); cm = 0: none.  The caller clears cm
+  // where the shared memory is not that of the test's own CTA.
+  int cm;
+  double ch[2];
+  double ce[2][kMat];
 };
 
 // Status of column q after Arnoldi step j (m = j + 1), returned to every
@@ -73,11 +79,20 @@ __device__ int residual_column(SmallState ss, const RoundCols& rc, int q, int j,
     const double hc = fmin(rc.hfirst[q], L);
     double rmax = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
-      expm_dev<G>(sh.H, pass == 0 ? hc : L, sh.E, m, sh.w);
+      double* E = sh.ce[pass];
+      expm_dev<G>(sh.H, pass == 0 ? hc : L, E, m, sh.w);
       // r = ||v|| |s h_{m+1,m} e_m^T e^{hH} e_1|, s making h_{m+1,m} dimensionless
-      rmax = fmax(rmax, ss.beta[q] * fabs(ss.rscale * hnext) * fabs(sh.E[(m - 1) * kLd + 0]));
+      rmax = fmax(rmax, ss.beta[q] * fabs(ss.rscale * hnext) * fabs(E[(m - 1) * kLd + 0]));
     }
     if (rmax < tol) st = 1;
+    if (G::rank() == 0) {
+      sh.cm = m;
+      sh.ch[0] = hc;
+      sh.ch[1] = L;
+    }
+    G::sync();
+  } else if (G::rank() == 0) {
+    sh.cm = 0;
   }
   if (st == 0 && m >= m_max) st = 3;
   if (G::rank() == 0) ss.status[q] = st;
@@ -121,16 +136,24 @@ __device__ void coef_column(SmallState ss, const RoundCols& rc, int q, double ga
   }
   const double* Ht = ss.Ht + (int64_t)q * kMaxB * kMaxM;
   const double beta = ss.beta[q];
-  rational_H<G>(Ht, m, gamma, sh.H, sh.w, ss.krylov);
+  // e^{hH} for h = t: from the residual test of this m when it took it
+  const bool cached = sh.cm == m;
+  auto expm_at = [&](double t) -> const double* {
+    if (cached && sh.ch[0] == t) return sh.ce[0];
+    if (cached && sh.ch[1] == t) return sh.ce[1];
+    expm_dev<G>(sh.H, t, sh.E, m, sh.w);
+    return sh.E;
+  };
+  if (!cached) rational_H<G>(Ht, m, gamma, sh.H, sh.w, ss.krylov);
   // segment end
-  expm_dev<G>(sh.H, rc.len[q], sh.E, m, sh.w);
-  for (int i = G::rank(); i < m; i += G::size()) yend[(int64_t)q * kMaxM + i] = beta * sh.E[i * kLd];
+  const double* E = expm_at(rc.len[q]);
+  for (int i = G::rank(); i < m; i += G::size()) yend[(int64_t)q * kMaxM + i] = beta * E[i * kLd];
   if (no <= 0) return;
   G::sync();
   // first output, then the propagator e^{dt H} for the equally spaced rest
-  expm_dev<G>(sh.H, rc.hfirst[q], sh.E, m, sh.w);
+  E = expm_at(rc.hfirst[q]);
   for (int i = G::rank(); i < m; i += G::size()) {
-    sh.y[i] = beta * sh.E[i * kLd];
+    sh.y[i] = beta * E[i * kLd];
     cq[i] = sh.y[i];
   }
   G::sync();

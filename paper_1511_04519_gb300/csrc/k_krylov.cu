@@ -243,6 +243,8 @@ coef_kernel(SmallState ss, RoundCols rc, double gamma, double dt_out, double* __
             int32_t* __restrict__ tcut) {
   extern __shared__ double smem_raw[];
   SmallShared& sh = *reinterpret_cast<SmallShared*>(smem_raw);
+  if (threadIdx.x == 0) sh.cm = 0;  // no residual test ran in this CTA
+  __syncthreads();
   coef_column(ss, rc, blockIdx.x, gamma, dt_out, coef, ldo, yend, tail_eps, pbound, tcut, sh);
 }
 

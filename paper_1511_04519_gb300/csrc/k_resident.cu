@@ -32,25 +32,26 @@ __device__ __forceinline__ double res_block_sum(double v, double* red) {
   return s;
 }
 
-constexpr int kResOffs = kResOffN * (kResidentMaxLevels + 1);  // staged in shared memory
+
+constexpr int kResBatch = 8;  // panel loads in flight per lane (masked FMAs cost full pipe time)
 
 // Part of sum over k < n of p[k * stride] v[k] taken by lane sub of a group
-// of lpr lanes (terms sub, sub + lpr, ...), eight loads in flight per step:
-// the panel entries come from L2, one round trip per eight terms per lane.
+// of lpr lanes (terms sub, sub + lpr, ...), kResBatch loads in flight per
+// step: the panel entries come from L2, one round trip per batch per lane.
 __device__ __forceinline__ double res_dot(const double* __restrict__ p, int64_t stride,
                                           const double* __restrict__ v, int n, int sub, int lpr) {
   double a0 = 0.0, a1 = 0.0;
-  for (int k = sub; k < n; k += 8 * lpr) {
-    double q[8], x[8];
+  for (int k = sub; k < n; k += kResBatch * lpr) {
+    double q[kResBatch], x[kResBatch];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < kResBatch; ++u) {
       const int kk = k + u * lpr;
       const bool ok = kk < n;
       q[u] = ok ? __ldg(p + (int64_t)kk * stride) : 0.0;
       x[u] = ok ? v[kk] : 0.0;
     }
 #pragma unroll
-    for (int u = 0; u < 8; u += 2) {
+    for (int u = 0; u < kResBatch; u += 2) {
       a0 = fma(q[u], x[u], a0);
       a1 = fma(q[u + 1], x[u + 1], a1);
     }
@@ -58,26 +59,26 @@ __device__ __forceinline__ double res_dot(const double* __restrict__ p, int64_t 
   return a0 + a1;
 }
 
-// the same over gathered entries: terms p[i * stride] v[idx[i]]
+// the same over gathered entries: terms p[i * stride] v[idx[i]] (idx in
+// shared memory)
 __device__ __forceinline__ double res_dot_gather(const double* __restrict__ p, int64_t stride,
-                                                 const int32_t* __restrict__ idx,
+                                                 const int* __restrict__ idx,
                                                  const double* __restrict__ v, int n, int sub,
                                                  int lpr) {
   double a0 = 0.0, a1 = 0.0;
-  for (int k = sub; k < n; k += 8 * lpr) {
-    double q[8];
-    int r[8];
+  for (int k = sub; k < n; k += kResBatch * lpr) {
+    double q[kResBatch], x[kResBatch];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < kResBatch; ++u) {
       const int kk = k + u * lpr;
       const bool ok = kk < n;
       q[u] = ok ? __ldg(p + (int64_t)kk * stride) : 0.0;
-      r[u] = ok ? __ldg(idx + kk) : -1;
+      x[u] = ok ? v[idx[kk]] : 0.0;
     }
 #pragma unroll
-    for (int u = 0; u < 8; u += 2) {
-      a0 = fma(q[u], r[u] >= 0 ? v[r[u]] : 0.0, a0);
-      a1 = fma(q[u + 1], r[u + 1] >= 0 ? v[r[u + 1]] : 0.0, a1);
+    for (int u = 0; u < kResBatch; u += 2) {
+      a0 = fma(q[u], x[u], a0);
+      a1 = fma(q[u + 1], x[u + 1], a1);
     }
   }
   return a0 + a1;
@@ -90,80 +91,111 @@ __device__ __forceinline__ double res_group_sum(double v, int lpr) {
   return v;
 }
 
-// x = X^{-1} b for one right-hand side with the factor F = L D L^T of X.
-// b (in: right-hand side, out: solution), y and U (scratch: n and P.uslots
-// doubles) are shared memory, lofs the plan's level offsets staged there; b
+// The plan's sections in shared memory (see ResidentPlan).
+struct ResSmem {
+  const int* offs;
+  const ResSup* sups;
+  const uint16_t* fsup;
+  const uint16_t* bsup;
+  const int* tgt;
+  const int* tpp;
+  const int* tslot;
+  const int* brows;
+};
+
+// Copy the plan blob into shared memory at pl (16-byte aligned) and point
+// into it; the caller synchronises before use.
+__device__ __forceinline__ ResSmem res_stage_plan(const ResidentPlan& P, unsigned char* pl) {
+  const int4* src = reinterpret_cast<const int4*>(P.blob);
+  int4* dst = reinterpret_cast<int4*>(pl);
+  for (int e = threadIdx.x; e < P.bytes / 16; e += blockDim.x) dst[e] = __ldg(src + e);
+  ResSmem m;
+  m.offs = reinterpret_cast<const int*>(pl + P.o_offs);
+  m.sups = reinterpret_cast<const ResSup*>(pl + P.o_sups);
+  m.fsup = reinterpret_cast<const uint16_t*>(pl + P.o_fsup);
+  m.bsup = reinterpret_cast<const uint16_t*>(pl + P.o_bsup);
+  m.tgt = reinterpret_cast<const int*>(pl + P.o_tgt);
+  m.tpp = reinterpret_cast<const int*>(pl + P.o_tpp);
+  m.tslot = reinterpret_cast<const int*>(pl + P.o_tslot);
+  m.brows = reinterpret_cast<const int*>(pl + P.o_brows);
+  return m;
+}
+
+// x = X^{-1} b for one right-hand side with the factor L D L^T of X (its
+// resident copy F).  b (in: right-hand side, out: solution), y and U
+// (scratch: n and P.uslots doubles) and the plan (m) are shared memory; b
 // must be complete and visible to the CTA on entry.
-//   forward, leaves first: [y_s; u_R] = P_s b_s with y_s scaled by D_s^{-1}
-//   as it is stored and u_R into U, then b_R -= u_R, each ancestor row by
-//   one thread, its contributions in a fixed order.  A level reads only b_s
-//   of its own supernodes, which no supernode of the level writes (the
-//   updates go to ancestors, which sit on higher levels);
+//   forward, leaves first: [D_s^{-1} y_s; u_R] = P'_s b_s (P'_s: P_s with
+//   D_s^{-1} folded into its diagonal block) with u_R into U, then
+//   b_R -= u_R, each ancestor row by one thread, its contributions in a
+//   fixed order.  A level reads only b_s of its own supernodes, which no
+//   supernode of the level writes (the updates go to ancestors, which sit on
+//   higher levels);
 //   backward, root first: x_s = P_s^T [D_s^{-1} y_s; -x_R] with x_R already
 //   final, written over b_s.
-// No atomics: the result does not depend on the order threads run in.  Every
-// thread runs the same number of loop trips (the group sums shuffle).
-__device__ void res_solve(const DevFactor& F, const ResidentPlan& P, const int* lofs,
-                          double* __restrict__ b, double* __restrict__ y, double* __restrict__ U) {
-  const int L = P.nlev, W = L + 1;
+// Only panel entries come from global memory.  No atomics: the result does
+// not depend on the order threads run in.  Every thread runs the same number
+// of loop trips (the group sums shuffle).
+__device__ void res_solve(const ResFactor& F, int nlev, const ResSmem& m, double* __restrict__ b,
+                          double* __restrict__ y, double* __restrict__ U) {
+  const int W = nlev + 1;
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int l = 0; l < L; ++l) {
-    const int r0 = lofs[kResOffR * W + l], nrow = lofs[kResOffR * W + l + 1] - r0;
-    const int lpr = lofs[kResOffFL * W + l];
+  for (int l = 0; l < nlev; ++l) {
+    const int r0 = m.offs[kResOffR * W + l], nrow = m.offs[kResOffR * W + l + 1] - r0;
+    const int lpr = m.offs[kResOffFL * W + l];
+    const int lb = m.offs[kResOffLB * W + l];
     const int sub = tid & (lpr - 1);
     for (int u0 = 0; u0 < nrow * lpr; u0 += nt) {
       const int t = (u0 + tid) / lpr;
       const bool live = t < nrow;
       double v = 0.0;
-      ResRow r{};
+      ResSup d{};
+      int i = 0;
       if (live) {
-        r = P.frow[r0 + t];
-        v = res_dot(F.pan_cm + r.p, r.ld, b + r.f, r.kend, sub, lpr);
+        d = m.sups[m.fsup[r0 + t]];
+        i = t - d.rb;
+        v = res_dot(F.fpan + d.p + i, d.ld, b + d.f, i < d.w ? i + 1 : d.w, sub, lpr);
       }
       v = res_group_sum(v, lpr);
       if (live && sub == 0) {
-        if (r.dst >= 0) y[r.dst] = v * __ldg(F.dinv + r.dst);
-        else U[-1 - r.dst] = v;
+        if (i < d.w) y[d.f + i] = v;
+        else U[d.gb + i - d.w - lb] = v;
       }
     }
     __syncthreads();
-    const int t0 = lofs[kResOffT * W + l], t1 = lofs[kResOffT * W + l + 1];
+    const int t0 = m.offs[kResOffT * W + l], t1 = m.offs[kResOffT * W + l + 1];
     if (t1 > t0) {
       for (int j = t0 + tid; j < t1; j += nt) {
-        const int row = P.ftgt[j];
-        const int e1 = P.fpp[j];
+        const int row = m.tgt[j];
         double acc = b[row];
-        for (int e = j > t0 ? P.fpp[j - 1] : 0; e < e1; ++e) acc -= U[e];
+        for (int e = j > 0 ? m.tpp[j - 1] : 0; e < m.tpp[j]; ++e) acc -= U[m.tslot[e]];
         b[row] = acc;
       }
       __syncthreads();
     }
   }
-  for (int l = L - 1; l >= 0; --l) {
-    const int c0 = lofs[kResOffC * W + l], ncol = lofs[kResOffC * W + l + 1] - c0;
-    const int lpr = lofs[kResOffBL * W + l];
+  for (int l = nlev - 1; l >= 0; --l) {
+    const int c0 = m.offs[kResOffC * W + l], ncol = m.offs[kResOffC * W + l + 1] - c0;
+    const int lpr = m.offs[kResOffBL * W + l];
     const int sub = tid & (lpr - 1);
     for (int u0 = 0; u0 < ncol * lpr; u0 += nt) {
       const int t = (u0 + tid) / lpr;
       const bool live = t < ncol;
       double v = 0.0;
-      ResCol c{};
+      ResSup d{};
+      int k = 0;
       if (live) {
-        c = P.bcol[c0 + t];
-        const double* __restrict__ p = F.pan_rm + c.p;  // (i, k) at i * w + k
-        v = res_dot(p + (int64_t)c.k * c.w, c.w, y + c.f + c.k, c.w - c.k, sub, lpr) -
-            res_dot_gather(p + (int64_t)c.w * c.w, c.w, F.sup_rows + c.rp + c.w, b, c.ld - c.w,
-                           sub, lpr);
+        d = m.sups[m.bsup[c0 + t]];
+        k = t - d.cb;
+        const double* __restrict__ p = F.bpan + d.p + k;  // (i, k) at i * w + k
+        v = res_dot(p + (int64_t)k * d.w, d.w, y + d.f + k, d.w - k, sub, lpr) -
+            res_dot_gather(p + (int64_t)d.w * d.w, d.w, m.brows + d.gb, b, d.ld - d.w, sub, lpr);
       }
       v = res_group_sum(v, lpr);
-      if (live && sub == 0) b[c.f + c.k] = v;
+      if (live && sub == 0) b[d.f + k] = v;
     }
     __syncthreads();
   }
-}
-
-__device__ __forceinline__ void res_stage_offsets(const ResidentPlan& P, int* lofs) {
-  for (int e = threadIdx.x; e < kResOffN * (P.nlev + 1); e += blockDim.x) lofs[e] = P.offs[e];
 }
 
 // hsh[k] = <V_k, b> for k < nb: one warp per basis vector
@@ -189,15 +221,15 @@ __host__ __device__ constexpr size_t res_small_bytes() {
   return (sizeof(SmallShared) + 15) & ~(size_t)15;
 }
 constexpr int kResHsh = 24;  // >= kMaxB, padded
-// solve kernel: b, y, U, then the level offsets
-size_t res_solve_smem_bytes(int64_t n, int uslots) {
-  return sizeof(double) * (2 * (size_t)n + (size_t)uslots) + sizeof(int) * kResOffs;
+// solve kernel: the plan (16-byte aligned), then b, y, U
+size_t res_solve_smem_bytes(int64_t n, const ResidentPlan& P) {
+  return sizeof(double) * (2 * (size_t)n + (size_t)P.uslots) + (size_t)P.bytes;
 }
 // round kernel: the small dense work, the dot products and reductions, then
 // as the solve kernel
-size_t res_smem_bytes(int64_t n, int uslots) {
+size_t res_smem_bytes(int64_t n, const ResidentPlan& P) {
   return res_small_bytes() + sizeof(double) * ((size_t)kResHsh + 32) +
-         res_solve_smem_bytes(n, uslots);
+         res_solve_smem_bytes(n, P);
 }
 
 __global__ void __launch_bounds__(kResidentThreads, 1) resident_round_kernel(ResidentArgs a) {
@@ -206,11 +238,12 @@ __global__ void __launch_bounds__(kResidentThreads, 1) resident_round_kernel(Res
   double* hsh = reinterpret_cast<double*>(smem_raw + res_small_bytes());
   int* stflag = reinterpret_cast<int*>(hsh + kResHsh - 1);  // past the kMaxB dot products
   double* red = hsh + kResHsh;
-  double* b = red + 32;
+  unsigned char* pl = reinterpret_cast<unsigned char*>(red + 32);  // 16-byte aligned
   const int64_t n = a.n;
+  double* b = reinterpret_cast<double*>(pl + a.plan.bytes);
   double* y = b + n;
   double* U = y + n;
-  int* lofs = reinterpret_cast<int*>(U + a.plan.uslots);
+  const int nlev = a.plan.nlev;
   const RoundCols& rc = a.rc;
   SmallState& ss = a.ss;
   const int q = blockIdx.x;
@@ -224,11 +257,12 @@ __global__ void __launch_bounds__(kResidentThreads, 1) resident_round_kernel(Res
   // z carried over the breakpoint (z_0 = x(0), z_j = z_{j-1} + L_{j-1} z'_{j-1})
   const bool first = rc.seg[q] == 0;
   const double lp = rc.lprev[q];
+  if (tid == 0) sh.cm = 0;  // no residual test has run yet
   for (int64_t i = tid; i < n; i += nt) {
     Z[i] = first ? X[i] : fma(lp, Zp[i], Z[i]);
     b[i] = 0.0;
   }
-  res_stage_offsets(a.plan, lofs);
+  const ResSmem ms = res_stage_plan(a.plan, pl);
   __syncthreads();
   // B s_j: the slopes of the column's sources on the segment
   {
@@ -254,14 +288,14 @@ __global__ void __launch_bounds__(kResidentThreads, 1) resident_round_kernel(Res
     }
   }
   __syncthreads();
-  res_solve(a.FG, a.plan, lofs, b, y, U);  // z' = G^{-1} B s_j
+  res_solve(a.FG, nlev, ms, b, y, U);  // z' = G^{-1} B s_j
   for (int64_t i = tid; i < n; i += nt) {
     const double zp = b[i];
     Zp[i] = zp;
     b[i] = zp * a.cperm[i];
   }
   __syncthreads();
-  res_solve(a.FG, a.plan, lofs, b, y, U);  // w = G^{-1} C z'
+  res_solve(a.FG, nlev, ms, b, y, U);  // w = G^{-1} C z'
   // start vector v = x + F (F = w - z, Eq. 6), beta = ||v||
   double acc = 0.0;
   for (int64_t i = tid; i < n; i += nt) {
@@ -290,7 +324,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1) resident_round_kernel(Res
       __syncthreads();
       for (int64_t i = tid; i < n; i += nt) b[i] = vj[i] * a.cperm[i];
       __syncthreads();
-      res_solve(a.F1, a.plan, lofs, b, y, U);
+      res_solve(a.F1, nlev, ms, b, y, U);
       // two classical Gram-Schmidt passes against v_0..v_j
       for (int pass = 0; pass < 2; ++pass) {
         res_dots(V, n, j + 1, b, hsh);
@@ -348,41 +382,60 @@ __global__ void __launch_bounds__(kResidentThreads, 1) resident_round_kernel(Res
 // column q sits at q * ldq + r(i) * ldi, r(i) = perm[i] (perm: new -> old,
 // the caller's order) or i (the factor's order).  b and x may alias.
 __global__ void __launch_bounds__(kResidentThreads, 1)
-resident_solve_kernel(DevFactor F, ResidentPlan P, const double* bin, double* xout, int64_t n,
+resident_solve_kernel(ResFactor F, ResidentPlan P, const double* bin, double* xout, int64_t n,
                       int64_t ldi, int64_t ldq, const int32_t* __restrict__ perm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* b = reinterpret_cast<double*>(smem_raw);
+  const ResSmem ms = res_stage_plan(P, smem_raw);
+  double* b = reinterpret_cast<double*>(smem_raw + P.bytes);
   double* y = b + n;
   double* U = y + n;
-  int* lofs = reinterpret_cast<int*>(U + P.uslots);
-  res_stage_offsets(P, lofs);
   const double* bq = bin + (int64_t)blockIdx.x * ldq;
   double* xq = xout + (int64_t)blockIdx.x * ldq;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) b[i] = bq[(perm ? perm[i] : i) * ldi];
   __syncthreads();
-  res_solve(F, P, lofs, b, y, U);
+  res_solve(F, P.nlev, ms, b, y, U);
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) xq[(perm ? perm[i] : i) * ldi] = b[i];
+}
+
+// Resident copy of one supernode's panel per CTA: forward rows with D^{-1}
+// folded into the diagonal block, backward columns as they are.
+__global__ void resident_store_kernel(DevFactor F, const ResStoreSup* __restrict__ sup,
+                                      double* __restrict__ fpan, double* __restrict__ bpan) {
+  const ResStoreSup d = sup[blockIdx.x];
+  const int64_t cnt = (int64_t)d.ld * d.w;
+  for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int i = (int)(e % d.ld);  // column-major: e = k * ld + i
+    const double sc = i < d.w ? F.dinv[d.f + i] : 1.0;
+    fpan[d.fdst + e] = F.pan_cm[d.src + e] * sc;
+    bpan[d.bdst + e] = F.pan_rm[d.src + e];
+  }
 }
 
 }  // namespace
 
-bool resident_fits(int64_t n, int uslots) {
+void resident_store(const DevFactor& F, const ResStoreSup* sup, int nsup, double* fpan, double* bpan,
+                    cudaStream_t st) {
+  if (nsup <= 0) return;
+  resident_store_kernel<<<nsup, 256, 0, st>>>(F, sup, fpan, bpan);
+}
+
+bool resident_fits(int64_t n, const ResidentPlan& P) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return n > 0 && n <= kResidentMaxN && res_smem_bytes(n, uslots) <= (size_t)optin;
+  return n > 0 && n <= kResidentMaxN && res_smem_bytes(n, P) <= (size_t)optin;
 }
 
-bool resident_set_limits(int64_t n, int uslots) {
+bool resident_set_limits(int64_t n, const ResidentPlan& P) {
   // the kernels' limits only grow: contexts of several sizes share them
   static size_t done = 0;
-  const size_t bytes = res_smem_bytes(n, uslots);
+  const size_t bytes = res_smem_bytes(n, P);
   if (bytes <= done) return true;
   const bool ok =
       cudaFuncSetAttribute(resident_round_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)bytes) == cudaSuccess &&
       cudaFuncSetAttribute(resident_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)res_solve_smem_bytes(n, uslots)) == cudaSuccess;
+                           (int)res_solve_smem_bytes(n, P)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     return false;
@@ -393,18 +446,18 @@ bool resident_set_limits(int64_t n, int uslots) {
 
 void resident_round(const ResidentArgs& a, int K, cudaStream_t st) {
   if (K <= 0) return;
-  resident_round_kernel<<<K, kResidentThreads, res_smem_bytes(a.n, a.plan.uslots), st>>>(a);
+  resident_round_kernel<<<K, kResidentThreads, res_smem_bytes(a.n, a.plan), st>>>(a);
 }
 
-void resident_solve(const DevFactor& F, const ResidentPlan& P, const double* b, double* x,
+void resident_solve(const ResFactor& F, const ResidentPlan& P, const double* b, double* x,
                     int64_t n, int ncols, int64_t ldi, int64_t ldq, const int32_t* perm,
                     cudaStream_t st) {
   if (ncols <= 0) return;
-  const size_t smem = res_solve_smem_bytes(n, P.uslots);
+  const size_t smem = res_solve_smem_bytes(n, P);
   resident_solve_kernel<<<ncols, kResidentThreads, smem, st>>>(F, P, b, x, n, ldi, ldq, perm);
 }
 
-float resident_time_solve(const DevFactor& F, const ResidentPlan& P, const double* b, double* x,
+float resident_time_solve(const ResFactor& F, const ResidentPlan& P, const double* b, double* x,
                           int64_t n, cudaStream_t st, int reps) {
   resident_solve(F, P, b, x, n, 1, 1, n, nullptr, st);
   cudaEvent_t e0, e1;

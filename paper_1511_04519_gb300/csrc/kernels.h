@@ -400,46 +400,58 @@ void adj_x0_obs(const int32_t* groups, int K, double* XB, int64_t n, const doubl
                 const int32_t* map, int nrows, cudaStream_t st);
 void adj_csum(const double* CB, int G, int64_t n, const int32_t* perm, double* dc, cudaStream_t st);
 
-// Resident rounds (k_resident.cu): on grids of at most kResidentMaxN nodes one
-// CTA runs a column's whole segment, its triangular substitutions level by
-// level inside the CTA.  Work lists per tree level (leaves first), each entry
-// carrying what its thread needs (no lookups through the supernode tables):
-//   forward, every panel row of the level's supernodes (frow): a diagonal
-//   row stores y (dst >= 0: its node), a row below the diagonal block stores
-//   its product in slot -1 - dst of a shared scratch, ordered by target row;
-//   then target ftgt[j] subtracts, in order, the slots from the previous
-//   target's fpp (0 for the level's first target) up to fpp[j]: all products in parallel, each sum in a fixed order (no
-//   atomics, reproducible);
-//   backward, the panel columns (bcol).
-// A level's dot products run lpr lanes each (1, 2, 4 or 8, more on levels
-// with few rows).  Level l's entries: frow [offs[R][l], offs[R][l+1]), ftgt
-// [offs[T][l], ...), bcol [offs[C][l], ...); offs[FL][l], offs[BL][l]: the
-// forward and backward lanes per dot product.
+// Resident rounds (k_resident.cu): on small grids one CTA runs a column's
+// whole segment, its triangular substitutions level by level inside the CTA.
+// The path keeps its own copy of each factor's panels stored level by level
+// (leaves first), D^{-1} folded into the diagonal blocks' forward rows, and a
+// plan small enough to sit in the CTA's shared memory for the whole kernel
+// (every global load then goes to panel entries; a load from L2 costs a CTA
+// with one column far more than the arithmetic):
+//   sups[s]: the supernode's panel offset p in the copies, first node f,
+//     width w, rows ld, its first forward row (rb) and backward column (cb)
+//     within its level, and the global number gb of its first row below the
+//     diagonal block;
+//   fsup / bsup: per level, the supernode of each forward row / backward
+//     column (row i = t - rb, column k = t - cb);
+//   forward: a diagonal row stores y, a row below the diagonal block stores
+//     its product in scratch slot gb + i - w - offs[LB][l]; then target
+//     tgt[j] subtracts, in order, the slots tslot[tpp[j-1] .. tpp[j]) (from 0
+//     for the level's first target): all products in parallel, each sum in a
+//     fixed order (no atomics, reproducible);
+//   brows[gb + i - w]: the ancestor node of row i >= w (backward gathers).
+// offs[X][l] for X = R, T, C: level l's first forward row, target, backward
+// column; FL, BL: lanes per dot product (1, 2, 4 or 8, more on levels with
+// few rows); LB: the level's first row below a diagonal block.
 constexpr int64_t kResidentMaxN = 8192;
 constexpr int kResidentMaxLevels = 64;
 constexpr int kResidentThreads = 512;
-constexpr int kResOffR = 0, kResOffT = 1, kResOffC = 2, kResOffFL = 3, kResOffBL = 4, kResOffN = 5;
-struct ResRow {     // row i of P_s: entries pan_cm[p + k * ld], k < kend, times b[f + k]
-  int64_t p;
-  int32_t f, dst, kend, ld;
+constexpr int kResOffR = 0, kResOffT = 1, kResOffC = 2, kResOffFL = 3, kResOffBL = 4,
+              kResOffLB = 5, kResOffN = 6;
+struct ResSup {
+  int32_t p, f, w, ld, rb, cb, gb;
 };
-struct ResCol {     // column k of P_s: entries pan_rm[p + i * w], k <= i < ld
-  int64_t p;
-  int64_t rp;       // row list of s (sup_rows + rp): the ancestors' nodes from i = w
-  int32_t f, k, w, ld;
+struct ResFactor {  // one factor's panels in the resident order
+  const double* fpan = nullptr;  // column-major per supernode, D^{-1} in the diagonal rows
+  const double* bpan = nullptr;  // row-major per supernode
 };
+// The plan is one blob (copied to shared memory at kernel start); o_* are
+// byte offsets of its sections, each 16-byte aligned.
 struct ResidentPlan {
-  const ResRow* frow = nullptr;
-  const int32_t* ftgt = nullptr;
-  const int32_t* fpp = nullptr;    // per target, the end of its level-local slots
-  const ResCol* bcol = nullptr;
-  const int32_t* offs = nullptr;   // [kResOffN][nlev + 1]
+  const unsigned char* blob = nullptr;
+  int32_t bytes = 0;
+  int32_t o_offs = 0, o_sups = 0, o_fsup = 0, o_bsup = 0, o_tgt = 0, o_tpp = 0, o_tslot = 0,
+          o_brows = 0;
   int32_t nlev = 0;
-  int32_t uslots = 0;              // largest number of below-diagonal rows of a level
+  int32_t uslots = 0;  // largest number of below-diagonal rows of a level
+};
+// where one supernode's panel goes in the resident copies
+struct ResStoreSup {
+  int64_t src, fdst, bdst;
+  int32_t f, w, ld;
 };
 struct ResidentArgs {
-  DevFactor F1;          // X1 of the Krylov space (C + gamma G, or G for the inverted space)
-  DevFactor FG;          // G
+  ResFactor F1;          // X1 of the Krylov space (C + gamma G, or G for the inverted space)
+  ResFactor FG;          // G
   ResidentPlan plan;
   double* Vb;            // basis slots, vstride apart
   int64_t vstride;
@@ -457,22 +469,26 @@ struct ResidentArgs {
   int32_t m_max;
   int64_t n;
 };
-// whether a grid of n nodes (and uslots scratch slots) fits one CTA's shared
-// memory on this device
-bool resident_fits(int64_t n, int uslots);
+// the resident copies of factor F (fpan, bpan: as many doubles as F's
+// panels) from the per-supernode map sup[nsup]
+void resident_store(const DevFactor& F, const ResStoreSup* sup, int nsup, double* fpan, double* bpan,
+                    cudaStream_t st);
+// whether a grid of n nodes with plan P fits one CTA's shared memory on this
+// device
+bool resident_fits(int64_t n, const ResidentPlan& P);
 // raise the kernels' shared-memory limits for them (false on failure)
-bool resident_set_limits(int64_t n, int uslots);
+bool resident_set_limits(int64_t n, const ResidentPlan& P);
 // one round: K CTAs, column q of rc by CTA q
 void resident_round(const ResidentArgs& a, int K, cudaStream_t st);
 // x_q = F^{-1} b_q for ncols columns, one CTA each: entry i of column q at
 // q * ldq + r(i) * ldi with r = perm (new -> old: the caller's order) or the
 // identity (the factor's order); b and x may alias
-void resident_solve(const DevFactor& F, const ResidentPlan& P, const double* b, double* x,
+void resident_solve(const ResFactor& F, const ResidentPlan& P, const double* b, double* x,
                     int64_t n, int ncols, int64_t ldi, int64_t ldq, const int32_t* perm,
                     cudaStream_t st);
 // best of reps (ms) of one CTA's solve pair x = F^{-1} b (b, x: n doubles of
 // the device); -1 on a CUDA error
-float resident_time_solve(const DevFactor& F, const ResidentPlan& P, const double* b, double* x,
+float resident_time_solve(const ResFactor& F, const ResidentPlan& P, const double* b, double* x,
                           int64_t n, cudaStream_t st, int reps);
 
 }  // namespace matex

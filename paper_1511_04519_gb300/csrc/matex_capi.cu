@@ -83,6 +83,8 @@ struct matex_ctx {
   // resident rounds (opts.resident): per-level work lists, the choice, and
   // the setup's timings of one solve pair both ways (ms, -1 if not taken)
   ResidentPlan rplan;
+  ResFactor rM, rG;          // the factors' resident copies
+  ResStoreSup* rsup = nullptr;
   bool resident_ok = false;  // plan built and shared-memory limits set
   bool resident = false;
   float res_pair_ms = -1.f, lvl_pair_ms = -1.f;
@@ -612,87 +614,131 @@ bool plan_levels(matex_ctx* c) {
   return true;
 }
 
-// Work lists of the resident rounds (see ResidentPlan): per tree level,
-// leaves first, the forward rows and backward columns supernode by
-// supernode (consecutive threads read consecutive panel entries); the
-// level's below-diagonal rows numbered by target row, contributions in
-// supernode order; per level and direction the lanes per dot product.
+// The resident rounds' plan blob (see ResidentPlan) and the resident copies
+// of both factors: per tree level, leaves first, the panels of its
+// supernodes one after another, their forward rows and backward columns in
+// supernode order (consecutive threads read consecutive panel entries), the
+// level's below-diagonal rows grouped by target row with contributions in
+// supernode order, and per level and direction the lanes per dot product.
 bool plan_resident(matex_ctx* c, int threads) {
   const Symbolic& S = c->S;
   const int nlev = (int)S.level_ptr.size() - 1;
-  if (nlev > kResidentMaxLevels) return false;
-  std::vector<ResRow> frow;
-  std::vector<ResCol> bc;
-  std::vector<int32_t> offs(kResOffN * (nlev + 1), 0), ftgt, fpp;
-  struct Upd { int32_t t, ord; size_t at; };
+  if (nlev > kResidentMaxLevels || S.nsup > 65535) return false;
+  std::vector<ResSup> sups(S.nsup);
+  std::vector<ResStoreSup> store;
+  std::vector<int32_t> offs(kResOffN * (nlev + 1), 0), tgt, tpp, tslot, brows;
+  std::vector<uint16_t> fsup, bsup;
+  struct Upd { int32_t t, ord, slot; };
   std::vector<Upd> up;
   int uslots = 0;
+  int64_t dst = 0;
   auto lanes = [&](int items, int longest) {
-    // one pass over the level when possible, no more lanes than the longest
-    // dot product has groups of eight terms
-    int l = 1;
-    while (l < 8 && items * (2 * l) <= threads && 8 * l < longest) l *= 2;
-    return l;
+    // lanes per dot product: the fewest L2 round trips, passes over the
+    // level's items times batches of 8 loads per lane (ties: fewer lanes)
+    int best = 1;
+    long long cost = -1;
+    for (int l = 1; l <= 8; l *= 2) {
+      const long long passes = ((long long)items * l + threads - 1) / threads;
+      const long long batches = (longest + 8LL * l - 1) / (8LL * l);
+      if (cost < 0 || passes * batches < cost) {
+        cost = passes * batches;
+        best = l;
+      }
+    }
+    return best;
   };
-  for (int l = 0; l < nlev; ++l) {
-    const int r0 = (int)frow.size();
-    offs[kResOffR * (nlev + 1) + l] = r0;
-    offs[kResOffT * (nlev + 1) + l] = (int32_t)ftgt.size();
-    offs[kResOffC * (nlev + 1) + l] = (int32_t)bc.size();
+  auto at = [&](int seg, int l) -> int32_t& { return offs[seg * (nlev + 1) + l]; };
+  for (int l = 0; l <= nlev; ++l) {
+    at(kResOffR, l) = (int32_t)fsup.size();
+    at(kResOffT, l) = (int32_t)tgt.size();
+    at(kResOffC, l) = (int32_t)bsup.size();
+    at(kResOffLB, l) = (int32_t)brows.size();
+    if (l == nlev) break;
     up.clear();
-    int fmax = 1, bmax = 1;
+    int fmax = 1, bmax = 1, rb = 0, cb = 0;
+    const int lb = (int)brows.size();
     for (int k = S.level_ptr[l]; k < S.level_ptr[l + 1]; ++k) {
       const int s = S.level_sups[k];
       const int f = S.sup_first[s];
       const int w = S.sup_first[s + 1] - f;
       const int64_t rp = S.sup_rowptr[s];
       const int ld = (int)(S.sup_rowptr[s + 1] - rp);
-      const int64_t po = S.pan_off[s];
-      for (int i = 0; i < ld; ++i) {
-        frow.push_back(ResRow{po + i, f, i < w ? f + i : 0, i < w ? i + 1 : w, ld});
-        if (i >= w) up.push_back(Upd{S.sup_rows[rp + i], (int32_t)up.size(), frow.size() - 1});
+      sups[s] = ResSup{(int32_t)dst, f, w, ld, rb, cb, (int32_t)brows.size()};
+      store.push_back(ResStoreSup{S.pan_off[s], dst, dst, f, w, ld});
+      for (int i = 0; i < ld; ++i) fsup.push_back((uint16_t)s);
+      for (int j = 0; j < w; ++j) bsup.push_back((uint16_t)s);
+      for (int i = w; i < ld; ++i) {
+        up.push_back(Upd{S.sup_rows[rp + i], (int32_t)up.size(), (int32_t)brows.size() - lb});
+        brows.push_back(S.sup_rows[rp + i]);
       }
-      for (int j = 0; j < w; ++j) bc.push_back(ResCol{po + j, rp, f, j, w, ld});
+      rb += ld;
+      cb += w;
+      dst += (int64_t)ld * w;
       fmax = std::max(fmax, w);
       bmax = std::max(bmax, ld);
     }
     std::sort(up.begin(), up.end(), [](const Upd& x, const Upd& y) {
       return x.t != y.t ? x.t < y.t : x.ord < y.ord;
     });
-    // target j takes the slots from the previous target's end (0 for the
-    // level's first) to fpp[j]
+    // target j subtracts the slots tslot[tpp[j-1] .. tpp[j]) (level-local,
+    // from 0 for the level's first target)
     for (size_t e = 0; e < up.size(); ++e) {
-      frow[up[e].at].dst = -1 - (int32_t)e;  // scratch slot, in target order
+      tslot.push_back(up[e].slot);
       if (e + 1 == up.size() || up[e + 1].t != up[e].t) {
-        ftgt.push_back(up[e].t);
-        fpp.push_back((int32_t)e + 1);
+        tgt.push_back(up[e].t);
+        tpp.push_back((int32_t)e + 1);
       }
     }
     uslots = std::max(uslots, (int)up.size());
-    offs[kResOffFL * (nlev + 1) + l] = lanes((int)frow.size() - r0, fmax);
-    offs[kResOffBL * (nlev + 1) + l] =
-        lanes((int)bc.size() - offs[kResOffC * (nlev + 1) + l], bmax);
+    at(kResOffFL, l) = lanes(rb, fmax);
+    at(kResOffBL, l) = lanes(cb, bmax);
   }
-  offs[kResOffR * (nlev + 1) + nlev] = (int32_t)frow.size();
-  offs[kResOffT * (nlev + 1) + nlev] = (int32_t)ftgt.size();
-  offs[kResOffC * (nlev + 1) + nlev] = (int32_t)bc.size();
+  if (dst > INT32_MAX) return false;
+  // tslot entries are level-local; tpp too, but stored after the level's
+  // earlier targets: make both absolute within the blob's lists
+  {
+    int32_t base = 0;
+    for (int l = 0; l < nlev; ++l) {
+      const int t0 = at(kResOffT, l), t1 = at(kResOffT, l + 1);
+      for (int j = t0; j < t1; ++j) tpp[j] += base;
+      if (t1 > t0) base = tpp[t1 - 1];
+    }
+  }
+  std::vector<unsigned char> blob;
+  auto put = [&](const void* d, size_t bytes) -> int32_t {
+    const size_t o = (blob.size() + 15) & ~(size_t)15;
+    blob.resize(o + bytes);
+    if (bytes) std::memcpy(blob.data() + o, d, bytes);
+    return (int32_t)o;
+  };
   ResidentPlan P;
-  ResRow* r1 = nullptr;
-  ResCol* c1 = nullptr;
-  int32_t *i1 = nullptr, *i2 = nullptr, *i3 = nullptr;
-  if (!c->upload(r1, frow.data(), frow.size()) || !c->upload(i1, ftgt.data(), ftgt.size()) ||
-      !c->upload(i2, fpp.data(), fpp.size()) || !c->upload(c1, bc.data(), bc.size()) ||
-      !c->upload(i3, offs.data(), offs.size()))
-    return false;
-  P.frow = r1;
-  P.ftgt = i1;
-  P.fpp = i2;
-  P.bcol = c1;
-  P.offs = i3;
+  P.o_offs = put(offs.data(), 4 * offs.size());
+  P.o_sups = put(sups.data(), sizeof(ResSup) * sups.size());
+  P.o_fsup = put(fsup.data(), 2 * fsup.size());
+  P.o_bsup = put(bsup.data(), 2 * bsup.size());
+  P.o_tgt = put(tgt.data(), 4 * tgt.size());
+  P.o_tpp = put(tpp.data(), 4 * tpp.size());
+  P.o_tslot = put(tslot.data(), 4 * tslot.size());
+  P.o_brows = put(brows.data(), 4 * brows.size());
+  blob.resize((blob.size() + 15) & ~(size_t)15);
+  P.bytes = (int32_t)blob.size();
   P.nlev = nlev;
   P.uslots = uslots;
+  unsigned char* bd = nullptr;
+  ResStoreSup* sd = nullptr;
+  double *fm = nullptr, *bm = nullptr, *fg = nullptr, *bg = nullptr;
+  if (!c->upload(bd, blob.data(), blob.size()) || !c->upload(sd, store.data(), store.size()) ||
+      !c->alloc(fm, (size_t)dst) || !c->alloc(bm, (size_t)dst) || !c->alloc(fg, (size_t)dst) ||
+      !c->alloc(bg, (size_t)dst))
+    return false;
+  P.blob = bd;
   c->rplan = P;
-  return true;
+  c->rsup = sd;
+  c->rM = ResFactor{fm, bm};
+  c->rG = ResFactor{fg, bg};
+  resident_store(c->fM, sd, (int)store.size(), fm, bm, c->st);
+  resident_store(c->fG, sd, (int)store.size(), fg, bg, c->st);
+  return cudaStreamSynchronize(c->st) == cudaSuccess;
 }
 
 int solve_cols(matex_ctx* c, const DevFactor& F, int ncols) {
@@ -1105,7 +1151,8 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
     int l = 1;
     // resident rounds: the DC and initial-state solves by the same one-CTA
     // substitution (no atomics anywhere in such a run: reproducible)
-    if (c->resident) resident_solve(F, c->rplan, c->Y, c->Y, n, K, c->ldy, 1, nullptr, st);
+    if (c->resident)
+      resident_solve(&F == &c->fM ? c->rM : c->rG, c->rplan, c->Y, c->Y, n, K, c->ldy, 1, nullptr, st);
     else l = solve_cols(c, F, K);
     prof_end(c, e, P_SOLVE, l, solve_flops(c, K), solve_bytes(c, K));
     launches += l;
@@ -1187,8 +1234,8 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
       // every column's whole segment in one launch (one CTA each), then the
       // recombination of the round's outputs
       ResidentArgs ra{};
-      ra.F1 = c->opts.krylov == 1 ? c->fG : c->fM;
-      ra.FG = c->fG;
+      ra.F1 = c->opts.krylov == 1 ? c->rG : c->rM;
+      ra.FG = c->rG;
       ra.plan = c->rplan;
       ra.Vb = c->Vb;
       ra.vstride = vstride;
@@ -2345,12 +2392,13 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
       n <= kResidentMaxN) {
     // resident rounds: one CTA's solve pair against the batched path's
     // single-column pair (in its tuned launch mode), best of five each
-    const DevFactor& F1 = o.krylov == 1 ? c->fG : c->fM;
-    if (plan_resident(c, kResidentThreads) && resident_fits(n, c->rplan.uslots) &&
-        resident_set_limits(n, c->rplan.uslots)) {
+    if (plan_resident(c, kResidentThreads) && resident_fits(n, c->rplan) &&
+        resident_set_limits(n, c->rplan)) {
       c->resident_ok = true;
       cudaMemsetAsync(c->Y, 0, sizeof(double) * (size_t)n * c->ldy, c->st);
-      c->res_pair_ms = resident_time_solve(F1, c->rplan, c->Y, c->Y2, n, c->st, 5);
+      const ResFactor& R1 = o.krylov == 1 ? c->rG : c->rM;
+      const DevFactor& F1 = o.krylov == 1 ? c->fG : c->fM;
+      c->res_pair_ms = resident_time_solve(R1, c->rplan, c->Y, c->Y2, n, c->st, 5);
       cudaEvent_t e0, e1;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
@@ -2432,6 +2480,12 @@ matex_status matex_set_caps(matex_ctx* c, const double* cap) {
             cudaMemcpy(c->c_perm, cp.data(), sizeof(double) * c->n, cudaMemcpyHostToDevice) ==
                 cudaSuccess;
   if (!ok) return cuda_check(c, "set_caps upload");
+  if (c->resident_ok) {
+    // the resident copy of the refactored C + gamma G
+    resident_store(c->fM, c->rsup, c->S.nsup, const_cast<double*>(c->rM.fpan),
+                   const_cast<double*>(c->rM.bpan), c->st);
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "set_caps resident copy");
+  }
   c->c_host.assign(cap, cap + c->n);
   c->taped = false;
   c->tr_h = 0.0;  // the trapezoidal factor C + h/2 G is refactored on its next use
@@ -2542,8 +2596,7 @@ matex_status matex_solve_resident(matex_ctx* c, int32_t which, int32_t ncols, co
   if (!c->resident_ok)
     return fail(c, MATEX_ERR_STATE, "this context has no resident solve (grid too large, or "
                                     "krylov 2, tape, tail_eps or resident = 1 at setup)");
-  const DevFactor& F = which == 0 ? c->fM : c->fG;
-  resident_solve(F, c->rplan, b, x, c->n, ncols, 1, c->n, c->perm, c->st);
+  resident_solve(which == 0 ? c->rM : c->rG, c->rplan, b, x, c->n, ncols, 1, c->n, c->perm, c->st);
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "resident solve sync");
   return cuda_check(c, "resident solve");
 }
@@ -2558,7 +2611,9 @@ matex_status matex_time_solve(matex_ctx* c, int32_t which, int32_t ncols, int32_
   const DevFactor& F = which % 2 == 0 ? c->fM : c->fG;
   // which 2, 3: the resident substitution, ncols columns of the buffer as n-vectors
   auto one = [&]() {
-    if (which >= 2) resident_solve(F, c->rplan, c->Y, c->Y, c->n, ncols, 1, c->n, nullptr, c->st);
+    if (which >= 2)
+      resident_solve(which == 2 ? c->rM : c->rG, c->rplan, c->Y, c->Y, c->n, ncols, 1, c->n, nullptr,
+                     c->st);
     else solve_cols(c, F, ncols);
   };
   cudaEvent_t e0 = nullptr, e1 = nullptr;
