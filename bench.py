@@ -284,7 +284,8 @@ def ncu_case(what: str) -> int:
     device, solve panels still larger than L2): one warm call, then the
     profiled call.  "solve": matex_solve of 16 columns with the persistent
     kernel; "levels": 64 columns with one launch per tree level; "run": one
-    full matex_run."""
+    full matex_run; "ksweep": bare solve pairs of 1, 4 and 64 columns on the
+    whole grid; "small": one run of the 1,024-node single-group grid."""
     import numpy as np
     import torch
 
@@ -298,6 +299,18 @@ def ncu_case(what: str) -> int:
     off = np.concatenate([[0], np.cumsum(np.diff(p.pwl_off)[sel])]).astype(np.int32)
     q = gridgen.with_sources(p, p.src_node[sel], off, p.pwl_t.reshape(-1, 3)[sel].ravel(),
                              p.pwl_v.reshape(-1, 3)[sel].ravel(), p.src_group[sel], groups)
+    if what == "small":
+        # the single-group 1,024-node grid as set up by default (resident
+        # rounds): one warm run, then one run inside the profiler range
+        sim = M.Sim(gridgen.config0(), graph=False)
+        x = sim.run()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        sim.run(x)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"ncu_case": what, "resident": sim.stats.resident}))
+        return 0
     if what == "ksweep":
         # the whole bench grid, level-by-level launches: one bare solve pair of
         # 1, 4 and 64 right-hand sides (each after its own warm-up call)
@@ -387,19 +400,49 @@ def batch_grids(args, M, stream):
     return res
 
 
+def small_grid(M, stream, steps):
+    """The single-group 1,024-node grid (192 sequential segments): a recorded
+    run, then `steps` timed graph replays, as set up by default (the setup
+    picks resident rounds here) and on the batched path (resident off)."""
+    import torch
+
+    import gridgen
+    p = gridgen.config0()
+    res = {"workload": "grid32x32_1group", "nodes": p.n, "groups": p.n_groups}
+    for name, mode in (("default", "auto"), ("batched_path", "off")):
+        t0 = time.perf_counter()
+        sim = M.Sim(p, stream=stream, resident=mode)
+        setup_s = time.perf_counter() - t0
+        x = sim.run()
+        sim.run(x)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            sim.run(x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        st = sim.stats.as_dict()
+        res[name] = {"ms": ms, "value": p.n * (p.n_out - 1) * p.n_groups / (ms / 1e3), "unit": UNIT,
+                     "resident": st["resident"], "kernel_launches": st["kernel_launches"],
+                     "rounds": st["rounds"], "sum_m": st["sum_m"], "setup_s": setup_s,
+                     "graph_replay": st["graph_replay"]}
+        del sim, x
+    res["resident_speedup"] = res["batched_path"]["ms"] / res["default"]["ms"]
+    return res
+
+
 def other_configs(M, stream, ramps_large=False):
-    """One recorded run, then one timed graph replay, of the single-group
-    1,024-node grid (about 190 sequential segments) and of the four-layer
+    """One recorded run, then one timed graph replay, of the four-layer
     1.44M-node grid with 256 uneven groups (64 sampled output rows), and with
-    ramps_large the same 1.44M-node grid decomposed into ramps (25,600
-    columns in batches of 256)."""
+    ramps_large the same grid decomposed into ramps (25,600 columns in
+    batches of 256)."""
     import numpy as np
     import torch
 
     import gridgen
     res = {}
-    cases = [("grid32x32_1group", gridgen.config0(), 0, "groups"),
-             ("mesh4x600x600_256groups", gridgen.config2(), 64, "groups")]
+    cases = [("mesh4x600x600_256groups", gridgen.config2(), 64, "groups")]
     if ramps_large:
         cases.append(("mesh4x600x600_256groups_ramps", gridgen.config2(), 64, "ramps"))
     for name, p, nrows, dec in cases:
@@ -447,19 +490,19 @@ def main():
     ap.add_argument("--no-tail", action="store_true",
                     help="skip the separately reported tail-skipping run (tail_eps > 0)")
     ap.add_argument("--other-configs", action="store_true",
-                    help="also time one graph-replayed run of the 1,024-node single-group grid "
-                         "and of the 1.44M-node 256-group grid (several minutes)")
+                    help="also time one graph-replayed run of the 1.44M-node 256-group grid "
+                         "(about four minutes with its setup and recorded run)")
     ap.add_argument("--ramps-large", action="store_true",
                     help="with --other-configs, also the 1.44M-node grid as ramps")
     ap.add_argument("--variants", action="store_true",
                     help="also run the inverted (I-MATEX) and standard (MEXP) Krylov spaces "
                          "on the bench grid (Table 1's comparison)")
-    ap.add_argument("--grids", type=int, default=0,
-                    help="also run that many of the 96 uneven single-layer grids as one "
-                         "batch graph launch and report their aggregate rate")
+    ap.add_argument("--grids", type=int, default=96,
+                    help="run that many of the 96 uneven single-layer grids as one batch graph "
+                         "launch and report their aggregate rate (0: skip)")
     ap.add_argument("--profile-step", action="store_true",
                     help="warm up, run one step inside cudaProfilerStart/Stop, print its stats")
-    ap.add_argument("--ncu-case", choices=["solve", "levels", "run", "ksweep"], default=None,
+    ap.add_argument("--ncu-case", choices=["solve", "levels", "run", "ksweep", "small"], default=None,
                     help="reduced case for full ncu captures: the same grid with 8 groups; "
                          "one warm call, then one call inside cudaProfilerStart/Stop")
     args = ap.parse_args()
@@ -780,6 +823,7 @@ def main():
             del sim3, X3, Xr, xbar
             torch.cuda.empty_cache()
 
+    smallg = small_grid(M, stream, args.steps)
     grids = batch_grids(args, M, stream) if args.grids else None
     others = other_configs(M, stream, args.ramps_large) if args.other_configs else None
 
@@ -805,7 +849,7 @@ def main():
                                                  "nonconv", "sweeps_M", "sweeps_G", "solve_columns",
                                                  "rounds", "kernel_launches", "graph_replay",
                                                  "graph_capture_ms")},
-            "batch_grids": grids, "other_configs": others,
+            "small_grid": smallg, "batch_grids": grids, "other_configs": others,
             "autotune": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in t.items()}
                          for t in tuning],
             "autotune_level_blocks": [{k: (round(v, 4) if isinstance(v, float) else v)
