@@ -129,6 +129,16 @@ typedef struct matex_opts {
                               pair against the batched path's single-column pair and takes the
                               resident rounds when they are at most twice as long (they also
                               replace the ~12 other launches of every Arnoldi step) */
+  int32_t tc_solve;        /* supernodes at least tc_min_width wide in the level solves: 0
+                              (default) chosen at setup per column count, 1 off, 2 on.  Their
+                              two dense products per supernode (P_s b_s forward, P_s^T [..]
+                              backward) run on the bf16 tensor cores as an error-free split of
+                              the FP64 operands into nine 6-bit digits (error of the order of an
+                              FP64 dot product), the rest of each level on the FP64 kernels.
+                              With 0 the setup times the solve pair both ways at each column
+                              count it tunes and keeps the tensor cores where they are faster.
+                              Level launches only (not the persistent solve) */
+  int32_t tc_min_width;    /* 0 (default): 64; else at least 32 */
 } matex_opts;
 
 /* Counters and timings of the last matex_run (or of setup for the setup_* fields). */
@@ -161,6 +171,9 @@ typedef struct matex_stats {
                               window tape and reverse work buffers (tape 2) */
   int32_t tc_rounds;       /* segment rounds of the last run whose V y ran on the tensor cores */
   int32_t resident;        /* 1: the segment rounds run as resident rounds (opts.resident) */
+  int32_t tc_solve_supernodes;  /* supernodes whose solve products can run on the tensor cores
+                                   (0: none or tc_solve off) */
+  int32_t tc_solve_min_cols;    /* smallest column count at which they do (0: never) */
 } matex_stats;
 
 void matex_default_opts(matex_opts* opts);

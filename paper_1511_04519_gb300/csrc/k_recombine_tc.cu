@@ -33,55 +33,21 @@
 #include <algorithm>
 
 #include "kernels.h"
+#include "tcgen05_util.cuh"
 
 namespace matex {
 
 namespace {
 
+using namespace tcx;
+
 constexpr int kTcM = 128;          // nodes per tile (MMA M)
 constexpr int kTcN = 48;           // outputs per tile (MMA N)
-constexpr int kTcK = 32;           // basis vectors per K step (two MMAs of K = 16)
-constexpr int kTcS = 9;            // slices per operand, pairs p + q <= kTcS - 1
-constexpr int kTcChunk = 448;      // basis vectors summed exactly before a drain (<= 455)
 constexpr int kTcThreads = 128;
 constexpr int kTcABytes = kTcM * kTcK * 2;  // one slice of an A tile: 8 KB
 constexpr int kTcBBytes = kTcN * kTcK * 2;  // one slice of a B tile: 3 KB
 constexpr int kTcStage = kTcS * (kTcABytes + kTcBBytes);
-constexpr int kTcSbo = (kTcK / 8) * 128;    // bytes between 8-row groups of a tile
 constexpr int kTcTmemCols = 512;
-
-// Byte offset of element (r, k) in a K-major tile of 8x8 core matrices
-// (8 rows of 16 bytes each, contiguous): core matrices along k are 128 bytes
-// apart, 8-row groups kTcSbo apart.
-__device__ __forceinline__ int tc_off(int r, int k) {
-  return (r >> 3) * kTcSbo + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
-}
-
-// The nine base-64 digits of r in (-1, 1), signed like r:
-// r = sum_p s[p] 64^-(p+1) + e, |e| < 2^-54.  |r| 2^54 is scaled exactly (a
-// power of two) and truncated to an integer below 2^54 once; the digits are
-// its 6-bit fields, taken with integer operations (the FP64 pipe does one
-// multiply and one conversion per value).
-__device__ __forceinline__ void slice9(double r, float (&s)[kTcS]) {
-  const unsigned long long q = __double2ull_rz(fabs(r) * 0x1p54);
-  const float sg = r < 0.0 ? -1.f : 1.f;
-#pragma unroll
-  for (int p = 0; p < kTcS; ++p) s[p] = sg * (float)(unsigned)((q >> (6 * (kTcS - 1 - p))) & 63ull);
-}
-
-// Power of two 2^e with max < 2^e (1 for max = 0).
-__device__ __forceinline__ double pow2_above(double mx) {
-  if (!(mx > 0.0)) return 1.0;
-  int e;
-  frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)
-  return ldexp(1.0, e);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
-  const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
-  return a | (b << 16);
-}
 
 // kmap[k] = offset of basis vector k (slot * vstride + j * n) and kq[k] =
 // (q << 5) | j, its column q and index j, for the round's columns in order;
@@ -199,82 +165,8 @@ tc_split_cols_kernel(const double* __restrict__ coef, int ldo, const int32_t* __
   }
 }
 
-// ---- tcgen05 building blocks (inline PTX) ------------------------------------
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Shared-memory matrix descriptor of a K-major tile without swizzle: start
-// address, byte offset between core matrices along K (leading) and along
-// M/N (stride), descriptor version 1.
-__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
-}
-
-// Instruction descriptor: FP32 accumulator, bf16 A and B, both K-major, M x N.
-constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-                              ((uint32_t)(kTcM >> 4) << 24);
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count));
-}
-
-// Bounded wait for the phase with parity `ph` of barrier b; false when it
-// did not complete within about two seconds.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t ph) {
-  uint64_t t0;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-  for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(smem_addr(b)), "r"(ph)
-        : "memory");
-    if (done) return true;
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    if (t - t0 > 2000000000ull) return false;
-  }
-}
-
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
-      "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(acc));
-}
-
-__device__ __forceinline__ void tc_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_addr(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_ld8(uint32_t taddr, uint32_t (&v)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                 "=r"(v[6]), "=r"(v[7])
-               : "r"(taddr));
-}
+// Instruction descriptor of this kernel's MMAs: M = 128 nodes, N = 48 outputs.
+constexpr uint32_t kTcIdesc = tc_idesc(kTcM, kTcN);
 
 struct TcGemm {
   const __nv_bfloat16* A;   // [node tiles][ksteps][kTcS][kTcM x kTcK]
@@ -370,7 +262,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(TcGemm g) {
               const uint64_t ad = tc_desc(a + p * kTcABytes + (kk / 8) * 128, 128, kTcSbo);
               const uint64_t bd = tc_desc(b + q * kTcBBytes + (kk / 8) * 128, 128, kTcSbo);
               const uint32_t acc = (s == s0 && p == 0 && kk == 0) ? 0u : 1u;
-              tc_mma(tmem + (uint32_t)((p + q) * kTcN), ad, bd, acc);
+              tc_mma(tmem + (uint32_t)((p + q) * kTcN), ad, bd, kTcIdesc, acc);
             }
         tc_commit(&freed[st]);
       }

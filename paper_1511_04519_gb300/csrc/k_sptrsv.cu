@@ -888,6 +888,11 @@ void set_solve_smem_limit(int bytes) {
   cudaFuncSetAttribute(bwd_level_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+void solve_level(bool fwd, const DevFactor& F, const LevelPlan& L, double* Y, double* Y2, int ldy,
+                 int ncols, cudaStream_t st, const SplitScratch* split) {
+  if (ncols > 0 && (fwd ? L.nf : L.nb) > 0) run_level(fwd, F, L, Y, Y2, ldy, ncols, st, split);
+}
+
 int solve_inplace(const DevFactor& F, const LevelPlan* levels, int nlev, double* Y, double* Y2,
                   int ldy, int ncols, cudaStream_t st, const SplitScratch* split) {
   if (ncols <= 0) return 0;

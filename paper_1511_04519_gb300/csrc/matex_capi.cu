@@ -82,6 +82,24 @@ struct matex_ctx {
   SplitScratch split;              // chunked reductions of the level launches
   // resident rounds (opts.resident): per-level work lists, the choice, and
   // the setup's timings of one solve pair both ways (ms, -1 if not taken)
+  // wide supernodes on the tensor cores (opts.tc_solve): the level plans
+  // without their split tasks, per level their (supernode, row tile) lists,
+  // the panel slices and row scales of both factors and directions, the
+  // per-call right-hand-side slices and column scales, and per column count
+  // whether a call uses them
+  int ts_minw = 0;
+  std::vector<LevelPlan> levels_n;
+  std::vector<TsLevel> ts_levels;
+  TsSup* ts_sups = nullptr;
+  int ts_n = 0;
+  __nv_bfloat16* tsA[2][2] = {};   // [factor M, G][forward, backward]
+  double* tsR[2][2] = {};
+  __nv_bfloat16* tsB = nullptr;
+  double* tsC = nullptr;
+  int ts_csld = 0;
+  int ts_mtf = 0, ts_mtb = 0;      // most row tiles of a wide supernode, per direction
+  std::vector<int8_t> ts_by_ncols;
+  int ts_min_cols = 0;
   ResidentPlan rplan;
   ResFactor rM, rG;          // the factors' resident copies
   ResStoreSup* rsup = nullptr;
@@ -551,6 +569,34 @@ bool plan_levels(matex_ctx* c) {
     c->levels[l].ftasks = fd + fofs[l];
     c->levels[l].btasks = bd + bofs[l];
   }
+  if (c->ts_minw > 0) {
+    // the same task lists without the split tasks of supernodes at least
+    // ts_minw wide (packed tasks hold supernodes at most 16 wide)
+    std::vector<int2> ftn, btn;
+    std::vector<size_t> fon(nlev + 1), bon(nlev + 1);
+    auto narrow = [&](const int2& t) { return t.x < 0 || sup_w(t.x) < c->ts_minw; };
+    for (int l = 0; l < nlev; ++l) {
+      fon[l] = ftn.size();
+      bon[l] = btn.size();
+      for (size_t e = fofs[l]; e < fofs[l + 1]; ++e)
+        if (narrow(ft[e])) ftn.push_back(ft[e]);
+      for (size_t e = bofs[l]; e < bofs[l + 1]; ++e)
+        if (narrow(bt[e])) btn.push_back(bt[e]);
+    }
+    fon[nlev] = ftn.size();
+    bon[nlev] = btn.size();
+    int2 *fdn = nullptr, *bdn = nullptr;
+    if (!c->upload(fdn, ftn.data(), ftn.size()) || !c->upload(bdn, btn.data(), btn.size()))
+      return false;
+    c->levels_n = c->levels;
+    for (int l = 0; l < nlev; ++l) {
+      LevelPlan& L = c->levels_n[l];
+      L.ftasks = fdn + fon[l];
+      L.btasks = bdn + bon[l];
+      L.nf = (int32_t)(fon[l + 1] - fon[l]);
+      L.nb = (int32_t)(bon[l + 1] - bon[l]);
+    }
+  }
   set_solve_smem_limit(std::max(smem_need, kSolveSmemTune));
   // persistent schedules for every column count 1..ldy
   std::vector<PersistLevel> pl((size_t)c->ldy * nlev);
@@ -741,10 +787,188 @@ bool plan_resident(matex_ctx* c, int threads) {
   return cudaStreamSynchronize(c->st) == cudaSuccess;
 }
 
+// Tensor-core products of the wide supernodes (k_sptrsv_tc.cu): their table,
+// per level the (supernode, row tile) lists of both directions, and the
+// panel slices of both factors.  False when there is no wide supernode or no
+// room (at most a quarter of the free memory), and the solves stay FP64.
+bool plan_ts(matex_ctx* c) {
+  const Symbolic& S = c->S;
+  const int nlev = (int)S.level_ptr.size() - 1;
+  std::vector<int32_t> wid(S.nsup, -1);
+  std::vector<TsSup> sups;
+  int64_t aF = 0, aB = 0, rF = 0, rB = 0, bo = 0;
+  int mtf = 0, mtb = 0;
+  for (int32_t s = 0; s < S.nsup; ++s) {
+    const int f = S.sup_first[s], w = S.sup_first[s + 1] - f;
+    if (w < c->ts_minw) continue;
+    const int ld = (int)(S.sup_rowptr[s + 1] - S.sup_rowptr[s]);
+    TsSup d{};
+    d.pan = S.pan_off[s];
+    d.rp = S.sup_rowptr[s];
+    d.f = f;
+    d.w = w;
+    d.ld = ld;
+    d.mt_f = ts_row_tiles(ld);
+    d.mt_b = ts_row_tiles(w);
+    d.a_f = aF;
+    aF += (int64_t)ts_a_bytes(ld, w);
+    d.a_b = aB;
+    aB += (int64_t)ts_a_bytes(w, ld);
+    d.rs_f = rF;
+    rF += 128LL * d.mt_f;
+    d.rs_b = rB;
+    rB += 128LL * d.mt_b;
+    d.b_f = d.b_b = bo;
+    bo += (int64_t)std::max(ts_b_bytes(w, c->ldy), ts_b_bytes(ld, c->ldy));
+    mtf = std::max(mtf, d.mt_f);
+    mtb = std::max(mtb, d.mt_b);
+    wid[s] = (int32_t)sups.size();
+    sups.push_back(d);
+  }
+  if (sups.empty()) return false;
+  c->ts_csld = (c->ldy + 31) & ~31;
+  const double need = 2.0 * (double)(aF + aB) + 16.0 * (double)(rF + rB) + (double)bo +
+                      8.0 * (double)sups.size() * c->ts_csld;
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  if (need > 0.25 * (double)free_b) return false;
+  std::vector<int32_t> list;
+  std::vector<int2> tf, tb;
+  std::vector<size_t> lo(nlev + 1), fo(nlev + 1), bo2(nlev + 1);
+  for (int l = 0; l < nlev; ++l) {
+    lo[l] = list.size();
+    fo[l] = tf.size();
+    bo2[l] = tb.size();
+    for (int k = S.level_ptr[l]; k < S.level_ptr[l + 1]; ++k) {
+      const int j = wid[S.level_sups[k]];
+      if (j < 0) continue;
+      list.push_back(j);
+      const int kf = ts_k_slices(sups[j].w), kb = ts_k_slices(sups[j].ld);
+      for (int kc = 0; kc < kf; ++kc)
+        for (int mt = 0; mt < sups[j].mt_f; ++mt) tf.push_back(make_int2(j, mt | (kc << 16)));
+      for (int kc = 0; kc < kb; ++kc)
+        for (int mt = 0; mt < sups[j].mt_b; ++mt) tb.push_back(make_int2(j, mt | (kc << 16)));
+    }
+  }
+  lo[nlev] = list.size();
+  fo[nlev] = tf.size();
+  bo2[nlev] = tb.size();
+  int32_t* ld = nullptr;
+  int2 *tfd = nullptr, *tbd = nullptr;
+  TsSup* sd = nullptr;
+  if (!c->upload(sd, sups.data(), sups.size()) || !c->upload(ld, list.data(), list.size()) ||
+      !c->upload(tfd, tf.data(), tf.size()) || !c->upload(tbd, tb.data(), tb.size()))
+    return false;
+  for (int fi = 0; fi < 2; ++fi) {
+    if (!c->alloc(c->tsA[fi][0], (size_t)aF / 2) || !c->alloc(c->tsA[fi][1], (size_t)aB / 2) ||
+        !c->alloc(c->tsR[fi][0], (size_t)rF) || !c->alloc(c->tsR[fi][1], (size_t)rB))
+      return false;
+  }
+  if (!c->alloc(c->tsB, (size_t)bo / 2) || !c->alloc(c->tsC, sups.size() * (size_t)c->ts_csld))
+    return false;
+  c->ts_sups = sd;
+  c->ts_n = (int)sups.size();
+  c->ts_levels.assign(nlev, TsLevel{});
+  for (int l = 0; l < nlev; ++l) {
+    TsLevel& L = c->ts_levels[l];
+    L.nsup = (int32_t)(lo[l + 1] - lo[l]);
+    L.list = ld + lo[l];
+    L.ntile_f = (int32_t)(fo[l + 1] - fo[l]);
+    L.tiles_f = tfd + fo[l];
+    L.ntile_b = (int32_t)(bo2[l + 1] - bo2[l]);
+    L.tiles_b = tbd + bo2[l];
+  }
+  for (int fi = 0; fi < 2; ++fi) {
+    const DevFactor& F = fi == 0 ? c->fM : c->fG;
+    ts_split_panels(F, sd, c->ts_n, mtf, true, c->tsA[fi][0], c->tsR[fi][0], c->st);
+    ts_split_panels(F, sd, c->ts_n, mtb, false, c->tsA[fi][1], c->tsR[fi][1], c->st);
+  }
+  c->ts_mtf = mtf;
+  c->ts_mtb = mtb;
+  ts_set_limits();
+  return cudaStreamSynchronize(c->st) == cudaSuccess;
+}
+
+int solve_ts(matex_ctx* c, const DevFactor& F, int fi, int ncols);
+
+// Per column count: whether the level solves put the wide supernodes on the
+// tensor cores.  opts.tc_solve 2: always; 0: where the solve pair (level
+// launches, best of three) is at least 5 % faster that way, at each column
+// count the launch-mode tuner measures (1, 2, 4, ..., the buffer width).
+void autotune_ts(matex_ctx* c) {
+  c->ts_by_ncols.assign(c->ldy + 1, 0);
+  c->ts_min_cols = 0;
+  if (c->ts_n == 0) return;
+  if (c->opts.tc_solve == 2) {
+    std::fill(c->ts_by_ncols.begin(), c->ts_by_ncols.end(), (int8_t)1);
+    c->ts_min_cols = 1;
+    return;
+  }
+  std::vector<int> reps;
+  for (int r = 1; r <= c->ldy; r *= 2) reps.push_back(r);
+  if (reps.back() != c->ldy) reps.push_back(c->ldy);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaMemsetAsync(c->Y, 0, sizeof(double) * (size_t)c->n * c->ldy, c->st);
+  cudaMemsetAsync(c->Y2, 0, sizeof(double) * (size_t)c->n * c->ldy, c->st);
+  auto best_of = [&](int K, bool ts) {
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(e0, c->st);
+      if (ts) solve_ts(c, c->fM, 0, K);
+      else solve_inplace(c->fM, c->levels.data(), (int)c->levels.size(), c->Y, c->Y2, c->ldy, K,
+                         c->st, &c->split);
+      cudaEventRecord(e1, c->st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) best = std::min(best, ms);  // the first is the warm-up
+    }
+    return best;
+  };
+  std::vector<int8_t> use(reps.size(), 0);
+  for (size_t b = 0; b < reps.size(); ++b) use[b] = best_of(reps[b], true) < 0.95f * best_of(reps[b], false);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (size_t b = 0; b < reps.size(); ++b) {
+    const int lo = reps[b];
+    const int hi = b + 1 < reps.size() ? reps[b + 1] - 1 : c->ldy;
+    for (int nc = lo; nc <= hi; ++nc) c->ts_by_ncols[nc] = use[b];
+    if (use[b] && c->ts_min_cols == 0) c->ts_min_cols = lo;
+  }
+  cudaGetLastError();
+}
+
+// The level-by-level solve pair with the wide supernodes' products on the
+// tensor cores (factor index fi: 0 = C + gamma G, 1 = G); returns launches.
+int solve_ts(matex_ctx* c, const DevFactor& F, int fi, int ncols) {
+  const int nlev = (int)c->levels_n.size();
+  int launches = 0;
+  int32_t* err = c->d_count + 1;
+  for (int l = 0; l < nlev; ++l) {
+    solve_level(true, F, c->levels_n[l], c->Y, c->Y2, c->ldy, ncols, c->st, &c->split);
+    ts_solve_level(F, c->ts_sups, c->ts_levels[l], true, c->tsA[fi][0], c->tsR[fi][0], c->tsB,
+                   c->tsC, c->ts_csld, c->Y, c->Y2, c->ldy, ncols, err, c->st);
+    launches += 3;
+  }
+  for (int l = nlev - 1; l >= 0; --l) {
+    solve_level(false, F, c->levels_n[l], c->Y, c->Y2, c->ldy, ncols, c->st, &c->split);
+    ts_solve_level(F, c->ts_sups, c->ts_levels[l], false, c->tsA[fi][1], c->tsR[fi][1], c->tsB,
+                   c->tsC, c->ts_csld, c->Y, c->Y2, c->ldy, ncols, err, c->st);
+    launches += 3;
+  }
+  return launches;
+}
+
 int solve_cols(matex_ctx* c, const DevFactor& F, int ncols) {
   if (ncols <= 0) return 0;
   int mode = c->opts.solve_mode;
   if (mode == 2) mode = c->mode_by_ncols.empty() ? 0 : c->mode_by_ncols[std::min(ncols, c->ldy)];
+  const int fi = F.pan_cm == c->fM.pan_cm ? 0 : F.pan_cm == c->fG.pan_cm ? 1 : -1;
+  if (mode == 1 && fi >= 0 && c->ts_n > 0 && !c->ts_by_ncols.empty() &&
+      c->ts_by_ncols[std::min(ncols, c->ldy)])
+    return solve_ts(c, F, fi, ncols);
   if (mode == 1)
     return solve_inplace(F, c->levels.data(), (int)c->levels.size(), c->Y, c->Y2, c->ldy, ncols,
                          c->st, &c->split);
@@ -1935,6 +2159,8 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   if (o.col_block != 0 && o.col_block != 1 && o.col_block != 2 && o.col_block != 4 && o.col_block != 8)
     return bad("col_block must be 0, 1, 2, 4 or 8");
   if (o.resident < 0 || o.resident > 2) return bad("resident must be 0, 1 or 2");
+  if (o.tc_solve < 0 || o.tc_solve > 2) return bad("tc_solve must be 0, 1 or 2");
+  if (o.tc_min_width != 0 && o.tc_min_width < 32) return bad("tc_min_width must be 0 or >= 32");
   if (o.resident == 2 && (o.krylov == 2 || o.tape || o.tail_eps > 0.0 || n > kResidentMaxN))
     return bad("resident rounds need n <= 8192, krylov 0 or 1, tape 0 and tail_eps 0");
   if (o.group_select >= n_groups) return bad("group_select out of range");
@@ -2263,6 +2489,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   if (!c->replay.empty()) ok = ok && c->upload(c->replay_d, c->replay.data(), c->replay.size());
   // work buffers
   c->ldy = roundup8(std::max({Kmax, 8, std::min<int>(n_groups, 256)}));
+  c->ts_minw = o.tc_solve == 1 ? 0 : (o.tc_min_width > 0 ? o.tc_min_width : kTsMinWidth);
   ok = ok && plan_levels(c);
   c->nchunks = (int)((n + kChunk - 1) / kChunk);
   const size_t G = (size_t)c->g_slots;
@@ -2388,6 +2615,12 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   }
   if (o.solve_mode == 2 && o.col_block == 0) autotune_levels(c);
   if (o.solve_mode == 2) autotune_solve(c);
+  if (c->ts_minw > 0 && o.solve_mode != 0) {
+    if (plan_ts(c)) autotune_ts(c);
+    cudaGetLastError();
+  }
+  c->setup_stats.tc_solve_supernodes = c->ts_n;
+  c->setup_stats.tc_solve_min_cols = c->ts_min_cols;
   if (o.resident != 1 && o.krylov != 2 && o.tape == 0 && o.tail_eps == 0.0 &&
       n <= kResidentMaxN) {
     // resident rounds: one CTA's solve pair against the batched path's
@@ -2480,6 +2713,12 @@ matex_status matex_set_caps(matex_ctx* c, const double* cap) {
             cudaMemcpy(c->c_perm, cp.data(), sizeof(double) * c->n, cudaMemcpyHostToDevice) ==
                 cudaSuccess;
   if (!ok) return cuda_check(c, "set_caps upload");
+  if (c->ts_n > 0) {
+    // the tensor-core slices of the refactored C + gamma G
+    ts_split_panels(c->fM, c->ts_sups, c->ts_n, c->ts_mtf, true, c->tsA[0][0], c->tsR[0][0], c->st);
+    ts_split_panels(c->fM, c->ts_sups, c->ts_n, c->ts_mtb, false, c->tsA[0][1], c->tsR[0][1], c->st);
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "set_caps slices");
+  }
   if (c->resident_ok) {
     // the resident copy of the refactored C + gamma G
     resident_store(c->fM, c->rsup, c->S.nsup, const_cast<double*>(c->rM.fpan),

@@ -34,7 +34,8 @@ class MatexOpts(C.Structure):
                 ("max_width", C.c_int32), ("strict", C.c_int32), ("solve_mode", C.c_int32),
                 ("tape", C.c_int32), ("krylov", C.c_int32), ("graph", C.c_int32),
                 ("tail_eps", C.c_double), ("tape_window", C.c_int32), ("tape_block", C.c_int32),
-                ("recombine", C.c_int32), ("decompose", C.c_int32), ("resident", C.c_int32)]
+                ("recombine", C.c_int32), ("decompose", C.c_int32), ("resident", C.c_int32),
+                ("tc_solve", C.c_int32), ("tc_min_width", C.c_int32)]
 
 
 class MatexStats(C.Structure):
@@ -47,7 +48,8 @@ class MatexStats(C.Structure):
                 ("kernel_launches", C.c_int32), ("rounds", C.c_int32),
                 ("graph_replay", C.c_int32), ("graph_capture_ms", C.c_double),
                 ("nnz_L_exact", C.c_int64), ("tape_window", C.c_int32), ("tape_block", C.c_int32),
-                ("tape_bytes", C.c_int64), ("tc_rounds", C.c_int32), ("resident", C.c_int32)]
+                ("tape_bytes", C.c_int64), ("tc_rounds", C.c_int32), ("resident", C.c_int32),
+                ("tc_solve_supernodes", C.c_int32), ("tc_solve_min_cols", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -330,7 +332,8 @@ class Sim:
     def __init__(self, p, col_block=0, group_select=-1, include_dc=True, rows=None,
                  replay_m=None, max_width=0, strict=False, stream=None, solve_mode=2,
                  tape=False, graph=True, krylov="R", tail_eps=0.0, tape_window=0, tape_block=0,
-                 recombine="auto", decompose="groups", resident="auto", **overrides):
+                 recombine="auto", decompose="groups", resident="auto", tc_solve="auto",
+                 tc_min_width=0, **overrides):
         o = matex_default_opts()
         o.graph = int(bool(graph))
         o.tail_eps = float(tail_eps)
@@ -346,6 +349,8 @@ class Sim:
         o.recombine = {"auto": 0, "tensor": 0, "fp64": 1}[recombine]
         o.decompose = {"groups": 0, "ramps": 1}[decompose]
         o.resident = {"auto": 0, "off": 1, "on": 2, 0: 0, 1: 1, 2: 2}[resident]
+        o.tc_solve = {"auto": 0, "off": 1, "on": 2, 0: 0, 1: 1, 2: 2}[tc_solve]
+        o.tc_min_width = int(tc_min_width)
         o.tape_window = int(tape_window)
         o.tape_block = int(tape_block)
         self._keep = []
