@@ -460,6 +460,15 @@ def other_configs(M, stream, ramps_large=False):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         st = sim.stats.as_dict()
+        sst = sim.setup_stats()
+        # one more run launch by launch, CUDA events around every kernel class
+        sim.profile(on=True)
+        sim.run(x)
+        torch.cuda.synchronize()
+        prof = sim.profile(on=False)
+        res[name + "_profile_ms"] = {k: v["ms"] for k, v in prof.items()}
+        res[name + "_tc_solve"] = {"supernodes": sst["tc_solve_supernodes"],
+                                   "min_cols": sst["tc_solve_min_cols"]}
         res[name] = {"nodes": p.n, "groups": p.n_groups, "ms": ms,
                      "value": p.n * (p.n_out - 1) * p.n_groups / (ms / 1e3), "unit": UNIT,
                      "setup_s": setup_s, "graph_replay": st["graph_replay"],
