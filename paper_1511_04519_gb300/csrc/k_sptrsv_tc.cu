@@ -12,18 +12,20 @@
 // (2 FMA per SM per clock on GB300) runs slowly.  Here every panel row is
 // scaled by a power of two and split into nine signed 6-bit digits once at
 // setup (both directions, both factors, in the MMA tile layout); the
-// right-hand sides are split per call, per column; the 45 digit-pair products
+// right-hand sides are split per call, per column and K slice; the 45
+// digit-pair products
 // with p + q <= 8 accumulate exactly in FP32 TMEM accumulators (sums below
 // 2^24) and are combined in 64-bit integers, so each result carries only the
 // truncation of the digits past the ninth (below 2^-52 of max|row| max|column|
 // per term, an FP64 dot product's rounding).
 //
-// Kernels: ts_split_a (setup: panel slices and row scales), ts_split_b (per
-// level and call: right-hand-side slices and column scales, gathering
-// [D^{-1} y_s; -x_R] in the backward), ts_gemm (bulk copies of the slice
-// tiles into shared memory, tcgen05.mma into nine TMEM accumulators, the
-// integer combination and the scatter of the solve in the epilogue: y_s to
-// Y2, -u_R by FP64 atomics into the ancestors' rows, x_s to Y).
+// Kernels: ts_split_a (setup: panel slices and row scales), ts_clear (per
+// level and call: the destination rows), ts_gemm (its K slice of the
+// right-hand sides split into shared memory, gathering [D^{-1} y_s; -x_R] in
+// the backward; bulk copies of the panel's slice tiles; tcgen05.mma into nine
+// TMEM accumulators; the integer combination and the scatter of the solve in
+// the epilogue: y_s to Y2, -u_R by FP64 atomics into the ancestors' rows,
+// x_s to Y).
 #include <cuda_bf16.h>
 
 #include "kernels.h"
@@ -40,7 +42,6 @@ constexpr int kTsN = 32;           // right-hand sides per tile (MMA N)
 constexpr int kTsThreads = 128;
 constexpr int kTsABytes = kTsM * kTcK * 2;  // one slice of an A tile: 8 KB
 constexpr int kTsBBytes = kTsN * kTcK * 2;  // one slice of a B tile: 2 KB
-constexpr int kTsStage = kTcS * (kTsABytes + kTsBBytes);
 constexpr int kTsTmemCols = 512;   // nine accumulators of 32 columns fit in 288
 constexpr uint32_t kTsIdesc = tc_idesc(kTsM, kTsN);
 constexpr int kTsSliceSteps = 4;   // K steps of one CTA (128 reduction values: exact sums)
@@ -94,106 +95,56 @@ ts_split_a_kernel(DevFactor F, const TsSup* __restrict__ sups, int fwd,
   }
 }
 
-constexpr int kTsSplitGroups = 32;                  // row groups of the split
-constexpr int kTsSplitThreads = kTsSplitGroups * kTsN;  // x 32 right-hand sides
-
-// Right-hand-side slices of the level's wide supernodes: CTA (j, nt) takes
-// supernode list[j] and right-hand sides nt*32 .. nt*32+31; thread (g, c)
-// takes right-hand side c and rows g, g + 32, ... (the max, four loads in
-// flight), then 8-row blocks g, g + 32, ... (the slices), so that a warp
-// reads 32 consecutive right-hand sides of one row.  B(k, q) = Y[f + k][q] forward,
-// [D^{-1} y_s; -x_R] backward.
-__global__ void __launch_bounds__(kTsSplitThreads)
-ts_split_b_kernel(DevFactor F, const TsSup* __restrict__ sups, const int32_t* __restrict__ list,
-                  int fwd, double* Y, double* Y2, int ldy, int ncols,
-                  __nv_bfloat16* __restrict__ B, double* __restrict__ colscale, int csld) {
-  __shared__ double red[kTsSplitGroups][kTsN];
-  const int j = list[blockIdx.x];
-  const TsSup d = sups[j];
-  const int nt = blockIdx.y, c = threadIdx.x & 31, g = threadIdx.x >> 5;
-  const int q = nt * kTsN + c;
-  const bool live = q < ncols;
-  const int kdim = fwd ? d.w : d.ld;
-  const int ksteps = (kdim + kTcK - 1) / kTcK;
-  const int32_t* rows = F.sup_rows + d.rp;
-  auto val = [&](int k) -> double {
-    if (!live || k >= kdim) return 0.0;
-    if (fwd) return Y[(int64_t)(d.f + k) * ldy + q];
-    if (k < d.w) return Y2[(int64_t)(d.f + k) * ldy + q] * F.dinv[d.f + k];
-    return -Y[(int64_t)rows[k] * ldy + q];
-  };
-  double mx = 0.0;
-  constexpr int G = kTsSplitGroups;
-  for (int k = g; k < kdim; k += 4 * G) {
-    const double v0 = val(k), v1 = val(k + G), v2 = val(k + 2 * G), v3 = val(k + 3 * G);
-    mx = fmax(fmax(mx, fmax(fabs(v0), fabs(v1))), fmax(fabs(v2), fabs(v3)));
-  }
-  // the products are accumulated by atomics over K slices: clear their
-  // destination rows of s (y_s in Y2 forward, x_s in Y backward; no one else
-  // reads them during this level)
-  if (live) {
-    double* dst = fwd ? Y2 : Y;
-    for (int k = g; k < d.w; k += G) dst[(int64_t)(d.f + k) * ldy + q] = 0.0;
-  }
-  red[g][c] = mx;
-  __syncthreads();
-  mx = 0.0;
-#pragma unroll 8
-  for (int e = 0; e < G; ++e) mx = fmax(mx, red[e][c]);
-  const double sc = pow2_above(mx);
-  if (g == 0) colscale[(int64_t)j * csld + q] = sc;
-  const double inv = 1.0 / sc;  // a power of two: exact
-  unsigned char* base = reinterpret_cast<unsigned char*>(B) + (fwd ? d.b_f : d.b_b) +
-                        (size_t)nt * ksteps * kTcS * kTsBBytes;
-  for (int blk8 = g; blk8 < ksteps * (kTcK / 8); blk8 += G) {
-    const int s = blk8 / (kTcK / 8), k8 = (blk8 % (kTcK / 8)) * 8;
-    unsigned char* blk = base + (size_t)s * kTcS * kTsBBytes;
-    float sl[8][kTcS];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) slice9(val(s * kTcK + k8 + u) * inv, sl[u]);
-#pragma unroll
-    for (int p = 0; p < kTcS; ++p) {
-      uint4 w4;
-      w4.x = pack_bf16x2(sl[0][p], sl[1][p]);
-      w4.y = pack_bf16x2(sl[2][p], sl[3][p]);
-      w4.z = pack_bf16x2(sl[4][p], sl[5][p]);
-      w4.w = pack_bf16x2(sl[6][p], sl[7][p]);
-      *reinterpret_cast<uint4*>(blk + (size_t)p * kTsBBytes + tc_off(c, k8)) = w4;
-    }
-  }
-}
-
 struct TsGemm {
   DevFactor F;
   const TsSup* sups;
-  const int2* tiles;        // {wide supernode, row tile} of the level
+  const int2* tiles;        // {wide supernode, row tile | K slice << 16} of the level
   const __nv_bfloat16* A;   // panel slices of this direction's factor
   const double* rowscale;
-  const __nv_bfloat16* B;
-  const double* colscale;
-  int csld;
   double* Y;
   double* Y2;
   int ldy, ncols, fwd;
   int32_t* err;             // raised when a bounded wait gives up
 };
 
+// Destination rows of the level's wide supernodes cleared for the GEMM's
+// atomics: y_s in Y2 (forward) or x_s in Y (backward), ncols columns; no one
+// else reads them during this level.
+__global__ void ts_clear_kernel(const TsSup* __restrict__ sups, const int32_t* __restrict__ list,
+                                int fwd, double* Y, double* Y2, int ldy, int ncols) {
+  const TsSup d = sups[list[blockIdx.x]];
+  double* dst = fwd ? Y2 : Y;
+  for (int e = threadIdx.x; e < d.w * ncols; e += blockDim.x) {
+    const int k = e / ncols, q = e - k * ncols;
+    dst[(int64_t)(d.f + k) * ldy + q] = 0.0;
+  }
+}
+
+constexpr int kTsSliceVals = kTsSliceSteps * kTcK;  // reduction values of one CTA
+constexpr int kTsBRes = kTsSliceSteps * kTcS * kTsBBytes;  // its resident B slices
+
 // One CTA per (row tile of a wide supernode, K slice of kTsSliceSteps steps,
 // 32 right-hand sides): a level's few wide supernodes become enough CTAs to
-// keep the SMs streaming slice tiles.  Thread 0 streams the slice tiles K
+// keep the SMs busy.  The CTA first splits its own part of the right-hand
+// sides: 128 reduction values x 32 columns read from Y / Y2 (thread (q, g):
+// right-hand side q, 8-value groups g, g + 4, ...: a warp reads 32
+// consecutive right-hand sides of one row), each column scaled by a power of
+// two over this K slice, cut into nine digits straight into the resident B
+// tiles in shared memory.  Then thread 0 streams the panel's slice tiles K
 // step by K step into two shared-memory stages (bulk copies, completion by
 // transaction count) and issues the MMAs of every slice pair p + q <= 8 into
-// accumulator d = p + q (the slice's at most 128 reduction values keep the
-// sums exact); then all 128 threads drain the accumulators (warp w: tile
-// rows 32w..32w+31), combine the nine integer sums exactly in 64-bit
-// integers and add the FP64 result by atomics (the K slices of a tile meet
-// there): forward y_s into Y2 and -u_R into the ancestors' rows of Y,
-// backward x_s into Y (both cleared by ts_split_b).
+// accumulator d = p + q (the slice's 128 values keep the sums exact); all 128
+// threads drain the accumulators (warp w: tile rows 32w..32w+31), combine the
+// nine integer sums exactly in 64-bit integers and add the FP64 result by
+// atomics (the K slices of a tile meet there): forward y_s into Y2 and -u_R
+// into the ancestors' rows of Y, backward x_s into Y (cleared by ts_clear).
 __global__ void __launch_bounds__(kTsThreads, 1) ts_gemm_kernel(TsGemm g) {
   extern __shared__ __align__(1024) unsigned char ts_smem[];
   __shared__ uint32_t tbase;
   __shared__ __align__(8) uint64_t full[2], freed[2], fin;
   __shared__ int failed;
+  __shared__ double cmax[kTsThreads / kTsN][kTsN];
+  __shared__ double cscale[kTsN];
   const int2 tl = g.tiles[blockIdx.x];
   const TsSup d = g.sups[tl.x];
   const int mt = tl.y & 0xFFFF, kc = tl.y >> 16, nt = blockIdx.y;
@@ -203,8 +154,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) ts_gemm_kernel(TsGemm g) {
   const int s0 = kc * kTsSliceSteps, s1 = min(ksteps, s0 + kTsSliceSteps);
   const unsigned char* Abase = reinterpret_cast<const unsigned char*>(g.A) + (g.fwd ? d.a_f : d.a_b) +
                                (size_t)mt * ksteps * kTcS * kTsABytes;
-  const unsigned char* Bbase = reinterpret_cast<const unsigned char*>(g.B) + (g.fwd ? d.b_f : d.b_b) +
-                               (size_t)nt * ksteps * kTcS * kTsBBytes;
+  unsigned char* Bres = ts_smem + 2 * (size_t)kTcS * kTsABytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -220,6 +170,62 @@ __global__ void __launch_bounds__(kTsThreads, 1) ts_gemm_kernel(TsGemm g) {
     mbar_init(&fin, 1);
     failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // ---- the right-hand sides' slices of this K slice --------------------------
+  {
+    const int q = lane;                 // right-hand side within the tile
+    const int qq = nt * kTsN + q;
+    const bool qlive = qq < g.ncols;
+    const int32_t* srow = g.F.sup_rows + d.rp;
+    auto val = [&](int k) -> double {   // k: within the K slice
+      const int kg = s0 * kTcK + k;
+      if (!qlive || kg >= kdim) return 0.0;
+      if (g.fwd) return g.Y[(int64_t)(d.f + kg) * g.ldy + qq];
+      if (kg < d.w) return g.Y2[(int64_t)(d.f + kg) * g.ldy + qq] * g.F.dinv[d.f + kg];
+      return -g.Y[(int64_t)srow[kg] * g.ldy + qq];
+    };
+    constexpr int NG = kTsSliceVals / 8 / (kTsThreads / kTsN);  // 8-value groups per thread
+    double v[NG][8];
+    double mx = 0.0;
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+      const int grp = warp + i * (kTsThreads / kTsN);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        v[i][u] = val(grp * 8 + u);
+        mx = fmax(mx, fabs(v[i][u]));
+      }
+    }
+    cmax[warp][q] = mx;
+    __syncthreads();
+    if (warp == 0) {
+      double m = 0.0;
+#pragma unroll
+      for (int e = 0; e < kTsThreads / kTsN; ++e) m = fmax(m, cmax[e][q]);
+      cscale[q] = pow2_above(m);
+    }
+    __syncthreads();
+    const double inv = 1.0 / cscale[q];  // a power of two: exact
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+      const int grp = warp + i * (kTsThreads / kTsN);
+      const int s = grp / (kTcK / 8), k8 = (grp % (kTcK / 8)) * 8;
+      float sl[8][kTcS];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) slice9(v[i][u] * inv, sl[u]);
+      unsigned char* blk = Bres + (size_t)s * kTcS * kTsBBytes;
+#pragma unroll
+      for (int p = 0; p < kTcS; ++p) {
+        uint4 w4;
+        w4.x = pack_bf16x2(sl[0][p], sl[1][p]);
+        w4.y = pack_bf16x2(sl[2][p], sl[3][p]);
+        w4.z = pack_bf16x2(sl[4][p], sl[5][p]);
+        w4.w = pack_bf16x2(sl[6][p], sl[7][p]);
+        *reinterpret_cast<uint4*>(blk + (size_t)p * kTsBBytes + tc_off(q, k8)) = w4;
+      }
+    }
+    // the generic-proxy stores must be visible to the tensor cores' reads
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -244,11 +250,9 @@ __global__ void __launch_bounds__(kTsThreads, 1) ts_gemm_kernel(TsGemm g) {
   if (threadIdx.x == 0) {
     auto issue_copy = [&](int s, int k) {
       const int st = k & 1;
-      unsigned char* a = ts_smem + (size_t)st * kTsStage;
-      unsigned char* b = a + kTcS * kTsABytes;
-      expect_tx(&full[st], kTsStage);
+      unsigned char* a = ts_smem + (size_t)st * kTcS * kTsABytes;
+      expect_tx(&full[st], kTcS * kTsABytes);
       bulk_load(a, Abase + (size_t)s * kTcS * kTsABytes, kTcS * kTsABytes, &full[st]);
-      bulk_load(b, Bbase + (size_t)s * kTcS * kTsBBytes, kTcS * kTsBBytes, &full[st]);
     };
     bool ok = true;
     int it = 0;  // K steps issued (stage = it & 1, use = it >> 1)
@@ -267,8 +271,8 @@ __global__ void __launch_bounds__(kTsThreads, 1) ts_gemm_kernel(TsGemm g) {
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a = smem_addr(ts_smem + (size_t)st * kTsStage);
-      const uint32_t b = a + kTcS * kTsABytes;
+      const uint32_t a = smem_addr(ts_smem + (size_t)st * kTcS * kTsABytes);
+      const uint32_t b = smem_addr(Bres + (size_t)(s - s0) * kTcS * kTsBBytes);
 #pragma unroll 1
       for (int p = 0; p < kTcS; ++p)
 #pragma unroll 1
@@ -308,8 +312,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) ts_gemm_kernel(TsGemm g) {
 #pragma unroll
         for (int dd = 5; dd < kTcS; ++dd)
           lo += (long long)__float2int_rz(__uint_as_float(v[dd][jj])) * (1ll << (6 * (8 - dd)));
-        const double val = fma((double)lo, 0x1p-24, (double)hi) *
-                           (rs * g.colscale[(int64_t)tl.x * g.csld + q] * 0x1p-36);
+        const double val = fma((double)lo, 0x1p-24, (double)hi) * (rs * cscale[cb + jj] * 0x1p-36);
         atomicAdd(dst + q, sign * val);
       }
     }
@@ -339,15 +342,13 @@ size_t ts_a_bytes(int rows, int kdim) {
   const size_t mt = (rows + kTsM - 1) / kTsM, ks = (kdim + kTcK - 1) / kTcK;
   return mt * ks * kTcS * kTsABytes;
 }
-size_t ts_b_bytes(int kdim, int ncols) {
-  const size_t nt = (ncols + kTsN - 1) / kTsN, ks = (kdim + kTcK - 1) / kTcK;
-  return nt * ks * kTcS * kTsBBytes;
-}
 int ts_row_tiles(int rows) { return (rows + kTsM - 1) / kTsM; }
 int ts_k_slices(int kdim) { return ((kdim + kTcK - 1) / kTcK + kTsSliceSteps - 1) / kTsSliceSteps; }
 
+constexpr int kTsSmem = 2 * kTcS * kTsABytes + kTsBRes;  // two panel stages, resident B slices
+
 void ts_set_limits() {
-  cudaFuncSetAttribute(ts_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kTsStage);
+  cudaFuncSetAttribute(ts_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTsSmem);
 }
 
 void ts_split_panels(const DevFactor& F, const TsSup* sups, int nsup, int max_mt, bool fwd,
@@ -358,18 +359,14 @@ void ts_split_panels(const DevFactor& F, const TsSup* sups, int nsup, int max_mt
 }
 
 void ts_solve_level(const DevFactor& F, const TsSup* sups, const TsLevel& L, bool fwd,
-                    const __nv_bfloat16* A, const double* rowscale, __nv_bfloat16* B,
-                    double* colscale, int csld, double* Y, double* Y2, int ldy, int ncols,
-                    int32_t* err, cudaStream_t st) {
-  const int nlist = fwd ? L.nsup : L.nsup;
+                    const __nv_bfloat16* A, const double* rowscale, double* Y, double* Y2, int ldy,
+                    int ncols, int32_t* err, cudaStream_t st) {
   const int ntiles = fwd ? L.ntile_f : L.ntile_b;
-  if (nlist <= 0 || ncols <= 0) return;
+  if (L.nsup <= 0 || ncols <= 0) return;
   const int nct = (ncols + kTsN - 1) / kTsN;
-  ts_split_b_kernel<<<dim3((unsigned)nlist, (unsigned)nct), kTsSplitThreads, 0, st>>>(
-      F, sups, L.list, fwd ? 1 : 0, Y, Y2, ldy, ncols, B, colscale, csld);
-  TsGemm g{F, sups, fwd ? L.tiles_f : L.tiles_b, A, rowscale, B, colscale, csld, Y, Y2,
-           ldy, ncols, fwd ? 1 : 0, err};
-  ts_gemm_kernel<<<dim3((unsigned)ntiles, (unsigned)nct), kTsThreads, 2 * kTsStage, st>>>(g);
+  ts_clear_kernel<<<(unsigned)L.nsup, 256, 0, st>>>(sups, L.list, fwd ? 1 : 0, Y, Y2, ldy, ncols);
+  TsGemm g{F, sups, fwd ? L.tiles_f : L.tiles_b, A, rowscale, Y, Y2, ldy, ncols, fwd ? 1 : 0, err};
+  ts_gemm_kernel<<<dim3((unsigned)ntiles, (unsigned)nct), kTsThreads, kTsSmem, st>>>(g);
 }
 
 }  // namespace matex

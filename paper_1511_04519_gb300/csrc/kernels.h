@@ -495,14 +495,13 @@ float resident_time_solve(const ResFactor& F, const ResidentPlan& P, const doubl
 // Wide supernodes of the level solves on the tensor cores (k_sptrsv_tc.cu).
 // Per wide supernode: its panel (offset pan, first node f, width w, rows ld,
 // row list rp), the row tiles of the forward (ld rows) and backward (w rows)
-// products, and byte offsets of its panel slices (a_f, a_b: into the
-// direction's slice store of the factor), of its row scales (rs_f, rs_b, in
-// doubles) and of its right-hand-side slices in the per-call buffer (b_f,
-// b_b).
+// products, and the offsets of its panel slices (a_f, a_b: bytes into the
+// direction's slice store of the factor) and of its row scales (rs_f, rs_b,
+// in doubles).
 struct TsSup {
   int64_t pan, rp;
   int32_t f, w, ld, mt_f, mt_b, pad;
-  int64_t a_f, a_b, rs_f, rs_b, b_f, b_b;
+  int64_t a_f, a_b, rs_f, rs_b;
 };
 // One tree level's wide supernodes (indices into the TsSup table) and the
 // tiles of its two products: {supernode, row tile | K slice << 16}.
@@ -514,7 +513,6 @@ struct TsLevel {
 };
 constexpr int kTsMinWidth = 64;  // default: supernodes at least this wide use the tensor cores
 size_t ts_a_bytes(int rows, int kdim);   // panel slices of one product
-size_t ts_b_bytes(int kdim, int ncols);  // right-hand-side slices of one product
 int ts_row_tiles(int rows);
 int ts_k_slices(int kdim);               // CTAs sharing one row tile (split reduction)
 void ts_set_limits();
@@ -524,9 +522,8 @@ void ts_split_panels(const DevFactor& F, const TsSup* sups, int nsup, int max_mt
 // the wide supernodes of one level, one direction, ncols right-hand sides of
 // the solve buffers (Y node-major, Y2 the forward intermediate)
 void ts_solve_level(const DevFactor& F, const TsSup* sups, const TsLevel& L, bool fwd,
-                    const __nv_bfloat16* A, const double* rowscale, __nv_bfloat16* B,
-                    double* colscale, int csld, double* Y, double* Y2, int ldy, int ncols,
-                    int32_t* err, cudaStream_t st);
+                    const __nv_bfloat16* A, const double* rowscale, double* Y, double* Y2, int ldy,
+                    int ncols, int32_t* err, cudaStream_t st);
 // one level launch of the FP64 solve (k_sptrsv.cu), the level's own tuned
 // column block
 void solve_level(bool fwd, const DevFactor& F, const LevelPlan& L, double* Y, double* Y2, int ldy,

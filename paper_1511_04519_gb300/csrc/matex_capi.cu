@@ -85,8 +85,7 @@ struct matex_ctx {
   // wide supernodes on the tensor cores (opts.tc_solve): the level plans
   // without their split tasks, per level their (supernode, row tile) lists,
   // the panel slices and row scales of both factors and directions, the
-  // per-call right-hand-side slices and column scales, and per column count
-  // whether a call uses them
+  // and per column count whether a call uses them
   int ts_minw = 0;
   std::vector<LevelPlan> levels_n;
   std::vector<TsLevel> ts_levels;
@@ -94,9 +93,6 @@ struct matex_ctx {
   int ts_n = 0;
   __nv_bfloat16* tsA[2][2] = {};   // [factor M, G][forward, backward]
   double* tsR[2][2] = {};
-  __nv_bfloat16* tsB = nullptr;
-  double* tsC = nullptr;
-  int ts_csld = 0;
   int ts_mtf = 0, ts_mtb = 0;      // most row tiles of a wide supernode, per direction
   std::vector<int8_t> ts_by_ncols;
   int ts_min_cols = 0;
@@ -794,9 +790,14 @@ bool plan_resident(matex_ctx* c, int threads) {
 bool plan_ts(matex_ctx* c) {
   const Symbolic& S = c->S;
   const int nlev = (int)S.level_ptr.size() - 1;
+  // the narrow levels launch with the column blocks tuned for the full ones
+  for (int l = 0; l < nlev && l < (int)c->levels_n.size(); ++l) {
+    c->levels_n[l].kbf = c->levels[l].kbf;
+    c->levels_n[l].kbb = c->levels[l].kbb;
+  }
   std::vector<int32_t> wid(S.nsup, -1);
   std::vector<TsSup> sups;
-  int64_t aF = 0, aB = 0, rF = 0, rB = 0, bo = 0;
+  int64_t aF = 0, aB = 0, rF = 0, rB = 0;
   int mtf = 0, mtb = 0;
   for (int32_t s = 0; s < S.nsup; ++s) {
     const int f = S.sup_first[s], w = S.sup_first[s + 1] - f;
@@ -818,17 +819,13 @@ bool plan_ts(matex_ctx* c) {
     rF += 128LL * d.mt_f;
     d.rs_b = rB;
     rB += 128LL * d.mt_b;
-    d.b_f = d.b_b = bo;
-    bo += (int64_t)std::max(ts_b_bytes(w, c->ldy), ts_b_bytes(ld, c->ldy));
     mtf = std::max(mtf, d.mt_f);
     mtb = std::max(mtb, d.mt_b);
     wid[s] = (int32_t)sups.size();
     sups.push_back(d);
   }
   if (sups.empty()) return false;
-  c->ts_csld = (c->ldy + 31) & ~31;
-  const double need = 2.0 * (double)(aF + aB) + 16.0 * (double)(rF + rB) + (double)bo +
-                      8.0 * (double)sups.size() * c->ts_csld;
+  const double need = 2.0 * (double)(aF + aB) + 16.0 * (double)(rF + rB);
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   if (need > 0.25 * (double)free_b) return false;
@@ -864,8 +861,6 @@ bool plan_ts(matex_ctx* c) {
         !c->alloc(c->tsR[fi][0], (size_t)rF) || !c->alloc(c->tsR[fi][1], (size_t)rB))
       return false;
   }
-  if (!c->alloc(c->tsB, (size_t)bo / 2) || !c->alloc(c->tsC, sups.size() * (size_t)c->ts_csld))
-    return false;
   c->ts_sups = sd;
   c->ts_n = (int)sups.size();
   c->ts_levels.assign(nlev, TsLevel{});
@@ -948,14 +943,14 @@ int solve_ts(matex_ctx* c, const DevFactor& F, int fi, int ncols) {
   int32_t* err = c->d_count + 1;
   for (int l = 0; l < nlev; ++l) {
     solve_level(true, F, c->levels_n[l], c->Y, c->Y2, c->ldy, ncols, c->st, &c->split);
-    ts_solve_level(F, c->ts_sups, c->ts_levels[l], true, c->tsA[fi][0], c->tsR[fi][0], c->tsB,
-                   c->tsC, c->ts_csld, c->Y, c->Y2, c->ldy, ncols, err, c->st);
+    ts_solve_level(F, c->ts_sups, c->ts_levels[l], true, c->tsA[fi][0], c->tsR[fi][0], c->Y, c->Y2,
+                   c->ldy, ncols, err, c->st);
     launches += 3;
   }
   for (int l = nlev - 1; l >= 0; --l) {
     solve_level(false, F, c->levels_n[l], c->Y, c->Y2, c->ldy, ncols, c->st, &c->split);
-    ts_solve_level(F, c->ts_sups, c->ts_levels[l], false, c->tsA[fi][1], c->tsR[fi][1], c->tsB,
-                   c->tsC, c->ts_csld, c->Y, c->Y2, c->ldy, ncols, err, c->st);
+    ts_solve_level(F, c->ts_sups, c->ts_levels[l], false, c->tsA[fi][1], c->tsR[fi][1], c->Y, c->Y2,
+                   c->ldy, ncols, err, c->st);
     launches += 3;
   }
   return launches;
