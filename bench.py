@@ -285,7 +285,9 @@ def ncu_case(what: str) -> int:
     profiled call.  "solve": matex_solve of 16 columns with the persistent
     kernel; "levels": 64 columns with one launch per tree level; "run": one
     full matex_run; "ksweep": bare solve pairs of 1, 4 and 64 columns on the
-    whole grid; "small": one run of the 1,024-node single-group grid."""
+    whole grid; "small": one run of the 1,024-node single-group grid;
+    "tcsolve": one 64-column solve pair of the whole grid with the wide panels
+    on the tensor cores."""
     import numpy as np
     import torch
 
@@ -299,6 +301,19 @@ def ncu_case(what: str) -> int:
     off = np.concatenate([[0], np.cumsum(np.diff(p.pwl_off)[sel])]).astype(np.int32)
     q = gridgen.with_sources(p, p.src_node[sel], off, p.pwl_t.reshape(-1, 3)[sel].ravel(),
                              p.pwl_v.reshape(-1, 3)[sel].ravel(), p.src_group[sel], groups)
+    if what == "tcsolve":
+        # the whole bench grid, wide panels forced onto the tensor cores: one
+        # 64-column solve pair of C + gamma G after a warm one
+        sim = M.Sim(p, tc_solve="on", solve_mode=1, include_dc=False,
+                    rows=np.arange(4, dtype=np.int32))
+        sim.time_solve(0, 64, reps=1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        sim.time_solve(0, 64, reps=1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"ncu_case": what, "max_memory_gb": torch.cuda.max_memory_allocated() / 1e9}))
+        return 0
     if what == "small":
         # the single-group 1,024-node grid as set up by default (resident
         # rounds): one warm run, then one run inside the profiler range
@@ -511,7 +526,7 @@ def main():
                          "launch and report their aggregate rate (0: skip)")
     ap.add_argument("--profile-step", action="store_true",
                     help="warm up, run one step inside cudaProfilerStart/Stop, print its stats")
-    ap.add_argument("--ncu-case", choices=["solve", "levels", "run", "ksweep", "small"], default=None,
+    ap.add_argument("--ncu-case", choices=["solve", "levels", "run", "ksweep", "small", "tcsolve"], default=None,
                     help="reduced case for full ncu captures: the same grid with 8 groups; "
                          "one warm call, then one call inside cudaProfilerStart/Stop")
     args = ap.parse_args()
