@@ -232,6 +232,53 @@ size_t res_smem_bytes(int64_t n, const ResidentPlan& P) {
          res_solve_smem_bytes(n, P);
 }
 
+// The input part of column q's segment (Eq. 5/6 with the segment's source
+// slopes s_j): z' = G^{-1} B s_j into Zp, w = G^{-1} C z' into W, and w left
+// in b.  Depends on the sources only, not on the state.  b, y, U, the plan
+// (ms) are shared memory; every thread of the CTA calls it.
+__device__ void res_inputs(const ResidentArgs& a, const ResSmem& ms, int q, double* __restrict__ b,
+                           double* __restrict__ y, double* __restrict__ U, double* __restrict__ Zp,
+                           double* __restrict__ W) {
+  const int64_t n = a.n;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const RoundCols& rc = a.rc;
+  for (int64_t i = tid; i < n; i += nt) b[i] = 0.0;
+  __syncthreads();
+  // B s_j: the slopes of the column's sources on the segment
+  {
+    const SourceTable& src = a.src;
+    const int sg = rc.sgroup ? rc.sgroup[q] : (int)rc.group[q];
+    const double l0 = rc.l0[q], L = rc.len[q], l1 = l0 + L;
+    const int p0 = src.grp_ptr[sg], p1 = src.grp_ptr[sg + 1];
+    auto slope = [&](int p) {
+      const int s = src.grp_src[p];
+      const int o = src.pwl_off[s], np = src.pwl_off[s + 1] - o;
+      const double u0 = pwl_eval(src.pwl_t + o, src.pwl_v + o, np, l0);
+      return (pwl_eval(src.pwl_t + o, src.pwl_v + o, np, l1) - u0) / L;
+    };
+    // slopes in parallel (y is free until the first solve), then added in
+    // source order by one thread: sources may share a node
+    if (p1 - p0 <= n) {
+      for (int p = p0 + tid; p < p1; p += nt) y[p - p0] = slope(p);
+      __syncthreads();
+      if (tid == 0)
+        for (int p = p0; p < p1; ++p) b[src.node[src.grp_src[p]]] += y[p - p0];
+    } else if (tid == 0) {
+      for (int p = p0; p < p1; ++p) b[src.node[src.grp_src[p]]] += slope(p);
+    }
+  }
+  __syncthreads();
+  res_solve(a.FG, a.plan.nlev, ms, b, y, U);  // z' = G^{-1} B s_j
+  for (int64_t i = tid; i < n; i += nt) {
+    const double zp = b[i];
+    Zp[i] = zp;
+    b[i] = zp * a.cperm[i];
+  }
+  __syncthreads();
+  res_solve(a.FG, a.plan.nlev, ms, b, y, U);  // w = G^{-1} C z'
+  for (int64_t i = tid; i < n; i += nt) W[i] = b[i];
+}
+
 __global__ void __launch_bounds__(kResidentThreads, 1) resident_round_kernel(ResidentArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmallShared& sh = *reinterpret_cast<SmallShared*>(smem_raw);
@@ -258,52 +305,33 @@ __global__ void __launch_bounds__(kResidentThreads, 1) resident_round_kernel(Res
   const bool first = rc.seg[q] == 0;
   const double lp = rc.lprev[q];
   if (tid == 0) sh.cm = 0;  // no residual test has run yet
-  for (int64_t i = tid; i < n; i += nt) {
-    Z[i] = first ? X[i] : fma(lp, Zp[i], Z[i]);
-    b[i] = 0.0;
-  }
   const ResSmem ms = res_stage_plan(a.plan, pl);
-  __syncthreads();
-  // B s_j: the slopes of the column's sources on the segment
-  {
-    const SourceTable& src = a.src;
-    const int sg = rc.sgroup ? rc.sgroup[q] : (int)g;
-    const double l0 = rc.l0[q], L = rc.len[q], l1 = l0 + L;
-    const int p0 = src.grp_ptr[sg], p1 = src.grp_ptr[sg + 1];
-    auto slope = [&](int p) {
-      const int s = src.grp_src[p];
-      const int o = src.pwl_off[s], np = src.pwl_off[s + 1] - o;
-      const double u0 = pwl_eval(src.pwl_t + o, src.pwl_v + o, np, l0);
-      return (pwl_eval(src.pwl_t + o, src.pwl_v + o, np, l1) - u0) / L;
-    };
-    // slopes in parallel (y is free until the first solve), then added in
-    // source order by one thread: sources may share a node
-    if (p1 - p0 <= n) {
-      for (int p = p0 + tid; p < p1; p += nt) y[p - p0] = slope(p);
-      __syncthreads();
-      if (tid == 0)
-        for (int p = p0; p < p1; ++p) b[src.node[src.grp_src[p]]] += y[p - p0];
-    } else if (tid == 0) {
-      for (int p = p0; p < p1; ++p) b[src.node[src.grp_src[p]]] += slope(p);
-    }
-  }
-  __syncthreads();
-  res_solve(a.FG, nlev, ms, b, y, U);  // z' = G^{-1} B s_j
-  for (int64_t i = tid; i < n; i += nt) {
-    const double zp = b[i];
-    Zp[i] = zp;
-    b[i] = zp * a.cperm[i];
-  }
-  __syncthreads();
-  res_solve(a.FG, nlev, ms, b, y, U);  // w = G^{-1} C z'
-  // start vector v = x + F (F = w - z, Eq. 6), beta = ||v||
   double acc = 0.0;
-  for (int64_t i = tid; i < n; i += nt) {
-    const double wv = b[i];
-    W[i] = wv;
-    const double v = X[i] + (wv - Z[i]);
-    b[i] = v;
-    acc = fma(v, v, acc);
+  if (a.zpre) {
+    // z' and w of this segment computed ahead (resident_inputs): the start
+    // vector v = x + F (F = w - z, Eq. 6) right away
+    const double* __restrict__ zq = a.zpre + (int64_t)q * n;
+    const double* __restrict__ wq = a.wpre + (int64_t)q * n;
+    for (int64_t i = tid; i < n; i += nt) {
+      const double z = first ? X[i] : fma(lp, Zp[i], Z[i]);
+      const double wv = wq[i];
+      Z[i] = z;
+      Zp[i] = zq[i];
+      W[i] = wv;
+      const double v = X[i] + (wv - z);
+      b[i] = v;
+      acc = fma(v, v, acc);
+    }
+    __syncthreads();
+  } else {
+    for (int64_t i = tid; i < n; i += nt) Z[i] = first ? X[i] : fma(lp, Zp[i], Z[i]);
+    res_inputs(a, ms, q, b, y, U, Zp, W);
+    // start vector v = x + F (F = w - z, Eq. 6), beta = ||v||
+    for (int64_t i = tid; i < n; i += nt) {
+      const double v = X[i] + (b[i] - Z[i]);
+      b[i] = v;
+      acc = fma(v, v, acc);
+    }
   }
   const double beta = sqrt(res_block_sum(acc, red));
   double* Ht = ss.Ht + (int64_t)q * kMaxB * kMaxM;
@@ -378,6 +406,19 @@ __global__ void __launch_bounds__(kResidentThreads, 1) resident_round_kernel(Res
   }
 }
 
+// The input solves of columns q (one CTA each) ahead of their rounds:
+// z' and w of column q into zpre + q n and wpre + q n.
+__global__ void __launch_bounds__(kResidentThreads, 1) resident_inputs_kernel(ResidentArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ResSmem ms = res_stage_plan(a.plan, smem_raw);
+  const int64_t n = a.n;
+  double* b = reinterpret_cast<double*>(smem_raw + a.plan.bytes);
+  double* y = b + n;
+  double* U = y + n;
+  const int q = blockIdx.x;
+  res_inputs(a, ms, q, b, y, U, a.zpre + (int64_t)q * n, a.wpre + (int64_t)q * n);
+}
+
 // Solve pairs x_q = F^{-1} b_q, one CTA per right-hand side q.  Entry i of
 // column q sits at q * ldq + r(i) * ldi, r(i) = perm[i] (perm: new -> old,
 // the caller's order) or i (the factor's order).  b and x may alias.
@@ -435,6 +476,8 @@ bool resident_set_limits(int64_t n, const ResidentPlan& P) {
       cudaFuncSetAttribute(resident_round_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)bytes) == cudaSuccess &&
       cudaFuncSetAttribute(resident_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)res_solve_smem_bytes(n, P)) == cudaSuccess &&
+      cudaFuncSetAttribute(resident_inputs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)res_solve_smem_bytes(n, P)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -447,6 +490,11 @@ bool resident_set_limits(int64_t n, const ResidentPlan& P) {
 void resident_round(const ResidentArgs& a, int K, cudaStream_t st) {
   if (K <= 0) return;
   resident_round_kernel<<<K, kResidentThreads, res_smem_bytes(a.n, a.plan), st>>>(a);
+}
+
+void resident_inputs(const ResidentArgs& a, int K, cudaStream_t st) {
+  if (K <= 0) return;
+  resident_inputs_kernel<<<K, kResidentThreads, res_solve_smem_bytes(a.n, a.plan), st>>>(a);
 }
 
 void resident_solve(const ResFactor& F, const ResidentPlan& P, const double* b, double* x,

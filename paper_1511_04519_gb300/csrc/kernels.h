@@ -469,6 +469,10 @@ struct ResidentArgs {
   double gamma, tol, dt_out;
   int32_t m_max;
   int64_t n;
+  // z' and w of column q at zpre + q n, wpre + q n: written by
+  // resident_inputs, read by resident_round (null: the round solves them)
+  double* zpre = nullptr;
+  double* wpre = nullptr;
 };
 // the resident copies of factor F (fpan, bpan: as many doubles as F's
 // panels) from the per-supernode map sup[nsup]
@@ -481,6 +485,9 @@ bool resident_fits(int64_t n, const ResidentPlan& P);
 bool resident_set_limits(int64_t n, const ResidentPlan& P);
 // one round: K CTAs, column q of rc by CTA q
 void resident_round(const ResidentArgs& a, int K, cudaStream_t st);
+// the input solves of K columns of rc ahead of their rounds (they depend on
+// the sources only): z', w of column q into a.zpre, a.wpre + q n
+void resident_inputs(const ResidentArgs& a, int K, cudaStream_t st);
 // x_q = F^{-1} b_q for ncols columns, one CTA each: entry i of column q at
 // q * ldq + r(i) * ldi with r = perm (new -> old: the caller's order) or the
 // identity (the factor's order); b and x may alias

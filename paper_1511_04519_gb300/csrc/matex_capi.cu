@@ -102,6 +102,9 @@ struct matex_ctx {
   bool resident_ok = false;  // plan built and shared-memory limits set
   bool resident = false;
   float res_pair_ms = -1.f, lvl_pair_ms = -1.f;
+  // resident rounds: every column record's z' and w, solved ahead of the
+  // rounds in one launch per run (null: each round kernel solves its own)
+  double *pre_zp = nullptr, *pre_w = nullptr;
   TcScratch tc;                    // tensor-core recombination (kdim_cap 0: not used)
   int32_t *ev_o_d = nullptr, *ev_q_d = nullptr;  // -P events of all rounds
   // persistent solve: per column count (1..ldy) one PersistLevel row per level
@@ -1445,6 +1448,35 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
   }
   s = cuda_check(c, "initial states");
   if (s != MATEX_OK) return s;
+  auto res_args = [&](const Round& r) {
+    ResidentArgs ra{};
+    ra.F1 = c->opts.krylov == 1 ? c->rG : c->rM;
+    ra.FG = c->rG;
+    ra.plan = c->rplan;
+    ra.cperm = c->c_perm;
+    ra.src = c->src;
+    ra.rc = round_cols(c, r);
+    ra.n = n;
+    if (c->pre_zp) {
+      ra.zpre = c->pre_zp + (int64_t)r.begin * n;
+      ra.wpre = c->pre_w + (int64_t)r.begin * n;
+    }
+    return ra;
+  };
+  if (c->resident && c->pre_zp && bi == 0) {
+    // the input solves of every column record (sources only, no state): one
+    // launch, one CTA per record, instead of two solves in each round kernel
+    Round all;
+    all.begin = 0;
+    all.K = (int32_t)c->n_records;
+    e = prof_begin(c);
+    resident_inputs(res_args(all), all.K, st);
+    prof_end(c, e, P_SOLVE, 1, 2.0 * solve_flops(c, 1) * all.K, 2.0 * solve_bytes(c, 1) * all.K);
+    launches++;
+    sweepsG += 2;
+    solve_cols_total += 2 * c->n_records;
+    if ((s = cuda_check(c, "input solves")) != MATEX_OK) return s;
+  }
   for (size_t ri = (size_t)r0; ri < (size_t)r1; ++ri) {
     const Round& r = rounds[ri];
     const int K = r.K;
@@ -1452,19 +1484,13 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
     if (c->resident) {
       // every column's whole segment in one launch (one CTA each), then the
       // recombination of the round's outputs
-      ResidentArgs ra{};
-      ra.F1 = c->opts.krylov == 1 ? c->rG : c->rM;
-      ra.FG = c->rG;
-      ra.plan = c->rplan;
+      ResidentArgs ra = res_args(r);
       ra.Vb = c->Vb;
       ra.vstride = vstride;
       ra.X = c->Xb;
       ra.Z = c->Zb;
       ra.Zp = c->Zpb;
       ra.W = c->Wb;
-      ra.cperm = c->c_perm;
-      ra.src = c->src;
-      ra.rc = rc;
       ra.ss = c->ss;
       ra.coef = c->coef;
       ra.ldo = c->n_times;
@@ -1476,7 +1502,6 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
       ra.tol = c->tol;
       ra.dt_out = c->dt_out;
       ra.m_max = c->m_max;
-      ra.n = n;
       e = prof_begin(c);
       resident_round(ra, K, st);
       prof_end(c, e, P_SOLVE, 1, 0.0, 0.0, (int)ri);
@@ -1485,8 +1510,10 @@ matex_status run_pass(matex_ctx* c, bool capture, PassCounts& pc) {
                 c->n_times, K, r.obeg_min, r.oend_max, c->dt_out, st, nullptr);
       prof_end(c, e, P_RECOMB, 1, 0.0, 0.0, (int)ri);
       launches += 2;
-      sweepsG += 2;
-      solve_cols_total += 2 * (int64_t)K;
+      if (!c->pre_zp) {
+        sweepsG += 2;
+        solve_cols_total += 2 * (int64_t)K;
+      }
       if ((s = cuda_check(c, "round")) != MATEX_OK) return s;
       continue;
     }
@@ -2645,6 +2672,15 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
       cudaEventDestroy(e1);
       c->lvl_pair_ms = best;
       c->resident = c->res_pair_ms > 0.f && (o.resident == 2 || c->res_pair_ms <= 2.f * best);
+      // room for every record's z' and w (at most a quarter of the free
+      // memory): the input solves then run ahead of the rounds
+      size_t free_b = 0, total_b = 0;
+      cudaMemGetInfo(&free_b, &total_b);
+      const double need = 16.0 * (double)c->n_records * (double)n;
+      if (c->resident && c->n_records > 0 && need <= 0.25 * (double)free_b &&
+          !(c->alloc(c->pre_zp, (size_t)c->n_records * n) &&
+            c->alloc(c->pre_w, (size_t)c->n_records * n)))
+        c->pre_zp = c->pre_w = nullptr;
     }
     cudaGetLastError();
   }

@@ -57,7 +57,10 @@ def resident_vs_oracle(M, p, case, ref=None, **kw):
     assert np.abs(X - Xo).max() <= TOL_SAME * p.vdd, case
     # the counters the host derives after a resident run match the batched run's
     assert sim.stats.solve_columns == off.stats.solve_columns
-    assert sim.stats.sum_m == off.stats.sum_m and sim.stats.sweeps_G == off.stats.sweeps_G
+    assert sim.stats.sum_m == off.stats.sum_m
+    # the resident run solves every record's z' and w ahead of the rounds in
+    # two sweeps, where the batched run takes two per round
+    assert sim.stats.sweeps_G in (off.stats.sweeps_G, off.stats.sweeps_G - 2 * off.stats.rounds + 2)
     return X, sim
 
 
