@@ -139,6 +139,15 @@ typedef struct matex_opts {
                               count it tunes and keeps the tensor cores where they are faster.
                               Level launches only (not the persistent solve) */
   int32_t tc_min_width;    /* 0 (default): 64; else at least 32 */
+  int32_t single_column;   /* solves of one right-hand side: 0 (default) chosen at setup, 1 off,
+                              2 on.  The single-column level kernels run one launch per tree level
+                              and direction like the level launches, with everything that does
+                              not depend on the right-hand side (work descriptors, panel entries,
+                              gather rows) loaded before the previous level completes and one
+                              group of lanes per output row or column (no partial sums through
+                              memory).  With 0 the setup times the single-column solve pair both
+                              ways and keeps the faster (the new kernels when at least 5 %
+                              faster) */
 } matex_opts;
 
 /* Counters and timings of the last matex_run (or of setup for the setup_* fields). */
@@ -174,6 +183,7 @@ typedef struct matex_stats {
   int32_t tc_solve_supernodes;  /* supernodes whose solve products can run on the tensor cores
                                    (0: none or tc_solve off) */
   int32_t tc_solve_min_cols;    /* smallest column count at which they do (0: never) */
+  int32_t single_column;        /* 1: single-column solves run the single-column level kernels */
 } matex_stats;
 
 void matex_default_opts(matex_opts* opts);

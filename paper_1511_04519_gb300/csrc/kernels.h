@@ -499,6 +499,36 @@ void resident_solve(const ResFactor& F, const ResidentPlan& P, const double* b, 
 float resident_time_solve(const ResFactor& F, const ResidentPlan& P, const double* b, double* x,
                           int64_t n, cudaStream_t st, int reps);
 
+// Single-right-hand-side level solves (k_sptrsv_k1.cu).  Per direction, the
+// supernodes of every level in launch order (sorted by group size, then
+// size) as records, and per level the warps' work: warp j of level l starts
+// at row (forward) or column (backward) i0 of record k0 and covers nslot
+// consecutive rows of the following records of the same group size, each by
+// 2^lg lanes.  fw_off / bw_off (host memory, nlev + 1 each) delimit the
+// levels' warps.
+struct K1Sup {
+  int64_t po, rp;  // panel offset, first entry of the row list
+  int32_t f, w, ld, pad;
+};
+struct K1Warp {
+  int32_t k0, i0;
+  int16_t lg, nslot;
+  int32_t pad;
+};
+struct K1Plan {
+  int32_t nlev = 0, nsup = 0;
+  const K1Sup* fsups = nullptr;
+  const K1Sup* bsups = nullptr;
+  const K1Warp* fwarps = nullptr;
+  const K1Warp* bwarps = nullptr;
+  const int32_t* fw_off = nullptr;
+  const int32_t* bw_off = nullptr;
+};
+// one solve pair x = F^{-1} b for the single column 0 of Y (node-major, ldy
+// apart; Y2 scratch of the same shape): one launch per level and direction,
+// chained by programmatic dependent launch; returns the launches
+int solve_k1(const DevFactor& F, const K1Plan& P, double* Y, double* Y2, int ldy, cudaStream_t st);
+
 // Wide supernodes of the level solves on the tensor cores (k_sptrsv_tc.cu).
 // Per wide supernode: its panel (offset pan, first node f, width w, rows ld,
 // row list rp), the row tiles of the forward (ld rows) and backward (w rows)

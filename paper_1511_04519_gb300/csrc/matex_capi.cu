@@ -105,6 +105,11 @@ struct matex_ctx {
   // resident rounds: every column record's z' and w, solved ahead of the
   // rounds in one launch per run (null: each round kernel solves its own)
   double *pre_zp = nullptr, *pre_w = nullptr;
+  // single-column level kernels (opts.single_column): their plan and whether
+  // solves of one column take them
+  K1Plan k1;
+  std::vector<int32_t> k1_fw_off, k1_bw_off;
+  bool k1_use = false;
   TcScratch tc;                    // tensor-core recombination (kdim_cap 0: not used)
   int32_t *ev_o_d = nullptr, *ev_q_d = nullptr;  // -P events of all rounds
   // persistent solve: per column count (1..ldy) one PersistLevel row per level
@@ -786,6 +791,125 @@ bool plan_resident(matex_ctx* c, int threads) {
   return cudaStreamSynchronize(c->st) == cudaSuccess;
 }
 
+// The single-column level kernels' plan (see K1Plan): per direction and
+// level, the level's supernodes sorted by the lanes one output row (column)
+// takes, G = 2^lg with 16 G >= its longest dot product (forward: w terms,
+// backward: w + r; at most 32 lanes, more trips beyond 512 terms), then by
+// that length; and the warps, each 32 / G consecutive rows of one G.
+bool plan_k1(matex_ctx* c) {
+  const Symbolic& S = c->S;
+  const int nlev = (int)S.level_ptr.size() - 1;
+  std::vector<K1Sup> recs[2];
+  std::vector<K1Warp> warps[2];
+  std::vector<int32_t> off[2];
+  for (int dir = 0; dir < 2; ++dir) {
+    const bool fwd = dir == 0;
+    off[dir].assign(nlev + 1, 0);
+    for (int l = 0; l < nlev; ++l) {
+      off[dir][l] = (int32_t)warps[dir].size();
+      struct Item { int lg, len, cnt; K1Sup d; };
+      std::vector<Item> it;
+      for (int k = S.level_ptr[l]; k < S.level_ptr[l + 1]; ++k) {
+        const int sn = S.level_sups[k];
+        K1Sup d{};
+        d.f = S.sup_first[sn];
+        d.w = S.sup_first[sn + 1] - d.f;
+        d.rp = S.sup_rowptr[sn];
+        d.ld = (int32_t)(S.sup_rowptr[sn + 1] - d.rp);
+        d.po = S.pan_off[sn];
+        const int len = fwd ? d.w : d.ld;
+        int lg = 0;
+        while (lg < 5 && 16 * (1 << lg) < len) ++lg;
+        it.push_back(Item{lg, len, fwd ? d.ld : d.w, d});
+      }
+      std::stable_sort(it.begin(), it.end(), [](const Item& a, const Item& b) {
+        return a.lg != b.lg ? a.lg < b.lg : a.len < b.len;
+      });
+      const int base = (int)recs[dir].size();
+      for (const Item& x : it) recs[dir].push_back(x.d);
+      for (size_t a = 0; a < it.size();) {
+        size_t e = a;
+        while (e < it.size() && it[e].lg == it[a].lg) ++e;
+        const int per = 32 >> it[a].lg;
+        size_t k = a;
+        int i0 = 0;
+        while (k < e) {
+          // the next warp: per rows from (k, i0) on, within this group size
+          size_t kk = k;
+          int ii = i0, take = 0;
+          while (take < per && kk < e) {
+            const int use = std::min(it[kk].cnt - ii, per - take);
+            take += use;
+            ii += use;
+            if (ii == it[kk].cnt) {
+              ++kk;
+              ii = 0;
+            }
+          }
+          warps[dir].push_back(K1Warp{base + (int32_t)k, i0, (int16_t)it[a].lg, (int16_t)take, 0});
+          k = kk;
+          i0 = ii;
+        }
+        a = e;
+      }
+    }
+    off[dir][nlev] = (int32_t)warps[dir].size();
+  }
+  K1Sup *fs = nullptr, *bs = nullptr;
+  K1Warp *fw = nullptr, *bw = nullptr;
+  if (!c->upload(fs, recs[0].data(), recs[0].size()) || !c->upload(bs, recs[1].data(), recs[1].size()) ||
+      !c->upload(fw, warps[0].data(), warps[0].size()) ||
+      !c->upload(bw, warps[1].data(), warps[1].size()))
+    return false;
+  c->k1_fw_off = off[0];
+  c->k1_bw_off = off[1];
+  c->k1.nlev = nlev;
+  c->k1.nsup = S.nsup;
+  c->k1.fsups = fs;
+  c->k1.bsups = bs;
+  c->k1.fwarps = fw;
+  c->k1.bwarps = bw;
+  c->k1.fw_off = c->k1_fw_off.data();
+  c->k1.bw_off = c->k1_bw_off.data();
+  return true;
+}
+
+int solve_cols(matex_ctx* c, const DevFactor& F, int ncols);
+
+// opts.single_column 2: the single-column kernels for every solve of one
+// column; 0 (with the tuned launch mode): where their solve pair is at least
+// 5 % faster than the tuned path's (best of three after a warm-up each).
+void autotune_k1(matex_ctx* c) {
+  c->k1_use = false;
+  if (!plan_k1(c)) return;
+  if (c->opts.single_column == 2) {
+    c->k1_use = true;
+    return;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaMemsetAsync(c->Y, 0, sizeof(double) * (size_t)c->n * c->ldy, c->st);
+  auto best_of = [&](bool k1) {
+    c->k1_use = k1;
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(e0, c->st);
+      solve_cols(c, c->fM, 1);
+      cudaEventRecord(e1, c->st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) best = std::min(best, ms);
+    }
+    return best;
+  };
+  const float ref = best_of(false), mine = best_of(true);
+  c->k1_use = cudaGetLastError() == cudaSuccess && mine < 0.95f * ref;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
 // Tensor-core products of the wide supernodes (k_sptrsv_tc.cu): their table,
 // per level the (supernode, row tile) lists of both directions, and the
 // panel slices of both factors.  False when there is no wide supernode or no
@@ -961,6 +1085,10 @@ int solve_ts(matex_ctx* c, const DevFactor& F, int fi, int ncols) {
 
 int solve_cols(matex_ctx* c, const DevFactor& F, int ncols) {
   if (ncols <= 0) return 0;
+  // one column: the single-column level kernels (any factor of this
+  // symbolic structure: C + gamma G, G, the trapezoidal one)
+  if (ncols == 1 && c->k1_use && F.sup_first == c->fM.sup_first)
+    return solve_k1(F, c->k1, c->Y, c->Y2, c->ldy, c->st);
   int mode = c->opts.solve_mode;
   if (mode == 2) mode = c->mode_by_ncols.empty() ? 0 : c->mode_by_ncols[std::min(ncols, c->ldy)];
   const int fi = F.pan_cm == c->fM.pan_cm ? 0 : F.pan_cm == c->fG.pan_cm ? 1 : -1;
@@ -2183,6 +2311,7 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   if (o.resident < 0 || o.resident > 2) return bad("resident must be 0, 1 or 2");
   if (o.tc_solve < 0 || o.tc_solve > 2) return bad("tc_solve must be 0, 1 or 2");
   if (o.tc_min_width != 0 && o.tc_min_width < 32) return bad("tc_min_width must be 0 or >= 32");
+  if (o.single_column < 0 || o.single_column > 2) return bad("single_column must be 0, 1 or 2");
   if (o.resident == 2 && (o.krylov == 2 || o.tape || o.tail_eps > 0.0 || n > kResidentMaxN))
     return bad("resident rounds need n <= 8192, krylov 0 or 1, tape 0 and tail_eps 0");
   if (o.group_select >= n_groups) return bad("group_select out of range");
@@ -2643,6 +2772,11 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
   }
   c->setup_stats.tc_solve_supernodes = c->ts_n;
   c->setup_stats.tc_solve_min_cols = c->ts_min_cols;
+  if (o.single_column == 2 || (o.single_column == 0 && o.solve_mode == 2)) {
+    autotune_k1(c);
+    cudaGetLastError();
+  }
+  c->setup_stats.single_column = c->k1_use ? 1 : 0;
   if (o.resident != 1 && o.krylov != 2 && o.tape == 0 && o.tail_eps == 0.0 &&
       n <= kResidentMaxN) {
     // resident rounds: one CTA's solve pair against the batched path's

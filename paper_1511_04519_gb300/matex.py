@@ -35,7 +35,8 @@ class MatexOpts(C.Structure):
                 ("tape", C.c_int32), ("krylov", C.c_int32), ("graph", C.c_int32),
                 ("tail_eps", C.c_double), ("tape_window", C.c_int32), ("tape_block", C.c_int32),
                 ("recombine", C.c_int32), ("decompose", C.c_int32), ("resident", C.c_int32),
-                ("tc_solve", C.c_int32), ("tc_min_width", C.c_int32)]
+                ("tc_solve", C.c_int32), ("tc_min_width", C.c_int32),
+                ("single_column", C.c_int32)]
 
 
 class MatexStats(C.Structure):
@@ -49,7 +50,8 @@ class MatexStats(C.Structure):
                 ("graph_replay", C.c_int32), ("graph_capture_ms", C.c_double),
                 ("nnz_L_exact", C.c_int64), ("tape_window", C.c_int32), ("tape_block", C.c_int32),
                 ("tape_bytes", C.c_int64), ("tc_rounds", C.c_int32), ("resident", C.c_int32),
-                ("tc_solve_supernodes", C.c_int32), ("tc_solve_min_cols", C.c_int32)]
+                ("tc_solve_supernodes", C.c_int32), ("tc_solve_min_cols", C.c_int32),
+                ("single_column", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -333,7 +335,7 @@ class Sim:
                  replay_m=None, max_width=0, strict=False, stream=None, solve_mode=2,
                  tape=False, graph=True, krylov="R", tail_eps=0.0, tape_window=0, tape_block=0,
                  recombine="auto", decompose="groups", resident="auto", tc_solve="auto",
-                 tc_min_width=0, **overrides):
+                 tc_min_width=0, single_column="auto", **overrides):
         o = matex_default_opts()
         o.graph = int(bool(graph))
         o.tail_eps = float(tail_eps)
@@ -351,6 +353,7 @@ class Sim:
         o.resident = {"auto": 0, "off": 1, "on": 2, 0: 0, 1: 1, 2: 2}[resident]
         o.tc_solve = {"auto": 0, "off": 1, "on": 2, 0: 0, 1: 1, 2: 2}[tc_solve]
         o.tc_min_width = int(tc_min_width)
+        o.single_column = {"auto": 0, "off": 1, "on": 2, 0: 0, 1: 1, 2: 2}[single_column]
         o.tape_window = int(tape_window)
         o.tape_block = int(tape_block)
         self._keep = []

@@ -134,7 +134,8 @@ def test_setup_rejects_bad_inputs_before_gpu(lib, mutation):
                                          ("decompose_tape", 1), ("recombine", 2),
                                          ("tape", 3), ("tape_window", -1), ("resident", 3),
                                          ("resident_krylov", 2), ("resident_tail", 1e-9),
-                                         ("tc_solve", 3), ("tc_min_width", 16)])
+                                         ("tc_solve", 3), ("tc_min_width", 16),
+                                         ("single_column", 3)])
 def test_setup_rejects_bad_options_before_gpu(lib, field, value):
     """Option checks run on the host before any device work: the status is
     MATEX_ERR_ARG with a message, on a machine without a GPU as well."""
@@ -184,6 +185,6 @@ def test_default_options_layout():
     M._lib.matex_default_opts(C.cast(buf, C.POINTER(M.MatexOpts)))
     assert bytes(buf[size:]) == b"\xa5" * 64
     assert M.MatexOpts.from_buffer(buf).tail_eps == 0.0
-    assert C.sizeof(M.MatexStats) == 3 * 8 + 8 + 4 * 12 + 8 + 4 * 4 + 8 + 8 + 4 * 2 + 8 + 8 + 8
+    assert C.sizeof(M.MatexStats) == 3 * 8 + 8 + 4 * 12 + 8 + 4 * 4 + 8 + 8 + 4 * 2 + 8 + 8 + 8 + 8
     assert (o.tape_window, o.tape_block, o.recombine, o.decompose, o.resident, o.tc_solve,
-            o.tc_min_width) == (0, 0, 0, 0, 0, 0, 0)
+            o.tc_min_width, o.single_column) == (0, 0, 0, 0, 0, 0, 0, 0)
