@@ -26,8 +26,8 @@ namespace matex {
 
 namespace {
 
-constexpr int kK1Threads = 128;
-constexpr int kK1Terms = 16;  // panel entries per lane per trip
+constexpr int kK1Threads = 32;  // one warp per CTA: a warp leaves as soon as it is done
+constexpr int kK1Terms = 16;  // panel entries per lane per trip (two FMA chains)
 
 __device__ __forceinline__ void k1_chain_wait() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -117,7 +117,7 @@ k1_fwd_kernel(DevFactor F, const K1Sup* __restrict__ sups, int nsup,
   k1_chain_wait();
   if (F.abort && *F.abort) return;
   const double* __restrict__ b = Y + (int64_t)L.d.f * ldy;
-  double acc = 0.0;
+  double acc = 0.0, acc2 = 0.0;
   for (int tr = 0; tr < trips; ++tr) {
     const int t0 = tr * kK1Terms * G + L.sub;
     if (tr > 0) {
@@ -134,9 +134,12 @@ k1_fwd_kernel(DevFactor F, const K1Sup* __restrict__ sups, int nsup,
       x[u] = t < n ? __ldcg(b + (int64_t)t * ldy) : 0.0;
     }
 #pragma unroll
-    for (int u = 0; u < kK1Terms; ++u) acc = fma(q[u], x[u], acc);
+    for (int u = 0; u < kK1Terms; u += 2) {
+      acc = fma(q[u], x[u], acc);
+      acc2 = fma(q[u + 1], x[u + 1], acc2);
+    }
   }
-  acc = k1_group_sum(acc, G);
+  acc = k1_group_sum(acc + acc2, G);
   if (L.live && L.sub == 0) {
     if (i < w) Y2[(int64_t)(L.d.f + i) * ldy] = acc * dinv;
     else atomicAdd(Y + (int64_t)orow * ldy, -acc);
@@ -167,7 +170,7 @@ k1_bwd_kernel(DevFactor F, const K1Sup* __restrict__ sups, int nsup,
   k1_chain_wait();
   if (F.abort && *F.abort) return;
   const double* __restrict__ y = Y2 + (int64_t)L.d.f * ldy;
-  double acc = 0.0;
+  double acc = 0.0, acc2 = 0.0;
   for (int tr = 0; tr < trips; ++tr) {
     const int t0 = tr * kK1Terms * G + L.sub;
     if (tr > 0) {
@@ -185,9 +188,12 @@ k1_bwd_kernel(DevFactor F, const K1Sup* __restrict__ sups, int nsup,
       v[u] = t >= n ? 0.0 : g[u] < 0 ? __ldcg(y + (int64_t)ii * ldy) : -__ldcg(Y + (int64_t)g[u] * ldy);
     }
 #pragma unroll
-    for (int u = 0; u < kK1Terms; ++u) acc = fma(q[u], v[u], acc);
+    for (int u = 0; u < kK1Terms; u += 2) {
+      acc = fma(q[u], v[u], acc);
+      acc2 = fma(q[u + 1], v[u + 1], acc2);
+    }
   }
-  acc = k1_group_sum(acc, G);
+  acc = k1_group_sum(acc + acc2, G);
   if (L.live && L.sub == 0) Y[(int64_t)(L.d.f + k) * ldy] = acc;
 }
 
