@@ -253,16 +253,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_kernel(TcGemm g) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t a = smem_addr(tc_smem + (size_t)st * kTcStage);
         const uint32_t b = a + kTcS * kTcABytes;
-#pragma unroll 1
+        // descriptors of the stage's first A and B slices; the others differ
+        // only in the start address field (16-byte units, no carry: shared
+        // memory addresses stay below 2^18)
+        const uint64_t ad0 = tc_desc(a, 128, kTcSbo), bd0 = tc_desc(b, 128, kTcSbo);
+        const uint32_t first = s == s0 ? 0u : 1u;
+#pragma unroll
         for (int p = 0; p < kTcS; ++p)
-#pragma unroll 1
+#pragma unroll
           for (int q = 0; q + p < kTcS; ++q)
 #pragma unroll
             for (int kk = 0; kk < kTcK; kk += 16) {
-              const uint64_t ad = tc_desc(a + p * kTcABytes + (kk / 8) * 128, 128, kTcSbo);
-              const uint64_t bd = tc_desc(b + q * kTcBBytes + (kk / 8) * 128, 128, kTcSbo);
-              const uint32_t acc = (s == s0 && p == 0 && kk == 0) ? 0u : 1u;
-              tc_mma(tmem + (uint32_t)((p + q) * kTcN), ad, bd, kTcIdesc, acc);
+              const uint64_t ad = ad0 + (uint64_t)((p * kTcABytes + (kk / 8) * 128) >> 4);
+              const uint64_t bd = bd0 + (uint64_t)((q * kTcBBytes + (kk / 8) * 128) >> 4);
+              tc_mma(tmem + (uint32_t)((p + q) * kTcN), ad, bd, kTcIdesc,
+                     (p == 0 && kk == 0) ? first : 1u);
             }
         tc_commit(&freed[st]);
       }
