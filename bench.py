@@ -658,6 +658,7 @@ def main():
                      "frac_fp64": fl / (best / 1e3) / 1e12 / fp64_peak})
     sptrsv["by_ncols"] = by_k
     sptrsv["k1"] = dict(by_k[0], algorithmic_bytes=2.0 * (12.0 * nnz + 4.0 * (p.n + 1)) + 40.0 * p.n,
+                        single_column_kernels=int(setup.get("single_column", 0)),
                         note="one right-hand side: the column count where the solve's bytes "
                              "dominate (0.2 flop/byte), so its roofline is HBM")
 

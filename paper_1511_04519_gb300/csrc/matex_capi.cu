@@ -876,15 +876,36 @@ bool plan_k1(matex_ctx* c) {
 
 int solve_cols(matex_ctx* c, const DevFactor& F, int ncols);
 
+std::string tune_key(matex_ctx* c);
+
 // opts.single_column 2: the single-column kernels for every solve of one
 // column; 0 (with the tuned launch mode): where their solve pair is at least
-// 5 % faster than the tuned path's (best of three after a warm-up each).
+// 5 % faster than the tuned path's (best of three after a warm-up each),
+// cached in MATEX_AUTOTUNE_CACHE like the other tuners' choices.
 void autotune_k1(matex_ctx* c) {
   c->k1_use = false;
   if (!plan_k1(c)) return;
   if (c->opts.single_column == 2) {
     c->k1_use = true;
     return;
+  }
+  const char* cache = std::getenv("MATEX_AUTOTUNE_CACHE");
+  const std::string key = "k1:" + tune_key(c);
+  if (cache) {
+    if (FILE* f = std::fopen(cache, "r")) {
+      char line[1024];
+      int found = -1;
+      while (std::fgets(line, sizeof(line), f)) {
+        const std::string l(line);
+        if (l.compare(0, key.size() + 1, key + " ") == 0 && l.size() > key.size() + 1)
+          found = l[key.size() + 1] == '1' ? 1 : 0;
+      }
+      std::fclose(f);
+      if (found >= 0) {
+        c->k1_use = found == 1;
+        return;
+      }
+    }
   }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -908,6 +929,12 @@ void autotune_k1(matex_ctx* c) {
   c->k1_use = cudaGetLastError() == cudaSuccess && mine < 0.95f * ref;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (cache) {
+    if (FILE* f = std::fopen(cache, "a")) {
+      std::fprintf(f, "%s %d\n", key.c_str(), c->k1_use ? 1 : 0);
+      std::fclose(f);
+    }
+  }
 }
 
 // Tensor-core products of the wide supernodes (k_sptrsv_tc.cu): their table,
