@@ -206,14 +206,17 @@ def measured_traffic():
     import hashlib
     import re
     path = os.path.join(ROOT, "profiles", "traffic_solve_mesh2x300x300.md")
-    src = os.path.join(ROOT, "paper_1511_04519_gb300", "csrc", "k_sptrsv.cu")
+    csrc = os.path.join(ROOT, "paper_1511_04519_gb300", "csrc")
     try:
         text = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256()
+        for f in ("k_sptrsv.cu", "k_sptrsv_k1.cu"):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+        sha = h.hexdigest()[:16]
     except OSError as exc:
         return None, f"no summary: {exc}"
     m_b = re.search(r"traffic_per_solve_call_bytes:\s*([0-9.eE+]+)", text)
-    m_s = re.search(r"k_sptrsv_cu_sha256_16:\s*([0-9a-f]+)", text)
+    m_s = re.search(r"solve_kernels_sha256_16:\s*([0-9a-f]+)", text)
     if not m_b or not m_s:
         return None, "summary without the traffic line"
     if m_s.group(1) != sha:
@@ -310,6 +313,18 @@ def ncu_case(what: str) -> int:
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
         sim.time_solve(0, 64, reps=1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"ncu_case": what, "max_memory_gb": torch.cuda.max_memory_allocated() / 1e9}))
+        return 0
+    if what == "k1":
+        # the whole bench grid, one right-hand side on the single-column level
+        # kernels: one solve pair of C + gamma G after a warm one
+        sim = M.Sim(p, single_column="on", include_dc=False, rows=np.arange(4, dtype=np.int32))
+        sim.time_solve(0, 1, reps=1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        sim.time_solve(0, 1, reps=1)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         print(json.dumps({"ncu_case": what, "max_memory_gb": torch.cuda.max_memory_allocated() / 1e9}))
@@ -526,7 +541,7 @@ def main():
                          "launch and report their aggregate rate (0: skip)")
     ap.add_argument("--profile-step", action="store_true",
                     help="warm up, run one step inside cudaProfilerStart/Stop, print its stats")
-    ap.add_argument("--ncu-case", choices=["solve", "levels", "run", "ksweep", "small", "tcsolve"], default=None,
+    ap.add_argument("--ncu-case", choices=["solve", "levels", "run", "ksweep", "small", "tcsolve", "k1"], default=None,
                     help="reduced case for full ncu captures: the same grid with 8 groups; "
                          "one warm call, then one call inside cudaProfilerStart/Stop")
     args = ap.parse_args()
