@@ -6,7 +6,7 @@
 // chain to one round trip after the previous level completes:
 //   - everything that does not depend on the right-hand side (the warp's
 //     work descriptor, its supernodes' sizes and offsets, the first panel
-//     entries of every lane, the ancestor rows of its gathers) is loaded
+//     entries of every lane, the ancestor rows of its first gathers) is loaded
 //     before griddepcontrol.wait, while the previous level still runs
 //     (programmatic dependent launch);
 //   - after the wait a lane loads its right-hand-side entries (all in flight
@@ -159,39 +159,58 @@ k1_bwd_kernel(DevFactor F, const K1Sup* __restrict__ sups, int nsup,
   const int trips = __reduce_max_sync(0xffffffffu, (n + kK1Terms * G - 1) / (kK1Terms * G));
   const double* __restrict__ P = F.pan_rm + L.d.po + k;  // entry (i, k) at P[i * w]
   const int32_t* __restrict__ rows = F.sup_rows + L.d.rp;
-  double q[kK1Terms];
-  int g[kK1Terms];  // ancestor row of a term below the diagonal block, -1 inside it
+  // the ancestor rows of the first three trips' gathers are loaded before
+  // the wait, so after it a trip's gathers wait only for the right-hand side
+  // (the later trips' panel entries load beside them)
+  constexpr int kPre = 3;
+  auto load_g = [&](int (&g)[kK1Terms], int tr) {
 #pragma unroll
-  for (int u = 0; u < kK1Terms; ++u) {
-    const int t = L.sub + G * u, ii = k + t;
-    q[u] = t < n ? __ldg(P + (int64_t)ii * w) : 0.0;
-    g[u] = t < n && ii >= w ? __ldg(rows + ii) : -1;
-  }
+    for (int u = 0; u < kK1Terms; ++u) {
+      const int t = tr * kK1Terms * G + L.sub + G * u, ii = k + t;
+      g[u] = t < n && ii >= w ? __ldg(rows + ii) : -1;
+    }
+  };
+  auto load_q = [&](double (&q)[kK1Terms], int tr) {
+#pragma unroll
+    for (int u = 0; u < kK1Terms; ++u) {
+      const int t = tr * kK1Terms * G + L.sub + G * u, ii = k + t;
+      q[u] = t < n ? __ldg(P + (int64_t)ii * w) : 0.0;
+    }
+  };
+  double q[kK1Terms];
+  int g[kPre][kK1Terms];
+  load_q(q, 0);
+#pragma unroll
+  for (int tp = 0; tp < kPre; ++tp)
+    if (tp < trips) load_g(g[tp], tp);
   k1_chain_wait();
   if (F.abort && *F.abort) return;
   const double* __restrict__ y = Y2 + (int64_t)L.d.f * ldy;
   double acc = 0.0, acc2 = 0.0;
-  for (int tr = 0; tr < trips; ++tr) {
-    const int t0 = tr * kK1Terms * G + L.sub;
-    if (tr > 0) {
-#pragma unroll
-      for (int u = 0; u < kK1Terms; ++u) {
-        const int t = t0 + G * u, ii = k + t;
-        q[u] = t < n ? __ldg(P + (int64_t)ii * w) : 0.0;
-        g[u] = t < n && ii >= w ? __ldg(rows + ii) : -1;
-      }
-    }
+  auto step = [&](const int (&gg)[kK1Terms], int tr) {
     double v[kK1Terms];
 #pragma unroll
     for (int u = 0; u < kK1Terms; ++u) {
-      const int t = t0 + G * u, ii = k + t;
-      v[u] = t >= n ? 0.0 : g[u] < 0 ? __ldcg(y + (int64_t)ii * ldy) : -__ldcg(Y + (int64_t)g[u] * ldy);
+      const int t = tr * kK1Terms * G + L.sub + G * u, ii = k + t;
+      v[u] = t >= n ? 0.0 : gg[u] < 0 ? __ldcg(y + (int64_t)ii * ldy) : -__ldcg(Y + (int64_t)gg[u] * ldy);
     }
 #pragma unroll
     for (int u = 0; u < kK1Terms; u += 2) {
       acc = fma(q[u], v[u], acc);
       acc2 = fma(q[u + 1], v[u + 1], acc2);
     }
+  };
+#pragma unroll
+  for (int tp = 0; tp < kPre; ++tp)
+    if (tp < trips) {
+      if (tp > 0) load_q(q, tp);
+      step(g[tp], tp);
+    }
+  for (int tr = kPre; tr < trips; ++tr) {
+    int gg[kK1Terms];
+    load_g(gg, tr);
+    load_q(q, tr);
+    step(gg, tr);
   }
   acc = k1_group_sum(acc + acc2, G);
   if (L.live && L.sub == 0) Y[(int64_t)(L.d.f + k) * ldy] = acc;
