@@ -5,8 +5,8 @@
 // round trips, not by bandwidth or the FP64 pipe.  These kernels shorten that
 // chain to one round trip after the previous level completes:
 //   - everything that does not depend on the right-hand side (the warp's
-//     work descriptor, its supernodes' sizes and offsets, the first panel
-//     entries of every lane, the ancestor rows of its first gathers) is loaded
+//     work descriptor, its supernodes' sizes and offsets, the panel entries
+//     of every lane's first trips, the ancestor rows of its first gathers) is loaded
 //     before griddepcontrol.wait, while the previous level still runs
 //     (programmatic dependent launch);
 //   - after the wait a lane loads its right-hand-side entries (all in flight
@@ -102,11 +102,19 @@ k1_fwd_kernel(DevFactor F, const K1Sup* __restrict__ sups, int nsup,
   const int n = L.live ? (i < w ? i + 1 : w) : 0;
   const int trips = __reduce_max_sync(0xffffffffu, (n + kK1Terms * G - 1) / (kK1Terms * G));
   const double* __restrict__ P = F.pan_cm + L.d.po + i;  // entry (i, t) at P[t * ld]
-  double q[kK1Terms];
+  // the first two trips' panel entries before the wait
+  double q[kK1Terms], q1[kK1Terms];
 #pragma unroll
   for (int u = 0; u < kK1Terms; ++u) {
     const int t = L.sub + G * u;
     q[u] = t < n ? __ldg(P + (int64_t)t * ld) : 0.0;
+  }
+  if (trips > 1) {
+#pragma unroll
+    for (int u = 0; u < kK1Terms; ++u) {
+      const int t = kK1Terms * G + L.sub + G * u;
+      q1[u] = t < n ? __ldg(P + (int64_t)t * ld) : 0.0;
+    }
   }
   int orow = 0;
   double dinv = 0.0;
@@ -120,7 +128,10 @@ k1_fwd_kernel(DevFactor F, const K1Sup* __restrict__ sups, int nsup,
   double acc = 0.0, acc2 = 0.0;
   for (int tr = 0; tr < trips; ++tr) {
     const int t0 = tr * kK1Terms * G + L.sub;
-    if (tr > 0) {
+    if (tr == 1) {
+#pragma unroll
+      for (int u = 0; u < kK1Terms; ++u) q[u] = q1[u];
+    } else if (tr > 1) {
 #pragma unroll
       for (int u = 0; u < kK1Terms; ++u) {
         const int t = t0 + G * u;
