@@ -128,7 +128,11 @@ typedef struct matex_opts {
                               MATEX_ERR_ARG otherwise.  With 0 the setup times one such solve
                               pair against the batched path's single-column pair and takes the
                               resident rounds when they are at most twice as long (they also
-                              replace the ~12 other launches of every Arnoldi step) */
+                              replace the ~12 other launches of every Arnoldi step).  The
+                              input solutions of every segment (sources only) are solved ahead
+                              of the rounds in one launch when they fit a quarter of the free
+                              memory; 3: as 2, but each round kernel solves its own (the path
+                              taken when they do not fit; the same results bit for bit) */
   int32_t tc_solve;        /* supernodes at least tc_min_width wide in the level solves: 0
                               (default) chosen at setup per column count, 1 off, 2 on.  Their
                               two dense products per supernode (P_s b_s forward, P_s^T [..]

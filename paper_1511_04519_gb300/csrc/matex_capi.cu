@@ -2335,11 +2335,11 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
     return bad("decompose = 1 (ramps) needs tape = 0 and group_select = -1");
   if (o.col_block != 0 && o.col_block != 1 && o.col_block != 2 && o.col_block != 4 && o.col_block != 8)
     return bad("col_block must be 0, 1, 2, 4 or 8");
-  if (o.resident < 0 || o.resident > 2) return bad("resident must be 0, 1 or 2");
+  if (o.resident < 0 || o.resident > 3) return bad("resident must be 0, 1, 2 or 3");
   if (o.tc_solve < 0 || o.tc_solve > 2) return bad("tc_solve must be 0, 1 or 2");
   if (o.tc_min_width != 0 && o.tc_min_width < 32) return bad("tc_min_width must be 0 or >= 32");
   if (o.single_column < 0 || o.single_column > 2) return bad("single_column must be 0, 1 or 2");
-  if (o.resident == 2 && (o.krylov == 2 || o.tape || o.tail_eps > 0.0 || n > kResidentMaxN))
+  if (o.resident >= 2 && (o.krylov == 2 || o.tape || o.tail_eps > 0.0 || n > kResidentMaxN))
     return bad("resident rounds need n <= 8192, krylov 0 or 1, tape 0 and tail_eps 0");
   if (o.group_select >= n_groups) return bad("group_select out of range");
   if (o.n_rows < 0 || (o.n_rows > 0 && !o.rows)) return bad("row list missing");
@@ -2832,20 +2832,21 @@ matex_status matex_setup(matex_ctx** out, int64_t n, const double* cap, const in
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       c->lvl_pair_ms = best;
-      c->resident = c->res_pair_ms > 0.f && (o.resident == 2 || c->res_pair_ms <= 2.f * best);
+      c->resident = c->res_pair_ms > 0.f && (o.resident >= 2 || c->res_pair_ms <= 2.f * best);
       // room for every record's z' and w (at most a quarter of the free
-      // memory): the input solves then run ahead of the rounds
+      // memory): the input solves then run ahead of the rounds (not with
+      // resident = 3, which keeps them in the round kernels)
       size_t free_b = 0, total_b = 0;
       cudaMemGetInfo(&free_b, &total_b);
       const double need = 16.0 * (double)c->n_records * (double)n;
-      if (c->resident && c->n_records > 0 && need <= 0.25 * (double)free_b &&
+      if (c->resident && o.resident != 3 && c->n_records > 0 && need <= 0.25 * (double)free_b &&
           !(c->alloc(c->pre_zp, (size_t)c->n_records * n) &&
             c->alloc(c->pre_w, (size_t)c->n_records * n)))
         c->pre_zp = c->pre_w = nullptr;
     }
     cudaGetLastError();
   }
-  if (o.resident == 2 && !c->resident) {
+  if (o.resident >= 2 && !c->resident) {
     g_setup_err = "resident rounds do not fit this device (shared memory or launch failed)";
     delete c;
     return MATEX_ERR_ARG;

@@ -350,7 +350,8 @@ class Sim:
         o.tape = {False: 0, True: 1, 0: 0, 1: 1, 2: 2, "full": 1, "checkpoint": 2}[tape]
         o.recombine = {"auto": 0, "tensor": 0, "fp64": 1}[recombine]
         o.decompose = {"groups": 0, "ramps": 1}[decompose]
-        o.resident = {"auto": 0, "off": 1, "on": 2, 0: 0, 1: 1, 2: 2}[resident]
+        o.resident = {"auto": 0, "off": 1, "on": 2, "on_inline_inputs": 3, 0: 0, 1: 1, 2: 2,
+                      3: 3}[resident]
         o.tc_solve = {"auto": 0, "off": 1, "on": 2, 0: 0, 1: 1, 2: 2}[tc_solve]
         o.tc_min_width = int(tc_min_width)
         o.single_column = {"auto": 0, "off": 1, "on": 2, 0: 0, 1: 1, 2: 2}[single_column]

@@ -132,7 +132,7 @@ def test_setup_rejects_bad_inputs_before_gpu(lib, mutation):
                                          ("solve_mode", 5), ("tape_tail", 1e-9),
                                          ("tape_krylov", 1), ("decompose", 2),
                                          ("decompose_tape", 1), ("recombine", 2),
-                                         ("tape", 3), ("tape_window", -1), ("resident", 3),
+                                         ("tape", 3), ("tape_window", -1), ("resident", 4),
                                          ("resident_krylov", 2), ("resident_tail", 1e-9),
                                          ("tc_solve", 3), ("tc_min_width", 16),
                                          ("single_column", 3)])

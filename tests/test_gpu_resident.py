@@ -193,6 +193,30 @@ def test_one_group_at_a_time_matches_batched(M):
     assert np.abs(Xs - Xb).max() <= 1e-13
 
 
+@pytest.mark.parametrize("case", ["config0", "12groups"])
+def test_input_solves_ahead_equal_inline_bit_for_bit(M, case):
+    """Every segment's z' and w solved ahead of the rounds (one launch) or by
+    each round kernel (resident = 3, the path when they do not fit memory):
+    the same code in the same order, so the same bits, new currents too."""
+    if case == "config0":
+        p = gridgen.config0()
+    else:
+        p = gridgen.small_mesh(20, nx=30, ny=25, layers=2, n_src=40,
+                               group_templates=[2, 3, 1, 4] * 3, t_end=0.6e-9, dt_out=5e-12)
+    ahead = M.Sim(p, resident="on")
+    inline = M.Sim(p, resident="on_inline_inputs")
+    Xa = ahead.run().cpu().numpy()
+    Xi = inline.run().cpu().numpy()
+    assert ahead.stats.resident == 1 and inline.stats.resident == 1
+    assert np.array_equal(Xa, Xi)
+    assert np.array_equal(ahead.m_sequence(), inline.m_sequence())
+    # the ahead launch is one more kernel per run
+    assert ahead.stats.kernel_launches == inline.stats.kernel_launches + 1
+    amp = np.random.default_rng(5).uniform(0.5, 2.0, p.n_src)
+    src_of = np.repeat(np.arange(p.n_src), np.diff(p.pwl_off))
+    assert np.array_equal(ahead.run_host(p.pwl_v * amp[src_of]), inline.run_host(p.pwl_v * amp[src_of]))
+
+
 def test_graph_replay_and_host_buffers_are_bit_identical(M):
     p = gridgen.small_mesh(10, nx=20, ny=18, layers=2, n_src=9, group_templates=[3, 3, 2])
     sim = M.Sim(p, resident="on")
