@@ -796,13 +796,12 @@ bool plan_resident(matex_ctx* c, int threads) {
 // takes, G = 2^lg with 16 G >= its longest dot product (forward: w terms,
 // backward: w + r; at most 32 lanes, more trips beyond 512 terms), then by
 // that length; and the warps, each 32 / G consecutive rows of one G.
-bool plan_k1(matex_ctx* c) {
-  const Symbolic& S = c->S;
+void build_k1_plan(const Symbolic& S, std::vector<K1Sup> (&recs)[2],
+                   std::vector<K1Warp> (&warps)[2], std::vector<int32_t> (&off)[2]) {
   const int nlev = (int)S.level_ptr.size() - 1;
-  std::vector<K1Sup> recs[2];
-  std::vector<K1Warp> warps[2];
-  std::vector<int32_t> off[2];
   for (int dir = 0; dir < 2; ++dir) {
+    recs[dir].clear();
+    warps[dir].clear();
     const bool fwd = dir == 0;
     off[dir].assign(nlev + 1, 0);
     for (int l = 0; l < nlev; ++l) {
@@ -855,6 +854,15 @@ bool plan_k1(matex_ctx* c) {
     }
     off[dir][nlev] = (int32_t)warps[dir].size();
   }
+}
+
+bool plan_k1(matex_ctx* c) {
+  const Symbolic& S = c->S;
+  std::vector<K1Sup> recs[2];
+  std::vector<K1Warp> warps[2];
+  std::vector<int32_t> off[2];
+  build_k1_plan(S, recs, warps, off);
+  const int nlev = (int)S.level_ptr.size() - 1;
   K1Sup *fs = nullptr, *bs = nullptr;
   K1Warp *fw = nullptr, *bw = nullptr;
   if (!c->upload(fs, recs[0].data(), recs[0].size()) || !c->upload(bs, recs[1].data(), recs[1].size()) ||
@@ -3245,6 +3253,94 @@ extern "C" matex_status matex_host_factor_solve(int64_t n, const int64_t* rowptr
       }
     }
     for (int64_t k = 0; k < n; ++k) x[(int64_t)q * n + S.perm[k]] = y[k];
+  }
+  return MATEX_OK;
+}
+
+// Host-only check of the single-column kernels' plan: builds it for G (the
+// setup's ordering and symbolic analysis) and walks every warp's lanes the
+// way the kernels find their rows (prefix of the row counts of the warp's
+// first 32 records, five-step search), checking that each lane lands in a
+// record of its level and group size, inside the record, and that every row
+// (forward) and column (backward) of every supernode is taken by exactly one
+// group of lanes.
+extern "C" matex_status matex_host_single_column_plan(int64_t n, const int64_t* rowptr,
+                                                      const int32_t* col, const double* val,
+                                                      int32_t max_width, int64_t* info) {
+  g_setup_err.clear();
+  if (n <= 0 || !rowptr || !col || !val) {
+    g_setup_err = "bad arguments";
+    return MATEX_ERR_ARG;
+  }
+  CsrSym A{n, rowptr, col, val};
+  std::vector<int32_t> nd;
+  Symbolic S;
+  std::string e = nested_dissection(A, nd);
+  if (e.empty()) e = symbolic_analysis(A, nd, max_width > 0 ? max_width : 1024, S);
+  if (!e.empty()) { g_setup_err = e; return MATEX_ERR_ARG; }
+  std::vector<K1Sup> recs[2];
+  std::vector<K1Warp> warps[2];
+  std::vector<int32_t> off[2];
+  build_k1_plan(S, recs, warps, off);
+  const int nlev = (int)S.level_ptr.size() - 1;
+  const int nsup = S.nsup;
+  int64_t errors = 0, units[2] = {0, 0};
+  for (int dir = 0; dir < 2; ++dir) {
+    const bool fwd = dir == 0;
+    const std::vector<K1Sup>& R = recs[dir];
+    auto count_of = [&](int r) { return fwd ? R[r].ld : R[r].w; };
+    auto lg_of = [&](int r) {
+      const int len = fwd ? R[r].w : R[r].ld;
+      int lg = 0;
+      while (lg < 5 && 16 * (1 << lg) < len) ++lg;
+      return lg;
+    };
+    std::vector<int64_t> first(R.size() + 1, 0);
+    for (size_t r = 0; r < R.size(); ++r) first[r + 1] = first[r] + count_of((int)r);
+    std::vector<int32_t> taken(first.back(), 0);
+    for (int l = 0; l < nlev; ++l) {
+      const int r0 = S.level_ptr[l], r1 = S.level_ptr[l + 1];
+      for (int wi = off[dir][l]; wi < off[dir][l + 1]; ++wi) {
+        const K1Warp wp = warps[dir][wi];
+        int pre[32];
+        for (int j = 0; j < 32; ++j) {
+          const int r = wp.k0 + j;
+          pre[j] = (j ? pre[j - 1] : 0) + (r < nsup ? count_of(r) : 0);
+        }
+        const int G = 1 << wp.lg;
+        if (wp.nslot < 1 || wp.nslot > 32 / G) ++errors;
+        for (int lane = 0; lane < 32; lane += G) {
+          const int slot = lane >> wp.lg;
+          if (slot >= wp.nslot) continue;
+          const int row = wp.i0 + slot;
+          int m = 0;
+          for (int b = 16; b > 0; b >>= 1)
+            if (pre[m + b - 1] <= row) m += b;
+          const int rec = wp.k0 + m;
+          const int i = row - (m > 0 ? pre[m - 1] : 0);
+          if (m >= 32 || rec < r0 || rec >= r1 || lg_of(rec) != wp.lg || i < 0 ||
+              i >= count_of(rec)) {
+            ++errors;
+            continue;
+          }
+          ++taken[first[rec] + i];
+        }
+      }
+    }
+    for (int32_t t : taken) errors += t != 1;
+    units[dir] = first.back();
+  }
+  if (info) {
+    info[0] = nlev;
+    info[1] = off[0][nlev];
+    info[2] = off[1][nlev];
+    info[3] = units[0];
+    info[4] = units[1];
+    info[5] = errors;
+  }
+  if (errors) {
+    g_setup_err = "single-column plan: " + std::to_string(errors) + " mapping errors";
+    return MATEX_ERR_STATE;
   }
   return MATEX_OK;
 }

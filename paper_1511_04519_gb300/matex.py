@@ -72,7 +72,8 @@ class MatexProfile(C.Structure):
 EXPORTS = ["matex_default_opts", "matex_setup", "matex_run", "matex_run_host", "matex_set_sources",
            "matex_solve", "matex_expm", "matex_get_m", "matex_get_sizes", "matex_get_setup_stats",
            "matex_last_error", "matex_status_string", "matex_destroy", "matex_set_profiling",
-           "matex_get_profile", "matex_host_factor_solve", "matex_set_batching",
+           "matex_get_profile", "matex_host_factor_solve", "matex_host_single_column_plan",
+           "matex_set_batching",
            "matex_debug_inject_wait", "matex_solve_noalloc", "matex_grad", "matex_set_caps",
            "matex_get_autotune", "matex_batch_create", "matex_batch_run", "matex_batch_last_error",
            "matex_batch_destroy", "matex_measure_fp64_peak", "matex_tr_run",

@@ -50,6 +50,34 @@ def host_factor_solve(lib, p, dshift, alpha, b, max_width=128):
     return st, x, info
 
 
+@pytest.mark.parametrize("case", ["config0", "ragged3layer", "fourlayer", "mesh2x200x200"])
+@pytest.mark.parametrize("width", [1, 16, 0])
+def test_single_column_plan_covers_every_row_once(lib, case, width):
+    """The single-column kernels' plan, walked lane by lane as the kernels
+    walk it: every panel row (forward) and supernode column (backward) is
+    taken by exactly one group of lanes of its own level and group size."""
+    if case == "config0":
+        p = gridgen.config0()
+    elif case == "ragged3layer":
+        p = gridgen.small_mesh(3, nx=23, ny=17, layers=3, n_src=6)
+    elif case == "fourlayer":
+        p = gridgen.config2(side=60, n_src=60, n_groups=4, n_pads=40, max_tpl=4)
+    else:
+        p = gridgen.small_mesh(4, nx=200, ny=200, layers=2, n_src=8)
+    f = lib.matex_host_single_column_plan
+    f.restype = C.c_int
+    info = np.zeros(6, np.int64)
+    st = f(C.c_int64(p.n), _P(p.g_rowptr, C.c_int64), _P(p.g_col, C.c_int32),
+           _P(p.g_val, C.c_double), C.c_int32(width), _P(info, C.c_int64))
+    assert st == 0, info
+    levels, fw, bw, rows, cols, errors = info
+    assert errors == 0 and levels >= 1 and fw >= 1 and bw >= 1
+    assert cols == p.n            # every node is one column of one supernode
+    assert rows >= p.n            # diagonal rows plus the rows below them
+    if width == 1:
+        assert rows - p.n > 0     # no amalgamation: the off-diagonal rows of L
+
+
 @pytest.mark.parametrize("case", ["small2layer", "config0", "ragged"])
 @pytest.mark.parametrize("width", [1, 7, 128])
 def test_host_factorisation_solves(lib, case, width):
