@@ -231,6 +231,23 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(x, pg, device):
+    """x (a time) as the job's clock sees it: the largest over the ranks of the
+    process group module pg (None: one process, x itself)."""
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job rate: every one of `world` ranks processed units_per_rank
+    in `seconds` (the slowest rank's time)."""
+    return world * units_per_rank / seconds
+
+
 def workload_config(p, world):
     """The `config` of both arms' JSON lines."""
     return {"workload": WORKLOAD, "nodes": p.n, "groups": p.n_groups,
@@ -611,12 +628,9 @@ def main():
     clocks = clk.stop()
     launches_per_step = sim.stats.kernel_launches
     stats = sim.stats.as_dict()
-    if pg is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, pg, "cuda")
     units = p.n * (p.n_out - 1) * p.n_groups
-    value = world * units / (ms / 1e3)
+    value = job_rate(units, world, ms / 1e3)
 
     # profiled steps (CUDA events around every kernel class on the run's stream)
     sim.profile(on=True)
@@ -702,11 +716,8 @@ def main():
     for _ in range(args.steps):
         sim.run_host(pin_v, pin_out)
     e2e_s = (time.perf_counter() - t0) / args.steps
-    if pg is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(pin_v.nbytes),
+    e2e_s = max_over_ranks(e2e_s, pg, "cuda")
+    e2e = {"value": job_rate(units, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(pin_v.nbytes),
            "d2h_bytes_per_step": int(pin_out.nbytes), "ms_per_step": e2e_s * 1e3}
 
     # the paper's comparison method on the same solves: fixed-step trapezoidal
