@@ -473,7 +473,9 @@ matex_status matex_host_factor_solve(int64_t n, const int64_t* rowptr, const int
                                      int64_t* info);
 
 /*
- * Host-only check of the single-column level kernels' work plan for G (host
+ * Host-only check of the work plan of the single-column level kernels (the
+ * operator apply of Alg. 1 and the input solves of Eq. 5/6 with one
+ * right-hand side) for G (host
  * CSR as for matex_host_factor_solve; max_width <= 0: the setup's default):
  * the same ordering, symbolic analysis and plan as matex_setup, then every
  * warp's lanes mapped to their rows the way the kernels do it.  info (host
