@@ -475,14 +475,14 @@ matex_status matex_host_factor_solve(int64_t n, const int64_t* rowptr, const int
 /*
  * Host-only check of the work plan of the single-column level kernels (the
  * operator apply of Alg. 1 and the input solves of Eq. 5/6 with one
- * right-hand side) for G (host
- * CSR as for matex_host_factor_solve; max_width <= 0: the setup's default):
- * the same ordering, symbolic analysis and plan as matex_setup, then every
- * warp's lanes mapped to their rows the way the kernels do it.  info (host
- * [6], may be NULL) receives {levels, forward warps, backward warps, panel
- * rows, supernode columns, mapping errors}.  MATEX_ERR_STATE when a lane
- * lands outside its level, group size or supernode, or a row or column is
- * not taken exactly once.  No GPU needed.
+ * right-hand side), built for G given as host CSR as for
+ * matex_host_factor_solve (max_width <= 0: the setup's default): the same
+ * ordering, symbolic analysis and plan as matex_setup, then every warp's
+ * lanes mapped to their rows the way the kernels do it.  info (host [6], may
+ * be NULL) receives {levels, forward warps, backward warps, panel rows,
+ * supernode columns, mapping errors}.  MATEX_ERR_STATE when a lane lands
+ * outside its level, group size or supernode, or a row or column is not
+ * taken exactly once.  No GPU needed.
  */
 matex_status matex_host_single_column_plan(int64_t n, const int64_t* rowptr, const int32_t* col,
                                            const double* val, int32_t max_width, int64_t* info);
